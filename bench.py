@@ -1,0 +1,400 @@
+"""Benchmark of the UBQP hot path on GB300: one JSON line on stdout (rank 0).
+
+A step is one pass of the whole hot path over one batch of synthetic starts on
+a device-resident instance: start generation, exact xQx evaluation of every
+start, the T(lambda) screen, steepest ascent of the passing starts and the
+best-of -- the loop body of Fig. 2 applied to a batch.  The default workload is
+the Table 1 shape at its largest size: n = 7000, dense Q (density 1.0, integer
+coefficients uniform in [-100, 100], seed 7000), 1000 uniformly random starts
+per step (a new batch every step), lambda = 0.5.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+With N > 1 (torchrun, one rank per GPU) every rank runs its own batches of the
+same instance (weak scaling, no data-path collective); the time is the max over
+ranks.  --impl reference times the CPU oracle (the reference arm of this
+project) on a bounded sample of the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "xQx evals/s and 1-flip moves/s at n=7000; served solves/s with p50/p99 latency"
+UNIT = "evals/s"
+L2_FLUSH_BYTES = 256 << 20
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--n", type=int, default=7000)
+    ap.add_argument("--density", type=float, default=1.0)
+    ap.add_argument("--starts", type=int, default=1000)
+    ap.add_argument("--lam", type=float, default=0.5)
+    ap.add_argument("--eval-path", choices=["auto", "tc", "plain"], default="auto")
+    ap.add_argument("--cpu-sample", type=int, default=160,
+                    help="starts in the oracle's timed sample")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu", action="store_true")
+    return ap.parse_args()
+
+
+def workload_name(a):
+    return f"table1-dense-n{a.n}" if a.density == 1.0 else f"n{a.n}-d{a.density}"
+
+
+def config_of(a, world):
+    return {"workload": workload_name(a), "n": a.n, "density": a.density,
+            "coeffs": "int8 uniform [-100,100]", "instance_seed": a.n,
+            "starts_per_step": a.starts, "start_mode": "RANDOM (new seed per step)",
+            "lambda": a.lam, "max_flips": 0, "eval_path": a.eval_path,
+            "l2": "flushed between steps (256 MiB write)",
+            "parallelism": f"replicas x{world}" if world > 1 else "single GPU"}
+
+
+# --------------------------------------------------------------------- clocks
+
+class ClockSampler:
+    """nvidia-smi samples during the timed region (SM clock, throttle reasons)."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.path = None
+
+    def __enter__(self):
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.out = open(self.path, "w")
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.Q}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=self.out, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+        return self
+
+    def __exit__(self, *exc):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+            self.out.close()
+
+    def summary(self):
+        if self.proc is None or self.path is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
+        rows = []
+        for line in open(self.path):
+            p = [x.strip() for x in line.split(",")]
+            if len(p) >= 9:
+                rows.append(p)
+        os.unlink(self.path)
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i in range(4) if r[5 + i] == "Active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(mx) if mx else None, "reasons": reasons,
+                "samples": len(rows)}
+
+
+# --------------------------------------------------------------------- oracle arm
+
+def cpu_sample(a, Q, S_cpu, seed):
+    """Whole path on the CPU oracle for S_cpu starts; returns (seconds, flips)."""
+    import oracle as orc
+    t0 = time.perf_counter()
+    X = orc.diversify(None, a.n, orc.RANDOM, seed, 0, S_cpu)
+    f = orc.eval(Q, X)
+    sc = orc.screen(f, a.lam)
+    _, f2, flips = orc.ascent(Q, X, f, sc["idx"])
+    orc.best(f2)
+    return time.perf_counter() - t0, int(flips.sum())
+
+
+def run_reference(a):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    from paper_1706_00037_gb300 import synth
+    import oracle as orc
+    orc.build()
+    Q = synth.make_instance(a.n, a.density, a.n)
+    S_cpu = max(4, min(a.starts, a.cpu_sample // 8))
+    for w in range(a.warmup):
+        cpu_sample(a, Q, S_cpu, 10_000 + w)
+    total = 0.0
+    for k in range(a.steps):
+        dt, _ = cpu_sample(a, Q, S_cpu, 20_000 + k)
+        total += dt
+    value = S_cpu * a.steps / total
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT,
+            "n_gpus": a.gpus, "steps": a.steps, "warmup": a.warmup,
+            "ms_per_step": 1e3 * total / a.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "int64", "data": "synthetic",
+            "config": dict(config_of(a, 1), starts_per_step=S_cpu),
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+                             "sample": f"{S_cpu} random starts per step through the whole "
+                                       f"path (of {a.starts}), single thread"},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+# --------------------------------------------------------------------- GPU arm
+
+def main():
+    a = parse()
+    if a.impl == "reference":
+        return run_reference(a)
+
+    import torch
+    import torch.distributed as dist
+    from paper_1706_00037_gb300 import synth, ubqp
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    else:
+        torch.cuda.set_device(0)
+    dev = torch.device("cuda", torch.cuda.current_device())
+    path = {"auto": ubqp.EVAL_AUTO, "tc": ubqp.EVAL_TC, "plain": ubqp.EVAL_PLAIN}[a.eval_path]
+
+    n, S = a.n, a.starts
+    Qh = synth.make_instance(n, a.density, n)
+    Qd = torch.from_numpy(Qh).to(dev)
+    inst = ubqp.Instance(Qd)
+    W = inst.words
+    stream = torch.cuda.current_stream()
+
+    X = torch.empty((S, W), dtype=torch.int64, device=dev)
+    f = torch.empty(S, dtype=torch.int64, device=dev)
+    idx = torch.empty(S, dtype=torch.int32, device=dev)
+    count = torch.empty(1, dtype=torch.int64, device=dev)
+    Tm = torch.empty(2, dtype=torch.float64, device=dev)
+    sst = torch.empty(3, dtype=torch.int64, device=dev)
+    bx = torch.empty(W, dtype=torch.int64, device=dev)
+    bf = torch.empty(2, dtype=torch.int64, device=dev)
+    ews = ubqp.eval_workspace_size(inst, S, path)
+    ws = torch.empty(max(ews, 16), dtype=torch.uint8, device=dev)
+    flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device=dev)
+    total_steps = a.warmup + a.steps
+    flips_all = torch.zeros((total_steps, S), dtype=torch.int32, device=dev)
+    names = ["diversify", "eval", "screen", "ascent", "best"]
+    evs = [[torch.cuda.Event(enable_timing=True) for _ in range(len(names) + 1)]
+           for _ in range(total_steps)]
+    lib = ubqp.load()
+    sp = ubqp._stream(stream)
+    import ctypes
+    P = ctypes.c_void_p
+
+    def step(k):
+        seed = 1_000_003 * (rank + 1) + k
+        e = evs[k]
+        e[0].record(stream)
+        ubqp._check(lib.ubqp_diversify(inst.handle, None, ubqp.RANDOM, seed, 0, S, 64,
+                                       P(X.data_ptr()), sp))
+        e[1].record(stream)
+        ubqp._check(lib.ubqp_eval(inst.handle, P(X.data_ptr()), S, P(f.data_ptr()), path,
+                                  P(ws.data_ptr()), ws.numel(), sp))
+        e[2].record(stream)
+        ubqp._check(lib.ubqp_screen(P(f.data_ptr()), S, a.lam, P(idx.data_ptr()),
+                                    P(count.data_ptr()), P(Tm.data_ptr()), P(sst.data_ptr()),
+                                    sp))
+        e[3].record(stream)
+        ubqp._check(lib.ubqp_ascent(inst.handle, P(X.data_ptr()), P(f.data_ptr()),
+                                    P(idx.data_ptr()), P(count.data_ptr()), S, 0,
+                                    P(flips_all[k].data_ptr()), sp))
+        e[4].record(stream)
+        ubqp._check(lib.ubqp_best(P(f.data_ptr()), P(X.data_ptr()), S, W, P(bx.data_ptr()),
+                                  P(bf.data_ptr()), sp))
+        e[5].record(stream)
+
+    for k in range(a.warmup):
+        flush.zero_()
+        step(k)
+    torch.cuda.synchronize()
+    inst.sync()
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    with ClockSampler(dev.index) as clk:
+        t_wall = time.perf_counter()
+        for k in range(a.warmup, total_steps):
+            flush.zero_()
+            step(k)
+        torch.cuda.synchronize()
+        t_wall = time.perf_counter() - t_wall
+    inst.sync()
+    per = np.zeros((a.steps, len(names)))
+    for i, k in enumerate(range(a.warmup, total_steps)):
+        for j in range(len(names)):
+            per[i, j] = evs[k][j].elapsed_time(evs[k][j + 1])
+    step_ms = per.sum(axis=1)
+    my_total = float(step_ms.sum())
+    flips_timed = int(flips_all[a.warmup:].sum().item())
+    if world > 1:
+        t = torch.tensor([my_total], dtype=torch.float64, device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        max_total = float(t.item())
+        fl = torch.tensor([flips_timed], dtype=torch.int64, device=dev)
+        dist.all_reduce(fl)
+        flips_all_ranks = int(fl.item())
+    else:
+        max_total, flips_all_ranks = my_total, flips_timed
+    clocks = clk.summary()
+
+    value = world * S * a.steps / (max_total / 1e3)
+    kern_ms = per.mean(axis=0)
+    kernels = {nm: {"ms_per_launch": float(kern_ms[j]),
+                    "share": float(kern_ms[j] / kern_ms.sum())} for j, nm in enumerate(names)}
+    asc_s = per[:, 3].sum() / 1e3
+    moves_per_s = flips_timed / asc_s if asc_s > 0 else None
+
+    # ---- roofline of the dominant kernel (ascent): algorithmic integer ops.
+    # Per ascended start: n*|x| row additions for y = Qx plus n gain formulas;
+    # per move: n gain updates plus n argmax comparisons.  Recomputed untimed.
+    passers, pop = 0, 0
+    for k in range(a.warmup, total_steps):
+        seed = 1_000_003 * (rank + 1) + k
+        ubqp.diversify(inst, S, mode=ubqp.RANDOM, seed=seed, out=X)
+        ubqp.eval(inst, X, path=path, out=f, ws=ws if ews else None)
+        sc = ubqp.screen(f, a.lam)
+        c = int(sc["count"].item())
+        if c:
+            rows = X[sc["idx"][:c].long()].cpu().numpy().view(np.uint8)
+            pop += int(np.unpackbits(rows).sum())
+        passers += c
+    asc_ops = n * pop + n * passers + 2 * n * flips_timed
+    peaks = {}
+    try:
+        peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except Exception:
+        pass
+    sm_max = float(peaks.get("sm_max_mhz", 2070.0))
+    n_sm = torch.cuda.get_device_properties(dev).multi_processor_count
+    alu_peak = n_sm * 128 * sm_max * 1e6  # INT32 lanes per SM per clock x max clock
+    dom = max(kernels, key=lambda k: kernels[k]["ms_per_launch"])
+    roof_asc = {"kernel": "ascent", "bound": "alu",
+                "achieved": asc_ops / asc_s / 1e12 if asc_s > 0 else None,
+                "peak": alu_peak / 1e12, "unit": "Tops/s (int32)",
+                "frac": (asc_ops / asc_s) / alu_peak if asc_s > 0 else None,
+                "traffic": None,
+                "peak_source": f"derived: {n_sm} SMs x 128 INT32 lanes x {sm_max:.0f} MHz"}
+    eval_s = per[:, 1].sum() / 1e3
+    eval_flops = float(S) * n * (n + 1) * a.steps  # 2 * S * n(n+1)/2 triangle MACs
+    tc = ubqp.EVAL_TC if path == ubqp.EVAL_AUTO else path
+    if tc == ubqp.EVAL_TC:
+        roof_eval = {"kernel": "eval", "bound": "tensor",
+                     "achieved": eval_flops / eval_s / 1e12, "unit": "TFLOP/s",
+                     "peak": float(peaks.get("bf16_tflops", 1858.6)),
+                     "peak_source": "MEASURED_PEAKS bf16_tflops (burst), of measured"}
+    else:
+        roof_eval = {"kernel": "eval", "bound": "alu",
+                     "achieved": eval_flops / 2 / eval_s / 1e12, "unit": "Tops/s (int32)",
+                     "peak": alu_peak / 1e12 * 4, "peak_source": "dp4a: 4 MACs per lane-op"}
+    roof_eval["frac"] = roof_eval["achieved"] / roof_eval["peak"]
+    roof_eval["traffic"] = None
+    roofline = roof_asc if dom == "ascent" else dict(roof_eval)
+
+    # ---- end to end through the public API with host buffers: H2D of the
+    # instance, prepare, solve, D2H of the result, every step.
+    e2e = None
+    if not a.no_e2e:
+        Qpin = torch.from_numpy(Qh).pin_memory()
+        params = ubqp.make_params(S, a.lam, mode=ubqp.RANDOM, seed=5, eval_path=path)
+        out_x = torch.empty(W, dtype=torch.int64).pin_memory()
+        out_f = torch.empty(2, dtype=torch.int64).pin_memory()
+        Qdev = torch.empty_like(Qd)
+        wsz = None
+
+        def e2e_step(k):
+            nonlocal wsz
+            Qdev.copy_(Qpin, non_blocking=True)
+            i2 = ubqp.Instance(Qdev)
+            params.seed = 77 + k
+            need = ubqp.solve_workspace_size(i2, params)
+            if wsz is None or wsz.numel() < need:
+                wsz = torch.empty(need, dtype=torch.uint8, device=dev)
+            bx2, bf2, _ = ubqp.solve(i2, params, ws=wsz, want_stats=False)
+            out_x.copy_(bx2, non_blocking=True)
+            out_f.copy_(bf2, non_blocking=True)
+            torch.cuda.synchronize()
+            i2.close()
+
+        ke = max(2, min(a.steps, 5))
+        for k in range(2):
+            e2e_step(k)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for k in range(ke):
+            e2e_step(100 + k)
+        torch.cuda.synchronize()
+        dt = time.perf_counter() - t0
+        e2e = {"value": world * S * ke / dt, "unit": UNIT,
+               "h2d_bytes_per_step": int(Qh.nbytes),
+               "d2h_bytes_per_step": int(out_x.numel() * 8 + out_f.numel() * 8),
+               "what": "instance Q from pinned host memory, ubqp_q_prepare, ubqp_solve, "
+                       "best solution and value back to host, per step"}
+
+    cpu = None
+    if rank == 0 and world == 1 and not a.no_cpu:
+        import oracle as orc
+        orc.build()
+        S_cpu = a.cpu_sample
+        dt, _ = cpu_sample(a, Qh, S_cpu, 4242)
+        cpu = {"value": S_cpu / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
+               "sample": f"{S_cpu} random starts of the same instance through the whole "
+                         f"path (eval, screen, ascent of passers, best), single thread, "
+                         f"{dt:.1f} s"}
+
+    if rank == 0:
+        launches_per_step = 5
+        line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+                "steps": a.steps, "warmup": a.warmup, "ms_per_step": max_total / a.steps,
+                "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+                "dtype": "int64", "data": "synthetic", "config": config_of(a, world),
+                "moves_per_s": moves_per_s * world if moves_per_s else None,
+                "eval_only_evals_per_s": S * a.steps / eval_s,
+                "paper_table1_context": {"evals_per_s_n7000_gtx780ti": 1000 / 3.5},
+                "passed_per_step": passers / a.steps, "flips_per_step": flips_timed / a.steps,
+                "kernels": kernels, "roofline": roofline, "roofline_eval": roof_eval,
+                "roofline_ascent": roof_asc, "cpu_baseline": cpu, "e2e": e2e,
+                "clocks": clocks, "gpu_launches": launches_per_step * a.steps,
+                "wall_s_timed_region": t_wall}
+        print(json.dumps(line), flush=True)
+    inst.close()
+    if world > 1:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,228 @@
+/*
+ * ubqp.h -- C ABI of libubqp: the GB300 (sm_103a) hot path of the
+ * GPU-screened diversified multi-start method for the Unconstrained Binary
+ * Quadratic Problem (M. Lewis, arXiv 1706.00037).
+ *
+ *   maximise f(x) = x^t Q x,  x in {0,1}^n,  Q symmetric integer   -- problem (P),
+ *   Introduction.
+ *
+ * The routines mirror the steps of Fig. 2 (Pseudocode section): the
+ * first-derivative start, start generation (EvaluateRandomStarts / Diversify),
+ * evaluation of xQx, the screen T(lambda) = Mean + lambda (Max - Mean), steepest
+ * ascent by 1-bit flips (PerformSteepestAscent) and keeping the best solution
+ * (UpdateBestAndT).  Every result is exact integer arithmetic; the only
+ * floating-point value is the screening threshold.
+ *
+ * Conventions shared by every call
+ * --------------------------------
+ *  - Pointers named *_dev (and every array argument unless stated otherwise)
+ *    are DEVICE pointers owned by the caller.  The library never frees caller
+ *    memory, allocates device memory only inside a ubqp_q handle, and never
+ *    synchronises a stream unless the call's comment says so.
+ *  - `stream` is a cudaStream_t passed as void* (NULL = the legacy default
+ *    stream).  All device work of a call is enqueued on it, in order.
+ *  - A solution x is bit-packed: W = ceil(n/64) uint64 words, bit j of x is
+ *    (x[j/64] >> (j%64)) & 1.  A batch of S solutions is S*W words, solution s
+ *    at X[s*W].  Bits >= n ("pad bits") must be 0; every routine that reads
+ *    solutions ignores them and every routine that writes solutions clears them.
+ *  - Return value: UBQP_OK or a negative ubqp_status.  Argument errors are
+ *    reported synchronously, before any work is enqueued.  A failed launch
+ *    returns UBQP_ERR_CUDA.  Errors found by a kernel while it runs (a wait
+ *    that timed out) are recorded in the handle and returned by the next
+ *    ubqp_sync() on that handle.  ubqp_last_error() gives a one-line detail of
+ *    the last failure on the calling thread.
+ *  - Exactness: the evaluation runs on the tensor cores in bf16 x bf16 -> fp32,
+ *    exact because every operand is an integer of magnitude <= 256 and every
+ *    partial sum an integer below 2^24.  ubqp_eval checks this bound at run time
+ *    (2 * max|Q| * n_pad < 2^24) and returns UBQP_ERR_RANGE when it fails.
+ */
+#ifndef UBQP_H
+#define UBQP_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define UBQP_ABI_VERSION 1
+
+typedef enum ubqp_status {
+  UBQP_OK = 0,
+  UBQP_ERR_ARG = -1,           /* bad pointer, size, alignment or flag            */
+  UBQP_ERR_NOT_SYMMETRIC = -2, /* Q is not symmetric (problem (P))               */
+  UBQP_ERR_RANGE = -3,         /* the exactness bound of the evaluation fails     */
+  UBQP_ERR_NOMEM = -4,         /* device allocation failed / workspace too small  */
+  UBQP_ERR_CUDA = -5,          /* a CUDA runtime call or launch failed            */
+  UBQP_ERR_TIMEOUT = -6,       /* a kernel's bounded wait expired                 */
+  UBQP_ERR_UNSUPPORTED = -7    /* size or mode this build does not handle         */
+} ubqp_status;
+
+/* Start generation modes (see ubqp_diversify). */
+enum { UBQP_MODE_RANDOM = 0, UBQP_MODE_DIVERSIFY = 1 };
+/* Evaluation paths (see ubqp_eval). */
+enum { UBQP_EVAL_AUTO = 0, UBQP_EVAL_TC = 1, UBQP_EVAL_PLAIN = 2 };
+
+/* Opaque prepared instance: device-resident Q in the layouts the kernels use,
+ * its row sums, max|Q|, the first-derivative start and an error word. */
+typedef struct ubqp_q ubqp_q;
+
+/* Static description of an error code; never NULL. */
+const char* ubqp_strerror(int status);
+/* Detail of the last failing call on this thread ("" if none). */
+const char* ubqp_last_error(void);
+/* UBQP_ABI_VERSION of the loaded library. */
+int ubqp_abi_version(void);
+
+/*
+ * ubqp_q_prepare -- copy Q to the device once (the one large host/device
+ * transfer of Fig. 2's MoveQtoGPU, Pseudocode section) and prepare it.
+ *   Q_dev   n rows of int8 coefficients, row stride ldq >= n bytes, device
+ *           memory; bytes beyond column n of a row are ignored.  Not retained.
+ *   n       1 <= n <= 16384.
+ *   out     receives the handle (NULL on failure).
+ * Checks that Q is symmetric (UBQP_ERR_NOT_SYMMETRIC otherwise), records max|Q|,
+ * builds the padded int8 copy used by the ascent, the tensor-core operand
+ * (bf16, lower triangle doubled, see ubqp_eval), the row sums and the
+ * first-derivative start.  Allocates about n_pad^2 * 3 bytes of device memory
+ * (n_pad = n rounded up to 1024) owned by the handle.  Synchronises `stream`
+ * once to read the validation result.
+ */
+int ubqp_q_prepare(const int8_t* Q_dev, int32_t n, int64_t ldq, void* stream,
+                   ubqp_q** out);
+/* Free a handle (NULL is a no-op).  Work using it must have completed. */
+void ubqp_q_destroy(ubqp_q* q);
+/* Size and layout of a prepared instance; any output pointer may be NULL.
+ * n_pad is the padded row stride of the device copies. */
+int ubqp_q_info(const ubqp_q* q, int32_t* n, int32_t* words, int32_t* n_pad,
+                int32_t* max_abs, int64_t* device_bytes);
+/* Synchronise `stream` and report (then clear) any error a kernel recorded in
+ * the handle's error word since the last ubqp_sync. */
+int ubqp_sync(const ubqp_q* q, void* stream);
+
+/*
+ * ubqp_first_derivative -- CalculateFirstDerivativeSolution (Fig. 2): the
+ * start with x_i = 1 iff sum_j Q_ij > 0 (a zero sum gives x_i = 0).  Copies the
+ * handle's precomputed start (W words) to x0_dev.  Async on `stream`.
+ */
+int ubqp_first_derivative(const ubqp_q* q, uint64_t* x0_dev, void* stream);
+
+/*
+ * ubqp_diversify -- S starts, written to X_dev (S*W words).  Async.
+ *   mode UBQP_MODE_RANDOM: uniform random solutions (the sample of
+ *        EvaluateRandomStarts, Fig. 2): word w of start s is
+ *        splitmix64(seed ^ s*0x9E3779B97F4A7C15 ^ w), pad bits cleared.
+ *   mode UBQP_MODE_DIVERSIFY: Diversify(x, best, i, Q_cols) of Fig. 2 around
+ *        the incumbent x0_dev (NULL = the first-derivative start).  Start s has
+ *        loop counter i = round*S + s: i = 0 is the incumbent, even i flips every
+ *        bit p with p mod h == o (Glover's h-pattern; j' = i/2, H = min(n,
+ *        div_H), h = 1 + (j'-1) mod H, o = ((j'-1)/H) mod h), odd i blends the
+ *        incumbent with a random partner through the AND of 1 + ((i-1)/2 mod 6)
+ *        random mask words.  div_H >= 1.
+ * SplitMix64 is the generator of Steele, Lea & Flood (2014).
+ */
+int ubqp_diversify(const ubqp_q* q, const uint64_t* x0_dev, int32_t mode,
+                   uint64_t seed, uint64_t round, int64_t S, int32_t div_H,
+                   uint64_t* X_dev, void* stream);
+
+/*
+ * ubqp_eval -- Evaluate(x) of Fig. 2 for a batch: f_dev[s] = x_s^t Q x_s (int64),
+ * s < S.  Async.
+ *   path UBQP_EVAL_TC: tensor-core contraction.  With Q' = 2*tril(Q,-1) +
+ *        diag(Q), f = sum_j x_j sum_{k<=j} Q'_jk x_k, so only the lower block
+ *        triangle of X * Q'^t is formed (tcgen05 kind::f16, bf16 operands,
+ *        fp32 accumulation in tensor memory, exact), and an int64 epilogue
+ *        folds the row-dot with x without writing the product.  Needs
+ *        ws_bytes >= ubqp_eval_workspace_size(q, S, path) of device scratch
+ *        (16-byte aligned) for the unpacked solutions.
+ *   path UBQP_EVAL_PLAIN: one block per solution on the CUDA cores (dp4a);
+ *        needs no workspace.
+ *   path UBQP_EVAL_AUTO: UBQP_EVAL_TC.
+ * Returns UBQP_ERR_RANGE if the exactness bound fails (see top of file).
+ */
+size_t ubqp_eval_workspace_size(const ubqp_q* q, int64_t S, int32_t path);
+int ubqp_eval(const ubqp_q* q, const uint64_t* X_dev, int64_t S, int64_t* f_dev,
+              int32_t path, void* ws, size_t ws_bytes, void* stream);
+
+/*
+ * ubqp_screen -- the screening function of the Pseudocode section,
+ * T(lambda) = Mean + lambda (Max - Mean), Mean and Max over the S values f_dev,
+ * and the pass test f_b > T of Fig. 2 (strict).  Async.
+ *   idx_dev     S int32: the passing indices, ascending, in idx_dev[0..count).
+ *   count_dev   1 int64: their number.
+ *   Tm_dev      2 doubles: {T, Mean}.
+ *   stats_dev   3 int64: {Max, lowest index attaining Max, sum of f}.
+ * The sum is exact in int64; Mean = sum / S, then T = Mean + lambda*(Max - Mean)
+ * as one subtraction, one multiplication and one addition in double, each
+ * rounded to nearest (no fused multiply-add).  Requires 1 <= S < 2^31.
+ */
+int ubqp_screen(const int64_t* f_dev, int64_t S, double lambda, int32_t* idx_dev,
+                int64_t* count_dev, double* Tm_dev, int64_t* stats_dev,
+                void* stream);
+
+/*
+ * ubqp_ascent -- PerformSteepestAscent(x, xQx, max_its) of Fig. 2 for the
+ * solutions X_dev[idx_dev[t]], t < *count_dev, in place: repeatedly flip the
+ * bit with the largest 1-flip gain Delta_i = Q_ii + 2(1-2x_i)(Qx)_i (Glover et
+ * al. 2002), lowest index on ties, while that gain is > 0 and fewer than
+ * max_flips flips were made (max_flips 0 = no cap).  f_dev[s] must hold
+ * f(x_s) on entry and holds the ascended value on exit.  flips_dev (S int32,
+ * may be NULL) receives each ascended start's flip count; entries of starts
+ * not listed are left untouched.  count is read on the device (no sync).
+ * S is the length of X_dev/f_dev (bounds idx).  Async.
+ */
+int ubqp_ascent(const ubqp_q* q, uint64_t* X_dev, int64_t* f_dev,
+                const int32_t* idx_dev, const int64_t* count_dev, int64_t S,
+                int32_t max_flips, int32_t* flips_dev, void* stream);
+
+/*
+ * ubqp_best -- UpdateBestAndT's bookkeeping (Fig. 2): the largest of the S
+ * values f_dev, the lowest index on ties.  Writes best_f_dev[0] = value,
+ * best_f_dev[1] = index and copies that solution's W words to best_x_dev.  Async.
+ */
+int ubqp_best(const int64_t* f_dev, const uint64_t* X_dev, int64_t S,
+              int32_t words, uint64_t* best_x_dev, int64_t* best_f_dev,
+              void* stream);
+
+/* One round of the loop body of Fig. 2 over a batch of starts. */
+typedef struct ubqp_params {
+  int64_t num_starts; /* S >= 1                                            */
+  double lambda;      /* screening parameter                                */
+  int32_t max_flips;  /* ascent cap per start, 0 = none                     */
+  int32_t mode;       /* UBQP_MODE_RANDOM or UBQP_MODE_DIVERSIFY            */
+  uint64_t seed;      /* start-generation seed                              */
+  uint64_t round;     /* loop-counter offset: start s has i = round*S + s   */
+  int32_t div_H;      /* h-pattern period bound (>= 1; 64 is customary)     */
+  int32_t eval_path;  /* UBQP_EVAL_*                                         */
+} ubqp_params;
+
+typedef struct ubqp_stats {
+  int64_t passed;         /* starts that passed the screen                 */
+  int64_t total_flips;    /* flips over all ascended starts                */
+  int64_t max_flips_seen; /* largest flip count of one start               */
+  int64_t batch_max;      /* Max of the screen (before ascent)             */
+  int64_t best_index;     /* start that gave the best solution             */
+  int64_t sum;            /* sum of evaluated f (before ascent)            */
+  double T;               /* screening threshold                           */
+  double mean;            /* Mean of the screen                            */
+} ubqp_stats;
+
+/*
+ * ubqp_solve -- one round on one stream with no host round trip: starts from
+ * the first-derivative solution (ubqp_diversify with x0 = NULL), ubqp_eval,
+ * ubqp_screen, ubqp_ascent of the passing starts, ubqp_best.  Writes best_x_dev
+ * (W words) and best_f_dev[0..1] = {best f, start index}.  ws must hold
+ * ubqp_solve_workspace_size(q, p) bytes (16-byte aligned).  If stats_host is
+ * not NULL the call synchronises `stream`, fills it and also reports any
+ * kernel-recorded error (as ubqp_sync does); otherwise it is fully async.
+ */
+size_t ubqp_solve_workspace_size(const ubqp_q* q, const ubqp_params* p);
+int ubqp_solve(const ubqp_q* q, const ubqp_params* p, uint64_t* best_x_dev,
+               int64_t* best_f_dev, ubqp_stats* stats_host, void* ws,
+               size_t ws_bytes, void* stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* UBQP_H */

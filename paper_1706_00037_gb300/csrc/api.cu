@@ -1,0 +1,319 @@
+// api.cu -- the extern "C" boundary of libubqp (declared in include/ubqp.h):
+// argument checks, the prepared-instance handle, workspace carving and the
+// one-round solve that chains the kernels on one stream.
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <new>
+
+#include "ubqp_internal.cuh"
+
+namespace {
+
+thread_local char g_last_error[512] = "";
+
+int fail(int status, const char* fmt, ...) __attribute__((format(printf, 2, 3)));
+int fail(int status, const char* fmt, ...) {
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(g_last_error, sizeof(g_last_error), fmt, ap);
+  va_end(ap);
+  return status;
+}
+
+int cuda_fail(cudaError_t e, const char* what) {
+  return fail(UBQP_ERR_CUDA, "%s: %s", what, cudaGetErrorString(e));
+}
+
+#define UBQP_CUDA(call)                                   \
+  do {                                                    \
+    cudaError_t e_ = (call);                              \
+    if (e_ != cudaSuccess) return cuda_fail(e_, #call);   \
+  } while (0)
+
+int64_t round_up(int64_t v, int64_t a) { return (v + a - 1) / a * a; }
+
+bool is_device_ptr(const void* p) {
+  cudaPointerAttributes a;
+  if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
+int resolve_path(int path) { return path == UBQP_EVAL_AUTO ? UBQP_EVAL_PLAIN : path; }
+
+// Workspace of ubqp_solve, carved in this order (each piece 256-byte aligned).
+struct SolveLayout {
+  size_t X, f, idx, flips, small, eval, total;
+};
+constexpr size_t kSmallBytes = 256;  // count, Tm, screen stats, stats out
+
+SolveLayout solve_layout(const ubqp_q* q, const ubqp_params* p) {
+  SolveLayout L{};
+  const int64_t S = p->num_starts;
+  size_t off = 0;
+  auto take = [&](size_t bytes) {
+    size_t at = off;
+    off += (size_t)round_up((int64_t)bytes, 256);
+    return at;
+  };
+  L.X = take((size_t)S * q->W * 8);
+  L.f = take((size_t)S * 8);
+  L.idx = take((size_t)S * 4);
+  L.flips = take((size_t)S * 4);
+  L.small = take(kSmallBytes);
+  const int path = resolve_path(p->eval_path);
+  L.eval = take(path == UBQP_EVAL_TC ? ubqp::eval_tc_workspace(q, S) : 0);
+  L.total = off;
+  return L;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* ubqp_strerror(int status) {
+  switch (status) {
+    case UBQP_OK: return "ok";
+    case UBQP_ERR_ARG: return "invalid argument";
+    case UBQP_ERR_NOT_SYMMETRIC: return "Q is not symmetric";
+    case UBQP_ERR_RANGE: return "coefficients exceed the exactness bound of the evaluation";
+    case UBQP_ERR_NOMEM: return "out of device memory or workspace too small";
+    case UBQP_ERR_CUDA: return "CUDA error";
+    case UBQP_ERR_TIMEOUT: return "a kernel wait timed out";
+    case UBQP_ERR_UNSUPPORTED: return "unsupported size or mode";
+    default: return "unknown status";
+  }
+}
+
+const char* ubqp_last_error(void) { return g_last_error; }
+
+int ubqp_abi_version(void) { return UBQP_ABI_VERSION; }
+
+void ubqp_q_destroy(ubqp_q* q) {
+  if (!q) return;
+  cudaFree(q->Q8);
+  cudaFree(q->Qt);
+  cudaFree(q->rowsum);
+  cudaFree(q->x0);
+  cudaFree(q->err);
+  delete q;
+}
+
+int ubqp_q_prepare(const int8_t* Q_dev, int32_t n, int64_t ldq, void* stream, ubqp_q** out) {
+  g_last_error[0] = 0;
+  if (!out) return fail(UBQP_ERR_ARG, "out is NULL");
+  *out = nullptr;
+  if (!Q_dev) return fail(UBQP_ERR_ARG, "Q_dev is NULL");
+  if (n < 1 || n > UBQP_MAX_N) return fail(UBQP_ERR_UNSUPPORTED, "n=%d outside [1, %d]", n, UBQP_MAX_N);
+  if (ldq < n) return fail(UBQP_ERR_ARG, "ldq=%lld < n=%d", (long long)ldq, n);
+  if (!is_device_ptr(Q_dev)) return fail(UBQP_ERR_ARG, "Q_dev is not device memory");
+  cudaStream_t st = (cudaStream_t)stream;
+  ubqp_q* h = new (std::nothrow) ubqp_q();
+  if (!h) return fail(UBQP_ERR_NOMEM, "host allocation failed");
+  h->n = n;
+  h->W = (int32_t)ubqp::words_of(n);
+  h->ldq = round_up(n, UBQP_ROW_ALIGN);
+  h->n_tc = (int32_t)round_up(n, UBQP_TC_ALIGN);
+  if (cudaGetDevice(&h->device) != cudaSuccess ||
+      cudaDeviceGetAttribute(&h->sm_count, cudaDevAttrMultiProcessorCount, h->device) !=
+          cudaSuccess) {
+    delete h;
+    return fail(UBQP_ERR_CUDA, "cannot query the current device");
+  }
+  size_t q8 = (size_t)n * h->ldq, qt = (size_t)h->n_tc * h->n_tc * 2;
+  if (cudaMalloc(&h->Q8, q8) != cudaSuccess || cudaMalloc(&h->Qt, qt) != cudaSuccess ||
+      cudaMalloc(&h->rowsum, sizeof(int32_t) * n) != cudaSuccess ||
+      cudaMalloc(&h->x0, sizeof(uint64_t) * h->W) != cudaSuccess ||
+      cudaMalloc(&h->err, 4 * sizeof(unsigned)) != cudaSuccess) {
+    cudaGetLastError();
+    ubqp_q_destroy(h);
+    return fail(UBQP_ERR_NOMEM, "device allocation of %zu bytes failed", q8 + qt);
+  }
+  h->scratch_flags = h->err + 1;
+  h->device_bytes = (int64_t)(q8 + qt + sizeof(int32_t) * n + 8 * h->W + 16);
+  cudaError_t e = ubqp::launch_prepare(Q_dev, n, ldq, h, st);
+  unsigned flags[2] = {0, 0};
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(flags, h->scratch_flags, sizeof(flags), cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  if (e != cudaSuccess) {
+    ubqp_q_destroy(h);
+    return cuda_fail(e, "prepare");
+  }
+  if (flags[0] != 0) {
+    ubqp_q_destroy(h);
+    return fail(UBQP_ERR_NOT_SYMMETRIC, "Q is not symmetric (%u tiles differ)", flags[0]);
+  }
+  h->max_abs = (int32_t)flags[1];
+  *out = h;
+  return UBQP_OK;
+}
+
+int ubqp_q_info(const ubqp_q* q, int32_t* n, int32_t* words, int32_t* n_pad, int32_t* max_abs,
+                int64_t* device_bytes) {
+  if (!q) return fail(UBQP_ERR_ARG, "q is NULL");
+  if (n) *n = q->n;
+  if (words) *words = q->W;
+  if (n_pad) *n_pad = (int32_t)q->ldq;
+  if (max_abs) *max_abs = q->max_abs;
+  if (device_bytes) *device_bytes = q->device_bytes;
+  return UBQP_OK;
+}
+
+int ubqp_sync(const ubqp_q* q, void* stream) {
+  if (!q) return fail(UBQP_ERR_ARG, "q is NULL");
+  cudaStream_t st = (cudaStream_t)stream;
+  UBQP_CUDA(cudaStreamSynchronize(st));
+  unsigned e = 0;
+  UBQP_CUDA(cudaMemcpy(&e, q->err, sizeof(unsigned), cudaMemcpyDeviceToHost));
+  if (e) {
+    UBQP_CUDA(cudaMemset(q->err, 0, sizeof(unsigned)));
+    if (e & UBQP_DEVERR_TIMEOUT) return fail(UBQP_ERR_TIMEOUT, "a kernel wait timed out");
+    return fail(UBQP_ERR_ARG, "a kernel saw an index outside [0, S)");
+  }
+  return UBQP_OK;
+}
+
+int ubqp_first_derivative(const ubqp_q* q, uint64_t* x0_dev, void* stream) {
+  if (!q || !x0_dev) return fail(UBQP_ERR_ARG, "NULL argument");
+  UBQP_CUDA(cudaMemcpyAsync(x0_dev, q->x0, 8 * (size_t)q->W, cudaMemcpyDeviceToDevice,
+                            (cudaStream_t)stream));
+  return UBQP_OK;
+}
+
+int ubqp_diversify(const ubqp_q* q, const uint64_t* x0_dev, int32_t mode, uint64_t seed,
+                   uint64_t round, int64_t S, int32_t div_H, uint64_t* X_dev, void* stream) {
+  if (!q || !X_dev) return fail(UBQP_ERR_ARG, "NULL argument");
+  if (S < 0) return fail(UBQP_ERR_ARG, "S < 0");
+  if (mode != UBQP_MODE_RANDOM && mode != UBQP_MODE_DIVERSIFY)
+    return fail(UBQP_ERR_ARG, "unknown mode %d", mode);
+  if (mode == UBQP_MODE_DIVERSIFY && div_H < 1) return fail(UBQP_ERR_ARG, "div_H < 1");
+  if (S == 0) return UBQP_OK;
+  const uint64_t* x0 = x0_dev ? x0_dev : q->x0;
+  UBQP_CUDA(ubqp::launch_diversify(x0, q->n, mode, seed, round, S, div_H, X_dev,
+                                   (cudaStream_t)stream));
+  return UBQP_OK;
+}
+
+size_t ubqp_eval_workspace_size(const ubqp_q* q, int64_t S, int32_t path) {
+  if (!q || S < 0) return 0;
+  return resolve_path(path) == UBQP_EVAL_TC ? ubqp::eval_tc_workspace(q, S) : 0;
+}
+
+int ubqp_eval(const ubqp_q* q, const uint64_t* X_dev, int64_t S, int64_t* f_dev, int32_t path,
+              void* ws, size_t ws_bytes, void* stream) {
+  if (!q || !X_dev || !f_dev) return fail(UBQP_ERR_ARG, "NULL argument");
+  if (S < 0) return fail(UBQP_ERR_ARG, "S < 0");
+  path = resolve_path(path);
+  if (path != UBQP_EVAL_TC && path != UBQP_EVAL_PLAIN)
+    return fail(UBQP_ERR_ARG, "unknown eval path %d", path);
+  if (S == 0) return UBQP_OK;
+  cudaStream_t st = (cudaStream_t)stream;
+  if (path == UBQP_EVAL_PLAIN) {
+    UBQP_CUDA(ubqp::launch_eval_plain(q, X_dev, S, f_dev, st));
+    return UBQP_OK;
+  }
+  // bf16 operands: |2 Q_jk| <= 256 is exact; fp32 partial sums stay below 2^24
+  if ((int64_t)2 * q->max_abs * q->n_tc >= (1 << 24))
+    return fail(UBQP_ERR_RANGE, "2*max|Q|*n_pad = %lld >= 2^24",
+                (long long)2 * q->max_abs * q->n_tc);
+  const size_t need = ubqp::eval_tc_workspace(q, S);
+  if (ws_bytes < need || (need && !ws))
+    return fail(UBQP_ERR_NOMEM, "eval workspace %zu < %zu bytes", ws_bytes, need);
+  if (((uintptr_t)ws & 15) != 0) return fail(UBQP_ERR_ARG, "workspace not 16-byte aligned");
+  cudaError_t e = ubqp::launch_eval_tc(q, X_dev, S, f_dev, ws, ws_bytes, st);
+  if (e == cudaErrorNotSupported)
+    return fail(UBQP_ERR_UNSUPPORTED, "tensor-core evaluation not available for this size");
+  if (e != cudaSuccess) return cuda_fail(e, "eval_tc");
+  return UBQP_OK;
+}
+
+int ubqp_screen(const int64_t* f_dev, int64_t S, double lambda, int32_t* idx_dev,
+                int64_t* count_dev, double* Tm_dev, int64_t* stats_dev, void* stream) {
+  if (!f_dev || !idx_dev || !count_dev || !Tm_dev || !stats_dev)
+    return fail(UBQP_ERR_ARG, "NULL argument");
+  if (S < 1 || S >= ((int64_t)1 << 31)) return fail(UBQP_ERR_ARG, "S=%lld outside [1, 2^31)", (long long)S);
+  if (!(lambda == lambda) || lambda > 1e300 || lambda < -1e300)
+    return fail(UBQP_ERR_ARG, "lambda is not finite");
+  UBQP_CUDA(ubqp::launch_screen(f_dev, S, lambda, idx_dev, count_dev, Tm_dev, stats_dev,
+                                (cudaStream_t)stream));
+  return UBQP_OK;
+}
+
+int ubqp_ascent(const ubqp_q* q, uint64_t* X_dev, int64_t* f_dev, const int32_t* idx_dev,
+                const int64_t* count_dev, int64_t S, int32_t max_flips, int32_t* flips_dev,
+                void* stream) {
+  if (!q || !X_dev || !f_dev || !idx_dev || !count_dev) return fail(UBQP_ERR_ARG, "NULL argument");
+  if (S < 0 || S >= ((int64_t)1 << 31)) return fail(UBQP_ERR_ARG, "S outside [0, 2^31)");
+  if (max_flips < 0) return fail(UBQP_ERR_ARG, "max_flips < 0");
+  if (S == 0) return UBQP_OK;
+  UBQP_CUDA(ubqp::launch_ascent(q, X_dev, f_dev, idx_dev, count_dev, S, max_flips, flips_dev,
+                                (cudaStream_t)stream));
+  return UBQP_OK;
+}
+
+int ubqp_best(const int64_t* f_dev, const uint64_t* X_dev, int64_t S, int32_t words,
+              uint64_t* best_x_dev, int64_t* best_f_dev, void* stream) {
+  if (!f_dev || !X_dev || !best_x_dev || !best_f_dev) return fail(UBQP_ERR_ARG, "NULL argument");
+  if (S < 1 || words < 1) return fail(UBQP_ERR_ARG, "S < 1 or words < 1");
+  UBQP_CUDA(ubqp::launch_best(f_dev, X_dev, S, words, best_x_dev, best_f_dev,
+                              (cudaStream_t)stream));
+  return UBQP_OK;
+}
+
+size_t ubqp_solve_workspace_size(const ubqp_q* q, const ubqp_params* p) {
+  if (!q || !p || p->num_starts < 1) return 0;
+  return solve_layout(q, p).total;
+}
+
+int ubqp_solve(const ubqp_q* q, const ubqp_params* p, uint64_t* best_x_dev, int64_t* best_f_dev,
+               ubqp_stats* stats_host, void* ws, size_t ws_bytes, void* stream) {
+  if (!q || !p || !best_x_dev || !best_f_dev || !ws) return fail(UBQP_ERR_ARG, "NULL argument");
+  if (p->num_starts < 1 || p->num_starts >= ((int64_t)1 << 31))
+    return fail(UBQP_ERR_ARG, "num_starts outside [1, 2^31)");
+  if (((uintptr_t)ws & 15) != 0) return fail(UBQP_ERR_ARG, "workspace not 16-byte aligned");
+  const SolveLayout L = solve_layout(q, p);
+  if (ws_bytes < L.total) return fail(UBQP_ERR_NOMEM, "workspace %zu < %zu bytes", ws_bytes, L.total);
+  const int64_t S = p->num_starts;
+  char* base = (char*)ws;
+  uint64_t* X = (uint64_t*)(base + L.X);
+  int64_t* f = (int64_t*)(base + L.f);
+  int32_t* idx = (int32_t*)(base + L.idx);
+  int32_t* flips = (int32_t*)(base + L.flips);
+  int64_t* count = (int64_t*)(base + L.small);
+  double* Tm = (double*)(base + L.small + 8);
+  int64_t* sstats = (int64_t*)(base + L.small + 24);
+  int64_t* sout = (int64_t*)(base + L.small + 48);
+  cudaStream_t st = (cudaStream_t)stream;
+  int r;
+  if ((r = ubqp_diversify(q, nullptr, p->mode, p->seed, p->round, S, p->div_H, X, stream)))
+    return r;
+  if ((r = ubqp_eval(q, X, S, f, p->eval_path, base + L.eval, L.total - L.eval, stream)))
+    return r;
+  if ((r = ubqp_screen(f, S, p->lambda, idx, count, Tm, sstats, stream))) return r;
+  UBQP_CUDA(cudaMemsetAsync(flips, 0, sizeof(int32_t) * S, st));
+  if ((r = ubqp_ascent(q, X, f, idx, count, S, p->max_flips, flips, stream))) return r;
+  if ((r = ubqp_best(f, X, S, q->W, best_x_dev, best_f_dev, stream))) return r;
+  UBQP_CUDA(ubqp::launch_solve_stats(count, idx, flips, Tm, sstats, best_f_dev, sout, st));
+  if (stats_host) {
+    int64_t hs[6];
+    double hd[2];
+    UBQP_CUDA(cudaMemcpyAsync(hs, sout, sizeof(hs), cudaMemcpyDeviceToHost, st));
+    UBQP_CUDA(cudaMemcpyAsync(hd, Tm, sizeof(hd), cudaMemcpyDeviceToHost, st));
+    if ((r = ubqp_sync(q, stream))) return r;
+    stats_host->passed = hs[0];
+    stats_host->total_flips = hs[1];
+    stats_host->max_flips_seen = hs[2];
+    stats_host->batch_max = hs[3];
+    stats_host->best_index = hs[4];
+    stats_host->sum = hs[5];
+    stats_host->T = hd[0];
+    stats_host->mean = hd[1];
+  }
+  return UBQP_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,98 @@
+// k_best.cu -- UpdateBestAndT's bookkeeping (Fig. 2): the best of a batch of
+// objective values, lowest start index on ties, and a copy of its solution;
+// plus the per-round statistics that ubqp_solve reports.
+#include <climits>
+
+#include "ubqp_internal.cuh"
+
+namespace ubqp {
+namespace {
+
+constexpr int THREADS = 1024;
+constexpr int WARPS = THREADS / 32;
+
+__global__ void __launch_bounds__(THREADS)
+best_kernel(const int64_t* __restrict__ f, const uint64_t* __restrict__ X, int64_t S, int W,
+            uint64_t* __restrict__ best_x, int64_t* __restrict__ best_f) {
+  __shared__ long long s_max[WARPS], s_arg[WARPS];
+  __shared__ long long s_best;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  long long mx = LLONG_MIN, am = LLONG_MAX;
+  for (int64_t b = threadIdx.x; b < S; b += THREADS) {
+    long long v = f[b];
+    if (v > mx) { mx = v; am = b; }
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    long long om = __shfl_xor_sync(0xffffffffu, mx, o);
+    long long oa = __shfl_xor_sync(0xffffffffu, am, o);
+    if (om > mx || (om == mx && oa < am)) { mx = om; am = oa; }
+  }
+  if (lane == 0) { s_max[warp] = mx; s_arg[warp] = am; }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    long long m = LLONG_MIN, a = LLONG_MAX;
+    for (int i = 0; i < WARPS; ++i)
+      if (s_max[i] > m || (s_max[i] == m && s_arg[i] < a)) { m = s_max[i]; a = s_arg[i]; }
+    best_f[0] = m;
+    best_f[1] = a;
+    s_best = a;
+  }
+  __syncthreads();
+  const long long a = s_best;
+  for (int w = threadIdx.x; w < W; w += THREADS) best_x[w] = X[a * W + w];
+}
+
+// out = {passed, total flips, max flips of one start, batch max, best index, sum}
+__global__ void __launch_bounds__(THREADS)
+solve_stats_kernel(const int64_t* __restrict__ count, const int32_t* __restrict__ idx,
+                   const int32_t* __restrict__ flips, const int64_t* __restrict__ sstats,
+                   const int64_t* __restrict__ best, int64_t* __restrict__ out) {
+  __shared__ long long s_tot[WARPS], s_mx[WARPS];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int64_t c = *count;
+  long long tot = 0, mx = 0;
+  for (int64_t t = threadIdx.x; t < c; t += THREADS) {
+    long long v = flips[idx[t]];
+    tot += v;
+    mx = v > mx ? v : mx;
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    tot += __shfl_xor_sync(0xffffffffu, tot, o);
+    long long v = __shfl_xor_sync(0xffffffffu, mx, o);
+    mx = v > mx ? v : mx;
+  }
+  if (lane == 0) { s_tot[warp] = tot; s_mx[warp] = mx; }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    long long t = 0, m = 0;
+    for (int i = 0; i < WARPS; ++i) {
+      t += s_tot[i];
+      m = s_mx[i] > m ? s_mx[i] : m;
+    }
+    out[0] = c;
+    out[1] = t;
+    out[2] = m;
+    out[3] = sstats[0];
+    out[4] = best[1];
+    out[5] = sstats[2];
+  }
+}
+
+}  // namespace
+
+cudaError_t launch_best(const int64_t* f, const uint64_t* X, int64_t S, int W,
+                        uint64_t* best_x, int64_t* best_f, cudaStream_t st) {
+  best_kernel<<<1, THREADS, 0, st>>>(f, X, S, W, best_x, best_f);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_solve_stats(const int64_t* count, const int32_t* idx, const int32_t* flips,
+                               const double* /*Tm*/, const int64_t* sstats,
+                               const int64_t* best, int64_t* out, cudaStream_t st) {
+  solve_stats_kernel<<<1, THREADS, 0, st>>>(count, idx, flips, sstats, best, out);
+  return cudaGetLastError();
+}
+
+}  // namespace ubqp

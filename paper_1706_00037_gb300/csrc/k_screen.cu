@@ -1,0 +1,90 @@
+// k_screen.cu -- the screen of the Pseudocode section: T(lambda) = Mean +
+// lambda (Max - Mean) over the batch, then the stable list of indices with
+// f_b > T (Fig. 2).  One block: an exact int64 sum and a max (lowest index on
+// ties) by warp shuffles, the threshold in double with explicitly rounded
+// operations (no FMA), then a block-wide ballot/prefix-sum compaction.
+#include <climits>
+
+#include "ubqp_internal.cuh"
+
+namespace ubqp {
+namespace {
+
+constexpr int THREADS = 1024;
+constexpr int WARPS = THREADS / 32;
+
+__global__ void __launch_bounds__(THREADS)
+screen_kernel(const int64_t* __restrict__ f, int64_t S, double lambda,
+              int32_t* __restrict__ idx, int64_t* __restrict__ count, double* __restrict__ Tm,
+              int64_t* __restrict__ stats) {
+  __shared__ long long s_sum[WARPS];
+  __shared__ long long s_max[WARPS];
+  __shared__ long long s_arg[WARPS];
+  __shared__ int s_cnt[WARPS];
+  __shared__ double s_T;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+
+  long long sum = 0, mx = LLONG_MIN, am = LLONG_MAX;
+  for (int64_t b = threadIdx.x; b < S; b += THREADS) {
+    long long v = f[b];
+    sum += v;
+    if (v > mx) { mx = v; am = b; }  // increasing b per thread: keeps lowest
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    sum += __shfl_xor_sync(0xffffffffu, sum, o);
+    long long om = __shfl_xor_sync(0xffffffffu, mx, o);
+    long long oa = __shfl_xor_sync(0xffffffffu, am, o);
+    if (om > mx || (om == mx && oa < am)) { mx = om; am = oa; }
+  }
+  if (lane == 0) { s_sum[warp] = sum; s_max[warp] = mx; s_arg[warp] = am; }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    long long t = 0, m = LLONG_MIN, a = LLONG_MAX;
+    for (int i = 0; i < WARPS; ++i) {
+      t += s_sum[i];
+      if (s_max[i] > m || (s_max[i] == m && s_arg[i] < a)) { m = s_max[i]; a = s_arg[i]; }
+    }
+    const double mean = __ddiv_rn(__ll2double_rn(t), __ll2double_rn(S));
+    const double diff = __dsub_rn(__ll2double_rn(m), mean);
+    const double scaled = __dmul_rn(lambda, diff);
+    const double T = __dadd_rn(mean, scaled);
+    s_T = T;
+    Tm[0] = T;
+    Tm[1] = mean;
+    stats[0] = m;
+    stats[1] = a;
+    stats[2] = t;
+  }
+  __syncthreads();
+  const double T = s_T;
+  // stable compaction, THREADS values per pass
+  int64_t base = 0;
+  for (int64_t b0 = 0; b0 < S; b0 += THREADS) {
+    const int64_t b = b0 + threadIdx.x;
+    const bool pass = b < S && __ll2double_rn(f[b]) > T;
+    const unsigned bal = __ballot_sync(0xffffffffu, pass);
+    if (lane == 0) s_cnt[warp] = __popc(bal);
+    __syncthreads();
+    int before = 0, total = 0;
+    for (int i = 0; i < WARPS; ++i) {
+      int c = s_cnt[i];
+      before += (i < warp) ? c : 0;
+      total += c;
+    }
+    if (pass) idx[base + before + __popc(bal & ((1u << lane) - 1u))] = (int32_t)b;
+    base += total;
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) *count = base;
+}
+
+}  // namespace
+
+cudaError_t launch_screen(const int64_t* f, int64_t S, double lambda, int32_t* idx,
+                          int64_t* count, double* Tm, int64_t* stats, cudaStream_t st) {
+  screen_kernel<<<1, THREADS, 0, st>>>(f, S, lambda, idx, count, Tm, stats);
+  return cudaGetLastError();
+}
+
+}  // namespace ubqp

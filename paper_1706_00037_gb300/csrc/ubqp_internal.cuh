@@ -1,0 +1,83 @@
+// ubqp_internal.cuh -- types and launchers shared by the translation units of
+// libubqp.  Not part of the public ABI (include/ubqp.h).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "../../include/ubqp.h"
+
+#define UBQP_ROW_ALIGN 1024  // row stride of the int8 copy (ascent rows)
+#define UBQP_TC_ALIGN 256    // padding of the tensor-core operand
+#define UBQP_MAX_N 16384
+
+// Error word bits recorded by kernels (cleared by ubqp_sync).
+#define UBQP_DEVERR_TIMEOUT 1u
+#define UBQP_DEVERR_BADIDX 2u
+
+struct ubqp_q {
+  int32_t n;        // variables
+  int32_t W;        // words per solution
+  int64_t ldq;      // row stride of Q8 (multiple of UBQP_ROW_ALIGN)
+  int32_t n_tc;     // n rounded up to UBQP_TC_ALIGN (rows/cols of Qt)
+  int32_t max_abs;  // max |Q_ij|
+  int8_t* Q8;       // n x ldq int8, zero beyond column n
+  uint16_t* Qt;     // n_tc x n_tc bf16 bits of Q' = 2 tril(Q,-1) + diag(Q)
+  int32_t* rowsum;  // n
+  uint64_t* x0;     // W words: first-derivative start
+  unsigned* err;    // device error word
+  unsigned* scratch_flags;  // device: [0] asymmetric count, [1] max |Q|
+  int64_t device_bytes;
+  int sm_count;
+  int device;
+};
+
+namespace ubqp {
+
+__host__ __device__ inline int64_t words_of(int64_t n) { return (n + 63) / 64; }
+
+// SplitMix64 (Steele, Lea & Flood 2014): the first output of the sequential
+// generator started at `state`.
+__host__ __device__ __forceinline__ uint64_t splitmix64(uint64_t state) {
+  uint64_t z = state + 0x9E3779B97F4A7C15ULL;
+  z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ULL;
+  z = (z ^ (z >> 27)) * 0x94D049BB133111EBULL;
+  return z ^ (z >> 31);
+}
+__host__ __device__ __forceinline__ uint64_t stream_word(uint64_t seed, uint64_t stream,
+                                                         uint64_t ctr) {
+  return splitmix64(seed ^ (stream * 0x9E3779B97F4A7C15ULL) ^ ctr);
+}
+
+// Mask of the valid bits of word w of an n-bit solution.
+__host__ __device__ __forceinline__ uint64_t valid_mask(int64_t n, int64_t w) {
+  int64_t lo = w * 64;
+  if (n >= lo + 64) return ~0ULL;
+  if (n <= lo) return 0ULL;
+  return (1ULL << (n - lo)) - 1ULL;
+}
+
+// ---- launchers (each returns cudaError_t of its launch) --------------------
+cudaError_t launch_prepare(const int8_t* Q, int n, int64_t ldq_in, ubqp_q* h,
+                           cudaStream_t st);
+cudaError_t launch_diversify(const uint64_t* x0, int n, int mode, uint64_t seed,
+                             uint64_t round, int64_t S, int div_H, uint64_t* X,
+                             cudaStream_t st);
+cudaError_t launch_eval_plain(const ubqp_q* h, const uint64_t* X, int64_t S,
+                              int64_t* f, cudaStream_t st);
+size_t eval_tc_workspace(const ubqp_q* h, int64_t S);
+cudaError_t launch_eval_tc(const ubqp_q* h, const uint64_t* X, int64_t S, int64_t* f,
+                           void* ws, size_t ws_bytes, cudaStream_t st);
+cudaError_t launch_screen(const int64_t* f, int64_t S, double lambda, int32_t* idx,
+                          int64_t* count, double* Tm, int64_t* stats, cudaStream_t st);
+cudaError_t launch_ascent(const ubqp_q* h, uint64_t* X, int64_t* f, const int32_t* idx,
+                          const int64_t* count, int64_t S, int32_t max_flips,
+                          int32_t* flips, cudaStream_t st);
+cudaError_t launch_best(const int64_t* f, const uint64_t* X, int64_t S, int W,
+                        uint64_t* best_x, int64_t* best_f, cudaStream_t st);
+cudaError_t launch_solve_stats(const int64_t* count, const int32_t* idx,
+                               const int32_t* flips, const double* Tm,
+                               const int64_t* sstats, const int64_t* best,
+                               int64_t* out, cudaStream_t st);
+
+}  // namespace ubqp

@@ -1,0 +1,247 @@
+"""Python binding of libubqp (the C ABI in include/ubqp.h).
+
+Argument marshalling only: every step of the hot path runs in the library's
+CUDA kernels.  PyTorch supplies device memory and the current stream.  If the
+library cannot be built or loaded this module raises -- there is no fallback.
+
+Solutions are bit-packed uint64 words; torch has no general uint64 support, so
+they travel in ``torch.int64`` tensors of shape (S, W) holding the same bits.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import torch
+
+from . import build as _build
+
+RANDOM, DIVERSIFY = 0, 1
+EVAL_AUTO, EVAL_TC, EVAL_PLAIN = 0, 1, 2
+
+OK = 0
+STATUS_NAMES = {0: "OK", -1: "ERR_ARG", -2: "ERR_NOT_SYMMETRIC", -3: "ERR_RANGE",
+                -4: "ERR_NOMEM", -5: "ERR_CUDA", -6: "ERR_TIMEOUT", -7: "ERR_UNSUPPORTED"}
+
+EXPORTS = ["ubqp_strerror", "ubqp_last_error", "ubqp_abi_version", "ubqp_q_prepare",
+           "ubqp_q_destroy", "ubqp_q_info", "ubqp_sync", "ubqp_first_derivative",
+           "ubqp_diversify", "ubqp_eval_workspace_size", "ubqp_eval", "ubqp_screen",
+           "ubqp_ascent", "ubqp_best", "ubqp_solve_workspace_size", "ubqp_solve"]
+
+
+class UbqpError(RuntimeError):
+    def __init__(self, status: int, detail: str):
+        self.status = status
+        super().__init__(f"{STATUS_NAMES.get(status, status)}: {detail}")
+
+
+class Params(ctypes.Structure):
+    _fields_ = [("num_starts", ctypes.c_int64), ("lambda_", ctypes.c_double),
+                ("max_flips", ctypes.c_int32), ("mode", ctypes.c_int32),
+                ("seed", ctypes.c_uint64), ("round", ctypes.c_uint64),
+                ("div_H", ctypes.c_int32), ("eval_path", ctypes.c_int32)]
+
+
+class Stats(ctypes.Structure):
+    _fields_ = [("passed", ctypes.c_int64), ("total_flips", ctypes.c_int64),
+                ("max_flips_seen", ctypes.c_int64), ("batch_max", ctypes.c_int64),
+                ("best_index", ctypes.c_int64), ("sum", ctypes.c_int64),
+                ("T", ctypes.c_double), ("mean", ctypes.c_double)]
+
+    def as_dict(self) -> dict:
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+_lib = None
+
+
+def library_path() -> str:
+    return _build.LIB
+
+
+def load() -> ctypes.CDLL:
+    """Build (if stale) and load libubqp.so; raise if that is impossible."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    path = _build.build()
+    if not os.path.exists(path):
+        raise RuntimeError(f"libubqp.so missing at {path}")
+    lib = ctypes.CDLL(path)
+    P, i32, i64, u64 = ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64, ctypes.c_uint64
+    sz, f64 = ctypes.c_size_t, ctypes.c_double
+    sig = {
+        "ubqp_strerror": (ctypes.c_char_p, [ctypes.c_int]),
+        "ubqp_last_error": (ctypes.c_char_p, []),
+        "ubqp_abi_version": (ctypes.c_int, []),
+        "ubqp_q_prepare": (ctypes.c_int, [P, i32, i64, P, ctypes.POINTER(P)]),
+        "ubqp_q_destroy": (None, [P]),
+        "ubqp_q_info": (ctypes.c_int, [P, P, P, P, P, P]),
+        "ubqp_sync": (ctypes.c_int, [P, P]),
+        "ubqp_first_derivative": (ctypes.c_int, [P, P, P]),
+        "ubqp_diversify": (ctypes.c_int, [P, P, i32, u64, u64, i64, i32, P, P]),
+        "ubqp_eval_workspace_size": (sz, [P, i64, i32]),
+        "ubqp_eval": (ctypes.c_int, [P, P, i64, P, i32, P, sz, P]),
+        "ubqp_screen": (ctypes.c_int, [P, i64, f64, P, P, P, P, P]),
+        "ubqp_ascent": (ctypes.c_int, [P, P, P, P, P, i64, i32, P, P]),
+        "ubqp_best": (ctypes.c_int, [P, P, i64, i32, P, P, P]),
+        "ubqp_solve_workspace_size": (sz, [P, ctypes.POINTER(Params)]),
+        "ubqp_solve": (ctypes.c_int, [P, ctypes.POINTER(Params), P, P, ctypes.POINTER(Stats),
+                                      P, sz, P]),
+    }
+    for name, (res, args) in sig.items():
+        fn = getattr(lib, name)
+        fn.restype = res
+        fn.argtypes = args
+    _lib = lib
+    return lib
+
+
+def _check(status: int):
+    if status != OK:
+        detail = load().ubqp_last_error().decode()
+        raise UbqpError(status, detail or load().ubqp_strerror(status).decode())
+
+
+def _stream(stream=None):
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return ctypes.c_void_p(s.cuda_stream)
+
+
+def _ptr(t: torch.Tensor | None):
+    if t is None:
+        return None
+    if not t.is_cuda:
+        raise ValueError("expected a CUDA tensor")
+    if not t.is_contiguous():
+        raise ValueError("expected a contiguous tensor")
+    return ctypes.c_void_p(t.data_ptr())
+
+
+def words(n: int) -> int:
+    return (n + 63) // 64
+
+
+class Instance:
+    """A prepared UBQP instance (device-resident Q); wraps ``ubqp_q*``."""
+
+    def __init__(self, Q: torch.Tensor, stream=None):
+        if Q.dtype != torch.int8 or Q.dim() != 2 or not Q.is_cuda:
+            raise ValueError("Q must be a 2-D int8 CUDA tensor")
+        Q = Q.contiguous()
+        n, ldq = Q.shape
+        h = ctypes.c_void_p()
+        _check(load().ubqp_q_prepare(_ptr(Q), n, ldq, _stream(stream), ctypes.byref(h)))
+        self._h = h
+        vals = [ctypes.c_int32() for _ in range(4)] + [ctypes.c_int64()]
+        _check(load().ubqp_q_info(h, *[ctypes.byref(v) for v in vals]))
+        self.n, self.words, self.n_pad, self.max_abs = (v.value for v in vals[:4])
+        self.device_bytes = vals[4].value
+        self.device = Q.device
+
+    @property
+    def handle(self):
+        if self._h is None:
+            raise RuntimeError("instance closed")
+        return self._h
+
+    def close(self):
+        if getattr(self, "_h", None) is not None:
+            load().ubqp_q_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def sync(self, stream=None):
+        _check(load().ubqp_sync(self.handle, _stream(stream)))
+
+
+def first_derivative(inst: Instance, stream=None) -> torch.Tensor:
+    x0 = torch.empty(inst.words, dtype=torch.int64, device=inst.device)
+    _check(load().ubqp_first_derivative(inst.handle, _ptr(x0), _stream(stream)))
+    return x0
+
+
+def diversify(inst: Instance, S: int, mode: int = DIVERSIFY, seed: int = 0, round_: int = 0,
+              div_H: int = 64, x0: torch.Tensor | None = None, out: torch.Tensor | None = None,
+              stream=None) -> torch.Tensor:
+    X = out if out is not None else torch.empty((S, inst.words), dtype=torch.int64,
+                                                device=inst.device)
+    _check(load().ubqp_diversify(inst.handle, _ptr(x0), mode, seed % 2**64, round_, S, div_H,
+                                 _ptr(X), _stream(stream)))
+    return X
+
+
+def eval_workspace_size(inst: Instance, S: int, path: int = EVAL_AUTO) -> int:
+    return int(load().ubqp_eval_workspace_size(inst.handle, S, path))
+
+
+def eval(inst: Instance, X: torch.Tensor, path: int = EVAL_AUTO, out: torch.Tensor | None = None,
+         ws: torch.Tensor | None = None, stream=None) -> torch.Tensor:  # noqa: A001
+    S = X.shape[0]
+    f = out if out is not None else torch.empty(S, dtype=torch.int64, device=inst.device)
+    need = eval_workspace_size(inst, S, path)
+    if ws is None and need:
+        ws = torch.empty(need, dtype=torch.uint8, device=inst.device)
+    nbytes = ws.numel() * ws.element_size() if ws is not None else 0
+    _check(load().ubqp_eval(inst.handle, _ptr(X), S, _ptr(f), path, _ptr(ws), nbytes,
+                            _stream(stream)))
+    return f
+
+
+def screen(f: torch.Tensor, lam: float, stream=None) -> dict:
+    S = f.shape[0]
+    dev = f.device
+    idx = torch.empty(max(S, 1), dtype=torch.int32, device=dev)
+    count = torch.empty(1, dtype=torch.int64, device=dev)
+    Tm = torch.empty(2, dtype=torch.float64, device=dev)
+    st = torch.empty(3, dtype=torch.int64, device=dev)
+    _check(load().ubqp_screen(_ptr(f), S, float(lam), _ptr(idx), _ptr(count), _ptr(Tm),
+                              _ptr(st), _stream(stream)))
+    return {"idx": idx, "count": count, "Tm": Tm, "stats": st}
+
+
+def ascent(inst: Instance, X: torch.Tensor, f: torch.Tensor, idx: torch.Tensor,
+           count: torch.Tensor, max_flips: int = 0, flips: torch.Tensor | None = None,
+           stream=None) -> torch.Tensor | None:
+    _check(load().ubqp_ascent(inst.handle, _ptr(X), _ptr(f), _ptr(idx), _ptr(count),
+                              X.shape[0], max_flips, _ptr(flips), _stream(stream)))
+    return flips
+
+
+def best(f: torch.Tensor, X: torch.Tensor, stream=None):
+    bx = torch.empty(X.shape[1], dtype=torch.int64, device=X.device)
+    bf = torch.empty(2, dtype=torch.int64, device=X.device)
+    _check(load().ubqp_best(_ptr(f), _ptr(X), f.shape[0], X.shape[1], _ptr(bx), _ptr(bf),
+                            _stream(stream)))
+    return bx, bf
+
+
+def make_params(S: int, lam: float, max_flips: int = 0, mode: int = DIVERSIFY, seed: int = 0,
+                round_: int = 0, div_H: int = 64, eval_path: int = EVAL_AUTO) -> Params:
+    return Params(S, float(lam), max_flips, mode, seed % 2**64, round_, div_H, eval_path)
+
+
+def solve_workspace_size(inst: Instance, params: Params) -> int:
+    return int(load().ubqp_solve_workspace_size(inst.handle, ctypes.byref(params)))
+
+
+def solve(inst: Instance, params: Params, ws: torch.Tensor | None = None,
+          best_x: torch.Tensor | None = None, best_f: torch.Tensor | None = None,
+          want_stats: bool = True, stream=None):
+    """One round (Fig. 2's loop body over a batch).  Returns (best_x, best_f[2], stats)."""
+    need = solve_workspace_size(inst, params)
+    if ws is None:
+        ws = torch.empty(need, dtype=torch.uint8, device=inst.device)
+    bx = best_x if best_x is not None else torch.empty(inst.words, dtype=torch.int64,
+                                                       device=inst.device)
+    bf = best_f if best_f is not None else torch.empty(2, dtype=torch.int64, device=inst.device)
+    st = Stats() if want_stats else None
+    _check(load().ubqp_solve(inst.handle, ctypes.byref(params), _ptr(bx), _ptr(bf),
+                             ctypes.byref(st) if st is not None else None, _ptr(ws),
+                             ws.numel(), _stream(stream)))
+    return bx, bf, (st.as_dict() if st is not None else None)
