@@ -42,7 +42,7 @@ bool is_device_ptr(const void* p) {
   return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
 }
 
-int resolve_path(int path) { return path == UBQP_EVAL_AUTO ? UBQP_EVAL_PLAIN : path; }
+int resolve_path(int path) { return path == UBQP_EVAL_AUTO ? UBQP_EVAL_TC : path; }
 
 // Workspace of ubqp_solve, carved in this order (each piece 256-byte aligned).
 struct SolveLayout {
@@ -99,6 +99,7 @@ void ubqp_q_destroy(ubqp_q* q) {
   cudaFree(q->rowsum);
   cudaFree(q->x0);
   cudaFree(q->err);
+  cudaFree(q->tc_chunks);
   delete q;
 }
 
@@ -148,6 +149,10 @@ int ubqp_q_prepare(const int8_t* Q_dev, int32_t n, int64_t ldq, void* stream, ub
     return fail(UBQP_ERR_NOT_SYMMETRIC, "Q is not symmetric (%u tiles differ)", flags[0]);
   }
   h->max_abs = (int32_t)flags[1];
+  if ((e = ubqp::eval_tc_prepare(h)) != cudaSuccess) {
+    ubqp_q_destroy(h);
+    return cuda_fail(e, "eval_tc_prepare");
+  }
   *out = h;
   return UBQP_OK;
 }

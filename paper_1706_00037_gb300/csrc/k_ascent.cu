@@ -1,20 +1,26 @@
 // k_ascent.cu -- PerformSteepestAscent of Fig. 2, batched: every listed start
 // is climbed by 1-bit flips, always taking the flip of largest gain (lowest
-// index on ties) while the gain is positive.  Gains follow the 1-flip move
-// values of Glover et al. (2002) that the Pseudocode section cites:
-//     Delta_i = Q_ii + 2 (1 - 2 x_i) y_i,  y = Q x,
-//     after flipping k (d = 1 - 2 x_k):  Delta_j += 2 (1 - 2 x_j) d Q_jk (j != k),
-//                                        Delta_k  = -Delta_k.
+// index on ties) while the gain is positive.  Gains are the 1-flip move values
+// of Glover et al. (2002) that the Pseudocode section cites,
+//     Delta_j = Q_jj + 2 (1 - 2 x_j) y_j,   y = Q x,
+// and a flip of bit k (d = 1 - 2 x_k before the flip) changes y by d times
+// column k of Q (= row k, Q being symmetric) and negates the sign of x_k.
 //
-// Design: a group of G threads owns one start at a time (G = 32: one warp, for
-// n <= 512; G = 256: one block).  Thread g of the group owns the 4*C elements
-// j = c*4G + 4g + e (c < C, e < 4) and keeps their gains in registers, so a
-// move streams one int8 row of Q (row k = column k, Q being symmetric) with
-// fully coalesced 4-byte loads, updates the gains and finds the next argmax in
-// the same pass.  The argmax key packs (gain, lowest index, x bit) into one
-// int64 so that a single max-reduction decides the move and tells every thread
-// the bit it flips.  Rows are read from L2 (the int8 Q of one instance, e.g.
-// 49 MB at n = 7000, stays resident there); nothing per move goes to HBM.
+// Design.  A group of T threads owns one start at a time (one warp for
+// n <= 512, else one block).  Thread g owns E = 16*C elements, in chunks of 16
+// consecutive indices: element e lives at j = (e/16)*16T + 16g + e%16, so one
+// move loads row k of the int8 Q with C fully coalesced 16-byte loads per
+// thread.  Per element the thread keeps, in registers,
+//     y_j,   S_j = 128 (1 - 2 x_j),   C_j = 64 Q_jj + 2 (31 - e) + x_j,
+// so that the argmax key  key_j = C_j + S_j y_j = 64 Delta_j + 2 (31 - e) + x_j
+// costs one multiply-add.  A move is therefore, per element: extract the
+// coefficient, y += d q, key = C + S y, running max -- four instructions.  The
+// key orders by gain, then by lower index inside the thread, and carries x_j in
+// its low bit; across threads the group reduces (gain, 2j + x) with warp
+// max/min reductions (redux.sync), so every thread learns k, x_k and Delta_k.
+// The thread owning k negates S_k and toggles the x bit of C_k.  Rows are read
+// from L2 (the int8 Q of one instance, e.g. 49 MB at n = 7000, stays resident
+// there); nothing per move goes to HBM.
 #include <climits>
 
 #include "ubqp_internal.cuh"
@@ -30,221 +36,215 @@ __device__ __forceinline__ uint64_t globaltimer() {
   return t;
 }
 
-__device__ __forceinline__ int sbyte(int w, int e) { return (int)(int8_t)(w >> (8 * e)); }
-
-__device__ __forceinline__ long long make_key(int gain, int j, int xbit) {
-  const unsigned low = ((unsigned)(0x7FFFFFFF - j) << 1) | (unsigned)xbit;
-  return (long long)gain * 4294967296LL + (long long)low;
+// Sign-extended byte i of w (PRMT with the sign-replicate selector).
+__device__ __forceinline__ int sbyte(uint32_t w, int i) {
+  return (int)__byte_perm(w, 0u, (unsigned)(i | ((8 | i) << 4) | ((8 | i) << 8) | ((8 | i) << 12)));
 }
 
-// Max-reduction of a key over the group.
-template <int G>
-struct GroupReduce;
+template <int T>
+struct Group;
 
+// One warp per start.
 template <>
-struct GroupReduce<32> {
-  __device__ __forceinline__ long long max(long long k) {
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-      long long v = __shfl_xor_sync(0xffffffffu, k, o);
-      k = v > k ? v : k;
-    }
-    return k;
+struct Group<32> {
+  __device__ __forceinline__ int rank() const { return threadIdx.x & 31; }
+  // returns {max gain, 2k + x_k} over the group
+  __device__ __forceinline__ int2 reduce(int gain, int jx) {
+    const int m = __reduce_max_sync(0xffffffffu, gain);
+    const int c = __reduce_min_sync(0xffffffffu, gain == m ? jx : INT_MAX);
+    return make_int2(m, c);
   }
   __device__ __forceinline__ bool any(bool p) { return __any_sync(0xffffffffu, p); }
   __device__ __forceinline__ void sync() { __syncwarp(); }
 };
 
-template <>
-struct GroupReduce<256> {
-  static constexpr int NW = 8;
-  long long (*buf)[NW];  // [2][NW] in shared memory
+// One block per start.
+template <int T>
+struct Group {
+  static constexpr int NW = T / 32;
+  int2 (*rec)[NW];  // [2][NW] shared
   int parity;
-  __device__ __forceinline__ long long max(long long k) {
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-      long long v = __shfl_xor_sync(0xffffffffu, k, o);
-      k = v > k ? v : k;
-    }
+  __device__ __forceinline__ int rank() const { return threadIdx.x; }
+  __device__ __forceinline__ int2 reduce(int gain, int jx) {
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    if (lane == 0) buf[parity][warp] = k;
+    const int m = __reduce_max_sync(0xffffffffu, gain);
+    const int c = __reduce_min_sync(0xffffffffu, gain == m ? jx : INT_MAX);
+    if (lane == 0) rec[parity][warp] = make_int2(m, c);
     __syncthreads();
-    k = lane < NW ? buf[parity][lane] : LLONG_MIN;
-#pragma unroll
-    for (int o = NW / 2; o > 0; o >>= 1) {
-      long long v = __shfl_xor_sync(0xffffffffu, k, o);
-      k = v > k ? v : k;
-    }
-    k = __shfl_sync(0xffffffffu, k, 0);
+    const int2 r = lane < NW ? rec[parity][lane] : make_int2(INT_MIN, INT_MAX);
+    const int m2 = __reduce_max_sync(0xffffffffu, r.x);
+    const int c2 = __reduce_min_sync(0xffffffffu, r.x == m2 ? r.y : INT_MAX);
     parity ^= 1;
-    return k;
+    return make_int2(m2, c2);
   }
   __device__ __forceinline__ bool any(bool p) { return __syncthreads_or(p) != 0; }
   __device__ __forceinline__ void sync() { __syncthreads(); }
 };
 
-// Ascent of one start by a group of G threads; g = rank in the group.
-template <int G, int C>
+template <int T, int C>
 __device__ __forceinline__ void ascend_one(const int8_t* __restrict__ Q8, int64_t ldq, int n,
                                            int W, uint64_t* __restrict__ x_g,
                                            int64_t* __restrict__ f_s, int32_t max_flips,
                                            int32_t* __restrict__ flips_s,
                                            unsigned* __restrict__ err, uint64_t* xs,
-                                           GroupReduce<G>& red, int g) {
-  static_assert(4 * C <= 64, "bit mask holds 64 elements per thread");
-  // ---- owned bits of x
-  uint64_t bits = 0;
+                                           Group<T>& grp) {
+  constexpr int E = 16 * C;
+  constexpr int CW = 16 * T;  // indices per chunk
+  static_assert(E <= 32, "local index must fit 5 bits");
+  const int g = grp.rank();
+
+  int y[E], S[E], Ck[E];
+  // ---- owned bits of x; C and S per element
 #pragma unroll
   for (int c = 0; c < C; ++c) {
-    const int j0 = c * 4 * G + 4 * g;
+    const int j0 = c * CW + 16 * g;
+    uint32_t nib = 0;
     if (j0 < n) {
-      uint64_t nib = (x_g[j0 >> 6] >> (j0 & 63)) & 0xFull;
-      const int valid = n - j0;
-      if (valid < 4) nib &= (1ull << valid) - 1ull;
-      bits |= nib << (4 * c);
+      nib = (uint32_t)((x_g[j0 >> 6] >> (j0 & 63)) & 0xFFFFull);
+      if (n - j0 < 16) nib &= (1u << (n - j0)) - 1u;
+    }
+#pragma unroll
+    for (int o = 0; o < 16; ++o) {
+      const int e = c * 16 + o, j = j0 + o;
+      const int xb = (int)((nib >> o) & 1u);
+      y[e] = 0;
+      if (j < n) {
+        const int qjj = Q8[(int64_t)j * ldq + j];
+        S[e] = xb ? -128 : 128;
+        Ck[e] = 64 * qjj + 2 * (31 - e) + xb;
+      } else {
+        S[e] = 0;
+        Ck[e] = INT_MIN;
+      }
     }
   }
-  // ---- y = Q x over the owned columns: sum the rows k with x_k = 1
-  int D[C][4];
-#pragma unroll
-  for (int c = 0; c < C; ++c)
-#pragma unroll
-    for (int e = 0; e < 4; ++e) D[c][e] = 0;
+  // ---- y = Q x on the owned columns: add the rows k with x_k = 1
   for (int w = 0; w < W; ++w) {
     uint64_t word = x_g[w] & valid_mask(n, w);
     while (word) {
-      // up to R rows in flight
-      constexpr int R = C <= 4 ? 4 : (C <= 8 ? 2 : 1);
+      constexpr int R = C == 1 ? 4 : 2;  // rows in flight
       int ks[R];
       int nk = 0;
 #pragma unroll
       for (int r = 0; r < R; ++r) {
+        ks[r] = 0;
         if (word) {
           ks[r] = w * 64 + __ffsll((long long)word) - 1;
           word &= word - 1;
           nk = r + 1;
-        } else {
-          ks[r] = -1;
         }
       }
-      int q[R][C];
+      uint4 q[R][C];
 #pragma unroll
       for (int r = 0; r < R; ++r)
 #pragma unroll
         for (int c = 0; c < C; ++c) {
-          const int j0 = c * 4 * G + 4 * g;
+          const int j0 = c * CW + 16 * g;
           q[r][c] = (r < nk && j0 < ldq)
-                        ? __ldg(reinterpret_cast<const int*>(Q8 + (int64_t)ks[r] * ldq + j0))
-                        : 0;
+                        ? __ldg(reinterpret_cast<const uint4*>(Q8 + (int64_t)ks[r] * ldq + j0))
+                        : make_uint4(0, 0, 0, 0);
         }
 #pragma unroll
       for (int r = 0; r < R; ++r)
 #pragma unroll
-        for (int c = 0; c < C; ++c)
+        for (int c = 0; c < C; ++c) {
+          const uint32_t wv[4] = {q[r][c].x, q[r][c].y, q[r][c].z, q[r][c].w};
 #pragma unroll
-          for (int e = 0; e < 4; ++e) D[c][e] += sbyte(q[r][c], e);
+          for (int o = 0; o < 16; ++o) y[c * 16 + o] += sbyte(wv[o >> 2], o & 3);
+        }
     }
   }
-  // ---- gains; elements beyond n get a sentinel that never wins
-  int bv = INT_MIN, bi = 0;
+  // ---- first argmax
+  int kmax = INT_MIN;
 #pragma unroll
-  for (int c = 0; c < C; ++c)
-#pragma unroll
-    for (int e = 0; e < 4; ++e) {
-      const int j = c * 4 * G + 4 * g + e;
-      if (j < n) {
-        const int qjj = Q8[(int64_t)j * ldq + j];
-        const int s = ((bits >> (4 * c + e)) & 1ull) ? -1 : 1;
-        D[c][e] = qjj + 2 * s * D[c][e];
-      } else {
-        D[c][e] = INT_MIN;
-      }
-      if (D[c][e] > bv) { bv = D[c][e]; bi = 4 * c + e; }
-    }
-  long long key = red.max(make_key(bv, (bi >> 2) * 4 * G + 4 * g + (bi & 3),
-                                   (int)((bits >> bi) & 1ull)));
+  for (int e = 0; e < E; ++e) kmax = max(kmax, Ck[e] + S[e] * y[e]);
+  auto reduce_key = [&](int kt) {
+    const int gain = kt >> 6;
+    const int e = 31 - ((kt >> 1) & 31);
+    const int j = (e >> 4) * CW + 16 * g + (e & 15);
+    return grp.reduce(gain, (j << 1) | (kt & 1));
+  };
+  int2 best = reduce_key(kmax);
+
   int64_t fval = *f_s;
   int flips = 0;
   const uint64_t t0 = globaltimer();
   for (;;) {
-    const long long dk = key >> 32;
     if (max_flips > 0 && flips >= max_flips) break;
-    if (dk <= 0) break;
+    if (best.x <= 0) break;
     if ((flips & 1023) == 1023) {
       const bool late = (int64_t)(globaltimer() - t0) > kTimeoutNs;
-      if (red.any(late)) {
+      if (grp.any(late)) {
         if (g == 0) atomicOr(err, UBQP_DEVERR_TIMEOUT);
         break;
       }
     }
-    const unsigned low = (unsigned)(key & 0xFFFFFFFFll);
-    const int k = 0x7FFFFFFF - (int)(low >> 1);
-    const int d2 = (low & 1u) ? -2 : 2;  // 2 d, d = 1 - 2 x_k (before the flip)
-    fval += dk;
+    const int k = best.y >> 1;
+    const int d = (best.y & 1) ? -1 : 1;  // 1 - 2 x_k before the flip
+    fval += best.x;
     ++flips;
     const int8_t* row = Q8 + (int64_t)k * ldq;
-    int q[C];
+    uint4 q[C];
 #pragma unroll
     for (int c = 0; c < C; ++c) {
-      const int j0 = c * 4 * G + 4 * g;
-      q[c] = j0 < ldq ? __ldg(reinterpret_cast<const int*>(row + j0)) : 0;
+      const int j0 = c * CW + 16 * g;
+      q[c] = j0 < ldq ? __ldg(reinterpret_cast<const uint4*>(row + j0)) : make_uint4(0, 0, 0, 0);
     }
-    const int kc = k / (4 * G);
-    const int kr = k - kc * 4 * G;
-    const int kc_mine = ((kr >> 2) == g) ? kc : -1;
-    const int ke = kr & 3;
-    bv = INT_MIN;
-    bi = 0;
+    // the owner of k flips x_k: negate S_k, toggle the x bit in C_k
+    const int kc = k / CW, kr = k - kc * CW;
+    if ((kr >> 4) == g) {
+      const int ek = kc * 16 + (kr & 15);
+#pragma unroll
+      for (int e = 0; e < E; ++e)
+        if (e == ek) {
+          S[e] = -S[e];
+          Ck[e] ^= 1;
+        }
+    }
+    kmax = INT_MIN;
 #pragma unroll
     for (int c = 0; c < C; ++c) {
-      if (c == kc_mine) {
-        // the owner of k: Delta_k -> -Delta_k, taking into account the generic
-        // update below, which sees the new bit and adds -2 Q_kk
-        const int qkk = sbyte(q[c], ke);
+      const uint32_t wv[4] = {q[c].x, q[c].y, q[c].z, q[c].w};
 #pragma unroll
-        for (int e = 0; e < 4; ++e)
-          if (e == ke) D[c][e] = -D[c][e] + 2 * qkk;
-        bits ^= 1ull << (4 * c + ke);
-      }
-#pragma unroll
-      for (int e = 0; e < 4; ++e) {
-        const int m = ((bits >> (4 * c + e)) & 1ull) ? -d2 : d2;
-        D[c][e] += m * sbyte(q[c], e);
-        if (D[c][e] > bv) { bv = D[c][e]; bi = 4 * c + e; }
+      for (int o = 0; o < 16; ++o) {
+        const int e = c * 16 + o;
+        y[e] += d * sbyte(wv[o >> 2], o & 3);
+        kmax = max(kmax, Ck[e] + S[e] * y[e]);
       }
     }
-    key = red.max(make_key(bv, (bi >> 2) * 4 * G + 4 * g + (bi & 3),
-                           (int)((bits >> bi) & 1ull)));
+    best = reduce_key(kmax);
   }
   // ---- write back f, flips and x
   if (g == 0) {
     *f_s = fval;
     if (flips_s) *flips_s = flips;
   }
-  for (int w = g; w < W; w += G) xs[w] = 0;
-  red.sync();
+  for (int w = g; w < W; w += T) xs[w] = 0;
+  grp.sync();
 #pragma unroll
   for (int c = 0; c < C; ++c) {
-    const int j0 = c * 4 * G + 4 * g;
-    const uint64_t nib = (bits >> (4 * c)) & 0xFull;
-    if (nib) atomicOr(reinterpret_cast<unsigned long long*>(&xs[j0 >> 6]),
-                      (unsigned long long)(nib << (j0 & 63)));
+    const int j0 = c * CW + 16 * g;
+    uint64_t bits = 0;
+#pragma unroll
+    for (int o = 0; o < 16; ++o) bits |= (uint64_t)(Ck[c * 16 + o] & 1 & (S[c * 16 + o] != 0)) << o;
+    if (bits) atomicOr(reinterpret_cast<unsigned long long*>(&xs[j0 >> 6]),
+                       (unsigned long long)(bits << (j0 & 63)));
   }
-  red.sync();
-  for (int w = g; w < W; w += G) x_g[w] = xs[w];
-  red.sync();
+  grp.sync();
+  for (int w = g; w < W; w += T) x_g[w] = xs[w];
+  grp.sync();
 }
 
-template <int C>
-__global__ void __launch_bounds__(256)
+template <int T, int C>
+__global__ void __launch_bounds__(T, 1)
 ascent_block_kernel(const int8_t* __restrict__ Q8, int64_t ldq, int n, int W,
                     uint64_t* __restrict__ X, int64_t* __restrict__ f,
                     const int32_t* __restrict__ idx, const int64_t* __restrict__ count,
                     int64_t S, int32_t max_flips, int32_t* __restrict__ flips,
                     unsigned* __restrict__ err) {
-  __shared__ long long red_buf[2][8];
+  __shared__ int2 rec[2][T / 32];
   __shared__ uint64_t xs[UBQP_MAX_N / 64];
-  GroupReduce<256> red{red_buf, 0};
+  Group<T> grp{rec, 0};
   const int64_t cnt = *count;
   for (int64_t t = blockIdx.x; t < cnt; t += gridDim.x) {
     const int s = idx[t];
@@ -252,11 +252,12 @@ ascent_block_kernel(const int8_t* __restrict__ Q8, int64_t ldq, int n, int W,
       if (threadIdx.x == 0) atomicOr(err, UBQP_DEVERR_BADIDX);
       continue;
     }
-    ascend_one<256, C>(Q8, ldq, n, W, X + (int64_t)s * W, f + s, max_flips,
-                       flips ? flips + s : nullptr, err, xs, red, threadIdx.x);
+    ascend_one<T, C>(Q8, ldq, n, W, X + (int64_t)s * W, f + s, max_flips,
+                     flips ? flips + s : nullptr, err, xs, grp);
   }
 }
 
+// Four independent warps per block, one start each (n <= 512).
 template <int C>
 __global__ void __launch_bounds__(128)
 ascent_warp_kernel(const int8_t* __restrict__ Q8, int64_t ldq, int n, int W,
@@ -264,8 +265,8 @@ ascent_warp_kernel(const int8_t* __restrict__ Q8, int64_t ldq, int n, int W,
                    const int32_t* __restrict__ idx, const int64_t* __restrict__ count,
                    int64_t S, int32_t max_flips, int32_t* __restrict__ flips,
                    unsigned* __restrict__ err) {
-  __shared__ uint64_t xs_all[4][8];
-  GroupReduce<32> red;
+  __shared__ uint64_t xs_all[4][16];
+  Group<32> grp;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int64_t cnt = *count;
   for (int64_t t = (int64_t)blockIdx.x * 4 + warp; t < cnt; t += (int64_t)gridDim.x * 4) {
@@ -275,7 +276,7 @@ ascent_warp_kernel(const int8_t* __restrict__ Q8, int64_t ldq, int n, int W,
       continue;
     }
     ascend_one<32, C>(Q8, ldq, n, W, X + (int64_t)s * W, f + s, max_flips,
-                      flips ? flips + s : nullptr, err, xs_all[warp], red, lane);
+                      flips ? flips + s : nullptr, err, xs_all[warp], grp);
   }
 }
 
@@ -284,19 +285,21 @@ int resident_grid(K kernel, int threads, int sm_count) {
   int per_sm = 0;
   if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, threads, 0) !=
           cudaSuccess ||
-      per_sm < 1)
+      per_sm < 1) {
+    cudaGetLastError();
     per_sm = 1;
+  }
   return per_sm * sm_count;
 }
 
-template <int C>
+template <int T, int C>
 cudaError_t launch_block(const ubqp_q* h, uint64_t* X, int64_t* f, const int32_t* idx,
                          const int64_t* count, int64_t S, int32_t max_flips, int32_t* flips,
                          cudaStream_t st) {
-  int grid = resident_grid(ascent_block_kernel<C>, 256, h->sm_count);
+  int grid = resident_grid(ascent_block_kernel<T, C>, T, h->sm_count);
   if ((int64_t)grid > S) grid = (int)S;
-  ascent_block_kernel<C><<<grid, 256, 0, st>>>(h->Q8, h->ldq, h->n, h->W, X, f, idx, count,
-                                               S, max_flips, flips, h->err);
+  ascent_block_kernel<T, C><<<grid, T, 0, st>>>(h->Q8, h->ldq, h->n, h->W, X, f, idx, count,
+                                                S, max_flips, flips, h->err);
   return cudaGetLastError();
 }
 
@@ -305,7 +308,7 @@ cudaError_t launch_warp(const ubqp_q* h, uint64_t* X, int64_t* f, const int32_t*
                         const int64_t* count, int64_t S, int32_t max_flips, int32_t* flips,
                         cudaStream_t st) {
   int grid = resident_grid(ascent_warp_kernel<C>, 128, h->sm_count);
-  int64_t need = (S + 3) / 4;
+  const int64_t need = (S + 3) / 4;
   if ((int64_t)grid > need) grid = (int)need;
   ascent_warp_kernel<C><<<grid, 128, 0, st>>>(h->Q8, h->ldq, h->n, h->W, X, f, idx, count, S,
                                               max_flips, flips, h->err);
@@ -318,36 +321,14 @@ cudaError_t launch_ascent(const ubqp_q* h, uint64_t* X, int64_t* f, const int32_
                           const int64_t* count, int64_t S, int32_t max_flips, int32_t* flips,
                           cudaStream_t st) {
   const int n = h->n;
-  if (n <= 512) {
-    switch ((n + 127) / 128) {
-      case 1: return launch_warp<1>(h, X, f, idx, count, S, max_flips, flips, st);
-      case 2: return launch_warp<2>(h, X, f, idx, count, S, max_flips, flips, st);
-      case 3: return launch_warp<3>(h, X, f, idx, count, S, max_flips, flips, st);
-      default: return launch_warp<4>(h, X, f, idx, count, S, max_flips, flips, st);
-    }
-  }
-#define UBQP_BLOCK_CASE(CC) \
-  case CC: return launch_block<CC>(h, X, f, idx, count, S, max_flips, flips, st);
-  switch ((n + 1023) / 1024) {
-    UBQP_BLOCK_CASE(1)
-    UBQP_BLOCK_CASE(2)
-    UBQP_BLOCK_CASE(3)
-    UBQP_BLOCK_CASE(4)
-    UBQP_BLOCK_CASE(5)
-    UBQP_BLOCK_CASE(6)
-    UBQP_BLOCK_CASE(7)
-    UBQP_BLOCK_CASE(8)
-    UBQP_BLOCK_CASE(9)
-    UBQP_BLOCK_CASE(10)
-    UBQP_BLOCK_CASE(11)
-    UBQP_BLOCK_CASE(12)
-    UBQP_BLOCK_CASE(13)
-    UBQP_BLOCK_CASE(14)
-    UBQP_BLOCK_CASE(15)
-    UBQP_BLOCK_CASE(16)
-    default: return cudaErrorInvalidValue;
-  }
-#undef UBQP_BLOCK_CASE
+  if (n <= 256) return launch_warp<1>(h, X, f, idx, count, S, max_flips, flips, st);
+  if (n <= 512) return launch_warp<2>(h, X, f, idx, count, S, max_flips, flips, st);
+  if (n <= 1024) return launch_block<64, 1>(h, X, f, idx, count, S, max_flips, flips, st);
+  if (n <= 2048) return launch_block<128, 1>(h, X, f, idx, count, S, max_flips, flips, st);
+  if (n <= 4096) return launch_block<256, 1>(h, X, f, idx, count, S, max_flips, flips, st);
+  if (n <= 8192) return launch_block<256, 2>(h, X, f, idx, count, S, max_flips, flips, st);
+  if (n <= 16384) return launch_block<512, 2>(h, X, f, idx, count, S, max_flips, flips, st);
+  return cudaErrorInvalidValue;
 }
 
 }  // namespace ubqp

@@ -1,10 +1,465 @@
-// k_eval_tc.cu -- tensor-core evaluation (placeholder until the tcgen05 kernel lands).
+// k_eval_tc.cu -- Evaluate(x) of Fig. 2 as a tensor-core contraction.
+//
+// Problem (P) with Q symmetric gives f(x) = x^t Q x = sum_j x_j sum_{k<=j} Q'_jk x_k
+// with Q' = 2 tril(Q,-1) + diag(Q), so a batch needs only the lower block
+// triangle of D = X Q'^t (X: S x n starts, 0/1).  D is formed on the 5th-gen
+// tensor cores (tcgen05.mma kind::f16, bf16 operands, fp32 accumulation in
+// tensor memory) and never written out: an epilogue folds f_s += sum_j x_sj D_sj
+// in int64 and adds it to f with one atomic per row and work unit.
+//
+// Exactness: x is 0/1 and |Q'| <= 256, both exact in bf16; every product is an
+// exact integer and one work unit sums at most KCH*BK = 1024 of them, so every
+// fp32 partial is an integer below 2^18 < 2^24 and is exact.  Integer atomics
+// make the result independent of the order in which units finish.
+//
+// Kernel structure (one persistent CTA per SM, 6 warps):
+//   warp 0  one thread issues TMA loads of A = unpacked X (128 x 64 bf16) and
+//           B = Q' rows (256 x 64 bf16) into a 4-stage shared-memory ring;
+//   warp 1  allocates 512 TMEM columns (two 128 x 256 fp32 accumulators) and
+//           one thread issues the MMAs (M=128, N=256, K=16);
+//   warps 2-5  the epilogue: tcgen05.ld of the accumulator rows, int64 dot
+//           with the solution bits, atomicAdd into f.
+// A work unit is (m-tile of 128 starts, N-block J of 256 columns, a K chunk of
+// at most 16 steps of 64 inside [0, 256 (J+1))); units run largest first,
+// round-robin over the CTAs, with the two accumulators letting the epilogue of
+// one unit overlap the MMAs of the next.  Every wait is bounded: on timeout the
+// kernel records UBQP_DEVERR_TIMEOUT, drains its in-flight copies and MMAs,
+// frees its tensor memory and returns.
+#include <cuda.h>
+
+#include <algorithm>
+#include <vector>
+
 #include "ubqp_internal.cuh"
 
 namespace ubqp {
-size_t eval_tc_workspace(const ubqp_q*, int64_t) { return 0; }
-cudaError_t launch_eval_tc(const ubqp_q*, const uint64_t*, int64_t, int64_t*, void*, size_t,
-                           cudaStream_t) {
-  return cudaErrorNotSupported;
+namespace {
+
+constexpr int BM = 128, BN = 256, BK = 64;
+constexpr int STAGES = 4;
+constexpr int A_BYTES = BM * BK * 2;
+constexpr int B_BYTES = BN * BK * 2;
+constexpr int STAGE_BYTES = A_BYTES + B_BYTES;
+constexpr int KCH = 16;  // max K steps (of BK) per work unit
+constexpr int THREADS = 192;
+constexpr uint32_t TMEM_COLS = 512;
+constexpr int SMEM_BYTES = 1024 + STAGES * STAGE_BYTES + 256;
+constexpr uint64_t kWaitNs = 2000ull * 1000 * 1000;
+
+// Instruction descriptor, kind::f16: D fp32 (bits 4-5 = 1), A bf16 (7-9 = 1),
+// B bf16 (10-12 = 1), both K-major (15, 16 = 0), N/8 at 17-22, M/16 at 24-28.
+constexpr uint32_t IDESC = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(BN >> 3) << 17) |
+                           ((uint32_t)(BM >> 4) << 24);
+
+__device__ __forceinline__ uint32_t su32(const void* p) {
+  return (uint32_t)__cvta_generic_to_shared(p);
 }
+__device__ __forceinline__ uint64_t gtimer() {
+  uint64_t t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+__device__ __forceinline__ void mbar_init(uint64_t* b, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(su32(b)), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* b, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(su32(b)),
+               "r"(bytes)
+               : "memory");
+}
+__device__ __forceinline__ void mbar_arrive(uint64_t* b) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(su32(b)) : "memory");
+}
+__device__ __forceinline__ bool mbar_try(uint64_t* b, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+      " selp.u32 %0, 1, 0, p;\n}\n"
+      : "=r"(ok)
+      : "r"(su32(b)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+// Bounded wait; false when this CTA is aborting (timeout here or elsewhere).
+__device__ __noinline__ bool mbar_wait(uint64_t* b, uint32_t parity, volatile int* abort_flag,
+                                       unsigned* err) {
+  uint64_t t0 = 0;
+  for (uint32_t i = 0;; ++i) {
+    if (mbar_try(b, parity)) return true;
+    if ((i & 63) == 63) {
+      if (*abort_flag) return false;
+      const uint64_t t = gtimer();
+      if (t0 == 0) {
+        t0 = t;
+      } else if (t - t0 > kWaitNs) {
+        *abort_flag = 1;
+        atomicOr(err, UBQP_DEVERR_TIMEOUT);
+        return false;
+      }
+    }
+  }
+}
+// Bounded wait used while draining: ignores the abort flag.
+__device__ __noinline__ void mbar_drain(uint64_t* b, uint32_t parity) {
+  const uint64_t t0 = gtimer();
+  while (!mbar_try(b, parity)) {
+    if (gtimer() - t0 > kWaitNs) return;
+  }
+}
+
+__device__ __forceinline__ void tma_load_2d(void* dst, const CUtensorMap* map, int x, int y,
+                                            uint64_t* bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
+      " [%0], [%1, {%2, %3}], [%4];" ::"r"(su32(dst)),
+      "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(su32(bar))
+      : "memory");
+}
+
+__device__ __forceinline__ void tc_fence_before() {
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+}
+__device__ __forceinline__ void tc_fence_after() {
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+}
+
+// Shared-memory matrix descriptor: K-major, 128-byte swizzle, 8-row groups
+// 1024 bytes apart (SBO), LBO unused for this layout (encoded as 16 bytes),
+// descriptor version 1 (bit 46), swizzle mode 2 = 128B (bits 61-63).
+__device__ __forceinline__ uint64_t sdesc(uint32_t saddr) {
+  uint64_t d = 0;
+  d |= (uint64_t)((saddr & 0x3FFFFu) >> 4);
+  d |= (uint64_t)1 << 16;
+  d |= (uint64_t)(1024 >> 4) << 32;
+  d |= (uint64_t)1 << 46;
+  d |= (uint64_t)2 << 61;
+  return d;
+}
+
+__device__ __forceinline__ void mma_bf16(uint32_t tmem_d, uint64_t a, uint64_t b,
+                                         uint32_t accumulate) {
+  asm volatile(
+      "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+      " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem_d),
+      "l"(a), "l"(b), "r"(IDESC), "r"(accumulate)
+      : "memory");
+}
+__device__ __forceinline__ void mma_commit(uint64_t* bar) {
+  asm volatile(
+      "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+          su32(bar))
+      : "memory");
+}
+
+#define UBQP_R8(i) "=r"(r[i]), "=r"(r[i + 1]), "=r"(r[i + 2]), "=r"(r[i + 3]), \
+                   "=r"(r[i + 4]), "=r"(r[i + 5]), "=r"(r[i + 6]), "=r"(r[i + 7])
+__device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&r)[32]) {
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10,"
+      " %11, %12, %13, %14, %15, %16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27,"
+      " %28, %29, %30, %31}, [%32];"
+      : UBQP_R8(0), UBQP_R8(8), UBQP_R8(16), UBQP_R8(24)
+      : "r"(taddr));
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+}
+#undef UBQP_R8
+
+struct Unit {
+  int nb, k0, nk, mt;
+};
+__device__ __forceinline__ Unit unit_of(const int4* __restrict__ chunks, int m_tiles, int u) {
+  const int4 c = chunks[u / m_tiles];
+  return Unit{c.x, c.y, c.z, u % m_tiles};
+}
+
+__global__ void __launch_bounds__(THREADS, 1)
+eval_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
+               const uint64_t* __restrict__ X, int W, int64_t S, int m_tiles,
+               const int4* __restrict__ chunks, int n_chunks, int64_t* __restrict__ f,
+               unsigned* __restrict__ err) {
+  extern __shared__ uint8_t smem_raw[];
+  uint8_t* smem = smem_raw + ((1024 - (su32(smem_raw) & 1023)) & 1023);
+  uint64_t* full = reinterpret_cast<uint64_t*>(smem + STAGES * STAGE_BYTES);
+  uint64_t* empty = full + STAGES;
+  uint64_t* tfull = empty + STAGES;
+  uint64_t* tempty = tfull + 2;
+  uint64_t* drain = tempty + 2;
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(drain + 1);
+  volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
+
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int n_units = n_chunks * m_tiles;
+
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < STAGES; ++s) {
+      mbar_init(&full[s], 1);
+      mbar_init(&empty[s], 1);
+    }
+    for (int a = 0; a < 2; ++a) {
+      mbar_init(&tfull[a], 1);
+      mbar_init(&tempty[a], 128);
+    }
+    mbar_init(drain, 1);
+    *abort_flag = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (warp == 1) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                     su32(tmem_slot)),
+                 "r"(TMEM_COLS)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = *tmem_slot;
+
+  if (warp == 0) {
+    if (lane == 0) {
+      // ---------------- TMA producer
+      asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&tmA)) : "memory");
+      asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&tmB)) : "memory");
+      int pending[STAGES];
+      for (int s = 0; s < STAGES; ++s) pending[s] = -1;
+      int stage = 0;
+      uint32_t phase = 0;
+      bool ok = true;
+      for (int u = blockIdx.x; u < n_units && ok; u += gridDim.x) {
+        const Unit un = unit_of(chunks, m_tiles, u);
+        for (int ks = 0; ks < un.nk; ++ks) {
+          if (!mbar_wait(&empty[stage], phase ^ 1u, abort_flag, err)) {
+            ok = false;
+            break;
+          }
+          uint8_t* sa = smem + stage * STAGE_BYTES;
+          mbar_expect_tx(&full[stage], STAGE_BYTES);
+          const int kx = (un.k0 + ks) * BK;
+          tma_load_2d(sa, &tmA, kx, un.mt * BM, &full[stage]);
+          tma_load_2d(sa + A_BYTES, &tmB, kx, un.nb * BN, &full[stage]);
+          pending[stage] = (int)phase;
+          if (++stage == STAGES) {
+            stage = 0;
+            phase ^= 1u;
+          }
+        }
+      }
+      if (!ok) {  // let every issued copy land before the CTA exits
+        for (int s = 0; s < STAGES; ++s)
+          if (pending[s] >= 0) mbar_drain(&full[s], (uint32_t)pending[s]);
+      }
+    }
+  } else if (warp == 1) {
+    if (lane == 0) {
+      // ---------------- MMA issuer
+      int stage = 0;
+      uint32_t phase = 0;
+      bool ok = true;
+      int t = 0;
+      for (int u = blockIdx.x; u < n_units && ok; u += gridDim.x, ++t) {
+        const Unit un = unit_of(chunks, m_tiles, u);
+        const int a = t & 1;
+        const uint32_t aphase = (uint32_t)((t >> 1) & 1);
+        if (!mbar_wait(&tempty[a], aphase ^ 1u, abort_flag, err)) {
+          ok = false;
+          break;
+        }
+        tc_fence_after();
+        const uint32_t d = tmem + (uint32_t)(a * BN);
+        for (int ks = 0; ks < un.nk; ++ks) {
+          if (!mbar_wait(&full[stage], phase, abort_flag, err)) {
+            ok = false;
+            break;
+          }
+          tc_fence_after();
+          const uint32_t sa = su32(smem + stage * STAGE_BYTES);
+          const uint64_t adesc = sdesc(sa), bdesc = sdesc(sa + A_BYTES);
+#pragma unroll
+          for (int kk = 0; kk < BK / 16; ++kk)
+            mma_bf16(d, adesc + (uint64_t)(2 * kk), bdesc + (uint64_t)(2 * kk),
+                     (ks | kk) != 0 ? 1u : 0u);
+          mma_commit(&empty[stage]);
+          if (++stage == STAGES) {
+            stage = 0;
+            phase ^= 1u;
+          }
+        }
+        if (ok) mma_commit(&tfull[a]);
+      }
+      if (!ok) {  // wait for the MMAs already issued before TMEM is freed
+        mma_commit(drain);
+        mbar_drain(drain, 0);
+      }
+    }
+  } else {
+    // ---------------- epilogue: warps 2..5 cover TMEM lanes 64-95, 96-127, 0-31, 32-63
+    const int q = warp & 3;
+    const int row = q * 32 + lane;
+    int t = 0;
+    for (int u = blockIdx.x; u < n_units; u += gridDim.x, ++t) {
+      const Unit un = unit_of(chunks, m_tiles, u);
+      const int a = t & 1;
+      const uint32_t aphase = (uint32_t)((t >> 1) & 1);
+      if (!mbar_wait(&tfull[a], aphase, abort_flag, err)) break;
+      tc_fence_after();
+      const int64_t s = (int64_t)un.mt * BM + row;
+      uint64_t xw[4];
+#pragma unroll
+      for (int i = 0; i < 4; ++i) {
+        const int w = un.nb * 4 + i;
+        xw[i] = (s < S && w < W) ? X[s * W + w] : 0ull;
+      }
+      int acc = 0;
+      const uint32_t base = tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(a * BN);
+#pragma unroll 1
+      for (int cc = 0; cc < BN / 32; ++cc) {
+        uint32_t r[32];
+        tmem_ld32(base + (uint32_t)(cc * 32), r);
+        const uint32_t bits = (uint32_t)(xw[cc >> 1] >> ((cc & 1) * 32));
+#pragma unroll
+        for (int i = 0; i < 32; ++i)
+          if ((bits >> i) & 1u) acc += __float2int_rn(__uint_as_float(r[i]));
+      }
+      tc_fence_before();
+      mbar_arrive(&tempty[a]);
+      if (s < S && acc != 0)
+        atomicAdd(reinterpret_cast<unsigned long long*>(&f[s]),
+                  (unsigned long long)(long long)acc);
+    }
+  }
+  __syncthreads();
+  if (warp == 1) {
+    tc_fence_after();
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem),
+                 "r"(TMEM_COLS)
+                 : "memory");
+  }
+}
+
+// Unpack bit-packed solutions into the bf16 A operand: S_p x n_tc, 0.0 / 1.0,
+// zero rows beyond S and zero columns beyond n.
+__global__ void unpack_bits_bf16(const uint64_t* __restrict__ X, int n, int W, int64_t S,
+                                 int64_t S_p, int n_tc, uint4* __restrict__ Xe) {
+  const int64_t per_row = n_tc / 8;
+  const int64_t total = S_p * per_row;
+  for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < total;
+       t += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t s = t / per_row;
+    const int c = (int)(t - s * per_row);
+    const int w = c >> 3;
+    uint32_t byte = 0;
+    if (s < S && w < W) byte = (uint32_t)(((X[s * W + w] & valid_mask(n, w)) >> ((c & 7) * 8)) & 0xFFu);
+    uint32_t v[4];
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+      const uint32_t lo = ((byte >> (2 * i)) & 1u) ? 0x3F80u : 0u;
+      const uint32_t hi = ((byte >> (2 * i + 1)) & 1u) ? 0x3F80u : 0u;
+      v[i] = lo | (hi << 16);
+    }
+    Xe[t] = make_uint4(v[0], v[1], v[2], v[3]);
+  }
+}
+
+using EncodeFn = CUresult (*)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*,
+                              const cuuint64_t*, const cuuint64_t*, const cuuint32_t*,
+                              const cuuint32_t*, CUtensorMapInterleave, CUtensorMapSwizzle,
+                              CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+EncodeFn encode_fn() {
+  static EncodeFn fn = nullptr;
+  static bool tried = false;
+  if (!tried) {
+    tried = true;
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000,
+                                         cudaEnableDefault, &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = reinterpret_cast<EncodeFn>(p);
+    else
+      cudaGetLastError();
+  }
+  return fn;
+}
+
+// 2-D bf16 row-major tensor [rows][cols], box = box_rows x 64 columns, 128B swizzle.
+bool make_map(CUtensorMap* m, const void* base, int64_t rows, int64_t cols, int box_rows) {
+  EncodeFn fn = encode_fn();
+  if (!fn) return false;
+  cuuint64_t dims[2] = {(cuuint64_t)cols, (cuuint64_t)rows};
+  cuuint64_t strides[1] = {(cuuint64_t)cols * 2};
+  cuuint32_t box[2] = {(cuuint32_t)BK, (cuuint32_t)box_rows};
+  cuuint32_t estr[2] = {1, 1};
+  return fn(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<void*>(base), dims, strides, box,
+            estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+            CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) ==
+         CUDA_SUCCESS;
+}
+
+int64_t padded_starts(int64_t S) { return (S + BM - 1) / BM * BM; }
+
+}  // namespace
+
+size_t eval_tc_workspace(const ubqp_q* h, int64_t S) {
+  return (size_t)padded_starts(S) * (size_t)h->n_tc * 2;
+}
+
+// Work chunks of the lower block triangle: for N-block J the K range is
+// [0, 256 (J+1)), split into near-equal chunks of at most KCH steps; sorted
+// largest first.  Stored in the handle as int4 {J, first K step, K steps, 0}.
+cudaError_t eval_tc_prepare(ubqp_q* h) {
+  const int NB = h->n_tc / BN;
+  std::vector<int4> ch;
+  for (int J = 0; J < NB; ++J) {
+    const int nk = (J + 1) * (BN / BK);
+    const int parts = (nk + KCH - 1) / KCH;
+    for (int p = 0, k0 = 0; p < parts; ++p) {
+      const int len = nk / parts + (p < nk % parts ? 1 : 0);
+      ch.push_back(make_int4(J, k0, len, 0));
+      k0 += len;
+    }
+  }
+  std::stable_sort(ch.begin(), ch.end(), [](const int4& a, const int4& b) { return a.z > b.z; });
+  h->tc_nchunks = (int)ch.size();
+  cudaError_t e = cudaMalloc(&h->tc_chunks, sizeof(int4) * ch.size());
+  if (e) return e;
+  e = cudaMemcpy(h->tc_chunks, ch.data(), sizeof(int4) * ch.size(), cudaMemcpyHostToDevice);
+  if (e) return e;
+  h->tc_ok = make_map(reinterpret_cast<CUtensorMap*>(h->tc_mapB), h->Qt, h->n_tc, h->n_tc, BN);
+  return cudaSuccess;
+}
+
+cudaError_t launch_eval_tc(const ubqp_q* h, const uint64_t* X, int64_t S, int64_t* f, void* ws,
+                           size_t ws_bytes, cudaStream_t st) {
+  if (!h->tc_ok) return cudaErrorNotSupported;
+  const int64_t S_p = padded_starts(S);
+  if (ws_bytes < eval_tc_workspace(h, S)) return cudaErrorInvalidValue;
+  cudaError_t e;
+  {
+    const int64_t total = S_p * (h->n_tc / 8);
+    int64_t blocks = (total + 255) / 256;
+    if (blocks > (int64_t)h->sm_count * 8) blocks = (int64_t)h->sm_count * 8;
+    unpack_bits_bf16<<<(unsigned)blocks, 256, 0, st>>>(X, h->n, h->W, S, S_p, h->n_tc,
+                                                      reinterpret_cast<uint4*>(ws));
+    if ((e = cudaGetLastError())) return e;
+  }
+  alignas(64) CUtensorMap mapA;
+  if (!make_map(&mapA, ws, S_p, h->n_tc, BM)) return cudaErrorInvalidValue;
+  if ((e = cudaMemsetAsync(f, 0, sizeof(int64_t) * S, st))) return e;
+  static bool attr = false;
+  if (!attr) {
+    if ((e = cudaFuncSetAttribute(eval_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  SMEM_BYTES)))
+      return e;
+    attr = true;
+  }
+  const int m_tiles = (int)(S_p / BM);
+  const int n_units = h->tc_nchunks * m_tiles;
+  const int grid = n_units < h->sm_count ? n_units : h->sm_count;
+  eval_tc_kernel<<<grid, THREADS, SMEM_BYTES, st>>>(
+      mapA, *reinterpret_cast<const CUtensorMap*>(h->tc_mapB), X, h->W, S, m_tiles,
+      reinterpret_cast<const int4*>(h->tc_chunks), h->tc_nchunks, f, h->err);
+  return cudaGetLastError();
+}
+
 }  // namespace ubqp

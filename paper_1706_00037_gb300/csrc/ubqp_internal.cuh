@@ -30,6 +30,12 @@ struct ubqp_q {
   int64_t device_bytes;
   int sm_count;
   int device;
+  // tensor-core evaluation: work chunks of the lower block triangle (int4
+  // {N-block, first K step, K steps, 0}) and the TMA descriptor of Qt
+  void* tc_chunks;
+  int tc_nchunks;
+  bool tc_ok;
+  alignas(64) unsigned char tc_mapB[128];
 };
 
 namespace ubqp {
@@ -66,6 +72,7 @@ cudaError_t launch_diversify(const uint64_t* x0, int n, int mode, uint64_t seed,
 cudaError_t launch_eval_plain(const ubqp_q* h, const uint64_t* X, int64_t S,
                               int64_t* f, cudaStream_t st);
 size_t eval_tc_workspace(const ubqp_q* h, int64_t S);
+cudaError_t eval_tc_prepare(ubqp_q* h);
 cudaError_t launch_eval_tc(const ubqp_q* h, const uint64_t* X, int64_t S, int64_t* f,
                            void* ws, size_t ws_bytes, cudaStream_t st);
 cudaError_t launch_screen(const int64_t* f, int64_t S, double lambda, int32_t* idx,

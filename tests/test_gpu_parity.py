@@ -94,14 +94,68 @@ def test_eval_plain_matches_oracle(n):
     assert np.array_equal(f.cpu().numpy(), orc.eval(Q, X))
 
 
+@pytest.mark.parametrize("n", NS)
+@pytest.mark.parametrize("S", [1, 37, 129, 300])
+def test_eval_tc_matches_oracle(n, S):
+    Q, inst = instance(n, 0.6, n + 200)
+    X = synth.random_solutions(n, S, n + S)
+    f = ubqp.eval(inst, words_dev(X), path=ubqp.EVAL_TC)
+    inst.sync()
+    assert np.array_equal(f.cpu().numpy(), orc.eval(Q, X))
+
+
+def test_eval_tc_extreme_coefficients_exact():
+    # |Q| at the int8 limits and dense 0/1 patterns: every fp32 partial stays an
+    # exact integer only if the chunked accumulation is right
+    n = 1500
+    Q = np.full((n, n), -128, np.int8)
+    np.fill_diagonal(Q, 127)
+    Q[:700, :700] = 127
+    inst = ubqp.Instance(dev(Q))
+    X = np.concatenate([synth.random_solutions(n, 60, 5), synth.random_solutions(n, 60, 6, 0.95),
+                        synth.pack_bits(np.ones((4, n), np.uint8)),
+                        np.zeros((1, synth.words(n)), np.uint64)])
+    f = ubqp.eval(inst, words_dev(X), path=ubqp.EVAL_TC)
+    inst.sync()
+    assert np.array_equal(f.cpu().numpy(), orc.eval(Q, X))
+
+
+@pytest.mark.parametrize("n,S", [(2500, 1000), (5000, 1000)])
+def test_eval_tc_equals_plain_at_table1_sizes(n, S):
+    Q, inst = instance(n, 1.0, n)
+    X = ubqp.diversify(inst, S, mode=ubqp.RANDOM, seed=n + 1)
+    ft = ubqp.eval(inst, X, path=ubqp.EVAL_TC)
+    fp = ubqp.eval(inst, X, path=ubqp.EVAL_PLAIN)
+    inst.sync()
+    assert torch.equal(ft, fp)
+    # sampled starts against the oracle (its inputs regenerated on the CPU)
+    Xh = orc.diversify(None, n, orc.RANDOM, n + 1, 0, S)
+    pick = np.array([0, 1, S // 2, S - 1])
+    assert np.array_equal(ft.cpu().numpy()[pick], orc.eval(Q, Xh[pick]))
+
+
+def test_eval_tc_workspace_errors():
+    n, S = 300, 50
+    Q, inst = instance(n, 0.5, 1)
+    X = words_dev(synth.random_solutions(n, S, 1))
+    need = ubqp.eval_workspace_size(inst, S, ubqp.EVAL_TC)
+    assert need == 128 * 512 * 2
+    small = torch.empty(need - 16, dtype=torch.uint8, device="cuda")
+    with pytest.raises(ubqp.UbqpError) as e:
+        ubqp.eval(inst, X, path=ubqp.EVAL_TC, ws=small)
+    assert e.value.status == -4
+    assert ubqp.eval_workspace_size(inst, S, ubqp.EVAL_PLAIN) == 0
+
+
 def test_eval_ignores_pad_bits():
     n = 70
     Q, inst = instance(n, 1.0, 2)
     X = synth.random_solutions(n, 9, 2)
     Xd = X.copy()
     Xd[:, -1] |= np.uint64(0xFFFF) << np.uint64(48)  # set bits >= n
-    f = ubqp.eval(inst, words_dev(Xd), path=ubqp.EVAL_PLAIN)
-    assert np.array_equal(f.cpu().numpy(), orc.eval(Q, X))
+    for path in (ubqp.EVAL_PLAIN, ubqp.EVAL_TC):
+        f = ubqp.eval(inst, words_dev(Xd), path=path)
+        assert np.array_equal(f.cpu().numpy(), orc.eval(Q, X))
 
 
 def test_eval_extreme_coefficients():
@@ -232,12 +286,13 @@ def test_best_matches_oracle():
     assert np.array_equal(words_host(bx), X[1])
 
 
+@pytest.mark.parametrize("path", [ubqp.EVAL_TC, ubqp.EVAL_PLAIN])
 @pytest.mark.parametrize("mode", [orc.DIVERSIFY, orc.RANDOM])
-def test_solve_small_instance_matches_oracle(mode):
+def test_solve_small_instance_matches_oracle(mode, path):
     # n = 100, density 0.1 (diagonal included), seed 0; 1000 starts, lambda 0.5
     n, S, lam = 100, 1000, 0.5
     Q, inst = instance(n, 0.1, 0)
-    p = ubqp.make_params(S, lam, mode=mode, seed=0, eval_path=ubqp.EVAL_PLAIN)
+    p = ubqp.make_params(S, lam, mode=mode, seed=0, eval_path=path)
     bx, bf, st = ubqp.solve(inst, p)
     want = orc.solve(Q, S, lam, seed=0, mode=mode)
     assert int(bf[0].item()) == want["best_f"] and int(bf[1].item()) == want["best_index"]
@@ -257,7 +312,7 @@ def test_solve_pipeline_steps_match_oracle(lam):
     sc = orc.screen(fv, lam)
     Xw, fw, _ = orc.ascent(Q, X, fv, sc["idx"])
     bw = orc.best(fw)
-    p = ubqp.make_params(S, lam, seed=3, eval_path=ubqp.EVAL_PLAIN)
+    p = ubqp.make_params(S, lam, seed=3)
     bx, bf, st = ubqp.solve(inst, p)
     assert st["passed"] == sc["count"] and st["T"] == sc["T"]
     assert (int(bf[0].item()), int(bf[1].item())) == bw
