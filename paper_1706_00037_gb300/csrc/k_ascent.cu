@@ -13,8 +13,9 @@
 // thread.  Per element the thread keeps, in registers,
 //     y_j,   S_j = 128 (1 - 2 x_j),   C_j = 64 Q_jj + 2 (31 - e) + x_j,
 // so that the argmax key  key_j = C_j + S_j y_j = 64 Delta_j + 2 (31 - e) + x_j
-// costs one multiply-add.  A move is therefore, per element: extract the
-// coefficient, y += d q, key = C + S y, running max -- four instructions.  The
+// costs one multiply-add.  A move is therefore, per element: y += d q as one
+// dp4a (d placed in the coefficient's byte lane), key = C + S y, running max --
+// three instructions.  The
 // key orders by gain, then by lower index inside the thread, and carries x_j in
 // its low bit; across threads the group reduces (gain, 2j + x) with warp
 // max/min reductions (redux.sync), so every thread learns k, x_k and Delta_k.
@@ -36,9 +37,10 @@ __device__ __forceinline__ uint64_t globaltimer() {
   return t;
 }
 
-// Sign-extended byte i of w (PRMT with the sign-replicate selector).
-__device__ __forceinline__ int sbyte(uint32_t w, int i) {
-  return (int)__byte_perm(w, 0u, (unsigned)(i | ((8 | i) << 4) | ((8 | i) << 8) | ((8 | i) << 12)));
+// acc + d * (signed byte i of w), for d in {-1, +1}, in one dp4a: the second
+// operand holds d in byte i and zeros elsewhere.
+__device__ __forceinline__ int byte_sel(int i, int d) {
+  return (int)((unsigned)(d & 0xFF) << (8 * i));
 }
 
 template <int T>
@@ -148,9 +150,10 @@ __device__ __forceinline__ void ascend_one(const int8_t* __restrict__ Q8, int64_
       for (int r = 0; r < R; ++r)
 #pragma unroll
         for (int c = 0; c < C; ++c) {
-          const uint32_t wv[4] = {q[r][c].x, q[r][c].y, q[r][c].z, q[r][c].w};
+          const int wv[4] = {(int)q[r][c].x, (int)q[r][c].y, (int)q[r][c].z, (int)q[r][c].w};
 #pragma unroll
-          for (int o = 0; o < 16; ++o) y[c * 16 + o] += sbyte(wv[o >> 2], o & 3);
+          for (int o = 0; o < 16; ++o)
+            y[c * 16 + o] = __dp4a(wv[o >> 2], byte_sel(o & 3, 1), y[c * 16 + o]);
         }
     }
   }
@@ -181,6 +184,7 @@ __device__ __forceinline__ void ascend_one(const int8_t* __restrict__ Q8, int64_
     }
     const int k = best.y >> 1;
     const int d = (best.y & 1) ? -1 : 1;  // 1 - 2 x_k before the flip
+    const int dsel[4] = {byte_sel(0, d), byte_sel(1, d), byte_sel(2, d), byte_sel(3, d)};
     fval += best.x;
     ++flips;
     const int8_t* row = Q8 + (int64_t)k * ldq;
@@ -204,11 +208,11 @@ __device__ __forceinline__ void ascend_one(const int8_t* __restrict__ Q8, int64_
     kmax = INT_MIN;
 #pragma unroll
     for (int c = 0; c < C; ++c) {
-      const uint32_t wv[4] = {q[c].x, q[c].y, q[c].z, q[c].w};
+      const int wv[4] = {(int)q[c].x, (int)q[c].y, (int)q[c].z, (int)q[c].w};
 #pragma unroll
       for (int o = 0; o < 16; ++o) {
         const int e = c * 16 + o;
-        y[e] += d * sbyte(wv[o >> 2], o & 3);
+        y[e] = __dp4a(wv[o >> 2], dsel[o & 3], y[e]);
         kmax = max(kmax, Ck[e] + S[e] * y[e]);
       }
     }
