@@ -146,6 +146,31 @@ int ubqp_eval(const ubqp_q* q, const uint64_t* X_dev, int64_t S, int64_t* f_dev,
               int32_t path, void* ws, size_t ws_bytes, void* stream);
 
 /*
+ * ubqp_eval_noalloc -- the tensor-core evaluation of ubqp_eval (same results,
+ * bit for bit) for callers that cannot allocate device memory or hand the
+ * library a workspace: for example a host whose device memory is entirely
+ * reserved by another allocator (a framework's caching pool, an application
+ * with a fixed memory budget), or a latency-critical loop that must not run
+ * cudaMalloc/cudaFree, which can synchronise the whole device.  The paper has
+ * no counterpart; this is an interface convenience only.
+ *   The scratch for the unpacked solutions is a static device array of
+ *   UBQP_EVAL_NOALLOC_MAX_BYTES built into the library, present on every GPU
+ *   that loads the library until the process exits.  A call needs
+ *   ceil(S/128)*128 * n_tc * 2 bytes of it (n_tc = n rounded up to 256); larger
+ *   requests return UBQP_ERR_UNSUPPORTED (e.g. 1000 starts fit up to n = 8192).
+ *   The call allocates nothing and calls no cudaMalloc/cudaFree.  The first
+ *   call on a device looks up the array's device address
+ *   (cudaGetSymbolAddress) with that device current; make that first call
+ *   before any stream capture.  All calls share the one array and it keeps the
+ *   last call's contents (each call overwrites the part it uses): calls whose
+ *   work overlaps on the GPU -- concurrent streams, or several host threads --
+ *   race on it and must be serialised by the caller.  Async on `stream`.
+ */
+#define UBQP_EVAL_NOALLOC_MAX_BYTES (16u << 20)
+int ubqp_eval_noalloc(const ubqp_q* q, const uint64_t* X_dev, int64_t S,
+                      int64_t* f_dev, void* stream);
+
+/*
  * ubqp_screen -- the screening function of the Pseudocode section,
  * T(lambda) = Mean + lambda (Max - Mean), Mean and Max over the S values f_dev,
  * and the pass test f_b > T of Fig. 2 (strict).  Async.

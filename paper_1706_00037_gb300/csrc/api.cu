@@ -236,6 +236,31 @@ int ubqp_eval(const ubqp_q* q, const uint64_t* X_dev, int64_t S, int64_t* f_dev,
   return UBQP_OK;
 }
 
+int ubqp_eval_noalloc(const ubqp_q* q, const uint64_t* X_dev, int64_t S, int64_t* f_dev,
+                      void* stream) {
+  if (!q || !X_dev || !f_dev) return fail(UBQP_ERR_ARG, "NULL argument");
+  if (S < 0) return fail(UBQP_ERR_ARG, "S < 0");
+  if (S == 0) return UBQP_OK;
+  if ((int64_t)2 * q->max_abs * q->n_tc >= (1 << 24))
+    return fail(UBQP_ERR_RANGE, "2*max|Q|*n_pad = %lld >= 2^24",
+                (long long)2 * q->max_abs * q->n_tc);
+  const size_t need = ubqp::eval_tc_workspace(q, S);
+  if (need > ubqp::eval_tc_static_capacity())
+    return fail(UBQP_ERR_UNSUPPORTED,
+                "ubqp_eval_noalloc: %lld starts at n=%d need %zu bytes of scratch, more than "
+                "the built-in %zu; use ubqp_eval with a workspace",
+                (long long)S, q->n, need, ubqp::eval_tc_static_capacity());
+  void* scratch = nullptr;
+  cudaError_t e = ubqp::eval_tc_static_scratch(&scratch);
+  if (e != cudaSuccess) return cuda_fail(e, "cudaGetSymbolAddress(eval scratch)");
+  e = ubqp::launch_eval_tc(q, X_dev, S, f_dev, scratch, ubqp::eval_tc_static_capacity(),
+                           (cudaStream_t)stream);
+  if (e == cudaErrorNotSupported)
+    return fail(UBQP_ERR_UNSUPPORTED, "tensor-core evaluation not available for this size");
+  if (e != cudaSuccess) return cuda_fail(e, "eval_tc (static scratch)");
+  return UBQP_OK;
+}
+
 int ubqp_screen(const int64_t* f_dev, int64_t S, double lambda, int32_t* idx_dev,
                 int64_t* count_dev, double* Tm_dev, int64_t* stats_dev, void* stream) {
   if (!f_dev || !idx_dev || !count_dev || !Tm_dev || !stats_dev)

@@ -28,6 +28,7 @@
 #include <cuda.h>
 
 #include <algorithm>
+#include <mutex>
 #include <vector>
 
 #include "ubqp_internal.cuh"
@@ -398,7 +399,37 @@ bool make_map(CUtensorMap* m, const void* base, int64_t rows, int64_t cols, int 
 
 int64_t padded_starts(int64_t S) { return (S + BM - 1) / BM * BM; }
 
+// Scratch of the allocation-free evaluation (ubqp_eval_noalloc): the unpacked
+// solutions live in this file-scope device array instead of caller workspace.
+// Every GPU that loads the library holds it until the process exits.
+static __device__ __align__(256) uint8_t g_eval_scratch[UBQP_EVAL_NOALLOC_MAX_BYTES];
+
+constexpr int kMaxDevices = 64;
+std::mutex g_scratch_mu;
+void* g_scratch_addr[kMaxDevices];  // device address of g_eval_scratch, per device
+
 }  // namespace
+
+size_t eval_tc_static_capacity() { return (size_t)UBQP_EVAL_NOALLOC_MAX_BYTES; }
+
+// Device address of the static scratch on the current device.  The host-side
+// name g_eval_scratch is only a stand-in; the real address comes from
+// cudaGetSymbolAddress, looked up once per device with that device current.
+cudaError_t eval_tc_static_scratch(void** out) {
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e) return e;
+  if (dev < 0 || dev >= kMaxDevices) return cudaErrorInvalidDevice;
+  std::lock_guard<std::mutex> lock(g_scratch_mu);
+  if (!g_scratch_addr[dev]) {
+    void* p = nullptr;
+    e = cudaGetSymbolAddress(&p, g_eval_scratch);
+    if (e) return e;
+    g_scratch_addr[dev] = p;
+  }
+  *out = g_scratch_addr[dev];
+  return cudaSuccess;
+}
 
 size_t eval_tc_workspace(const ubqp_q* h, int64_t S) {
   return (size_t)padded_starts(S) * (size_t)h->n_tc * 2;

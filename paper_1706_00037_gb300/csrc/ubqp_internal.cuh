@@ -73,6 +73,8 @@ cudaError_t launch_eval_plain(const ubqp_q* h, const uint64_t* X, int64_t S,
                               int64_t* f, cudaStream_t st);
 size_t eval_tc_workspace(const ubqp_q* h, int64_t S);
 cudaError_t eval_tc_prepare(ubqp_q* h);
+size_t eval_tc_static_capacity();
+cudaError_t eval_tc_static_scratch(void** out);
 cudaError_t launch_eval_tc(const ubqp_q* h, const uint64_t* X, int64_t S, int64_t* f,
                            void* ws, size_t ws_bytes, cudaStream_t st);
 cudaError_t launch_screen(const int64_t* f, int64_t S, double lambda, int32_t* idx,

@@ -25,7 +25,8 @@ STATUS_NAMES = {0: "OK", -1: "ERR_ARG", -2: "ERR_NOT_SYMMETRIC", -3: "ERR_RANGE"
 
 EXPORTS = ["ubqp_strerror", "ubqp_last_error", "ubqp_abi_version", "ubqp_q_prepare",
            "ubqp_q_destroy", "ubqp_q_info", "ubqp_sync", "ubqp_first_derivative",
-           "ubqp_diversify", "ubqp_eval_workspace_size", "ubqp_eval", "ubqp_screen",
+           "ubqp_diversify", "ubqp_eval_workspace_size", "ubqp_eval", "ubqp_eval_noalloc",
+           "ubqp_screen",
            "ubqp_ascent", "ubqp_best", "ubqp_solve_workspace_size", "ubqp_solve"]
 
 
@@ -82,6 +83,7 @@ def load() -> ctypes.CDLL:
         "ubqp_diversify": (ctypes.c_int, [P, P, i32, u64, u64, i64, i32, P, P]),
         "ubqp_eval_workspace_size": (sz, [P, i64, i32]),
         "ubqp_eval": (ctypes.c_int, [P, P, i64, P, i32, P, sz, P]),
+        "ubqp_eval_noalloc": (ctypes.c_int, [P, P, i64, P, P]),
         "ubqp_screen": (ctypes.c_int, [P, i64, f64, P, P, P, P, P]),
         "ubqp_ascent": (ctypes.c_int, [P, P, P, P, P, i64, i32, P, P]),
         "ubqp_best": (ctypes.c_int, [P, P, i64, i32, P, P, P]),
@@ -190,6 +192,16 @@ def eval(inst: Instance, X: torch.Tensor, path: int = EVAL_AUTO, out: torch.Tens
     nbytes = ws.numel() * ws.element_size() if ws is not None else 0
     _check(load().ubqp_eval(inst.handle, _ptr(X), S, _ptr(f), path, _ptr(ws), nbytes,
                             _stream(stream)))
+    return f
+
+
+def eval_noalloc(inst: Instance, X: torch.Tensor, out: torch.Tensor | None = None,
+                 stream=None) -> torch.Tensor:
+    """Tensor-core evaluation with the library's built-in static scratch
+    (no workspace, no device allocation inside the library)."""
+    S = X.shape[0]
+    f = out if out is not None else torch.empty(S, dtype=torch.int64, device=inst.device)
+    _check(load().ubqp_eval_noalloc(inst.handle, _ptr(X), S, _ptr(f), _stream(stream)))
     return f
 
 
