@@ -37,10 +37,6 @@ __device__ __forceinline__ uint64_t globaltimer() {
   return t;
 }
 
-__device__ __forceinline__ void prefetch_l1(const void* p) {
-  asm volatile("prefetch.global.L1 [%0];" ::"l"(p));
-}
-
 // acc + d * (signed byte i of w), for d in {-1, +1}, in one dp4a: the second
 // operand holds d in byte i and zeros elsewhere.
 __device__ __forceinline__ int byte_sel(int i, int d) {
@@ -70,23 +66,11 @@ struct Group {
   static constexpr int NW = T / 32;
   int2 (*rec)[NW];  // [2][NW] shared
   int parity;
-  // row-prefetch context: the int8 rows of Q (stride ldq) and n
-  const int8_t* Q8;
-  int64_t ldq;
-  int n;
   __device__ __forceinline__ int rank() const { return threadIdx.x; }
   __device__ __forceinline__ int2 reduce(int gain, int jx) {
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int m = __reduce_max_sync(0xffffffffu, gain);
     const int c = __reduce_min_sync(0xffffffffu, gain == m ? jx : INT_MAX);
-    // The group's winner is one of the warps' candidates: start pulling this
-    // warp's candidate row into L1 now.  A candidate usually stays its warp's
-    // best for several moves before it wins, so its row is often resident by
-    // the time it is needed.
-    if (m > 0 && (c >> 1) < n) {
-      const int8_t* row = Q8 + (int64_t)(c >> 1) * ldq;
-      for (int64_t off = (int64_t)lane * 128; off < ldq; off += 32 * 128) prefetch_l1(row + off);
-    }
     if (lane == 0) rec[parity][warp] = make_int2(m, c);
     __syncthreads();
     const int2 r = lane < NW ? rec[parity][lane] : make_int2(INT_MIN, INT_MAX);
@@ -136,23 +120,7 @@ __device__ __forceinline__ void ascend_one(const int8_t* __restrict__ Q8, int64_
       }
     }
   }
-  // ---- y = Q x on the owned columns: add the rows k with x_k = 1, with a
-  // second cursor PF rows ahead prefetching this thread's chunks into L1
-  constexpr int PF = 16;
-  int pw = 0;
-  uint64_t pword = W > 0 ? (x_g[0] & valid_mask(n, 0)) : 0ull;
-  auto prefetch_next = [&]() {
-    while (!pword && ++pw < W) pword = x_g[pw] & valid_mask(n, pw);
-    if (!pword) return;
-    const int k = pw * 64 + __ffsll((long long)pword) - 1;
-    pword &= pword - 1;
-#pragma unroll
-    for (int c = 0; c < C; ++c) {
-      const int j0 = c * CW + 16 * g;
-      if (j0 < ldq) prefetch_l1(Q8 + (int64_t)k * ldq + j0);
-    }
-  };
-  for (int i = 0; i < PF; ++i) prefetch_next();
+  // ---- y = Q x on the owned columns: add the rows k with x_k = 1
   for (int w = 0; w < W; ++w) {
     uint64_t word = x_g[w] & valid_mask(n, w);
     while (word) {
@@ -168,8 +136,6 @@ __device__ __forceinline__ void ascend_one(const int8_t* __restrict__ Q8, int64_
           nk = r + 1;
         }
       }
-#pragma unroll
-      for (int r = 0; r < R; ++r) prefetch_next();
       uint4 q[R][C];
 #pragma unroll
       for (int r = 0; r < R; ++r)
@@ -282,7 +248,7 @@ ascent_block_kernel(const int8_t* __restrict__ Q8, int64_t ldq, int n, int W,
                     unsigned* __restrict__ err) {
   __shared__ int2 rec[2][T / 32];
   __shared__ uint64_t xs[UBQP_MAX_N / 64];
-  Group<T> grp{rec, 0, Q8, ldq, n};
+  Group<T> grp{rec, 0};
   const int64_t cnt = *count;
   for (int64_t t = blockIdx.x; t < cnt; t += gridDim.x) {
     const int s = idx[t];
