@@ -46,7 +46,7 @@
 extern "C" {
 #endif
 
-#define UBQP_ABI_VERSION 1
+#define UBQP_ABI_VERSION 2
 
 typedef enum ubqp_status {
   UBQP_OK = 0,
@@ -83,9 +83,9 @@ int ubqp_abi_version(void);
  *   n       1 <= n <= 16384.
  *   out     receives the handle (NULL on failure).
  * Checks that Q is symmetric (UBQP_ERR_NOT_SYMMETRIC otherwise), records max|Q|,
- * builds the padded int8 copy used by the ascent, the tensor-core operand
- * (bf16, lower triangle doubled, see ubqp_eval), the row sums and the
- * first-derivative start.  Allocates about n_pad^2 * 3 bytes of device memory
+ * builds the padded int8 copy used by the ascent, the tensor-core operands
+ * (bf16: Q' for ubqp_eval, Q for the ascent's start-up), the row sums and the
+ * first-derivative start.  Allocates about n_pad^2 * 5 bytes of device memory
  * (n_pad = n rounded up to 1024) owned by the handle.  Synchronises `stream`
  * once to read the validation result.
  */
@@ -194,12 +194,20 @@ int ubqp_screen(const int64_t* f_dev, int64_t S, double lambda, int32_t* idx_dev
  * max_flips flips were made (max_flips 0 = no cap).  f_dev[s] must hold
  * f(x_s) on entry and holds the ascended value on exit.  flips_dev (S int32,
  * may be NULL) receives each ascended start's flip count; entries of starts
- * not listed are left untouched.  count is read on the device (no sync).
- * S is the length of X_dev/f_dev (bounds idx).  Async.
+ * not listed are left untouched.  The indices must be distinct and in [0, S)
+ * (an index outside is skipped and reported by ubqp_sync).  count is read on
+ * the device (no sync).  S is the length of X_dev/f_dev.  Async.
+ *   ws / ws_bytes: device scratch (16-byte aligned) of at least
+ *   ubqp_ascent_workspace_size(q, S) bytes lets the start-up y = Q x of all
+ *   listed starts run as one tensor-core product (bf16 Q, fp32 accumulation,
+ *   exact); with ws NULL or smaller the start-up sums the rows of Q on the
+ *   CUDA cores instead.  Results are identical either way.
  */
+size_t ubqp_ascent_workspace_size(const ubqp_q* q, int64_t S);
 int ubqp_ascent(const ubqp_q* q, uint64_t* X_dev, int64_t* f_dev,
                 const int32_t* idx_dev, const int64_t* count_dev, int64_t S,
-                int32_t max_flips, int32_t* flips_dev, void* stream);
+                int32_t max_flips, int32_t* flips_dev, void* ws, size_t ws_bytes,
+                void* stream);
 
 /*
  * ubqp_best -- UpdateBestAndT's bookkeeping (Fig. 2): the largest of the S

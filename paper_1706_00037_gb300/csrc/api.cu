@@ -48,6 +48,8 @@ int resolve_path(int path) { return path == UBQP_EVAL_AUTO ? UBQP_EVAL_TC : path
 struct SolveLayout {
   size_t X, f, idx, flips, small, eval, total;
 };
+// The evaluation and the ascent's start-up run one after the other, so they
+// share one scratch region sized for the larger of the two.
 constexpr size_t kSmallBytes = 256;  // count, Tm, screen stats, stats out
 
 SolveLayout solve_layout(const ubqp_q* q, const ubqp_params* p) {
@@ -65,7 +67,9 @@ SolveLayout solve_layout(const ubqp_q* q, const ubqp_params* p) {
   L.flips = take((size_t)S * 4);
   L.small = take(kSmallBytes);
   const int path = resolve_path(p->eval_path);
-  L.eval = take(path == UBQP_EVAL_TC ? ubqp::eval_tc_workspace(q, S) : 0);
+  const size_t ev = path == UBQP_EVAL_TC ? ubqp::eval_tc_workspace(q, S) : 0;
+  const size_t as = ubqp::ascent_tc_workspace(q, S);
+  L.eval = take(ev > as ? ev : as);
   L.total = off;
   return L;
 }
@@ -96,6 +100,7 @@ void ubqp_q_destroy(ubqp_q* q) {
   if (!q) return;
   cudaFree(q->Q8);
   cudaFree(q->Qt);
+  cudaFree(q->Qf);
   cudaFree(q->rowsum);
   cudaFree(q->x0);
   cudaFree(q->err);
@@ -126,15 +131,16 @@ int ubqp_q_prepare(const int8_t* Q_dev, int32_t n, int64_t ldq, void* stream, ub
   }
   size_t q8 = (size_t)n * h->ldq, qt = (size_t)h->n_tc * h->n_tc * 2;
   if (cudaMalloc(&h->Q8, q8) != cudaSuccess || cudaMalloc(&h->Qt, qt) != cudaSuccess ||
+      cudaMalloc(&h->Qf, qt) != cudaSuccess ||
       cudaMalloc(&h->rowsum, sizeof(int32_t) * n) != cudaSuccess ||
       cudaMalloc(&h->x0, sizeof(uint64_t) * h->W) != cudaSuccess ||
       cudaMalloc(&h->err, 4 * sizeof(unsigned)) != cudaSuccess) {
     cudaGetLastError();
     ubqp_q_destroy(h);
-    return fail(UBQP_ERR_NOMEM, "device allocation of %zu bytes failed", q8 + qt);
+    return fail(UBQP_ERR_NOMEM, "device allocation of %zu bytes failed", q8 + 2 * qt);
   }
   h->scratch_flags = h->err + 1;
-  h->device_bytes = (int64_t)(q8 + qt + sizeof(int32_t) * n + 8 * h->W + 16);
+  h->device_bytes = (int64_t)(q8 + 2 * qt + sizeof(int32_t) * n + 8 * h->W + 16);
   cudaError_t e = ubqp::launch_prepare(Q_dev, n, ldq, h, st);
   unsigned flags[2] = {0, 0};
   if (e == cudaSuccess)
@@ -273,15 +279,30 @@ int ubqp_screen(const int64_t* f_dev, int64_t S, double lambda, int32_t* idx_dev
   return UBQP_OK;
 }
 
+size_t ubqp_ascent_workspace_size(const ubqp_q* q, int64_t S) {
+  if (!q || S < 0) return 0;
+  return ubqp::ascent_tc_workspace(q, S);
+}
+
 int ubqp_ascent(const ubqp_q* q, uint64_t* X_dev, int64_t* f_dev, const int32_t* idx_dev,
                 const int64_t* count_dev, int64_t S, int32_t max_flips, int32_t* flips_dev,
-                void* stream) {
+                void* ws, size_t ws_bytes, void* stream) {
   if (!q || !X_dev || !f_dev || !idx_dev || !count_dev) return fail(UBQP_ERR_ARG, "NULL argument");
   if (S < 0 || S >= ((int64_t)1 << 31)) return fail(UBQP_ERR_ARG, "S outside [0, 2^31)");
   if (max_flips < 0) return fail(UBQP_ERR_ARG, "max_flips < 0");
+  if (ws && ((uintptr_t)ws & 15) != 0) return fail(UBQP_ERR_ARG, "workspace not 16-byte aligned");
   if (S == 0) return UBQP_OK;
-  UBQP_CUDA(ubqp::launch_ascent(q, X_dev, f_dev, idx_dev, count_dev, S, max_flips, flips_dev,
-                                (cudaStream_t)stream));
+  cudaStream_t st = (cudaStream_t)stream;
+  float* Y = nullptr;
+  if (ws && ws_bytes >= ubqp::ascent_tc_workspace(q, S) &&
+      (int64_t)q->max_abs * q->n_tc < (1 << 24)) {
+    cudaError_t e = ubqp::launch_ascent_init_tc(q, X_dev, idx_dev, count_dev, S, ws, ws_bytes,
+                                                &Y, st);
+    if (e == cudaErrorNotSupported) Y = nullptr;
+    else if (e != cudaSuccess) return cuda_fail(e, "ascent start-up (tensor cores)");
+  }
+  UBQP_CUDA(ubqp::launch_ascent(q, X_dev, f_dev, idx_dev, count_dev, S, max_flips, flips_dev, Y,
+                                st));
   return UBQP_OK;
 }
 
@@ -325,7 +346,9 @@ int ubqp_solve(const ubqp_q* q, const ubqp_params* p, uint64_t* best_x_dev, int6
     return r;
   if ((r = ubqp_screen(f, S, p->lambda, idx, count, Tm, sstats, stream))) return r;
   UBQP_CUDA(cudaMemsetAsync(flips, 0, sizeof(int32_t) * S, st));
-  if ((r = ubqp_ascent(q, X, f, idx, count, S, p->max_flips, flips, stream))) return r;
+  if ((r = ubqp_ascent(q, X, f, idx, count, S, p->max_flips, flips, base + L.eval,
+                       L.total - L.eval, stream)))
+    return r;
   if ((r = ubqp_best(f, X, S, q->W, best_x_dev, best_f_dev, stream))) return r;
   UBQP_CUDA(ubqp::launch_solve_stats(count, idx, flips, Tm, sstats, best_f_dev, sout, st));
   if (stats_host) {

@@ -84,12 +84,13 @@ struct Group {
 };
 
 template <int T, int C>
-__device__ __forceinline__ void ascend_one(const int8_t* __restrict__ Q8, int64_t ldq, int n,
+__device__ __forceinline__ void ascend_one(const int8_t* __restrict__ Q8, int64_t ldq,
+                                           int64_t ldy, int n,
                                            int W, uint64_t* __restrict__ x_g,
                                            int64_t* __restrict__ f_s, int32_t max_flips,
                                            int32_t* __restrict__ flips_s,
                                            unsigned* __restrict__ err, uint64_t* xs,
-                                           Group<T>& grp) {
+                                           const float* __restrict__ y_g, Group<T>& grp) {
   constexpr int E = 16 * C;
   constexpr int CW = 16 * T;  // indices per chunk
   static_assert(E <= 32, "local index must fit 5 bits");
@@ -120,8 +121,26 @@ __device__ __forceinline__ void ascend_one(const int8_t* __restrict__ Q8, int64_
       }
     }
   }
-  // ---- y = Q x on the owned columns: add the rows k with x_k = 1
-  for (int w = 0; w < W; ++w) {
+  // ---- y = Q x on the owned columns: from the tensor-core start-up when
+  // given (y_g, exact integers in fp32), else by adding the rows k with x_k = 1
+  if (y_g) {
+#pragma unroll
+    for (int c = 0; c < C; ++c) {
+      const int j0 = c * CW + 16 * g;
+      if (j0 < ldy) {
+        const float4* src = reinterpret_cast<const float4*>(y_g + j0);
+#pragma unroll
+        for (int v = 0; v < 4; ++v) {
+          const float4 t4 = src[v];
+          y[c * 16 + 4 * v + 0] = __float2int_rn(t4.x);
+          y[c * 16 + 4 * v + 1] = __float2int_rn(t4.y);
+          y[c * 16 + 4 * v + 2] = __float2int_rn(t4.z);
+          y[c * 16 + 4 * v + 3] = __float2int_rn(t4.w);
+        }
+      }
+    }
+  }
+  for (int w = 0; w < W && !y_g; ++w) {
     uint64_t word = x_g[w] & valid_mask(n, w);
     while (word) {
       constexpr int R = C == 1 ? 4 : 2;  // rows in flight
@@ -245,7 +264,7 @@ ascent_block_kernel(const int8_t* __restrict__ Q8, int64_t ldq, int n, int W,
                     uint64_t* __restrict__ X, int64_t* __restrict__ f,
                     const int32_t* __restrict__ idx, const int64_t* __restrict__ count,
                     int64_t S, int32_t max_flips, int32_t* __restrict__ flips,
-                    unsigned* __restrict__ err) {
+                    const float* __restrict__ Y, int64_t ldy, unsigned* __restrict__ err) {
   __shared__ int2 rec[2][T / 32];
   __shared__ uint64_t xs[UBQP_MAX_N / 64];
   Group<T> grp{rec, 0};
@@ -256,8 +275,8 @@ ascent_block_kernel(const int8_t* __restrict__ Q8, int64_t ldq, int n, int W,
       if (threadIdx.x == 0) atomicOr(err, UBQP_DEVERR_BADIDX);
       continue;
     }
-    ascend_one<T, C>(Q8, ldq, n, W, X + (int64_t)s * W, f + s, max_flips,
-                     flips ? flips + s : nullptr, err, xs, grp);
+    ascend_one<T, C>(Q8, ldq, ldy, n, W, X + (int64_t)s * W, f + s, max_flips,
+                     flips ? flips + s : nullptr, err, xs, Y ? Y + t * ldy : nullptr, grp);
   }
 }
 
@@ -268,7 +287,7 @@ ascent_warp_kernel(const int8_t* __restrict__ Q8, int64_t ldq, int n, int W,
                    uint64_t* __restrict__ X, int64_t* __restrict__ f,
                    const int32_t* __restrict__ idx, const int64_t* __restrict__ count,
                    int64_t S, int32_t max_flips, int32_t* __restrict__ flips,
-                   unsigned* __restrict__ err) {
+                   const float* __restrict__ Y, int64_t ldy, unsigned* __restrict__ err) {
   __shared__ uint64_t xs_all[4][16];
   Group<32> grp;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -279,8 +298,9 @@ ascent_warp_kernel(const int8_t* __restrict__ Q8, int64_t ldq, int n, int W,
       if (lane == 0) atomicOr(err, UBQP_DEVERR_BADIDX);
       continue;
     }
-    ascend_one<32, C>(Q8, ldq, n, W, X + (int64_t)s * W, f + s, max_flips,
-                      flips ? flips + s : nullptr, err, xs_all[warp], grp);
+    ascend_one<32, C>(Q8, ldq, ldy, n, W, X + (int64_t)s * W, f + s, max_flips,
+                      flips ? flips + s : nullptr, err, xs_all[warp],
+                      Y ? Y + t * ldy : nullptr, grp);
   }
 }
 
@@ -299,23 +319,23 @@ int resident_grid(K kernel, int threads, int sm_count) {
 template <int T, int C>
 cudaError_t launch_block(const ubqp_q* h, uint64_t* X, int64_t* f, const int32_t* idx,
                          const int64_t* count, int64_t S, int32_t max_flips, int32_t* flips,
-                         cudaStream_t st) {
+                         const float* Y, cudaStream_t st) {
   int grid = resident_grid(ascent_block_kernel<T, C>, T, h->sm_count);
   if ((int64_t)grid > S) grid = (int)S;
   ascent_block_kernel<T, C><<<grid, T, 0, st>>>(h->Q8, h->ldq, h->n, h->W, X, f, idx, count,
-                                                S, max_flips, flips, h->err);
+                                                S, max_flips, flips, Y, h->n_tc, h->err);
   return cudaGetLastError();
 }
 
 template <int C>
 cudaError_t launch_warp(const ubqp_q* h, uint64_t* X, int64_t* f, const int32_t* idx,
                         const int64_t* count, int64_t S, int32_t max_flips, int32_t* flips,
-                        cudaStream_t st) {
+                        const float* Y, cudaStream_t st) {
   int grid = resident_grid(ascent_warp_kernel<C>, 128, h->sm_count);
   const int64_t need = (S + 3) / 4;
   if ((int64_t)grid > need) grid = (int)need;
   ascent_warp_kernel<C><<<grid, 128, 0, st>>>(h->Q8, h->ldq, h->n, h->W, X, f, idx, count, S,
-                                              max_flips, flips, h->err);
+                                              max_flips, flips, Y, h->n_tc, h->err);
   return cudaGetLastError();
 }
 
@@ -323,15 +343,15 @@ cudaError_t launch_warp(const ubqp_q* h, uint64_t* X, int64_t* f, const int32_t*
 
 cudaError_t launch_ascent(const ubqp_q* h, uint64_t* X, int64_t* f, const int32_t* idx,
                           const int64_t* count, int64_t S, int32_t max_flips, int32_t* flips,
-                          cudaStream_t st) {
+                          const float* Y, cudaStream_t st) {
   const int n = h->n;
-  if (n <= 256) return launch_warp<1>(h, X, f, idx, count, S, max_flips, flips, st);
-  if (n <= 512) return launch_warp<2>(h, X, f, idx, count, S, max_flips, flips, st);
-  if (n <= 1024) return launch_block<64, 1>(h, X, f, idx, count, S, max_flips, flips, st);
-  if (n <= 2048) return launch_block<128, 1>(h, X, f, idx, count, S, max_flips, flips, st);
-  if (n <= 4096) return launch_block<256, 1>(h, X, f, idx, count, S, max_flips, flips, st);
-  if (n <= 8192) return launch_block<256, 2>(h, X, f, idx, count, S, max_flips, flips, st);
-  if (n <= 16384) return launch_block<512, 2>(h, X, f, idx, count, S, max_flips, flips, st);
+  if (n <= 256) return launch_warp<1>(h, X, f, idx, count, S, max_flips, flips, Y, st);
+  if (n <= 512) return launch_warp<2>(h, X, f, idx, count, S, max_flips, flips, Y, st);
+  if (n <= 1024) return launch_block<64, 1>(h, X, f, idx, count, S, max_flips, flips, Y, st);
+  if (n <= 2048) return launch_block<128, 1>(h, X, f, idx, count, S, max_flips, flips, Y, st);
+  if (n <= 4096) return launch_block<256, 1>(h, X, f, idx, count, S, max_flips, flips, Y, st);
+  if (n <= 8192) return launch_block<256, 2>(h, X, f, idx, count, S, max_flips, flips, Y, st);
+  if (n <= 16384) return launch_block<512, 2>(h, X, f, idx, count, S, max_flips, flips, Y, st);
   return cudaErrorInvalidValue;
 }
 

@@ -173,10 +173,15 @@ __device__ __forceinline__ Unit unit_of(const int4* __restrict__ chunks, int m_t
   return Unit{c.x, c.y, c.z, u % m_tiles};
 }
 
+// YMODE = false: f_s += sum_j x_sj D_sj over the lower block triangle (Evaluate).
+// YMODE = true:  Y = Xe Qf^t over the full square, accumulated in fp32 (exact
+// integers) with vector atomics -- y = Q x for the starts an ascent climbs.
+template <bool YMODE>
 __global__ void __launch_bounds__(THREADS, 1)
 eval_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
                const uint64_t* __restrict__ X, int W, int64_t S, int m_tiles,
                const int4* __restrict__ chunks, int n_chunks, int64_t* __restrict__ f,
+               const int64_t* __restrict__ count, float* __restrict__ Y, int64_t ldy,
                unsigned* __restrict__ err) {
   extern __shared__ uint8_t smem_raw[];
   uint8_t* smem = smem_raw + ((1024 - (su32(smem_raw) & 1023)) & 1023);
@@ -189,6 +194,12 @@ eval_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ 
   volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  int64_t rows = S;
+  if (YMODE) {
+    const int64_t c = *count;
+    rows = c < S ? (c > 0 ? c : 0) : S;
+    m_tiles = (int)((rows + BM - 1) / BM);
+  }
   const int n_units = n_chunks * m_tiles;
 
   if (threadIdx.x == 0) {
@@ -304,28 +315,47 @@ eval_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ 
       if (!mbar_wait(&tfull[a], aphase, abort_flag, err)) break;
       tc_fence_after();
       const int64_t s = (int64_t)un.mt * BM + row;
-      uint64_t xw[4];
-#pragma unroll
-      for (int i = 0; i < 4; ++i) {
-        const int w = un.nb * 4 + i;
-        xw[i] = (s < S && w < W) ? X[s * W + w] : 0ull;
-      }
-      int acc = 0;
       const uint32_t base = tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(a * BN);
+      if (YMODE) {
+        float* yrow = Y + s * ldy + (int64_t)un.nb * BN;
 #pragma unroll 1
-      for (int cc = 0; cc < BN / 32; ++cc) {
-        uint32_t r[32];
-        tmem_ld32(base + (uint32_t)(cc * 32), r);
-        const uint32_t bits = (uint32_t)(xw[cc >> 1] >> ((cc & 1) * 32));
+        for (int cc = 0; cc < BN / 32; ++cc) {
+          uint32_t r[32];
+          tmem_ld32(base + (uint32_t)(cc * 32), r);
+          if (s < rows) {
 #pragma unroll
-        for (int i = 0; i < 32; ++i)
-          if ((bits >> i) & 1u) acc += __float2int_rn(__uint_as_float(r[i]));
+            for (int i = 0; i < 8; ++i)
+              atomicAdd(reinterpret_cast<float4*>(yrow + cc * 32 + 4 * i),
+                        make_float4(__uint_as_float(r[4 * i]), __uint_as_float(r[4 * i + 1]),
+                                    __uint_as_float(r[4 * i + 2]),
+                                    __uint_as_float(r[4 * i + 3])));
+          }
+        }
+        tc_fence_before();
+        mbar_arrive(&tempty[a]);
+      } else {
+        uint64_t xw[4];
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+          const int w = un.nb * 4 + i;
+          xw[i] = (s < S && w < W) ? X[s * W + w] : 0ull;
+        }
+        int acc = 0;
+#pragma unroll 1
+        for (int cc = 0; cc < BN / 32; ++cc) {
+          uint32_t r[32];
+          tmem_ld32(base + (uint32_t)(cc * 32), r);
+          const uint32_t bits = (uint32_t)(xw[cc >> 1] >> ((cc & 1) * 32));
+#pragma unroll
+          for (int i = 0; i < 32; ++i)
+            if ((bits >> i) & 1u) acc += __float2int_rn(__uint_as_float(r[i]));
+        }
+        tc_fence_before();
+        mbar_arrive(&tempty[a]);
+        if (s < S && acc != 0)
+          atomicAdd(reinterpret_cast<unsigned long long*>(&f[s]),
+                    (unsigned long long)(long long)acc);
       }
-      tc_fence_before();
-      mbar_arrive(&tempty[a]);
-      if (s < S && acc != 0)
-        atomicAdd(reinterpret_cast<unsigned long long*>(&f[s]),
-                  (unsigned long long)(long long)acc);
     }
   }
   __syncthreads();
@@ -337,19 +367,31 @@ eval_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ 
   }
 }
 
-// Unpack bit-packed solutions into the bf16 A operand: S_p x n_tc, 0.0 / 1.0,
-// zero rows beyond S and zero columns beyond n.
+// Unpack bit-packed solutions into the bf16 A operand: S_p x n_tc of 0.0 / 1.0.
+// Row t is solution idx[t] (t < *count) when idx is given, else solution t
+// (t < S); other rows and columns >= n are zero.
 __global__ void unpack_bits_bf16(const uint64_t* __restrict__ X, int n, int W, int64_t S,
-                                 int64_t S_p, int n_tc, uint4* __restrict__ Xe) {
+                                 const int32_t* __restrict__ idx,
+                                 const int64_t* __restrict__ count, int64_t S_p, int n_tc,
+                                 uint4* __restrict__ Xe) {
   const int64_t per_row = n_tc / 8;
   const int64_t total = S_p * per_row;
+  int64_t rows = S;
+  if (idx) {
+    const int64_t c = *count;
+    rows = c < S ? c : S;
+  }
   for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < total;
        t += (int64_t)gridDim.x * blockDim.x) {
-    const int64_t s = t / per_row;
-    const int c = (int)(t - s * per_row);
+    const int64_t r = t / per_row;
+    const int c = (int)(t - r * per_row);
     const int w = c >> 3;
     uint32_t byte = 0;
-    if (s < S && w < W) byte = (uint32_t)(((X[s * W + w] & valid_mask(n, w)) >> ((c & 7) * 8)) & 0xFFu);
+    if (r < rows && w < W) {
+      const int64_t src = idx ? (int64_t)idx[r] : r;
+      if (src >= 0 && src < S)
+        byte = (uint32_t)(((X[src * W + w] & valid_mask(n, w)) >> ((c & 7) * 8)) & 0xFFu);
+    }
     uint32_t v[4];
 #pragma unroll
     for (int i = 0; i < 4; ++i) {
@@ -435,14 +477,15 @@ size_t eval_tc_workspace(const ubqp_q* h, int64_t S) {
   return (size_t)padded_starts(S) * (size_t)h->n_tc * 2;
 }
 
-// Work chunks of the lower block triangle: for N-block J the K range is
-// [0, 256 (J+1)), split into near-equal chunks of at most KCH steps; sorted
-// largest first.  Stored in the handle as int4 {J, first K step, K steps, 0}.
-cudaError_t eval_tc_prepare(ubqp_q* h) {
-  const int NB = h->n_tc / BN;
+// Work chunks {N-block, first K step, K steps, 0}, sorted largest first.
+// Evaluation: for N-block J the K range is [0, 256 (J+1)) (lower block
+// triangle); ascent start-up (y = Q x): the full K range for every J.  Both are
+// split into near-equal chunks of at most KCH steps.
+static std::vector<int4> make_chunks(int NB, bool full) {
   std::vector<int4> ch;
+  const int nk_full = NB * (BN / BK);
   for (int J = 0; J < NB; ++J) {
-    const int nk = (J + 1) * (BN / BK);
+    const int nk = full ? nk_full : (J + 1) * (BN / BK);
     const int parts = (nk + KCH - 1) / KCH;
     for (int p = 0, k0 = 0; p < parts; ++p) {
       const int len = nk / parts + (p < nk % parts ? 1 : 0);
@@ -451,12 +494,68 @@ cudaError_t eval_tc_prepare(ubqp_q* h) {
     }
   }
   std::stable_sort(ch.begin(), ch.end(), [](const int4& a, const int4& b) { return a.z > b.z; });
-  h->tc_nchunks = (int)ch.size();
-  cudaError_t e = cudaMalloc(&h->tc_chunks, sizeof(int4) * ch.size());
+  return ch;
+}
+
+cudaError_t eval_tc_prepare(ubqp_q* h) {
+  const int NB = h->n_tc / BN;
+  std::vector<int4> tri = make_chunks(NB, false), full = make_chunks(NB, true);
+  h->tc_nchunks = (int)tri.size();
+  h->tc_nchunks_y = (int)full.size();
+  cudaError_t e = cudaMalloc(&h->tc_chunks, sizeof(int4) * (tri.size() + full.size()));
   if (e) return e;
-  e = cudaMemcpy(h->tc_chunks, ch.data(), sizeof(int4) * ch.size(), cudaMemcpyHostToDevice);
+  e = cudaMemcpy(h->tc_chunks, tri.data(), sizeof(int4) * tri.size(), cudaMemcpyHostToDevice);
   if (e) return e;
-  h->tc_ok = make_map(reinterpret_cast<CUtensorMap*>(h->tc_mapB), h->Qt, h->n_tc, h->n_tc, BN);
+  e = cudaMemcpy(reinterpret_cast<int4*>(h->tc_chunks) + tri.size(), full.data(),
+                 sizeof(int4) * full.size(), cudaMemcpyHostToDevice);
+  if (e) return e;
+  h->tc_ok = make_map(reinterpret_cast<CUtensorMap*>(h->tc_mapB), h->Qt, h->n_tc, h->n_tc, BN) &&
+             make_map(reinterpret_cast<CUtensorMap*>(h->tc_mapF), h->Qf, h->n_tc, h->n_tc, BN);
+  return cudaSuccess;
+}
+
+size_t ascent_tc_workspace(const ubqp_q* h, int64_t S) {
+  return (size_t)padded_starts(S) * (size_t)h->n_tc * (2 + 4);
+}
+
+// y = Q x for the starts idx[0 .. *count) into Y (fp32, row t = idx[t], stride
+// n_tc), on the tensor cores.  ws holds the unpacked starts then Y.
+cudaError_t launch_ascent_init_tc(const ubqp_q* h, const uint64_t* X, const int32_t* idx,
+                                  const int64_t* count, int64_t S, void* ws, size_t ws_bytes,
+                                  float** Y_out, cudaStream_t st) {
+  if (!h->tc_ok) return cudaErrorNotSupported;
+  const int64_t S_p = padded_starts(S);
+  if (ws_bytes < ascent_tc_workspace(h, S)) return cudaErrorInvalidValue;
+  uint8_t* Xe = reinterpret_cast<uint8_t*>(ws);
+  float* Y = reinterpret_cast<float*>(Xe + (size_t)S_p * h->n_tc * 2);
+  cudaError_t e;
+  {
+    const int64_t total = S_p * (h->n_tc / 8);
+    int64_t blocks = (total + 255) / 256;
+    if (blocks > (int64_t)h->sm_count * 8) blocks = (int64_t)h->sm_count * 8;
+    unpack_bits_bf16<<<(unsigned)blocks, 256, 0, st>>>(X, h->n, h->W, S, idx, count, S_p,
+                                                      h->n_tc, reinterpret_cast<uint4*>(Xe));
+    if ((e = cudaGetLastError())) return e;
+  }
+  alignas(64) CUtensorMap mapA;
+  if (!make_map(&mapA, Xe, S_p, h->n_tc, BM)) return cudaErrorInvalidValue;
+  if ((e = cudaMemsetAsync(Y, 0, (size_t)S_p * h->n_tc * 4, st))) return e;
+  static bool attr = false;
+  if (!attr) {
+    if ((e = cudaFuncSetAttribute(eval_tc_kernel<true>,
+                                  cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_BYTES)))
+      return e;
+    attr = true;
+  }
+  const int m_tiles = (int)(S_p / BM);
+  const int n_units = h->tc_nchunks_y * m_tiles;
+  const int grid = n_units < h->sm_count ? n_units : h->sm_count;
+  eval_tc_kernel<true><<<grid, THREADS, SMEM_BYTES, st>>>(
+      mapA, *reinterpret_cast<const CUtensorMap*>(h->tc_mapF), X, h->W, S, m_tiles,
+      reinterpret_cast<const int4*>(h->tc_chunks) + h->tc_nchunks, h->tc_nchunks_y, nullptr,
+      count, Y, h->n_tc, h->err);
+  if ((e = cudaGetLastError())) return e;
+  *Y_out = Y;
   return cudaSuccess;
 }
 
@@ -470,7 +569,8 @@ cudaError_t launch_eval_tc(const ubqp_q* h, const uint64_t* X, int64_t S, int64_
     const int64_t total = S_p * (h->n_tc / 8);
     int64_t blocks = (total + 255) / 256;
     if (blocks > (int64_t)h->sm_count * 8) blocks = (int64_t)h->sm_count * 8;
-    unpack_bits_bf16<<<(unsigned)blocks, 256, 0, st>>>(X, h->n, h->W, S, S_p, h->n_tc,
+    unpack_bits_bf16<<<(unsigned)blocks, 256, 0, st>>>(X, h->n, h->W, S, nullptr, nullptr,
+                                                      S_p, h->n_tc,
                                                       reinterpret_cast<uint4*>(ws));
     if ((e = cudaGetLastError())) return e;
   }
@@ -479,17 +579,18 @@ cudaError_t launch_eval_tc(const ubqp_q* h, const uint64_t* X, int64_t S, int64_
   if ((e = cudaMemsetAsync(f, 0, sizeof(int64_t) * S, st))) return e;
   static bool attr = false;
   if (!attr) {
-    if ((e = cudaFuncSetAttribute(eval_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                  SMEM_BYTES)))
+    if ((e = cudaFuncSetAttribute(eval_tc_kernel<false>,
+                                  cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_BYTES)))
       return e;
     attr = true;
   }
   const int m_tiles = (int)(S_p / BM);
   const int n_units = h->tc_nchunks * m_tiles;
   const int grid = n_units < h->sm_count ? n_units : h->sm_count;
-  eval_tc_kernel<<<grid, THREADS, SMEM_BYTES, st>>>(
+  eval_tc_kernel<false><<<grid, THREADS, SMEM_BYTES, st>>>(
       mapA, *reinterpret_cast<const CUtensorMap*>(h->tc_mapB), X, h->W, S, m_tiles,
-      reinterpret_cast<const int4*>(h->tc_chunks), h->tc_nchunks, f, h->err);
+      reinterpret_cast<const int4*>(h->tc_chunks), h->tc_nchunks, f, nullptr, nullptr, 0,
+      h->err);
   return cudaGetLastError();
 }
 

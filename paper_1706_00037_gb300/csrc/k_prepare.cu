@@ -1,6 +1,7 @@
 // k_prepare.cu -- one pass over Q: symmetry check (problem (P) requires a
 // symmetric Q), max|Q|, the padded int8 copy read by the ascent, the bf16
-// tensor-core operand Q' = 2*tril(Q,-1) + diag(Q), and the row sums behind the
+// tensor-core operands Q' = 2*tril(Q,-1) + diag(Q) (evaluation) and Q (the
+// ascent's y = Q x), and the row sums behind the
 // first-derivative start of Fig. 2 (CalculateFirstDerivativeSolution).
 #include <cuda_bf16.h>
 
@@ -14,7 +15,8 @@ constexpr int ROWS = 8;  // block is TILE x ROWS threads, 4 rows per thread
 
 __global__ void __launch_bounds__(TILE* ROWS)
 prepare_tiles(const int8_t* __restrict__ Q, int n, int64_t ldq_in, int8_t* __restrict__ Q8,
-              int64_t ldq, uint16_t* __restrict__ Qt, int n_tc, int32_t* __restrict__ rowsum,
+              int64_t ldq, uint16_t* __restrict__ Qt, uint16_t* __restrict__ Qf, int n_tc,
+              int32_t* __restrict__ rowsum,
               unsigned* __restrict__ flags) {
   __shared__ int8_t tr[TILE][TILE + 4];
   const int bj = blockIdx.y * TILE, bk = blockIdx.x * TILE;
@@ -36,6 +38,7 @@ prepare_tiles(const int8_t* __restrict__ Q, int n, int64_t ldq_in, int8_t* __res
       Q8[(int64_t)j * ldq + k] = (int8_t)v;
       int w = k < j ? 2 * v : (k == j ? v : 0);
       Qt[(int64_t)j * n_tc + k] = __bfloat16_as_ushort(__float2bfloat16_rn((float)w));
+      Qf[(int64_t)j * n_tc + k] = __bfloat16_as_ushort(__float2bfloat16_rn((float)v));
     }
     amax = max(amax, abs(v));
     // row partial sum over this tile's 32 columns
@@ -72,11 +75,12 @@ cudaError_t launch_prepare(const int8_t* Q, int n, int64_t ldq_in, ubqp_q* h,
   cudaError_t e;
   if ((e = cudaMemsetAsync(h->Q8, 0, (size_t)h->n * h->ldq, st))) return e;
   if ((e = cudaMemsetAsync(h->Qt, 0, (size_t)h->n_tc * h->n_tc * 2, st))) return e;
+  if ((e = cudaMemsetAsync(h->Qf, 0, (size_t)h->n_tc * h->n_tc * 2, st))) return e;
   if ((e = cudaMemsetAsync(h->rowsum, 0, sizeof(int32_t) * n, st))) return e;
   if ((e = cudaMemsetAsync(h->scratch_flags, 0, 2 * sizeof(unsigned), st))) return e;
   if ((e = cudaMemsetAsync(h->err, 0, sizeof(unsigned), st))) return e;
   dim3 grid((n + TILE - 1) / TILE, (n + TILE - 1) / TILE), block(TILE, ROWS);
-  prepare_tiles<<<grid, block, 0, st>>>(Q, n, ldq_in, h->Q8, h->ldq, h->Qt, h->n_tc,
+  prepare_tiles<<<grid, block, 0, st>>>(Q, n, ldq_in, h->Q8, h->ldq, h->Qt, h->Qf, h->n_tc,
                                          h->rowsum, h->scratch_flags);
   if ((e = cudaGetLastError())) return e;
   first_derivative_bits<<<(h->W + 127) / 128, 128, 0, st>>>(h->rowsum, n, h->W, h->x0);

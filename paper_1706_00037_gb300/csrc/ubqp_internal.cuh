@@ -23,6 +23,7 @@ struct ubqp_q {
   int32_t max_abs;  // max |Q_ij|
   int8_t* Q8;       // n x ldq int8, zero beyond column n
   uint16_t* Qt;     // n_tc x n_tc bf16 bits of Q' = 2 tril(Q,-1) + diag(Q)
+  uint16_t* Qf;     // n_tc x n_tc bf16 bits of Q (full, for y = Q x)
   int32_t* rowsum;  // n
   uint64_t* x0;     // W words: first-derivative start
   unsigned* err;    // device error word
@@ -32,10 +33,12 @@ struct ubqp_q {
   int device;
   // tensor-core evaluation: work chunks of the lower block triangle (int4
   // {N-block, first K step, K steps, 0}) and the TMA descriptor of Qt
-  void* tc_chunks;
+  void* tc_chunks;   // evaluation chunks, then the full-square chunks
   int tc_nchunks;
+  int tc_nchunks_y;
   bool tc_ok;
-  alignas(64) unsigned char tc_mapB[128];
+  alignas(64) unsigned char tc_mapB[128];  // TMA descriptor of Qt
+  alignas(64) unsigned char tc_mapF[128];  // TMA descriptor of Qf
 };
 
 namespace ubqp {
@@ -74,6 +77,10 @@ cudaError_t launch_eval_plain(const ubqp_q* h, const uint64_t* X, int64_t S,
 size_t eval_tc_workspace(const ubqp_q* h, int64_t S);
 cudaError_t eval_tc_prepare(ubqp_q* h);
 size_t eval_tc_static_capacity();
+size_t ascent_tc_workspace(const ubqp_q* h, int64_t S);
+cudaError_t launch_ascent_init_tc(const ubqp_q* h, const uint64_t* X, const int32_t* idx,
+                                  const int64_t* count, int64_t S, void* ws, size_t ws_bytes,
+                                  float** Y_out, cudaStream_t st);
 cudaError_t eval_tc_static_scratch(void** out);
 cudaError_t launch_eval_tc(const ubqp_q* h, const uint64_t* X, int64_t S, int64_t* f,
                            void* ws, size_t ws_bytes, cudaStream_t st);
@@ -81,7 +88,7 @@ cudaError_t launch_screen(const int64_t* f, int64_t S, double lambda, int32_t* i
                           int64_t* count, double* Tm, int64_t* stats, cudaStream_t st);
 cudaError_t launch_ascent(const ubqp_q* h, uint64_t* X, int64_t* f, const int32_t* idx,
                           const int64_t* count, int64_t S, int32_t max_flips,
-                          int32_t* flips, cudaStream_t st);
+                          int32_t* flips, const float* Y, cudaStream_t st);
 cudaError_t launch_best(const int64_t* f, const uint64_t* X, int64_t S, int W,
                         uint64_t* best_x, int64_t* best_f, cudaStream_t st);
 cudaError_t launch_solve_stats(const int64_t* count, const int32_t* idx,

@@ -27,7 +27,8 @@ EXPORTS = ["ubqp_strerror", "ubqp_last_error", "ubqp_abi_version", "ubqp_q_prepa
            "ubqp_q_destroy", "ubqp_q_info", "ubqp_sync", "ubqp_first_derivative",
            "ubqp_diversify", "ubqp_eval_workspace_size", "ubqp_eval", "ubqp_eval_noalloc",
            "ubqp_screen",
-           "ubqp_ascent", "ubqp_best", "ubqp_solve_workspace_size", "ubqp_solve"]
+           "ubqp_ascent_workspace_size", "ubqp_ascent", "ubqp_best", "ubqp_solve_workspace_size",
+           "ubqp_solve"]
 
 
 class UbqpError(RuntimeError):
@@ -85,7 +86,8 @@ def load() -> ctypes.CDLL:
         "ubqp_eval": (ctypes.c_int, [P, P, i64, P, i32, P, sz, P]),
         "ubqp_eval_noalloc": (ctypes.c_int, [P, P, i64, P, P]),
         "ubqp_screen": (ctypes.c_int, [P, i64, f64, P, P, P, P, P]),
-        "ubqp_ascent": (ctypes.c_int, [P, P, P, P, P, i64, i32, P, P]),
+        "ubqp_ascent_workspace_size": (sz, [P, i64]),
+        "ubqp_ascent": (ctypes.c_int, [P, P, P, P, P, i64, i32, P, P, sz, P]),
         "ubqp_best": (ctypes.c_int, [P, P, i64, i32, P, P, P]),
         "ubqp_solve_workspace_size": (sz, [P, ctypes.POINTER(Params)]),
         "ubqp_solve": (ctypes.c_int, [P, ctypes.POINTER(Params), P, P, ctypes.POINTER(Stats),
@@ -217,11 +219,24 @@ def screen(f: torch.Tensor, lam: float, stream=None) -> dict:
     return {"idx": idx, "count": count, "Tm": Tm, "stats": st}
 
 
+def ascent_workspace_size(inst: Instance, S: int) -> int:
+    return int(load().ubqp_ascent_workspace_size(inst.handle, S))
+
+
 def ascent(inst: Instance, X: torch.Tensor, f: torch.Tensor, idx: torch.Tensor,
            count: torch.Tensor, max_flips: int = 0, flips: torch.Tensor | None = None,
+           ws: torch.Tensor | None = None, use_ws: bool = True,
            stream=None) -> torch.Tensor | None:
-    _check(load().ubqp_ascent(inst.handle, _ptr(X), _ptr(f), _ptr(idx), _ptr(count),
-                              X.shape[0], max_flips, _ptr(flips), _stream(stream)))
+    """Steepest ascent of X[idx[:count]] in place.  With use_ws (default) a
+    workspace is allocated if none is given, so the start-up runs on the tensor
+    cores; use_ws=False selects the CUDA-core start-up."""
+    S = X.shape[0]
+    if ws is None and use_ws:
+        ws = torch.empty(max(ascent_workspace_size(inst, S), 16), dtype=torch.uint8,
+                         device=X.device)
+    nbytes = ws.numel() if ws is not None else 0
+    _check(load().ubqp_ascent(inst.handle, _ptr(X), _ptr(f), _ptr(idx), _ptr(count), S,
+                              max_flips, _ptr(flips), _ptr(ws), nbytes, _stream(stream)))
     return flips
 
 

@@ -199,23 +199,25 @@ def test_screen_all_equal_and_threshold_ties():
 
 # ----------------------------------------------------------------- ascent
 
-def _ascent_case(n, density, seed, S, max_flips=0, idx=None):
+def _ascent_case(n, density, seed, S, max_flips=0, idx=None, use_ws=True):
     Q, inst = instance(n, density, seed)
     X = synth.random_solutions(n, S, seed + 1)
     fv = orc.eval(Q, X)
     idx = np.arange(S, dtype=np.int32) if idx is None else np.asarray(idx, np.int32)
     Xd, fd = words_dev(X), dev(fv)
     flips = torch.full((S,), -1, dtype=torch.int32, device="cuda")
-    ubqp.ascent(inst, Xd, fd, dev(idx), dev(np.array([len(idx)], np.int64)), max_flips, flips)
+    ubqp.ascent(inst, Xd, fd, dev(idx), dev(np.array([len(idx)], np.int64)), max_flips, flips,
+                use_ws=use_ws)
     inst.sync()
     Xw, fw, flw = orc.ascent(Q, X, fv, idx, max_flips)
     flw = np.where(np.isin(np.arange(S), idx), flw, -1)
     return words_host(Xd), fd.cpu().numpy(), flips.cpu().numpy(), Xw, fw, flw
 
 
+@pytest.mark.parametrize("use_ws", [True, False], ids=["tc_startup", "core_startup"])
 @pytest.mark.parametrize("n", NS)
-def test_ascent_matches_oracle(n):
-    Xg, fg, flg, Xw, fw, flw = _ascent_case(n, 0.5, n + 7, 24)
+def test_ascent_matches_oracle(n, use_ws):
+    Xg, fg, flg, Xw, fw, flw = _ascent_case(n, 0.5, n + 7, 24, use_ws=use_ws)
     assert np.array_equal(fg, fw)
     assert np.array_equal(flg, flw)
     assert np.array_equal(Xg, Xw)
@@ -225,8 +227,30 @@ def test_ascent_matches_oracle(n):
 def test_ascent_subset_and_untouched(n, density):
     S = 40
     idx = [3, 0, 17, 39, 22]
-    Xg, fg, flg, Xw, fw, flw = _ascent_case(n, density, 11, S, idx=idx)
-    assert np.array_equal(fg, fw) and np.array_equal(flg, flw) and np.array_equal(Xg, Xw)
+    for use_ws in (True, False):
+        Xg, fg, flg, Xw, fw, flw = _ascent_case(n, density, 11, S, idx=idx, use_ws=use_ws)
+        assert np.array_equal(fg, fw) and np.array_equal(flg, flw) and np.array_equal(Xg, Xw)
+
+
+def test_ascent_startup_extreme_coefficients():
+    # |Q| at the int8 limits: the tensor-core start-up y = Q x must stay exact
+    n, S = 1200, 30
+    Q = np.full((n, n), -128, np.int8)
+    np.fill_diagonal(Q, 127)
+    Q[:500, :500] = 127
+    inst = ubqp.Instance(dev(Q))
+    X = np.concatenate([synth.random_solutions(n, S - 2, 3, 0.9),
+                        synth.pack_bits(np.ones((1, n), np.uint8)),
+                        np.zeros((1, synth.words(n)), np.uint64)])
+    fv = orc.eval(Q, X)
+    Xd, fd = words_dev(X), dev(fv)
+    flips = torch.zeros(S, dtype=torch.int32, device="cuda")
+    ubqp.ascent(inst, Xd, fd, dev(np.arange(S, dtype=np.int32)), dev(np.array([S], np.int64)),
+                0, flips)
+    inst.sync()
+    Xw, fw, flw = orc.ascent(Q, X, fv, np.arange(S, dtype=np.int32))
+    assert np.array_equal(fd.cpu().numpy(), fw) and np.array_equal(flips.cpu().numpy(), flw)
+    assert np.array_equal(words_host(Xd), Xw)
 
 
 @pytest.mark.parametrize("n", [50, 600])
