@@ -232,6 +232,34 @@ def test_ascent_subset_and_untouched(n, density):
         assert np.array_equal(fg, fw) and np.array_equal(flg, flw) and np.array_equal(Xg, Xw)
 
 
+@pytest.mark.parametrize("n,extreme", [(8192, True), (9000, False)],
+                         ids=["n8192_wide_gains", "n9000_block512"])
+def test_ascent_large_n_paths(n, extreme):
+    # n = 8192 with |Q| = 128 exceeds the packed-key gain bound (two-step warp
+    # reduction); n = 9000 takes the 512-thread groups
+    S = 3
+    if extreme:
+        r = np.random.default_rng(1)
+        Q = np.where(r.random((n, n)) < 0.5, 127, -128).astype(np.int8)
+        Q = np.triu(Q) + np.triu(Q, 1).T
+    else:
+        Q = synth.make_instance(n, 0.5, 9)
+    inst = ubqp.Instance(dev(Q))
+    X = synth.random_solutions(n, S, 4)
+    fv = orc.eval(Q, X)
+    for use_ws in (True, False):
+        Xd, fd = words_dev(X), dev(fv)
+        flips = torch.zeros(S, dtype=torch.int32, device="cuda")
+        ubqp.ascent(inst, Xd, fd, dev(np.arange(S, dtype=np.int32)),
+                    dev(np.array([S], np.int64)), 0, flips, use_ws=use_ws)
+        inst.sync()
+        if use_ws:
+            Xw, fw, flw = orc.ascent(Q, X, fv, np.arange(S, dtype=np.int32))
+        assert np.array_equal(fd.cpu().numpy(), fw)
+        assert np.array_equal(flips.cpu().numpy(), flw)
+        assert np.array_equal(words_host(Xd), Xw)
+
+
 def test_ascent_startup_extreme_coefficients():
     # |Q| at the int8 limits: the tensor-core start-up y = Q x must stay exact
     n, S = 1200, 30
