@@ -3,31 +3,31 @@
 // index on ties) while the gain is positive.  Gains are the 1-flip move values
 // of Glover et al. (2002) that the Pseudocode section cites,
 //     Delta_j = Q_jj + 2 (1 - 2 x_j) y_j,   y = Q x,
-// and flipping bit k (d = 1 - 2 x_k before the flip) changes them by
-//     Delta_j += 2 (1 - 2 x_j) d Q_jk  (j != k),   Delta_k -> -Delta_k.
+// and a flip of bit k (d = 1 - 2 x_k before the flip) changes y by d times
+// column k of Q (= row k, Q being symmetric) and negates the sign of x_k.
 //
 // Design.  A group of T threads owns one start at a time (one warp for
 // n <= 512, else one block).  Thread g owns E = 16*C elements, in chunks of 16
 // consecutive indices: element e lives at j = (e/16)*16T + 16g + e%16, so one
 // move loads row k of the int8 Q (= column k, Q being symmetric) with C fully
-// coalesced 16-byte loads per thread.  Per element the thread keeps in
-// registers only the argmax key and two dp4a selectors:
-//     key_j = 32 Delta_j + (31 - e)      (gain first, then lower index)
-//     SP_j  = 64 (1 - 2 x_j) in the byte lane of j's coefficient, SN_j = -SP_j,
-// so a move is, per element, key_j = dp4a(row word, SP_j or SN_j, key_j) and a
-// running max: two instructions (the sign of d picks the selector set for the
-// whole move).  The owner of k negates key_k (with the diagonal correction),
-// swaps its selectors and flips its x bit.  Four independent running maxima
-// keep the dependency chains short.  The group reduces (gain, 2j + x_j): a warp
-// uses one redux.sync on a packed 32-bit (gain, warp-local index) key when the
-// gain bound allows it (|Delta| < 2^21), else two; a block then combines its
-// warps' records from shared memory with a small register tree.
+// coalesced 16-byte loads per thread.  Per element the thread keeps, in
+// registers,
+//     y_j,   S_j = 128 (1 - 2 x_j),   C_j = 64 Q_jj + 2 (31 - e) + x_j,
+// so that the argmax key  key_j = C_j + S_j y_j = 64 Delta_j + 2 (31 - e) + x_j
+// costs one multiply-add.  A move is therefore, per element: y += d q as one
+// dp4a (d placed in the coefficient's byte lane), key = C + S y, and a running
+// max kept in four independent chains.  The key orders by gain, then by lower
+// index inside the thread, and carries x_j in its low bit; across threads the
+// group reduces (gain, 2j + x) with warp max/min reductions (redux.sync), so
+// every thread learns k, x_k and Delta_k.  The thread owning k negates S_k and
+// toggles the x bit of C_k.  Rows are read from L2 (the int8 Q of one
+// instance, e.g. 49 MB at n = 7000, stays resident there); nothing per move
+// goes to HBM.  The chain of moves is latency-bound: per move a dependent L2
+// row fetch, the update and a block-wide reduction.
 //
 // Start-up: y = Q x of every listed start comes from the tensor-core product of
 // the ascent workspace when given (exact integers in fp32), else each group
-// sums the rows k with x_k = 1 on the CUDA cores.  Rows are read from L2 (the
-// int8 Q of one instance, e.g. 49 MB at n = 7000, stays resident there);
-// nothing per move goes to HBM.
+// sums the rows k with x_k = 1 on the CUDA cores.
 #include <climits>
 
 #include "ubqp_internal.cuh"
@@ -43,127 +43,92 @@ __device__ __forceinline__ uint64_t globaltimer() {
   return t;
 }
 
-// Selector placing the signed byte v in lane i (for dp4a).
-__device__ __forceinline__ int lane_sel(int i, int v) {
-  return (int)((unsigned)(v & 0xFF) << (8 * i));
+// acc + d * (signed byte i of w), for d in {-1, +1}, in one dp4a: the second
+// operand holds d in byte i and zeros elsewhere.
+__device__ __forceinline__ int byte_sel(int i, int d) {
+  return (int)((unsigned)(d & 0xFF) << (8 * i));
 }
 
-__device__ __forceinline__ int word_of(const uint4& q, int i) {
-  return (int)(i == 0 ? q.x : i == 1 ? q.y : i == 2 ? q.z : q.w);
-}
-
-// Winner of a group reduction: the move's gain and 2k + x_k.
-struct Win {
-  int gain, jx;
-};
-
-__device__ __forceinline__ bool better(int2 a, int2 b) {
-  return a.x > b.x || (a.x == b.x && a.y < b.y);
-}
-
-// Warp-level best from each thread's best key.  kt = 32 gain + (31 - e),
-// e = the thread's local element, x = its x bit.  PACKED: one redux on
-// gain * 1024 + (1023 - warp-local index); needs |gain| < 2^21.
-template <int T, bool PACKED>
-__device__ __forceinline__ int2 warp_best(int kt, int xbit, int g, int lane) {
-  constexpr int CW = 16 * T;
-  const int gain = kt >> 5;
-  const int e = 31 - (kt & 31);
-  const int wl = (e >> 4) * 512 + lane * 16 + (e & 15);  // order of j within the warp
-  if (PACKED) {
-    // a thread whose elements all lie beyond n carries the INT_MIN sentinel;
-    // clamp it below every real gain so the packed product cannot overflow
-    const int kw = max(gain, -(1 << 21)) * 1024 + (1023 - wl);
-    const int m = __reduce_max_sync(0xffffffffu, kw);
-    const int lw = 1023 - (m & 1023);
-    const int lane_w = (lw >> 4) & 31;
-    const int jw = (lw >> 9) * CW + 16 * (g - lane + lane_w) + (lw & 15);
-    const int xw = __shfl_sync(0xffffffffu, xbit, lane_w);
-    return make_int2(m >> 10, 2 * jw + xw);
-  } else {
-    const int j = (e >> 4) * CW + 16 * g + (e & 15);
-    const int m = __reduce_max_sync(0xffffffffu, gain);
-    const int c = __reduce_min_sync(0xffffffffu, gain == m ? 2 * j + xbit : INT_MAX);
-    return make_int2(m, c);
-  }
-}
+template <int T>
+struct Group;
 
 // One warp per start.
-template <bool PACKED>
-struct WarpGroup {
-  static constexpr int T = 32;
+template <>
+struct Group<32> {
   __device__ __forceinline__ int rank() const { return threadIdx.x & 31; }
-  __device__ __forceinline__ Win reduce(int kt, int xbit) {
-    const int g = rank();
-    const int2 w = warp_best<32, PACKED>(kt, xbit, g, g);
-    return Win{w.x, w.y};
+  // returns {max gain, 2k + x_k} over the group
+  __device__ __forceinline__ int2 reduce(int gain, int jx) {
+    const int m = __reduce_max_sync(0xffffffffu, gain);
+    const int c = __reduce_min_sync(0xffffffffu, gain == m ? jx : INT_MAX);
+    return make_int2(m, c);
   }
   __device__ __forceinline__ bool any(bool p) { return __any_sync(0xffffffffu, p); }
   __device__ __forceinline__ void sync() { __syncwarp(); }
 };
 
 // One block per start.
-template <int TT, bool PACKED>
-struct BlockGroup {
-  static constexpr int T = TT;
-  static constexpr int NW = TT / 32;
-  int2 (*rec)[NW];  // [2][NW] shared: {gain, 2j + x}
+template <int T>
+struct Group {
+  static constexpr int NW = T / 32;
+  int2 (*rec)[NW];  // [2][NW] shared
   int parity;
   __device__ __forceinline__ int rank() const { return threadIdx.x; }
-  __device__ __forceinline__ Win reduce(int kt, int xbit) {
+  __device__ __forceinline__ int2 reduce(int gain, int jx) {
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const int2 w = warp_best<TT, PACKED>(kt, xbit, threadIdx.x, lane);
-    if (lane == 0) rec[parity][warp] = w;
+    const int m = __reduce_max_sync(0xffffffffu, gain);
+    const int c = __reduce_min_sync(0xffffffffu, gain == m ? jx : INT_MAX);
+    if (lane == 0) rec[parity][warp] = make_int2(m, c);
     __syncthreads();
-    // every thread combines the NW records: a tree of pairwise bests
-    int2 r[NW];
-#pragma unroll
-    for (int i = 0; i < NW; i += 2) {
-      const int4 v = *reinterpret_cast<const int4*>(&rec[parity][i]);
-      r[i] = make_int2(v.x, v.y);
-      r[i + 1] = make_int2(v.z, v.w);
-    }
-#pragma unroll
-    for (int step = 1; step < NW; step *= 2)
-#pragma unroll
-      for (int i = 0; i + step < NW; i += 2 * step)
-        if (better(r[i + step], r[i])) r[i] = r[i + step];
+    const int2 r = lane < NW ? rec[parity][lane] : make_int2(INT_MIN, INT_MAX);
+    const int m2 = __reduce_max_sync(0xffffffffu, r.x);
+    const int c2 = __reduce_min_sync(0xffffffffu, r.x == m2 ? r.y : INT_MAX);
     parity ^= 1;
-    return Win{r[0].x, r[0].y};
+    return make_int2(m2, c2);
   }
   __device__ __forceinline__ bool any(bool p) { return __syncthreads_or(p) != 0; }
   __device__ __forceinline__ void sync() { __syncthreads(); }
 };
 
-template <int C, class G>
+template <int T, int C>
 __device__ __forceinline__ void ascend_one(const int8_t* __restrict__ Q8, int64_t ldq,
-                                           int64_t ldy, int n, int W,
-                                           uint64_t* __restrict__ x_g,
+                                           int64_t ldy, int n,
+                                           int W, uint64_t* __restrict__ x_g,
                                            int64_t* __restrict__ f_s, int32_t max_flips,
                                            int32_t* __restrict__ flips_s,
                                            unsigned* __restrict__ err, uint64_t* xs,
-                                           const float* __restrict__ y_g, G& grp) {
-  constexpr int T = G::T;
+                                           const float* __restrict__ y_g, Group<T>& grp) {
   constexpr int E = 16 * C;
   constexpr int CW = 16 * T;  // indices per chunk
   static_assert(E <= 32, "local index must fit 5 bits");
   const int g = grp.rank();
 
-  // ---- owned bits of x
-  uint32_t xm = 0;
+  int y[E], S[E], Ck[E];
+  // ---- owned bits of x; C and S per element
 #pragma unroll
   for (int c = 0; c < C; ++c) {
     const int j0 = c * CW + 16 * g;
+    uint32_t nib = 0;
     if (j0 < n) {
-      uint32_t nib = (uint32_t)((x_g[j0 >> 6] >> (j0 & 63)) & 0xFFFFull);
+      nib = (uint32_t)((x_g[j0 >> 6] >> (j0 & 63)) & 0xFFFFull);
       if (n - j0 < 16) nib &= (1u << (n - j0)) - 1u;
-      xm |= nib << (16 * c);
+    }
+#pragma unroll
+    for (int o = 0; o < 16; ++o) {
+      const int e = c * 16 + o, j = j0 + o;
+      const int xb = (int)((nib >> o) & 1u);
+      y[e] = 0;
+      if (j < n) {
+        const int qjj = Q8[(int64_t)j * ldq + j];
+        S[e] = xb ? -128 : 128;
+        Ck[e] = 64 * qjj + 2 * (31 - e) + xb;
+      } else {
+        S[e] = 0;
+        Ck[e] = INT_MIN;
+      }
     }
   }
-  // ---- y = Q x on the owned columns
-  int key[E];
-#pragma unroll
-  for (int e = 0; e < E; ++e) key[e] = 0;  // holds y until the keys are formed
+  // ---- y = Q x on the owned columns: from the tensor-core start-up when
+  // given (y_g, exact integers in fp32), else by adding the rows k with x_k = 1
   if (y_g) {
 #pragma unroll
     for (int c = 0; c < C; ++c) {
@@ -173,92 +138,68 @@ __device__ __forceinline__ void ascend_one(const int8_t* __restrict__ Q8, int64_
 #pragma unroll
         for (int v = 0; v < 4; ++v) {
           const float4 t4 = src[v];
-          key[c * 16 + 4 * v + 0] = __float2int_rn(t4.x);
-          key[c * 16 + 4 * v + 1] = __float2int_rn(t4.y);
-          key[c * 16 + 4 * v + 2] = __float2int_rn(t4.z);
-          key[c * 16 + 4 * v + 3] = __float2int_rn(t4.w);
+          y[c * 16 + 4 * v + 0] = __float2int_rn(t4.x);
+          y[c * 16 + 4 * v + 1] = __float2int_rn(t4.y);
+          y[c * 16 + 4 * v + 2] = __float2int_rn(t4.z);
+          y[c * 16 + 4 * v + 3] = __float2int_rn(t4.w);
         }
-      }
-    }
-  } else {
-    for (int w = 0; w < W; ++w) {
-      uint64_t word = x_g[w] & valid_mask(n, w);
-      while (word) {
-        constexpr int R = C == 1 ? 4 : 2;  // rows in flight
-        int ks[R];
-        int nk = 0;
-#pragma unroll
-        for (int r = 0; r < R; ++r) {
-          ks[r] = 0;
-          if (word) {
-            ks[r] = w * 64 + __ffsll((long long)word) - 1;
-            word &= word - 1;
-            nk = r + 1;
-          }
-        }
-        uint4 q[R][C];
-#pragma unroll
-        for (int r = 0; r < R; ++r)
-#pragma unroll
-          for (int c = 0; c < C; ++c) {
-            const int j0 = c * CW + 16 * g;
-            q[r][c] = (r < nk && j0 < ldq) ? __ldg(reinterpret_cast<const uint4*>(
-                                                 Q8 + (int64_t)ks[r] * ldq + j0))
-                                           : make_uint4(0, 0, 0, 0);
-          }
-#pragma unroll
-        for (int r = 0; r < R; ++r)
-#pragma unroll
-          for (int c = 0; c < C; ++c)
-#pragma unroll
-            for (int o = 0; o < 16; ++o)
-              key[c * 16 + o] =
-                  __dp4a(word_of(q[r][c], o >> 2), lane_sel(o & 3, 1), key[c * 16 + o]);
       }
     }
   }
-  // ---- keys and selectors; elements beyond n never win and never change
-  int SP[E], SN[E];
+  for (int w = 0; w < W && !y_g; ++w) {
+    uint64_t word = x_g[w] & valid_mask(n, w);
+    while (word) {
+      constexpr int R = C == 1 ? 4 : 2;  // rows in flight
+      int ks[R];
+      int nk = 0;
 #pragma unroll
-  for (int c = 0; c < C; ++c)
-#pragma unroll
-    for (int o = 0; o < 16; ++o) {
-      const int e = c * 16 + o, j = c * CW + 16 * g + o;
-      if (j < n) {
-        const int s = ((xm >> e) & 1u) ? -1 : 1;
-        const int qjj = Q8[(int64_t)j * ldq + j];
-        key[e] = 32 * (qjj + 2 * s * key[e]) + (31 - e);
-        SP[e] = lane_sel(o & 3, 64 * s);
-        SN[e] = lane_sel(o & 3, -64 * s);
-      } else {
-        key[e] = INT_MIN;
-        SP[e] = 0;
-        SN[e] = 0;
+      for (int r = 0; r < R; ++r) {
+        ks[r] = 0;
+        if (word) {
+          ks[r] = w * 64 + __ffsll((long long)word) - 1;
+          word &= word - 1;
+          nk = r + 1;
+        }
       }
-    }
-  auto thread_best = [&]() {
-    int km0 = INT_MIN, km1 = INT_MIN, km2 = INT_MIN, km3 = INT_MIN;
+      uint4 q[R][C];
 #pragma unroll
-    for (int e = 0; e < E; e += 4) {
-      km0 = max(km0, key[e]);
-      km1 = max(km1, key[e + 1]);
-      km2 = max(km2, key[e + 2]);
-      km3 = max(km3, key[e + 3]);
+      for (int r = 0; r < R; ++r)
+#pragma unroll
+        for (int c = 0; c < C; ++c) {
+          const int j0 = c * CW + 16 * g;
+          q[r][c] = (r < nk && j0 < ldq)
+                        ? __ldg(reinterpret_cast<const uint4*>(Q8 + (int64_t)ks[r] * ldq + j0))
+                        : make_uint4(0, 0, 0, 0);
+        }
+#pragma unroll
+      for (int r = 0; r < R; ++r)
+#pragma unroll
+        for (int c = 0; c < C; ++c) {
+          const int wv[4] = {(int)q[r][c].x, (int)q[r][c].y, (int)q[r][c].z, (int)q[r][c].w};
+#pragma unroll
+          for (int o = 0; o < 16; ++o)
+            y[c * 16 + o] = __dp4a(wv[o >> 2], byte_sel(o & 3, 1), y[c * 16 + o]);
+        }
     }
-    return max(max(km0, km1), max(km2, km3));
+  }
+  // ---- first argmax
+  int kmax = INT_MIN;
+#pragma unroll
+  for (int e = 0; e < E; ++e) kmax = max(kmax, Ck[e] + S[e] * y[e]);
+  auto reduce_key = [&](int kt) {
+    const int gain = kt >> 6;
+    const int e = 31 - ((kt >> 1) & 31);
+    const int j = (e >> 4) * CW + 16 * g + (e & 15);
+    return grp.reduce(gain, (j << 1) | (kt & 1));
   };
-  auto reduce_keys = [&](int kt) {
-    const int e = 31 - (kt & 31);
-    return grp.reduce(kt, (int)((xm >> e) & 1u));
-  };
-  Win best = reduce_keys(thread_best());
+  int2 best = reduce_key(kmax);
 
   int64_t fval = *f_s;
   int flips = 0;
   const uint64_t t0 = globaltimer();
   for (;;) {
     if (max_flips > 0 && flips >= max_flips) break;
-    if (best.gain <= 0) break;
+    if (best.x <= 0) break;
     if ((flips & 1023) == 1023) {
       const bool late = (int64_t)(globaltimer() - t0) > kTimeoutNs;
       if (grp.any(late)) {
@@ -266,9 +207,10 @@ __device__ __forceinline__ void ascend_one(const int8_t* __restrict__ Q8, int64_
         break;
       }
     }
-    const int k = best.jx >> 1;
-    const bool dpos = (best.jx & 1) == 0;  // d = 1 - 2 x_k before the flip
-    fval += best.gain;
+    const int k = best.y >> 1;
+    const int d = (best.y & 1) ? -1 : 1;  // 1 - 2 x_k before the flip
+    const int dsel[4] = {byte_sel(0, d), byte_sel(1, d), byte_sel(2, d), byte_sel(3, d)};
+    fval += best.x;
     ++flips;
     const int8_t* row = Q8 + (int64_t)k * ldq;
     uint4 q[C];
@@ -277,41 +219,30 @@ __device__ __forceinline__ void ascend_one(const int8_t* __restrict__ Q8, int64_
       const int j0 = c * CW + 16 * g;
       q[c] = j0 < ldq ? __ldg(reinterpret_cast<const uint4*>(row + j0)) : make_uint4(0, 0, 0, 0);
     }
-    // the owner of k flips x_k: key_k -> key of -Delta_k (pre-corrected for the
-    // -64 Q_kk the generic update below adds with the new selectors), swap the
-    // selectors, toggle the bit
+    // the owner of k flips x_k: negate S_k, toggle the x bit in C_k
     const int kc = k / CW, kr = k - kc * CW;
     if ((kr >> 4) == g) {
-      const int ko = kr & 15, ek = kc * 16 + ko;
-      int qw = 0;
-#pragma unroll
-      for (int c = 0; c < C; ++c)
-        if (c == kc) qw = word_of(q[c], ko >> 2);
-      const int qkk = (int)(int8_t)(qw >> (8 * (ko & 3)));
+      const int ek = kc * 16 + (kr & 15);
 #pragma unroll
       for (int e = 0; e < E; ++e)
         if (e == ek) {
-          key[e] = -key[e] + 2 * (31 - e) + 64 * qkk;
-          const int t = SP[e];
-          SP[e] = SN[e];
-          SN[e] = t;
+          S[e] = -S[e];
+          Ck[e] ^= 1;
         }
-      xm ^= 1u << ek;
     }
-    if (dpos) {
+    int km[4] = {INT_MIN, INT_MIN, INT_MIN, INT_MIN};
 #pragma unroll
-      for (int c = 0; c < C; ++c)
+    for (int c = 0; c < C; ++c) {
+      const int wv[4] = {(int)q[c].x, (int)q[c].y, (int)q[c].z, (int)q[c].w};
 #pragma unroll
-        for (int o = 0; o < 16; ++o)
-          key[c * 16 + o] = __dp4a(word_of(q[c], o >> 2), SP[c * 16 + o], key[c * 16 + o]);
-    } else {
-#pragma unroll
-      for (int c = 0; c < C; ++c)
-#pragma unroll
-        for (int o = 0; o < 16; ++o)
-          key[c * 16 + o] = __dp4a(word_of(q[c], o >> 2), SN[c * 16 + o], key[c * 16 + o]);
+      for (int o = 0; o < 16; ++o) {
+        const int e = c * 16 + o;
+        y[e] = __dp4a(wv[o >> 2], dsel[o & 3], y[e]);
+        km[o & 3] = max(km[o & 3], Ck[e] + S[e] * y[e]);
+      }
     }
-    best = reduce_keys(thread_best());
+    kmax = max(max(km[0], km[1]), max(km[2], km[3]));
+    best = reduce_key(kmax);
   }
   // ---- write back f, flips and x
   if (g == 0) {
@@ -323,7 +254,9 @@ __device__ __forceinline__ void ascend_one(const int8_t* __restrict__ Q8, int64_
 #pragma unroll
   for (int c = 0; c < C; ++c) {
     const int j0 = c * CW + 16 * g;
-    const uint64_t bits = (xm >> (16 * c)) & 0xFFFFu;
+    uint64_t bits = 0;
+#pragma unroll
+    for (int o = 0; o < 16; ++o) bits |= (uint64_t)(Ck[c * 16 + o] & 1 & (S[c * 16 + o] != 0)) << o;
     if (bits) atomicOr(reinterpret_cast<unsigned long long*>(&xs[j0 >> 6]),
                        (unsigned long long)(bits << (j0 & 63)));
   }
@@ -332,16 +265,16 @@ __device__ __forceinline__ void ascend_one(const int8_t* __restrict__ Q8, int64_
   grp.sync();
 }
 
-template <int T, int C, bool PACKED>
+template <int T, int C>
 __global__ void __launch_bounds__(T, 1)
 ascent_block_kernel(const int8_t* __restrict__ Q8, int64_t ldq, int n, int W,
                     uint64_t* __restrict__ X, int64_t* __restrict__ f,
                     const int32_t* __restrict__ idx, const int64_t* __restrict__ count,
                     int64_t S, int32_t max_flips, int32_t* __restrict__ flips,
                     const float* __restrict__ Y, int64_t ldy, unsigned* __restrict__ err) {
-  __shared__ __align__(16) int2 rec[2][T / 32];
+  __shared__ int2 rec[2][T / 32];
   __shared__ uint64_t xs[UBQP_MAX_N / 64];
-  BlockGroup<T, PACKED> grp{rec, 0};
+  Group<T> grp{rec, 0};
   const int64_t cnt = *count;
   for (int64_t t = blockIdx.x; t < cnt; t += gridDim.x) {
     const int s = idx[t];
@@ -349,13 +282,13 @@ ascent_block_kernel(const int8_t* __restrict__ Q8, int64_t ldq, int n, int W,
       if (threadIdx.x == 0) atomicOr(err, UBQP_DEVERR_BADIDX);
       continue;
     }
-    ascend_one<C>(Q8, ldq, ldy, n, W, X + (int64_t)s * W, f + s, max_flips,
-                  flips ? flips + s : nullptr, err, xs, Y ? Y + t * ldy : nullptr, grp);
+    ascend_one<T, C>(Q8, ldq, ldy, n, W, X + (int64_t)s * W, f + s, max_flips,
+                     flips ? flips + s : nullptr, err, xs, Y ? Y + t * ldy : nullptr, grp);
   }
 }
 
 // Four independent warps per block, one start each (n <= 512).
-template <int C, bool PACKED>
+template <int C>
 __global__ void __launch_bounds__(128)
 ascent_warp_kernel(const int8_t* __restrict__ Q8, int64_t ldq, int n, int W,
                    uint64_t* __restrict__ X, int64_t* __restrict__ f,
@@ -363,7 +296,7 @@ ascent_warp_kernel(const int8_t* __restrict__ Q8, int64_t ldq, int n, int W,
                    int64_t S, int32_t max_flips, int32_t* __restrict__ flips,
                    const float* __restrict__ Y, int64_t ldy, unsigned* __restrict__ err) {
   __shared__ uint64_t xs_all[4][16];
-  WarpGroup<PACKED> grp;
+  Group<32> grp;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int64_t cnt = *count;
   for (int64_t t = (int64_t)blockIdx.x * 4 + warp; t < cnt; t += (int64_t)gridDim.x * 4) {
@@ -372,9 +305,9 @@ ascent_warp_kernel(const int8_t* __restrict__ Q8, int64_t ldq, int n, int W,
       if (lane == 0) atomicOr(err, UBQP_DEVERR_BADIDX);
       continue;
     }
-    ascend_one<C>(Q8, ldq, ldy, n, W, X + (int64_t)s * W, f + s, max_flips,
-                  flips ? flips + s : nullptr, err, xs_all[warp], Y ? Y + t * ldy : nullptr,
-                  grp);
+    ascend_one<32, C>(Q8, ldq, ldy, n, W, X + (int64_t)s * W, f + s, max_flips,
+                      flips ? flips + s : nullptr, err, xs_all[warp],
+                      Y ? Y + t * ldy : nullptr, grp);
   }
 }
 
@@ -390,51 +323,27 @@ int resident_grid(K kernel, int threads, int sm_count) {
   return per_sm * sm_count;
 }
 
-struct Args {
-  const ubqp_q* h;
-  uint64_t* X;
-  int64_t* f;
-  const int32_t* idx;
-  const int64_t* count;
-  int64_t S;
-  int32_t max_flips;
-  int32_t* flips;
-  const float* Y;
-  cudaStream_t st;
-};
-
-template <int T, int C, bool PACKED>
-cudaError_t launch_block(const Args& a) {
-  auto kern = ascent_block_kernel<T, C, PACKED>;
-  int grid = resident_grid(kern, T, a.h->sm_count);
-  if ((int64_t)grid > a.S) grid = (int)a.S;
-  kern<<<grid, T, 0, a.st>>>(a.h->Q8, a.h->ldq, a.h->n, a.h->W, a.X, a.f, a.idx, a.count, a.S,
-                             a.max_flips, a.flips, a.Y, a.h->n_tc, a.h->err);
+template <int T, int C>
+cudaError_t launch_block(const ubqp_q* h, uint64_t* X, int64_t* f, const int32_t* idx,
+                         const int64_t* count, int64_t S, int32_t max_flips, int32_t* flips,
+                         const float* Y, cudaStream_t st) {
+  int grid = resident_grid(ascent_block_kernel<T, C>, T, h->sm_count);
+  if ((int64_t)grid > S) grid = (int)S;
+  ascent_block_kernel<T, C><<<grid, T, 0, st>>>(h->Q8, h->ldq, h->n, h->W, X, f, idx, count,
+                                                S, max_flips, flips, Y, h->n_tc, h->err);
   return cudaGetLastError();
 }
 
-template <int C, bool PACKED>
-cudaError_t launch_warp(const Args& a) {
-  auto kern = ascent_warp_kernel<C, PACKED>;
-  int grid = resident_grid(kern, 128, a.h->sm_count);
-  const int64_t need = (a.S + 3) / 4;
+template <int C>
+cudaError_t launch_warp(const ubqp_q* h, uint64_t* X, int64_t* f, const int32_t* idx,
+                        const int64_t* count, int64_t S, int32_t max_flips, int32_t* flips,
+                        const float* Y, cudaStream_t st) {
+  int grid = resident_grid(ascent_warp_kernel<C>, 128, h->sm_count);
+  const int64_t need = (S + 3) / 4;
   if ((int64_t)grid > need) grid = (int)need;
-  kern<<<grid, 128, 0, a.st>>>(a.h->Q8, a.h->ldq, a.h->n, a.h->W, a.X, a.f, a.idx, a.count,
-                               a.S, a.max_flips, a.flips, a.Y, a.h->n_tc, a.h->err);
+  ascent_warp_kernel<C><<<grid, 128, 0, st>>>(h->Q8, h->ldq, h->n, h->W, X, f, idx, count, S,
+                                              max_flips, flips, Y, h->n_tc, h->err);
   return cudaGetLastError();
-}
-
-template <bool PACKED>
-cudaError_t launch_sized(const Args& a) {
-  const int n = a.h->n;
-  if (n <= 256) return launch_warp<1, PACKED>(a);
-  if (n <= 512) return launch_warp<2, PACKED>(a);
-  if (n <= 1024) return launch_block<64, 1, PACKED>(a);
-  if (n <= 2048) return launch_block<128, 1, PACKED>(a);
-  if (n <= 4096) return launch_block<256, 1, PACKED>(a);
-  if (n <= 8192) return launch_block<256, 2, PACKED>(a);
-  if (n <= 16384) return launch_block<512, 2, PACKED>(a);
-  return cudaErrorInvalidValue;
 }
 
 }  // namespace
@@ -442,11 +351,15 @@ cudaError_t launch_sized(const Args& a) {
 cudaError_t launch_ascent(const ubqp_q* h, uint64_t* X, int64_t* f, const int32_t* idx,
                           const int64_t* count, int64_t S, int32_t max_flips, int32_t* flips,
                           const float* Y, cudaStream_t st) {
-  const Args a{h, X, f, idx, count, S, max_flips, flips, Y, st};
-  // |Delta_j| <= |Q_jj| + 2 sum_k |Q_jk| <= max|Q| (2n + 1): the packed key
-  // holds gains below 2^21 in magnitude
-  const int64_t bound = (int64_t)h->max_abs * (2 * (int64_t)h->n + 1);
-  return bound < (1 << 21) ? launch_sized<true>(a) : launch_sized<false>(a);
+  const int n = h->n;
+  if (n <= 256) return launch_warp<1>(h, X, f, idx, count, S, max_flips, flips, Y, st);
+  if (n <= 512) return launch_warp<2>(h, X, f, idx, count, S, max_flips, flips, Y, st);
+  if (n <= 1024) return launch_block<64, 1>(h, X, f, idx, count, S, max_flips, flips, Y, st);
+  if (n <= 2048) return launch_block<128, 1>(h, X, f, idx, count, S, max_flips, flips, Y, st);
+  if (n <= 4096) return launch_block<256, 1>(h, X, f, idx, count, S, max_flips, flips, Y, st);
+  if (n <= 8192) return launch_block<512, 1>(h, X, f, idx, count, S, max_flips, flips, Y, st);
+  if (n <= 16384) return launch_block<512, 2>(h, X, f, idx, count, S, max_flips, flips, Y, st);
+  return cudaErrorInvalidValue;
 }
 
 }  // namespace ubqp
