@@ -123,6 +123,30 @@ class ClockSampler:
                 "samples": len(rows)}
 
 
+def profiled_traffic(summary: str, key: str):
+    """DRAM bytes per launch recorded in a committed ncu summary, or None when
+    the kernel's source changed since the capture (sha256 prefix recorded)."""
+    import hashlib
+    try:
+        text = open(os.path.join(ROOT, "profiles", summary)).read()
+    except OSError:
+        return None
+    val, src, digest = None, None, None
+    for line in text.splitlines():
+        if line.startswith(key + ":"):
+            val = int(line.split(":")[1])
+        if line.startswith("source:"):
+            parts = line.split()
+            src, digest = parts[1], parts[-1]
+    if val is None or src is None:
+        return None
+    try:
+        now = hashlib.sha256(open(os.path.join(ROOT, src), "rb").read()).hexdigest()[:16]
+    except OSError:
+        return None
+    return val if now == digest else None
+
+
 # --------------------------------------------------------------------- oracle arm
 
 def cpu_sample(a, Q, S_cpu, seed):
@@ -330,7 +354,8 @@ def main():
                 "achieved": asc_ops / asc_s / 1e12 if asc_s > 0 else None,
                 "peak": alu_peak / 1e12, "unit": "Tops/s (int32)",
                 "frac": (asc_ops / asc_s) / alu_peak if asc_s > 0 else None,
-                "traffic": None,
+                "traffic": profiled_traffic("ascent_block_n7000_dense.md",
+                                            "traffic_bytes_per_launch") if n == 7000 else None,
                 "peak_source": f"derived: {n_sm} SMs x 128 INT32 lanes x {sm_max:.0f} MHz"}
     eval_s = per[:, 1].sum() / 1e3
     eval_flops = float(S) * n * (n + 1) * a.steps  # 2 * S * n(n+1)/2 triangle MACs
@@ -345,7 +370,9 @@ def main():
                      "achieved": eval_flops / 2 / eval_s / 1e12, "unit": "Tops/s (int32)",
                      "peak": alu_peak / 1e12 * 4, "peak_source": "dp4a: 4 MACs per lane-op"}
     roof_eval["frac"] = roof_eval["achieved"] / roof_eval["peak"]
-    roof_eval["traffic"] = None
+    roof_eval["traffic"] = (profiled_traffic("eval_tc_n7000_dense.md",
+                                             "traffic_bytes_per_launch_eval")
+                            if n == 7000 and tc == ubqp.EVAL_TC else None)
     roofline = roof_asc if dom == "ascent" else dict(roof_eval)
 
     # ---- end to end through the public API with host buffers: H2D of the
