@@ -125,6 +125,13 @@ int ubqp_first_derivative(const ubqp_q* q, uint64_t* x0_dev, void* stream);
 int ubqp_diversify(const ubqp_q* q, const uint64_t* x0_dev, int32_t mode,
                    uint64_t seed, uint64_t round, int64_t S, int32_t div_H,
                    uint64_t* X_dev, void* stream);
+/* Starts s_begin .. s_begin+S_local-1 of a batch of S_total (loop counters
+ * round*S_total + s, RANDOM streams s), written to X_dev[0 .. S_local*W): the
+ * slice of ubqp_diversify's output that one rank of a sharded batch needs. */
+int ubqp_diversify_range(const ubqp_q* q, const uint64_t* x0_dev, int32_t mode,
+                         uint64_t seed, uint64_t round, int64_t S_total,
+                         int64_t s_begin, int64_t S_local, int32_t div_H,
+                         uint64_t* X_dev, void* stream);
 
 /*
  * ubqp_eval -- Evaluate(x) of Fig. 2 for a batch: f_dev[s] = x_s^t Q x_s (int64),
@@ -177,7 +184,7 @@ int ubqp_eval_noalloc(const ubqp_q* q, const uint64_t* X_dev, int64_t S,
  *   idx_dev     S int32: the passing indices, ascending, in idx_dev[0..count).
  *   count_dev   1 int64: their number.
  *   Tm_dev      2 doubles: {T, Mean}.
- *   stats_dev   3 int64: {Max, lowest index attaining Max, sum of f}.
+ *   stats_dev   3 int64: {sum of f, Max, lowest index attaining Max}.
  * The sum is exact in int64; Mean = sum / S, then T = Mean + lambda*(Max - Mean)
  * as one subtraction, one multiplication and one addition in double, each
  * rounded to nearest (no fused multiply-add).  Requires 1 <= S < 2^31.
@@ -185,6 +192,26 @@ int ubqp_eval_noalloc(const ubqp_q* q, const uint64_t* X_dev, int64_t S,
 int ubqp_screen(const int64_t* f_dev, int64_t S, double lambda, int32_t* idx_dev,
                 int64_t* count_dev, double* Tm_dev, int64_t* stats_dev,
                 void* stream);
+
+/*
+ * The screen in two steps, for a batch sharded over several ranks (each rank
+ * holding a contiguous range of the starts):
+ * ubqp_screen_stats -- stats_dev (3 int64) = {sum of f, Max, lowest index
+ *   attaining Max + offset} over this rank's S values (offset = the global
+ *   index of its first start).  The ranks combine these exactly (sum: add;
+ *   Max: max; index: the lowest among the ranks attaining the global Max).
+ * ubqp_screen_apply -- with the combined gstats_dev {sum, Max, ...} of all
+ *   S_total starts: Tm_dev = {T, Mean} computed as in ubqp_screen (every rank
+ *   obtains the identical T), then the passing local indices of this rank's
+ *   f_dev, ascending, in idx_dev[0 .. *count_dev).
+ * ubqp_screen is ubqp_screen_stats (offset 0) followed by ubqp_screen_apply
+ * with S_total = S.  Both async.
+ */
+int ubqp_screen_stats(const int64_t* f_dev, int64_t S, int64_t offset,
+                      int64_t* stats_dev, void* stream);
+int ubqp_screen_apply(const int64_t* f_dev, int64_t S, const int64_t* gstats_dev,
+                      int64_t S_total, double lambda, int32_t* idx_dev,
+                      int64_t* count_dev, double* Tm_dev, void* stream);
 
 /*
  * ubqp_ascent -- PerformSteepestAscent(x, xQx, max_its) of Fig. 2 for the

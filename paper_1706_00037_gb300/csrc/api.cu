@@ -195,18 +195,27 @@ int ubqp_first_derivative(const ubqp_q* q, uint64_t* x0_dev, void* stream) {
   return UBQP_OK;
 }
 
-int ubqp_diversify(const ubqp_q* q, const uint64_t* x0_dev, int32_t mode, uint64_t seed,
-                   uint64_t round, int64_t S, int32_t div_H, uint64_t* X_dev, void* stream) {
+int ubqp_diversify_range(const ubqp_q* q, const uint64_t* x0_dev, int32_t mode, uint64_t seed,
+                         uint64_t round, int64_t S_total, int64_t s_begin, int64_t S_local,
+                         int32_t div_H, uint64_t* X_dev, void* stream) {
   if (!q || !X_dev) return fail(UBQP_ERR_ARG, "NULL argument");
-  if (S < 0) return fail(UBQP_ERR_ARG, "S < 0");
+  if (S_total < 0 || s_begin < 0 || S_local < 0 || s_begin + S_local > S_total)
+    return fail(UBQP_ERR_ARG, "range [%lld, %lld) outside a batch of %lld", (long long)s_begin,
+                (long long)(s_begin + S_local), (long long)S_total);
   if (mode != UBQP_MODE_RANDOM && mode != UBQP_MODE_DIVERSIFY)
     return fail(UBQP_ERR_ARG, "unknown mode %d", mode);
   if (mode == UBQP_MODE_DIVERSIFY && div_H < 1) return fail(UBQP_ERR_ARG, "div_H < 1");
-  if (S == 0) return UBQP_OK;
+  if (S_local == 0) return UBQP_OK;
   const uint64_t* x0 = x0_dev ? x0_dev : q->x0;
-  UBQP_CUDA(ubqp::launch_diversify(x0, q->n, mode, seed, round, S, div_H, X_dev,
-                                   (cudaStream_t)stream));
+  UBQP_CUDA(ubqp::launch_diversify(x0, q->n, mode, seed, round, S_total, s_begin, S_local, div_H,
+                                   X_dev, (cudaStream_t)stream));
   return UBQP_OK;
+}
+
+int ubqp_diversify(const ubqp_q* q, const uint64_t* x0_dev, int32_t mode, uint64_t seed,
+                   uint64_t round, int64_t S, int32_t div_H, uint64_t* X_dev, void* stream) {
+  if (S < 0) return fail(UBQP_ERR_ARG, "S < 0");
+  return ubqp_diversify_range(q, x0_dev, mode, seed, round, S, 0, S, div_H, X_dev, stream);
 }
 
 size_t ubqp_eval_workspace_size(const ubqp_q* q, int64_t S, int32_t path) {
@@ -267,6 +276,31 @@ int ubqp_eval_noalloc(const ubqp_q* q, const uint64_t* X_dev, int64_t S, int64_t
   return UBQP_OK;
 }
 
+int ubqp_screen_stats(const int64_t* f_dev, int64_t S, int64_t offset, int64_t* stats_dev,
+                      void* stream) {
+  if (!f_dev || !stats_dev) return fail(UBQP_ERR_ARG, "NULL argument");
+  if (S < 0 || S >= ((int64_t)1 << 31) || offset < 0)
+    return fail(UBQP_ERR_ARG, "S=%lld or offset=%lld out of range", (long long)S,
+                (long long)offset);
+  UBQP_CUDA(ubqp::launch_screen_stats(f_dev, S, offset, stats_dev, (cudaStream_t)stream));
+  return UBQP_OK;
+}
+
+int ubqp_screen_apply(const int64_t* f_dev, int64_t S, const int64_t* gstats_dev,
+                      int64_t S_total, double lambda, int32_t* idx_dev, int64_t* count_dev,
+                      double* Tm_dev, void* stream) {
+  if (!f_dev || !gstats_dev || !idx_dev || !count_dev || !Tm_dev)
+    return fail(UBQP_ERR_ARG, "NULL argument");
+  if (S < 0 || S >= ((int64_t)1 << 31) || S_total < 1 || S_total < S)
+    return fail(UBQP_ERR_ARG, "S=%lld / S_total=%lld out of range", (long long)S,
+                (long long)S_total);
+  if (!(lambda == lambda) || lambda > 1e300 || lambda < -1e300)
+    return fail(UBQP_ERR_ARG, "lambda is not finite");
+  UBQP_CUDA(ubqp::launch_screen_apply(f_dev, S, gstats_dev, S_total, lambda, idx_dev, count_dev,
+                                      Tm_dev, (cudaStream_t)stream));
+  return UBQP_OK;
+}
+
 int ubqp_screen(const int64_t* f_dev, int64_t S, double lambda, int32_t* idx_dev,
                 int64_t* count_dev, double* Tm_dev, int64_t* stats_dev, void* stream) {
   if (!f_dev || !idx_dev || !count_dev || !Tm_dev || !stats_dev)
@@ -274,8 +308,10 @@ int ubqp_screen(const int64_t* f_dev, int64_t S, double lambda, int32_t* idx_dev
   if (S < 1 || S >= ((int64_t)1 << 31)) return fail(UBQP_ERR_ARG, "S=%lld outside [1, 2^31)", (long long)S);
   if (!(lambda == lambda) || lambda > 1e300 || lambda < -1e300)
     return fail(UBQP_ERR_ARG, "lambda is not finite");
-  UBQP_CUDA(ubqp::launch_screen(f_dev, S, lambda, idx_dev, count_dev, Tm_dev, stats_dev,
-                                (cudaStream_t)stream));
+  int r;
+  if ((r = ubqp_screen_stats(f_dev, S, 0, stats_dev, stream))) return r;
+  if ((r = ubqp_screen_apply(f_dev, S, stats_dev, S, lambda, idx_dev, count_dev, Tm_dev, stream)))
+    return r;
   return UBQP_OK;
 }
 

@@ -74,9 +74,9 @@ solve_stats_kernel(const int64_t* __restrict__ count, const int32_t* __restrict_
     out[0] = c;
     out[1] = t;
     out[2] = m;
-    out[3] = sstats[0];
+    out[3] = sstats[1];
     out[4] = best[1];
-    out[5] = sstats[2];
+    out[5] = sstats[0];
   }
 }
 

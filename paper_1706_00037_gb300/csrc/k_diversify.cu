@@ -7,14 +7,18 @@
 namespace ubqp {
 namespace {
 
+// Starts s_begin .. s_begin + S_local - 1 of a batch of S_total (loop counter
+// i = round * S_total + s), written to X[(s - s_begin) * W + w].
 __global__ void diversify_words(const uint64_t* __restrict__ x0, int n, int W, int mode,
-                                uint64_t seed, uint64_t round, int64_t S, int div_H,
-                                uint64_t* __restrict__ X) {
-  const int64_t total = S * W;
+                                uint64_t seed, uint64_t round, int64_t S_total, int64_t s_begin,
+                                int64_t S_local, int div_H, uint64_t* __restrict__ X) {
+  const int64_t total = S_local * W;
+  const int64_t S = S_total;
   for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < total;
        t += (int64_t)gridDim.x * blockDim.x) {
-    const int64_t s = t / W;
-    const int w = (int)(t - s * W);
+    const int64_t sl = t / W;
+    const int w = (int)(t - sl * W);
+    const int64_t s = s_begin + sl;
     uint64_t v;
     if (mode == UBQP_MODE_RANDOM) {
       v = stream_word(seed, (uint64_t)s, (uint64_t)w);
@@ -50,14 +54,14 @@ __global__ void diversify_words(const uint64_t* __restrict__ x0, int n, int W, i
 }  // namespace
 
 cudaError_t launch_diversify(const uint64_t* x0, int n, int mode, uint64_t seed,
-                             uint64_t round, int64_t S, int div_H, uint64_t* X,
-                             cudaStream_t st) {
+                             uint64_t round, int64_t S_total, int64_t s_begin,
+                             int64_t S_local, int div_H, uint64_t* X, cudaStream_t st) {
   const int W = (int)words_of(n);
-  int64_t total = S * W;
+  int64_t total = S_local * W;
   int64_t blocks = (total + 255) / 256;
   if (blocks > 152 * 16) blocks = 152 * 16;
-  diversify_words<<<(unsigned)blocks, 256, 0, st>>>(x0, n, W, mode, seed, round, S, div_H,
-                                                   X);
+  diversify_words<<<(unsigned)blocks, 256, 0, st>>>(x0, n, W, mode, seed, round, S_total,
+                                                   s_begin, S_local, div_H, X);
   return cudaGetLastError();
 }
 

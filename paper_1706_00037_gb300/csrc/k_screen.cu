@@ -1,8 +1,10 @@
 // k_screen.cu -- the screen of the Pseudocode section: T(lambda) = Mean +
 // lambda (Max - Mean) over the batch, then the stable list of indices with
-// f_b > T (Fig. 2).  One block: an exact int64 sum and a max (lowest index on
-// ties) by warp shuffles, the threshold in double with explicitly rounded
-// operations (no FMA), then a block-wide ballot/prefix-sum compaction.
+// f_b > T (Fig. 2).  Two single-block kernels: the statistics (an exact int64
+// sum and a max with its lowest index, by warp shuffles), and the threshold in
+// double with explicitly rounded operations (no FMA) followed by a block-wide
+// ballot/prefix-sum compaction.  The split lets a batch sharded over ranks
+// combine the statistics before the threshold.
 #include <climits>
 
 #include "ubqp_internal.cuh"
@@ -13,17 +15,14 @@ namespace {
 constexpr int THREADS = 1024;
 constexpr int WARPS = THREADS / 32;
 
+// stats = {sum of f, max f, lowest index attaining it + offset}
 __global__ void __launch_bounds__(THREADS)
-screen_kernel(const int64_t* __restrict__ f, int64_t S, double lambda,
-              int32_t* __restrict__ idx, int64_t* __restrict__ count, double* __restrict__ Tm,
-              int64_t* __restrict__ stats) {
+screen_stats_kernel(const int64_t* __restrict__ f, int64_t S, int64_t offset,
+                    int64_t* __restrict__ stats) {
   __shared__ long long s_sum[WARPS];
   __shared__ long long s_max[WARPS];
   __shared__ long long s_arg[WARPS];
-  __shared__ int s_cnt[WARPS];
-  __shared__ double s_T;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-
   long long sum = 0, mx = LLONG_MIN, am = LLONG_MAX;
   for (int64_t b = threadIdx.x; b < S; b += THREADS) {
     long long v = f[b];
@@ -45,20 +44,32 @@ screen_kernel(const int64_t* __restrict__ f, int64_t S, double lambda,
       t += s_sum[i];
       if (s_max[i] > m || (s_max[i] == m && s_arg[i] < a)) { m = s_max[i]; a = s_arg[i]; }
     }
-    const double mean = __ddiv_rn(__ll2double_rn(t), __ll2double_rn(S));
-    const double diff = __dsub_rn(__ll2double_rn(m), mean);
+    stats[0] = t;
+    stats[1] = m;
+    stats[2] = (S > 0) ? a + offset : LLONG_MAX;
+  }
+}
+
+// T from the (possibly multi-rank) stats, then the stable list of local
+// indices with f_b > T.
+__global__ void __launch_bounds__(THREADS)
+screen_apply_kernel(const int64_t* __restrict__ f, int64_t S, const int64_t* __restrict__ gstats,
+                    int64_t S_total, double lambda, int32_t* __restrict__ idx,
+                    int64_t* __restrict__ count, double* __restrict__ Tm) {
+  __shared__ int s_cnt[WARPS];
+  __shared__ double s_T;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  if (threadIdx.x == 0) {
+    const double mean = __ddiv_rn(__ll2double_rn(gstats[0]), __ll2double_rn(S_total));
+    const double diff = __dsub_rn(__ll2double_rn(gstats[1]), mean);
     const double scaled = __dmul_rn(lambda, diff);
     const double T = __dadd_rn(mean, scaled);
     s_T = T;
     Tm[0] = T;
     Tm[1] = mean;
-    stats[0] = m;
-    stats[1] = a;
-    stats[2] = t;
   }
   __syncthreads();
   const double T = s_T;
-  // stable compaction, THREADS values per pass
   int64_t base = 0;
   for (int64_t b0 = 0; b0 < S; b0 += THREADS) {
     const int64_t b = b0 + threadIdx.x;
@@ -81,9 +92,16 @@ screen_kernel(const int64_t* __restrict__ f, int64_t S, double lambda,
 
 }  // namespace
 
-cudaError_t launch_screen(const int64_t* f, int64_t S, double lambda, int32_t* idx,
-                          int64_t* count, double* Tm, int64_t* stats, cudaStream_t st) {
-  screen_kernel<<<1, THREADS, 0, st>>>(f, S, lambda, idx, count, Tm, stats);
+cudaError_t launch_screen_stats(const int64_t* f, int64_t S, int64_t offset, int64_t* stats,
+                                cudaStream_t st) {
+  screen_stats_kernel<<<1, THREADS, 0, st>>>(f, S, offset, stats);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_screen_apply(const int64_t* f, int64_t S, const int64_t* gstats,
+                                int64_t S_total, double lambda, int32_t* idx, int64_t* count,
+                                double* Tm, cudaStream_t st) {
+  screen_apply_kernel<<<1, THREADS, 0, st>>>(f, S, gstats, S_total, lambda, idx, count, Tm);
   return cudaGetLastError();
 }
 

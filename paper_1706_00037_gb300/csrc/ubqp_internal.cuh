@@ -70,8 +70,8 @@ __host__ __device__ __forceinline__ uint64_t valid_mask(int64_t n, int64_t w) {
 cudaError_t launch_prepare(const int8_t* Q, int n, int64_t ldq_in, ubqp_q* h,
                            cudaStream_t st);
 cudaError_t launch_diversify(const uint64_t* x0, int n, int mode, uint64_t seed,
-                             uint64_t round, int64_t S, int div_H, uint64_t* X,
-                             cudaStream_t st);
+                             uint64_t round, int64_t S_total, int64_t s_begin,
+                             int64_t S_local, int div_H, uint64_t* X, cudaStream_t st);
 cudaError_t launch_eval_plain(const ubqp_q* h, const uint64_t* X, int64_t S,
                               int64_t* f, cudaStream_t st);
 size_t eval_tc_workspace(const ubqp_q* h, int64_t S);
@@ -84,8 +84,11 @@ cudaError_t launch_ascent_init_tc(const ubqp_q* h, const uint64_t* X, const int3
 cudaError_t eval_tc_static_scratch(void** out);
 cudaError_t launch_eval_tc(const ubqp_q* h, const uint64_t* X, int64_t S, int64_t* f,
                            void* ws, size_t ws_bytes, cudaStream_t st);
-cudaError_t launch_screen(const int64_t* f, int64_t S, double lambda, int32_t* idx,
-                          int64_t* count, double* Tm, int64_t* stats, cudaStream_t st);
+cudaError_t launch_screen_stats(const int64_t* f, int64_t S, int64_t offset, int64_t* stats,
+                                cudaStream_t st);
+cudaError_t launch_screen_apply(const int64_t* f, int64_t S, const int64_t* gstats,
+                                int64_t S_total, double lambda, int32_t* idx, int64_t* count,
+                                double* Tm, cudaStream_t st);
 cudaError_t launch_ascent(const ubqp_q* h, uint64_t* X, int64_t* f, const int32_t* idx,
                           const int64_t* count, int64_t S, int32_t max_flips,
                           int32_t* flips, const float* Y, cudaStream_t st);

@@ -25,8 +25,8 @@ STATUS_NAMES = {0: "OK", -1: "ERR_ARG", -2: "ERR_NOT_SYMMETRIC", -3: "ERR_RANGE"
 
 EXPORTS = ["ubqp_strerror", "ubqp_last_error", "ubqp_abi_version", "ubqp_q_prepare",
            "ubqp_q_destroy", "ubqp_q_info", "ubqp_sync", "ubqp_first_derivative",
-           "ubqp_diversify", "ubqp_eval_workspace_size", "ubqp_eval", "ubqp_eval_noalloc",
-           "ubqp_screen",
+           "ubqp_diversify", "ubqp_diversify_range", "ubqp_eval_workspace_size", "ubqp_eval",
+           "ubqp_eval_noalloc", "ubqp_screen", "ubqp_screen_stats", "ubqp_screen_apply",
            "ubqp_ascent_workspace_size", "ubqp_ascent", "ubqp_best", "ubqp_solve_workspace_size",
            "ubqp_solve"]
 
@@ -82,10 +82,13 @@ def load() -> ctypes.CDLL:
         "ubqp_sync": (ctypes.c_int, [P, P]),
         "ubqp_first_derivative": (ctypes.c_int, [P, P, P]),
         "ubqp_diversify": (ctypes.c_int, [P, P, i32, u64, u64, i64, i32, P, P]),
+        "ubqp_diversify_range": (ctypes.c_int, [P, P, i32, u64, u64, i64, i64, i64, i32, P, P]),
         "ubqp_eval_workspace_size": (sz, [P, i64, i32]),
         "ubqp_eval": (ctypes.c_int, [P, P, i64, P, i32, P, sz, P]),
         "ubqp_eval_noalloc": (ctypes.c_int, [P, P, i64, P, P]),
         "ubqp_screen": (ctypes.c_int, [P, i64, f64, P, P, P, P, P]),
+        "ubqp_screen_stats": (ctypes.c_int, [P, i64, i64, P, P]),
+        "ubqp_screen_apply": (ctypes.c_int, [P, i64, P, i64, f64, P, P, P, P]),
         "ubqp_ascent_workspace_size": (sz, [P, i64]),
         "ubqp_ascent": (ctypes.c_int, [P, P, P, P, P, i64, i32, P, P, sz, P]),
         "ubqp_best": (ctypes.c_int, [P, P, i64, i32, P, P, P]),
@@ -178,6 +181,38 @@ def diversify(inst: Instance, S: int, mode: int = DIVERSIFY, seed: int = 0, roun
     _check(load().ubqp_diversify(inst.handle, _ptr(x0), mode, seed % 2**64, round_, S, div_H,
                                  _ptr(X), _stream(stream)))
     return X
+
+
+def diversify_range(inst: Instance, S_total: int, s_begin: int, S_local: int,
+                    mode: int = DIVERSIFY, seed: int = 0, round_: int = 0, div_H: int = 64,
+                    x0: torch.Tensor | None = None, out: torch.Tensor | None = None,
+                    stream=None) -> torch.Tensor:
+    X = out if out is not None else torch.empty((S_local, inst.words), dtype=torch.int64,
+                                                device=inst.device)
+    _check(load().ubqp_diversify_range(inst.handle, _ptr(x0), mode, seed % 2**64, round_,
+                                       S_total, s_begin, S_local, div_H, _ptr(X),
+                                       _stream(stream)))
+    return X
+
+
+def screen_stats(f: torch.Tensor, offset: int = 0, out: torch.Tensor | None = None,
+                 stream=None) -> torch.Tensor:
+    """{sum, max, lowest argmax + offset} of f (int64[3], on f's device)."""
+    st = out if out is not None else torch.empty(3, dtype=torch.int64, device=f.device)
+    _check(load().ubqp_screen_stats(_ptr(f), f.shape[0], offset, _ptr(st), _stream(stream)))
+    return st
+
+
+def screen_apply(f: torch.Tensor, gstats: torch.Tensor, S_total: int, lam: float,
+                 stream=None) -> dict:
+    S = f.shape[0]
+    dev = f.device
+    idx = torch.empty(max(S, 1), dtype=torch.int32, device=dev)
+    count = torch.empty(1, dtype=torch.int64, device=dev)
+    Tm = torch.empty(2, dtype=torch.float64, device=dev)
+    _check(load().ubqp_screen_apply(_ptr(f), S, _ptr(gstats), S_total, float(lam), _ptr(idx),
+                                    _ptr(count), _ptr(Tm), _stream(stream)))
+    return {"idx": idx, "count": count, "Tm": Tm}
 
 
 def eval_workspace_size(inst: Instance, S: int, path: int = EVAL_AUTO) -> int:

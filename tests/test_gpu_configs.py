@@ -45,8 +45,8 @@ def check_round(Q, n, S, lam, mode, seed, r, x0, n_eval=4, n_climb=2):
     assert np.array_equal(r["f0"][pick], orc.eval(Q, Xh[pick]))
     # screen: properties at any size
     f0 = r["f0"]
-    assert r["stats"][0] == f0.max() and r["stats"][1] == int(np.argmax(f0))
-    assert r["stats"][2] == int(f0.sum())
+    assert r["stats"][1] == f0.max() and r["stats"][2] == int(np.argmax(f0))
+    assert r["stats"][0] == int(f0.sum())
     assert r["mean"] == float(np.float64(int(f0.sum())) / np.float64(S))
     assert list(r["idx"]) == [b for b in range(S) if float(f0[b]) > r["T"]]
     # ascent of sampled passers against the oracle

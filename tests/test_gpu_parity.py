@@ -185,7 +185,7 @@ def test_screen_matches_oracle(S, lam):
     assert np.array_equal(out["idx"][:c].cpu().numpy(), want["idx"])
     Tm = out["Tm"].cpu().numpy()
     assert Tm[0] == want["T"] and Tm[1] == want["mean"]
-    assert list(out["stats"].cpu().numpy()) == [want["max"], want["argmax"], want["sum"]]
+    assert list(out["stats"].cpu().numpy()) == [want["sum"], want["max"], want["argmax"]]
 
 
 def test_screen_all_equal_and_threshold_ties():
