@@ -201,9 +201,11 @@ int ubqp_screen(const int64_t* f_dev, int64_t S, double lambda, int32_t* idx_dev
  *   index of its first start).  The ranks combine these exactly (sum: add;
  *   Max: max; index: the lowest among the ranks attaining the global Max).
  * ubqp_screen_apply -- with the combined gstats_dev {sum, Max, ...} of all
- *   S_total starts: Tm_dev = {T, Mean} computed as in ubqp_screen (every rank
- *   obtains the identical T), then the passing local indices of this rank's
- *   f_dev, ascending, in idx_dev[0 .. *count_dev).
+ *   S_total starts: Tm_dev = {T, Mean} computed as in ubqp_screen with
+ *   Mean = sum / S_total (every rank obtains the identical T), then the passing
+ *   local indices of this rank's f_dev, ascending, in idx_dev[0 .. *count_dev).
+ *   (ubqp_search uses it with the random sample's sum and size and the
+ *   incumbent's value as Max.)
  * ubqp_screen is ubqp_screen_stats (offset 0) followed by ubqp_screen_apply
  * with S_total = S.  Both async.
  */
@@ -281,6 +283,39 @@ size_t ubqp_solve_workspace_size(const ubqp_q* q, const ubqp_params* p);
 int ubqp_solve(const ubqp_q* q, const ubqp_params* p, uint64_t* best_x_dev,
                int64_t* best_f_dev, ubqp_stats* stats_host, void* ws,
                size_t ws_bytes, void* stream);
+
+/* The search of Fig. 2, run in rounds of starts_per_round starts. */
+typedef struct ubqp_search_params {
+  int64_t num_samples;      /* random solutions behind Mean (EvaluateRandomStarts) */
+  int64_t starts_per_round; /* S: starts per round (the loop body on a batch)      */
+  int32_t rounds;           /* rounds; loop counters run 0 .. rounds*S - 1         */
+  int32_t max_flips;        /* ascent cap per start, 0 = none                      */
+  double lambda;            /* screening parameter                                 */
+  uint64_t seed;            /* seed of the sample and of the diversification       */
+  int32_t div_H;            /* h-pattern period bound (>= 1)                       */
+  int32_t eval_path;        /* UBQP_EVAL_*                                          */
+} ubqp_search_params;
+
+/*
+ * ubqp_search -- the whole loop of Fig. 2 on the device, batched by rounds:
+ * Mean = mean of num_samples uniform random solutions (EvaluateRandomStarts);
+ * the incumbent starts as the first-derivative solution, whose value is the
+ * first Max (CalculateFirstDerivativeSolution, CalculateT).  Round r
+ * diversifies starts_per_round starts around the current incumbent (loop
+ * counters r*S + s, as ubqp_diversify), evaluates them, screens them with
+ * T = Mean + lambda (Max - Mean) where Max is the incumbent's value, climbs
+ * every start above T, and replaces the incumbent by the round's best when
+ * that is strictly better (UpdateBestAndT).  Within a round the incumbent and
+ * T are fixed.  Outputs (device): best_x_dev (W words), best_f_dev[0] (its
+ * value; 1 int64), history_dev[r] = incumbent value after round r (rounds
+ * int64), stats_dev = {starts that passed, flips, sum over the sample}
+ * (3 int64).  No host round trip: fully async on `stream`.  ws must hold
+ * ubqp_search_workspace_size(q, p) bytes (16-byte aligned).
+ */
+size_t ubqp_search_workspace_size(const ubqp_q* q, const ubqp_search_params* p);
+int ubqp_search(const ubqp_q* q, const ubqp_search_params* p, uint64_t* best_x_dev,
+                int64_t* best_f_dev, int64_t* history_dev, int64_t* stats_dev,
+                void* ws, size_t ws_bytes, void* stream);
 
 #ifdef __cplusplus
 }

@@ -69,6 +69,7 @@ def _load():
         "orc_best": (i64, [P, i64, P]),
         "orc_solve": (None, [P, i32, i64, i64, f64, i32, u64, i32, i32, P, P, P, P]),
         "orc_brute_force": (i64, [P, i32, i64, P]),
+        "orc_search": (None, [P, i32, i64, i64, i64, i32, f64, i32, u64, i32, P, P, P, P]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -212,6 +213,20 @@ def solve(Q, S: int, lam: float, max_flips: int = 0, seed: int = 0,
             "total_flips": int(st[1]), "max_flips_seen": int(st[2]),
             "batch_max": int(st[3]), "best_index": int(st[4]), "sum": int(st[5]),
             "T": float(sf[0]), "mean": float(sf[1])}
+
+
+def search(Q, num_samples: int, S: int, rounds: int, lam: float, max_flips: int = 0,
+           seed: int = 0, div_H: int = 64) -> dict:
+    """Multi-round search of Fig. 2 (see ubqp_oracle.c)."""
+    Q, n, ldq = _q(Q)
+    bx = np.zeros(words(n), np.uint64)
+    bf = np.zeros(1, np.int64)
+    hist = np.zeros(max(rounds, 1), np.int64)
+    st = np.zeros(3, np.int64)
+    _load().orc_search(_p(Q), n, ldq, num_samples, S, rounds, float(lam), max_flips,
+                       seed & (2**64 - 1), div_H, _p(bx), _p(bf), _p(hist), _p(st))
+    return {"best_x": bx, "best_f": int(bf[0]), "history": hist[:rounds].copy(),
+            "passed": int(st[0]), "total_flips": int(st[1]), "sample_sum": int(st[2])}
 
 
 def brute_force(Q):

@@ -331,3 +331,73 @@ int64_t orc_brute_force(const int8_t* Q, int32_t n, int64_t ldq,
   if (argmax_bits) *argmax_bits = best_p;
   return best;
 }
+
+/*
+ * The search of Fig. 2 run in rounds of S starts (the loop body applied to a
+ * batch at a time).  Before the loop: EvaluateRandomStarts -- the mean of
+ * num_samples uniform random solutions (RANDOM mode, seed) -- and
+ * CalculateFirstDerivativeSolution, whose value is the initial Max.  Round r:
+ * S starts diversified around the incumbent with loop counters r*S + s (so the
+ * very first start, i = 0, is the first-derivative solution itself), their
+ * values, the screen T = Mean + lambda (Max - Mean) with the sample Mean and
+ * the incumbent's value as Max (the text after Fig. 2: Mean from sampling, Max
+ * the best so far), ascent of every start with xQx > T, then UpdateBestAndT:
+ * the round's best replaces the incumbent when strictly better (so Max and T
+ * rise).  Reading: within a round the incumbent and T stay fixed (batched).
+ * history[r] = incumbent value after round r; stats = {passed, flips} totals.
+ */
+void orc_search(const int8_t* Q, int32_t n, int64_t ldq, int64_t num_samples,
+                int64_t S, int32_t rounds, double lambda, int32_t max_flips,
+                uint64_t seed, int32_t div_H, uint64_t* best_x, int64_t* best_f,
+                int64_t* history, int64_t* stats) {
+  int64_t W = orc_words(n);
+  /* sample mean */
+  uint64_t* Xs = (uint64_t*)calloc((size_t)(num_samples * W), sizeof(uint64_t));
+  int64_t* fs = (int64_t*)calloc((size_t)num_samples, sizeof(int64_t));
+  orc_diversify(NULL, n, 0, seed, 0, num_samples, div_H, Xs);
+  orc_eval(Q, n, ldq, Xs, num_samples, fs);
+  int64_t sample_sum = 0;
+  for (int64_t b = 0; b < num_samples; ++b) sample_sum += fs[b];
+  double mean = (double)sample_sum / (double)num_samples;
+  free(Xs);
+  free(fs);
+  /* incumbent = first-derivative start */
+  uint64_t* inc = (uint64_t*)calloc((size_t)W, sizeof(uint64_t));
+  orc_first_derivative(Q, n, ldq, inc);
+  int64_t inc_f = orc_f(Q, n, ldq, inc);
+  uint64_t* X = (uint64_t*)calloc((size_t)(S * W), sizeof(uint64_t));
+  int64_t* f = (int64_t*)calloc((size_t)S, sizeof(int64_t));
+  int32_t* flips = (int32_t*)calloc((size_t)S, sizeof(int32_t));
+  int64_t passed = 0, total_flips = 0;
+  for (int32_t r = 0; r < rounds; ++r) {
+    orc_diversify(inc, n, 1, seed, (uint64_t)r, S, div_H, X);
+    orc_eval(Q, n, ldq, X, S, f);
+    double diff = (double)inc_f - mean;
+    double scaled = lambda * diff;
+    double T = mean + scaled;
+    for (int64_t s = 0; s < S; ++s) {
+      flips[s] = 0;
+      if ((double)f[s] > T) {
+        flips[s] = orc_ascent1(Q, n, ldq, X + s * W, f + s, max_flips, NULL, 0);
+        ++passed;
+        total_flips += flips[s];
+      }
+    }
+    int64_t bi = 0;
+    int64_t bf = orc_best(f, S, &bi);
+    if (bf > inc_f) {
+      inc_f = bf;
+      memcpy(inc, X + bi * W, (size_t)W * sizeof(uint64_t));
+    }
+    history[r] = inc_f;
+  }
+  memcpy(best_x, inc, (size_t)W * sizeof(uint64_t));
+  *best_f = inc_f;
+  stats[0] = passed;
+  stats[1] = total_flips;
+  stats[2] = sample_sum;
+  free(inc);
+  free(X);
+  free(f);
+  free(flips);
+}

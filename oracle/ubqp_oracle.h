@@ -80,6 +80,15 @@ void orc_solve(const int8_t* Q, int32_t n, int64_t ldq, int64_t S,
                int32_t div_H, uint64_t* best_x, int64_t* best_f,
                int64_t* stats, double* stats_fp);
 
+/* The search of Fig. 2 in rounds of S starts around the incumbent, with the
+ * random-sample Mean and the incumbent value as Max in T(lambda).  history
+ * (rounds entries) receives the incumbent value after each round; stats =
+ * {passed, total flips, sample sum}. */
+void orc_search(const int8_t* Q, int32_t n, int64_t ldq, int64_t num_samples,
+                int64_t S, int32_t rounds, double lambda, int32_t max_flips,
+                uint64_t seed, int32_t div_H, uint64_t* best_x, int64_t* best_f,
+                int64_t* history, int64_t* stats);
+
 /* Exhaustive search over all 2^n solutions (n <= 24): global maximum and the
  * lowest-numbered maximiser (solution number = its bit pattern). */
 int64_t orc_brute_force(const int8_t* Q, int32_t n, int64_t ldq,

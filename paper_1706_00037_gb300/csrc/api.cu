@@ -291,7 +291,7 @@ int ubqp_screen_apply(const int64_t* f_dev, int64_t S, const int64_t* gstats_dev
                       double* Tm_dev, void* stream) {
   if (!f_dev || !gstats_dev || !idx_dev || !count_dev || !Tm_dev)
     return fail(UBQP_ERR_ARG, "NULL argument");
-  if (S < 0 || S >= ((int64_t)1 << 31) || S_total < 1 || S_total < S)
+  if (S < 0 || S >= ((int64_t)1 << 31) || S_total < 1)
     return fail(UBQP_ERR_ARG, "S=%lld / S_total=%lld out of range", (long long)S,
                 (long long)S_total);
   if (!(lambda == lambda) || lambda > 1e300 || lambda < -1e300)
@@ -402,6 +402,106 @@ int ubqp_solve(const ubqp_q* q, const ubqp_params* p, uint64_t* best_x_dev, int6
     stats_host->T = hd[0];
     stats_host->mean = hd[1];
   }
+  return UBQP_OK;
+}
+
+// Workspace of ubqp_search.
+struct SearchLayout {
+  size_t Xs, fs, X, f, idx, flips, small, inc_x, cand_x, scratch, total;
+};
+
+SearchLayout search_layout(const ubqp_q* q, const ubqp_search_params* p) {
+  SearchLayout L{};
+  size_t off = 0;
+  auto take = [&](size_t bytes) {
+    size_t at = off;
+    off += (size_t)round_up((int64_t)bytes, 256);
+    return at;
+  };
+  const int64_t S = p->starts_per_round, NS = p->num_samples;
+  L.Xs = take((size_t)NS * q->W * 8);
+  L.fs = take((size_t)NS * 8);
+  L.X = take((size_t)S * q->W * 8);
+  L.f = take((size_t)S * 8);
+  L.idx = take((size_t)S * 4);
+  L.flips = take((size_t)S * 4);
+  L.small = take(256);
+  L.inc_x = take((size_t)q->W * 8);
+  L.cand_x = take((size_t)q->W * 8);
+  const int path = resolve_path(p->eval_path);
+  const int64_t big = S > NS ? S : NS;
+  const size_t ev = path == UBQP_EVAL_TC ? ubqp::eval_tc_workspace(q, big) : 0;
+  const size_t as = ubqp::ascent_tc_workspace(q, S);
+  L.scratch = take(ev > as ? ev : as);
+  L.total = off;
+  return L;
+}
+
+size_t ubqp_search_workspace_size(const ubqp_q* q, const ubqp_search_params* p) {
+  if (!q || !p || p->starts_per_round < 1 || p->num_samples < 1) return 0;
+  return search_layout(q, p).total;
+}
+
+int ubqp_search(const ubqp_q* q, const ubqp_search_params* p, uint64_t* best_x_dev,
+                int64_t* best_f_dev, int64_t* history_dev, int64_t* stats_dev, void* ws,
+                size_t ws_bytes, void* stream) {
+  if (!q || !p || !best_x_dev || !best_f_dev || !stats_dev || !ws)
+    return fail(UBQP_ERR_ARG, "NULL argument");
+  if (p->starts_per_round < 1 || p->starts_per_round >= ((int64_t)1 << 31) ||
+      p->num_samples < 1 || p->num_samples >= ((int64_t)1 << 31) || p->rounds < 0 ||
+      p->max_flips < 0)
+    return fail(UBQP_ERR_ARG, "starts, samples, rounds or max_flips out of range");
+  if (p->rounds > 0 && !history_dev) return fail(UBQP_ERR_ARG, "history_dev is NULL");
+  if (((uintptr_t)ws & 15) != 0) return fail(UBQP_ERR_ARG, "workspace not 16-byte aligned");
+  const SearchLayout L = search_layout(q, p);
+  if (ws_bytes < L.total) return fail(UBQP_ERR_NOMEM, "workspace %zu < %zu bytes", ws_bytes, L.total);
+  char* base = (char*)ws;
+  uint64_t* Xs = (uint64_t*)(base + L.Xs);
+  int64_t* fs = (int64_t*)(base + L.fs);
+  uint64_t* X = (uint64_t*)(base + L.X);
+  int64_t* f = (int64_t*)(base + L.f);
+  int32_t* idx = (int32_t*)(base + L.idx);
+  int32_t* flips = (int32_t*)(base + L.flips);
+  int64_t* count = (int64_t*)(base + L.small);
+  double* Tm = (double*)(base + L.small + 8);
+  int64_t* gstats = (int64_t*)(base + L.small + 24);
+  int64_t* sstats = (int64_t*)(base + L.small + 48);
+  int64_t* cand = (int64_t*)(base + L.small + 72);
+  uint64_t* inc_x = (uint64_t*)(base + L.inc_x);
+  uint64_t* cand_x = (uint64_t*)(base + L.cand_x);
+  void* scratch = base + L.scratch;
+  const size_t scratch_bytes = L.total - L.scratch;
+  const int64_t S = p->starts_per_round, NS = p->num_samples;
+  cudaStream_t st = (cudaStream_t)stream;
+  int r;
+  // EvaluateRandomStarts: the sample's sum gives Mean
+  if ((r = ubqp_diversify(q, nullptr, UBQP_MODE_RANDOM, p->seed, 0, NS, p->div_H, Xs, stream)))
+    return r;
+  if ((r = ubqp_eval(q, Xs, NS, fs, p->eval_path, scratch, scratch_bytes, stream))) return r;
+  if ((r = ubqp_screen_stats(fs, NS, 0, sstats, stream))) return r;
+  UBQP_CUDA(cudaMemcpyAsync(gstats, sstats, 8, cudaMemcpyDeviceToDevice, st));
+  // CalculateFirstDerivativeSolution: the incumbent and the initial Max
+  UBQP_CUDA(cudaMemcpyAsync(inc_x, q->x0, 8 * (size_t)q->W, cudaMemcpyDeviceToDevice, st));
+  if ((r = ubqp_eval(q, inc_x, 1, best_f_dev, p->eval_path, scratch, scratch_bytes, stream)))
+    return r;
+  UBQP_CUDA(cudaMemsetAsync(stats_dev, 0, 3 * sizeof(int64_t), st));
+  for (int32_t rd = 0; rd < p->rounds; ++rd) {
+    if ((r = ubqp_diversify(q, inc_x, UBQP_MODE_DIVERSIFY, p->seed, (uint64_t)rd, S, p->div_H,
+                            X, stream)))
+      return r;
+    if ((r = ubqp_eval(q, X, S, f, p->eval_path, scratch, scratch_bytes, stream))) return r;
+    UBQP_CUDA(cudaMemcpyAsync(gstats + 1, best_f_dev, 8, cudaMemcpyDeviceToDevice, st));
+    if ((r = ubqp_screen_apply(f, S, gstats, NS, p->lambda, idx, count, Tm, stream))) return r;
+    UBQP_CUDA(cudaMemsetAsync(flips, 0, sizeof(int32_t) * S, st));
+    if ((r = ubqp_ascent(q, X, f, idx, count, S, p->max_flips, flips, scratch, scratch_bytes,
+                         stream)))
+      return r;
+    if ((r = ubqp_best(f, X, S, q->W, cand_x, cand, stream))) return r;
+    UBQP_CUDA(ubqp::launch_search_update(cand, X, q->W, count, idx, flips, best_f_dev, inc_x,
+                                         history_dev + rd, stats_dev, st));
+  }
+  UBQP_CUDA(cudaMemcpyAsync(stats_dev + 2, sstats, 8, cudaMemcpyDeviceToDevice, st));
+  UBQP_CUDA(cudaMemcpyAsync(best_x_dev, inc_x, 8 * (size_t)q->W, cudaMemcpyDeviceToDevice, st));
   return UBQP_OK;
 }
 

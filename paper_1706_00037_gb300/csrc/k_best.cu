@@ -80,7 +80,49 @@ solve_stats_kernel(const int64_t* __restrict__ count, const int32_t* __restrict_
   }
 }
 
+// UpdateBestAndT of Fig. 2 after a round: the round's best {value, index}
+// replaces the incumbent when strictly better; history[round] = incumbent
+// value; stats {passed, flips} accumulate the round's counts.
+__global__ void __launch_bounds__(THREADS)
+search_update_kernel(const int64_t* __restrict__ cand, const uint64_t* __restrict__ X, int W,
+                     const int64_t* __restrict__ count, const int32_t* __restrict__ idx,
+                     const int32_t* __restrict__ flips, int64_t* __restrict__ inc_f,
+                     uint64_t* __restrict__ inc_x, int64_t* __restrict__ history,
+                     int64_t* __restrict__ stats) {
+  __shared__ long long s_tot[WARPS];
+  __shared__ int s_take;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int64_t c = *count;
+  long long tot = 0;
+  for (int64_t t = threadIdx.x; t < c; t += THREADS) tot += flips[idx[t]];
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) tot += __shfl_xor_sync(0xffffffffu, tot, o);
+  if (lane == 0) s_tot[warp] = tot;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    long long t = 0;
+    for (int i = 0; i < WARPS; ++i) t += s_tot[i];
+    stats[0] += c;
+    stats[1] += t;
+    s_take = cand[0] > inc_f[0];
+    if (s_take) inc_f[0] = cand[0];
+    *history = inc_f[0];
+  }
+  __syncthreads();
+  if (s_take)
+    for (int w = threadIdx.x; w < W; w += THREADS) inc_x[w] = X[cand[1] * W + w];
+}
+
 }  // namespace
+
+cudaError_t launch_search_update(const int64_t* cand, const uint64_t* X, int W,
+                                 const int64_t* count, const int32_t* idx, const int32_t* flips,
+                                 int64_t* inc_f, uint64_t* inc_x, int64_t* history,
+                                 int64_t* stats, cudaStream_t st) {
+  search_update_kernel<<<1, THREADS, 0, st>>>(cand, X, W, count, idx, flips, inc_f, inc_x,
+                                              history, stats);
+  return cudaGetLastError();
+}
 
 cudaError_t launch_best(const int64_t* f, const uint64_t* X, int64_t S, int W,
                         uint64_t* best_x, int64_t* best_f, cudaStream_t st) {

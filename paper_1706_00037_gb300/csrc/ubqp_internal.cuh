@@ -94,6 +94,10 @@ cudaError_t launch_ascent(const ubqp_q* h, uint64_t* X, int64_t* f, const int32_
                           int32_t* flips, const float* Y, cudaStream_t st);
 cudaError_t launch_best(const int64_t* f, const uint64_t* X, int64_t S, int W,
                         uint64_t* best_x, int64_t* best_f, cudaStream_t st);
+cudaError_t launch_search_update(const int64_t* cand, const uint64_t* X, int W,
+                                 const int64_t* count, const int32_t* idx, const int32_t* flips,
+                                 int64_t* inc_f, uint64_t* inc_x, int64_t* history,
+                                 int64_t* stats, cudaStream_t st);
 cudaError_t launch_solve_stats(const int64_t* count, const int32_t* idx,
                                const int32_t* flips, const double* Tm,
                                const int64_t* sstats, const int64_t* best,

@@ -28,7 +28,7 @@ EXPORTS = ["ubqp_strerror", "ubqp_last_error", "ubqp_abi_version", "ubqp_q_prepa
            "ubqp_diversify", "ubqp_diversify_range", "ubqp_eval_workspace_size", "ubqp_eval",
            "ubqp_eval_noalloc", "ubqp_screen", "ubqp_screen_stats", "ubqp_screen_apply",
            "ubqp_ascent_workspace_size", "ubqp_ascent", "ubqp_best", "ubqp_solve_workspace_size",
-           "ubqp_solve"]
+           "ubqp_solve", "ubqp_search_workspace_size", "ubqp_search"]
 
 
 class UbqpError(RuntimeError):
@@ -41,6 +41,13 @@ class Params(ctypes.Structure):
     _fields_ = [("num_starts", ctypes.c_int64), ("lambda_", ctypes.c_double),
                 ("max_flips", ctypes.c_int32), ("mode", ctypes.c_int32),
                 ("seed", ctypes.c_uint64), ("round", ctypes.c_uint64),
+                ("div_H", ctypes.c_int32), ("eval_path", ctypes.c_int32)]
+
+
+class SearchParams(ctypes.Structure):
+    _fields_ = [("num_samples", ctypes.c_int64), ("starts_per_round", ctypes.c_int64),
+                ("rounds", ctypes.c_int32), ("max_flips", ctypes.c_int32),
+                ("lambda_", ctypes.c_double), ("seed", ctypes.c_uint64),
                 ("div_H", ctypes.c_int32), ("eval_path", ctypes.c_int32)]
 
 
@@ -95,6 +102,8 @@ def load() -> ctypes.CDLL:
         "ubqp_solve_workspace_size": (sz, [P, ctypes.POINTER(Params)]),
         "ubqp_solve": (ctypes.c_int, [P, ctypes.POINTER(Params), P, P, ctypes.POINTER(Stats),
                                       P, sz, P]),
+        "ubqp_search_workspace_size": (sz, [P, ctypes.POINTER(SearchParams)]),
+        "ubqp_search": (ctypes.c_int, [P, ctypes.POINTER(SearchParams), P, P, P, P, P, sz, P]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -307,3 +316,20 @@ def solve(inst: Instance, params: Params, ws: torch.Tensor | None = None,
                              ctypes.byref(st) if st is not None else None, _ptr(ws),
                              ws.numel(), _stream(stream)))
     return bx, bf, (st.as_dict() if st is not None else None)
+
+
+def search(inst: Instance, num_samples: int, starts_per_round: int, rounds: int, lam: float,
+           max_flips: int = 0, seed: int = 0, div_H: int = 64, eval_path: int = EVAL_AUTO,
+           stream=None) -> dict:
+    """The multi-round search of Fig. 2 (ubqp_search); returns device tensors."""
+    p = SearchParams(num_samples, starts_per_round, rounds, max_flips, float(lam),
+                     seed % 2**64, div_H, eval_path)
+    need = int(load().ubqp_search_workspace_size(inst.handle, ctypes.byref(p)))
+    ws = torch.empty(max(need, 16), dtype=torch.uint8, device=inst.device)
+    bx = torch.empty(inst.words, dtype=torch.int64, device=inst.device)
+    bf = torch.empty(1, dtype=torch.int64, device=inst.device)
+    hist = torch.empty(max(rounds, 1), dtype=torch.int64, device=inst.device)
+    st = torch.empty(3, dtype=torch.int64, device=inst.device)
+    _check(load().ubqp_search(inst.handle, ctypes.byref(p), _ptr(bx), _ptr(bf), _ptr(hist),
+                              _ptr(st), _ptr(ws), ws.numel(), _stream(stream)))
+    return {"best_x": bx, "best_f": bf, "history": hist[:rounds], "stats": st}

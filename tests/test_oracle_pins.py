@@ -382,3 +382,37 @@ def test_instance_generator_shape_and_density():
     Q = synth.make_instance(50, 0.5, 1)
     Q[3, 7] += 1
     assert orc.validate(Q)[0] == -2
+
+
+# ---------------------------------------------------------------- multi-round search
+
+def test_search_pins():
+    n = 60
+    Q = synth.make_instance(n, 0.4, 2)
+    r = orc.search(Q, num_samples=200, S=16, rounds=6, lam=0.5, seed=3)
+    # the incumbent only improves, and is the value of the returned solution
+    assert all(a <= b for a, b in zip(r["history"], r["history"][1:]))
+    assert r["best_f"] == r["history"][-1] == _f_np(Q, synth.unpack_bits(r["best_x"], n))
+    # the first start of round 0 is the first-derivative solution, which passes
+    # any lambda < 1 screen once the sample mean lies below it, so the result is
+    # at least its steepest-ascent local optimum
+    x0 = orc.first_derivative(Q)
+    f0 = _f_np(Q, synth.unpack_bits(x0, n))
+    _, f_loc, _, _ = orc.ascent1(Q, x0, f0)
+    assert r["best_f"] >= f_loc
+    # the sample mean comes from the random sample: its sum is the oracle's f sum
+    Xs = orc.diversify(None, n, orc.RANDOM, 3, 0, 200)
+    assert r["sample_sum"] == sum(_f_np(Q, x) for x in synth.unpack_bits(Xs, n))
+
+
+def test_search_small_n_reaches_a_local_optimum_below_global():
+    n = 14
+    Q = synth.make_instance(n, 0.8, 5)
+    gmax, _ = orc.brute_force(Q)
+    r = orc.search(Q, num_samples=64, S=8, rounds=4, lam=0.3, seed=1)
+    assert r["best_f"] <= gmax
+    x = synth.unpack_bits(r["best_x"], n).astype(np.int64)
+    for i in range(n):  # the incumbent is a 1-flip local optimum
+        y = x.copy()
+        y[i] ^= 1
+        assert _f_np(Q, y) <= r["best_f"]
