@@ -284,6 +284,46 @@ int ubqp_solve(const ubqp_q* q, const ubqp_params* p, uint64_t* best_x_dev,
                int64_t* best_f_dev, ubqp_stats* stats_host, void* ws,
                size_t ws_bytes, void* stream);
 
+/*
+ * Batches of instances: one round (as ubqp_solve, with the same parameters) for
+ * every instance of a batch of uneven n, run together.  Per-instance start
+ * generation and evaluation run concurrently on internal streams; the screen,
+ * the ascent of every passing start of every instance (one persistent launch,
+ * largest instances first) and the best-of are one launch each.  Each
+ * instance's result is bit-identical to ubqp_solve on that instance alone.
+ *
+ * ubqp_batch_create -- plan a batch over `count` prepared instances (all on the
+ *   current device; the handles must outlive the plan).  Allocates the plan's
+ *   device memory (workspace, results, descriptors) and internal streams.
+ * ubqp_batch_run -- one round for all instances with start-generation seed
+ *   `seed` (replaces p->seed), async on `stream`; launches the captured graph
+ *   when there is one.
+ * ubqp_batch_tune -- the autotuner: times the run for the candidate ascent
+ *   group shapes (threads x chunks that hold the largest n), evaluation paths
+ *   and fork/join stream counts on this batch and keeps the fastest; drops a
+ *   captured graph.  Synchronises `stream`.
+ * ubqp_batch_capture -- records one run into a CUDA graph (after one plain
+ *   run); later ubqp_batch_run calls replay it.  Synchronises `stream`.
+ * ubqp_batch_result -- device pointers to instance i's best solution (W words)
+ *   and {value, start index} (2 int64), valid after the run completes.
+ * ubqp_batch_config -- the configuration in use (any pointer may be NULL).
+ * The paper runs one instance at a time; batching is this library's addition.
+ */
+typedef struct ubqp_batch ubqp_batch;
+int ubqp_batch_create(const ubqp_q* const* qs, int32_t count, const ubqp_params* p,
+                      ubqp_batch** out);
+void ubqp_batch_destroy(ubqp_batch* b);
+int ubqp_batch_run(ubqp_batch* b, uint64_t seed, void* stream);
+int ubqp_batch_tune(ubqp_batch* b, void* stream);
+int ubqp_batch_capture(ubqp_batch* b, void* stream);
+int ubqp_batch_result(const ubqp_batch* b, int32_t i, const uint64_t** best_x_dev,
+                      const int64_t** best_f_dev);
+int ubqp_batch_config(const ubqp_batch* b, int32_t* asc_threads, int32_t* asc_chunks,
+                      int32_t* eval_path, int32_t* streams, int32_t* graph);
+/* Copies instance i's result to caller memory (W words, 2 int64), async. */
+int ubqp_batch_get(const ubqp_batch* b, int32_t i, uint64_t* best_x_dev, int64_t* best_f_dev,
+                   void* stream);
+
 /* The search of Fig. 2, run in rounds of starts_per_round starts. */
 typedef struct ubqp_search_params {
   int64_t num_samples;      /* random solutions behind Mean (EvaluateRandomStarts) */

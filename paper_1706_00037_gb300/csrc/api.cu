@@ -9,17 +9,22 @@
 #include "ubqp_internal.cuh"
 
 namespace {
-
 thread_local char g_last_error[512] = "";
+}  // namespace
 
-int fail(int status, const char* fmt, ...) __attribute__((format(printf, 2, 3)));
-int fail(int status, const char* fmt, ...) {
+namespace ubqp {
+int record_error(int status, const char* fmt, ...) {
   va_list ap;
   va_start(ap, fmt);
   vsnprintf(g_last_error, sizeof(g_last_error), fmt, ap);
   va_end(ap);
   return status;
 }
+}  // namespace ubqp
+
+namespace {
+
+#define fail ubqp::record_error
 
 int cuda_fail(cudaError_t e, const char* what) {
   return fail(UBQP_ERR_CUDA, "%s: %s", what, cudaGetErrorString(e));

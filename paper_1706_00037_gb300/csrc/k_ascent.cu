@@ -287,6 +287,30 @@ ascent_block_kernel(const int8_t* __restrict__ Q8, int64_t ldq, int n, int W,
   }
 }
 
+// All passing starts of a batch of instances in one persistent launch: item
+// t = (instance, position in its passing list); every instance has n <= 16 T C.
+template <int T, int C>
+__global__ void __launch_bounds__(T, 1)
+ascent_batch_kernel(const BatchDesc* __restrict__ d, const int2* __restrict__ items,
+                    const int64_t* __restrict__ n_items, int32_t max_flips) {
+  __shared__ int2 rec[2][T / 32];
+  __shared__ uint64_t xs[UBQP_MAX_N / 64];
+  Group<T> grp{rec, 0};
+  const int64_t cnt = *n_items;
+  for (int64_t t = blockIdx.x; t < cnt; t += gridDim.x) {
+    const int2 it = items[t];
+    const BatchDesc& b = d[it.x];
+    const int s = b.idx[it.y];
+    if (s < 0 || s >= b.S) {
+      if (threadIdx.x == 0) atomicOr(b.err, UBQP_DEVERR_BADIDX);
+      continue;
+    }
+    ascend_one<T, C>(b.Q8, b.ldq, b.ldy, b.n, b.W, b.X + (int64_t)s * b.W, b.f + s, max_flips,
+                     b.flips ? b.flips + s : nullptr, b.err, xs,
+                     b.Y ? b.Y + (int64_t)it.y * b.ldy : nullptr, grp);
+  }
+}
+
 // Four independent warps per block, one start each (n <= 512).
 template <int C>
 __global__ void __launch_bounds__(128)
@@ -346,7 +370,45 @@ cudaError_t launch_warp(const ubqp_q* h, uint64_t* X, int64_t* f, const int32_t*
   return cudaGetLastError();
 }
 
+template <int T, int C>
+cudaError_t launch_ascent_batch_tc(const BatchDesc* d, const int2* items, const int64_t* n_items,
+                                   int32_t max_flips, int grid, cudaStream_t st) {
+  ascent_batch_kernel<T, C><<<grid, T, 0, st>>>(d, items, n_items, max_flips);
+  return cudaGetLastError();
+}
+
 }  // namespace
+
+bool ascent_batch_supported(int T, int C) {
+  return (T == 64 || T == 128 || T == 256 || T == 512) && (C == 1 || C == 2);
+}
+
+int ascent_batch_grid(int T, int C, int sm_count) {
+  int per_sm = 0;
+  cudaError_t e = cudaErrorInvalidValue;
+#define UBQP_OCC(TT, CC)                                                                     \
+  if (T == TT && C == CC)                                                                    \
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, ascent_batch_kernel<TT, CC>, \
+                                                      TT, 0);
+  UBQP_OCC(64, 1) UBQP_OCC(64, 2) UBQP_OCC(128, 1) UBQP_OCC(128, 2)
+  UBQP_OCC(256, 1) UBQP_OCC(256, 2) UBQP_OCC(512, 1) UBQP_OCC(512, 2)
+#undef UBQP_OCC
+  if (e != cudaSuccess || per_sm < 1) {
+    cudaGetLastError();
+    per_sm = 1;
+  }
+  return per_sm * sm_count;
+}
+
+cudaError_t launch_ascent_batch(const BatchDesc* d, const int2* items, const int64_t* n_items,
+                                int T, int C, int32_t max_flips, int grid, cudaStream_t st) {
+#define UBQP_ASC(TT, CC) \
+  if (T == TT && C == CC) return launch_ascent_batch_tc<TT, CC>(d, items, n_items, max_flips, grid, st);
+  UBQP_ASC(64, 1) UBQP_ASC(64, 2) UBQP_ASC(128, 1) UBQP_ASC(128, 2)
+  UBQP_ASC(256, 1) UBQP_ASC(256, 2) UBQP_ASC(512, 1) UBQP_ASC(512, 2)
+#undef UBQP_ASC
+  return cudaErrorInvalidValue;
+}
 
 cudaError_t launch_ascent(const ubqp_q* h, uint64_t* X, int64_t* f, const int32_t* idx,
                           const int64_t* count, int64_t S, int32_t max_flips, int32_t* flips,

@@ -11,9 +11,9 @@ namespace {
 constexpr int THREADS = 1024;
 constexpr int WARPS = THREADS / 32;
 
-__global__ void __launch_bounds__(THREADS)
-best_kernel(const int64_t* __restrict__ f, const uint64_t* __restrict__ X, int64_t S, int W,
-            uint64_t* __restrict__ best_x, int64_t* __restrict__ best_f) {
+__device__ void block_best(const int64_t* __restrict__ f, const uint64_t* __restrict__ X,
+                           int64_t S, int W, uint64_t* __restrict__ best_x,
+                           int64_t* __restrict__ best_f) {
   __shared__ long long s_max[WARPS], s_arg[WARPS];
   __shared__ long long s_best;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -41,6 +41,33 @@ best_kernel(const int64_t* __restrict__ f, const uint64_t* __restrict__ X, int64
   __syncthreads();
   const long long a = s_best;
   for (int w = threadIdx.x; w < W; w += THREADS) best_x[w] = X[a * W + w];
+}
+
+__global__ void __launch_bounds__(THREADS)
+best_kernel(const int64_t* __restrict__ f, const uint64_t* __restrict__ X, int64_t S, int W,
+            uint64_t* __restrict__ best_x, int64_t* __restrict__ best_f) {
+  block_best(f, X, S, W, best_x, best_f);
+}
+
+// One block per instance of a batch.
+__global__ void __launch_bounds__(THREADS) best_batch_kernel(const BatchDesc* __restrict__ d) {
+  const BatchDesc& b = d[blockIdx.x];
+  block_best(b.f, b.X, b.S, b.W, b.best_x, b.best_f);
+}
+
+// The batch's ascent work list: (instance, position in its passing list) for
+// every passing start, instances in the given order (largest first).
+__global__ void __launch_bounds__(THREADS)
+batch_items_kernel(const BatchDesc* __restrict__ d, const int32_t* __restrict__ order, int count,
+                   int2* __restrict__ items, int64_t* __restrict__ n_items) {
+  int64_t base = 0;
+  for (int k = 0; k < count; ++k) {
+    const int i = order[k];
+    const int64_t c = *d[i].count;
+    for (int64_t t = threadIdx.x; t < c; t += THREADS) items[base + t] = make_int2(i, (int)t);
+    base += c;
+  }
+  if (threadIdx.x == 0) *n_items = base;
 }
 
 // out = {passed, total flips, max flips of one start, batch max, best index, sum}
@@ -113,6 +140,8 @@ search_update_kernel(const int64_t* __restrict__ cand, const uint64_t* __restric
     for (int w = threadIdx.x; w < W; w += THREADS) inc_x[w] = X[cand[1] * W + w];
 }
 
+__global__ void set_u64_kernel(uint64_t* dst, uint64_t v) { *dst = v; }
+
 }  // namespace
 
 cudaError_t launch_search_update(const int64_t* cand, const uint64_t* X, int W,
@@ -121,6 +150,22 @@ cudaError_t launch_search_update(const int64_t* cand, const uint64_t* X, int W,
                                  int64_t* stats, cudaStream_t st) {
   search_update_kernel<<<1, THREADS, 0, st>>>(cand, X, W, count, idx, flips, inc_f, inc_x,
                                               history, stats);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_set_u64(uint64_t* dst, uint64_t v, cudaStream_t st) {
+  set_u64_kernel<<<1, 1, 0, st>>>(dst, v);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_best_batch(const BatchDesc* d, int count, cudaStream_t st) {
+  best_batch_kernel<<<count, THREADS, 0, st>>>(d);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_batch_items(const BatchDesc* d, const int32_t* order, int count, int2* items,
+                               int64_t* n_items, cudaStream_t st) {
+  batch_items_kernel<<<1, THREADS, 0, st>>>(d, order, count, items, n_items);
   return cudaGetLastError();
 }
 

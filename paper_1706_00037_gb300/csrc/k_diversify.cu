@@ -11,7 +11,9 @@ namespace {
 // i = round * S_total + s), written to X[(s - s_begin) * W + w].
 __global__ void diversify_words(const uint64_t* __restrict__ x0, int n, int W, int mode,
                                 uint64_t seed, uint64_t round, int64_t S_total, int64_t s_begin,
-                                int64_t S_local, int div_H, uint64_t* __restrict__ X) {
+                                int64_t S_local, int div_H, uint64_t* __restrict__ X,
+                                const uint64_t* __restrict__ seed_dev) {
+  if (seed_dev) seed = *seed_dev;
   const int64_t total = S_local * W;
   const int64_t S = S_total;
   for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < total;
@@ -55,13 +57,14 @@ __global__ void diversify_words(const uint64_t* __restrict__ x0, int n, int W, i
 
 cudaError_t launch_diversify(const uint64_t* x0, int n, int mode, uint64_t seed,
                              uint64_t round, int64_t S_total, int64_t s_begin,
-                             int64_t S_local, int div_H, uint64_t* X, cudaStream_t st) {
+                             int64_t S_local, int div_H, uint64_t* X, cudaStream_t st,
+                             const uint64_t* seed_dev) {
   const int W = (int)words_of(n);
   int64_t total = S_local * W;
   int64_t blocks = (total + 255) / 256;
   if (blocks > 152 * 16) blocks = 152 * 16;
   diversify_words<<<(unsigned)blocks, 256, 0, st>>>(x0, n, W, mode, seed, round, S_total,
-                                                   s_begin, S_local, div_H, X);
+                                                   s_begin, S_local, div_H, X, seed_dev);
   return cudaGetLastError();
 }
 

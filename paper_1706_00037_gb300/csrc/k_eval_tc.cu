@@ -520,9 +520,13 @@ size_t ascent_tc_workspace(const ubqp_q* h, int64_t S) {
 
 // y = Q x for the starts idx[0 .. *count) into Y (fp32, row t = idx[t], stride
 // n_tc), on the tensor cores.  ws holds the unpacked starts then Y.
+bool eval_tc_map_A(void* out128, const void* Xe, int64_t S, int n_tc) {
+  return make_map(reinterpret_cast<CUtensorMap*>(out128), Xe, padded_starts(S), n_tc, BM);
+}
+
 cudaError_t launch_ascent_init_tc(const ubqp_q* h, const uint64_t* X, const int32_t* idx,
                                   const int64_t* count, int64_t S, void* ws, size_t ws_bytes,
-                                  float** Y_out, cudaStream_t st) {
+                                  float** Y_out, cudaStream_t st, const void* mapA_in) {
   if (!h->tc_ok) return cudaErrorNotSupported;
   const int64_t S_p = padded_starts(S);
   if (ws_bytes < ascent_tc_workspace(h, S)) return cudaErrorInvalidValue;
@@ -538,7 +542,8 @@ cudaError_t launch_ascent_init_tc(const ubqp_q* h, const uint64_t* X, const int3
     if ((e = cudaGetLastError())) return e;
   }
   alignas(64) CUtensorMap mapA;
-  if (!make_map(&mapA, Xe, S_p, h->n_tc, BM)) return cudaErrorInvalidValue;
+  if (mapA_in) mapA = *reinterpret_cast<const CUtensorMap*>(mapA_in);
+  else if (!make_map(&mapA, Xe, S_p, h->n_tc, BM)) return cudaErrorInvalidValue;
   if ((e = cudaMemsetAsync(Y, 0, (size_t)S_p * h->n_tc * 4, st))) return e;
   static bool attr = false;
   if (!attr) {
@@ -560,7 +565,7 @@ cudaError_t launch_ascent_init_tc(const ubqp_q* h, const uint64_t* X, const int3
 }
 
 cudaError_t launch_eval_tc(const ubqp_q* h, const uint64_t* X, int64_t S, int64_t* f, void* ws,
-                           size_t ws_bytes, cudaStream_t st) {
+                           size_t ws_bytes, cudaStream_t st, const void* mapA_in) {
   if (!h->tc_ok) return cudaErrorNotSupported;
   const int64_t S_p = padded_starts(S);
   if (ws_bytes < eval_tc_workspace(h, S)) return cudaErrorInvalidValue;
@@ -575,7 +580,8 @@ cudaError_t launch_eval_tc(const ubqp_q* h, const uint64_t* X, int64_t S, int64_
     if ((e = cudaGetLastError())) return e;
   }
   alignas(64) CUtensorMap mapA;
-  if (!make_map(&mapA, ws, S_p, h->n_tc, BM)) return cudaErrorInvalidValue;
+  if (mapA_in) mapA = *reinterpret_cast<const CUtensorMap*>(mapA_in);
+  else if (!make_map(&mapA, ws, S_p, h->n_tc, BM)) return cudaErrorInvalidValue;
   if ((e = cudaMemsetAsync(f, 0, sizeof(int64_t) * S, st))) return e;
   static bool attr = false;
   if (!attr) {

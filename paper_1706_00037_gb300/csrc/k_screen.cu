@@ -15,10 +15,9 @@ namespace {
 constexpr int THREADS = 1024;
 constexpr int WARPS = THREADS / 32;
 
-// stats = {sum of f, max f, lowest index attaining it + offset}
-__global__ void __launch_bounds__(THREADS)
-screen_stats_kernel(const int64_t* __restrict__ f, int64_t S, int64_t offset,
-                    int64_t* __restrict__ stats) {
+// stats = {sum of f, max f, lowest index attaining it + offset}; one block.
+__device__ void block_screen_stats(const int64_t* __restrict__ f, int64_t S, int64_t offset,
+                                   int64_t* __restrict__ stats) {
   __shared__ long long s_sum[WARPS];
   __shared__ long long s_max[WARPS];
   __shared__ long long s_arg[WARPS];
@@ -48,14 +47,21 @@ screen_stats_kernel(const int64_t* __restrict__ f, int64_t S, int64_t offset,
     stats[1] = m;
     stats[2] = (S > 0) ? a + offset : LLONG_MAX;
   }
+  __syncthreads();
+}
+
+__global__ void __launch_bounds__(THREADS)
+screen_stats_kernel(const int64_t* __restrict__ f, int64_t S, int64_t offset,
+                    int64_t* __restrict__ stats) {
+  block_screen_stats(f, S, offset, stats);
 }
 
 // T from the (possibly multi-rank) stats, then the stable list of local
 // indices with f_b > T.
-__global__ void __launch_bounds__(THREADS)
-screen_apply_kernel(const int64_t* __restrict__ f, int64_t S, const int64_t* __restrict__ gstats,
-                    int64_t S_total, double lambda, int32_t* __restrict__ idx,
-                    int64_t* __restrict__ count, double* __restrict__ Tm) {
+__device__ void block_screen_apply(const int64_t* __restrict__ f, int64_t S,
+                                   const int64_t* gstats, int64_t S_total, double lambda,
+                                   int32_t* __restrict__ idx, int64_t* __restrict__ count,
+                                   double* __restrict__ Tm) {
   __shared__ int s_cnt[WARPS];
   __shared__ double s_T;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -90,11 +96,31 @@ screen_apply_kernel(const int64_t* __restrict__ f, int64_t S, const int64_t* __r
   if (threadIdx.x == 0) *count = base;
 }
 
+__global__ void __launch_bounds__(THREADS)
+screen_apply_kernel(const int64_t* __restrict__ f, int64_t S, const int64_t* __restrict__ gstats,
+                    int64_t S_total, double lambda, int32_t* __restrict__ idx,
+                    int64_t* __restrict__ count, double* __restrict__ Tm) {
+  block_screen_apply(f, S, gstats, S_total, lambda, idx, count, Tm);
+}
+
+// One block per instance of a batch: the screen of ubqp_screen on its values.
+__global__ void __launch_bounds__(THREADS)
+screen_batch_kernel(const BatchDesc* __restrict__ d, double lambda) {
+  const BatchDesc& b = d[blockIdx.x];
+  block_screen_stats(b.f, b.S, 0, b.stats);
+  block_screen_apply(b.f, b.S, b.stats, b.S, lambda, b.idx, b.count, b.Tm);
+}
+
 }  // namespace
 
 cudaError_t launch_screen_stats(const int64_t* f, int64_t S, int64_t offset, int64_t* stats,
                                 cudaStream_t st) {
   screen_stats_kernel<<<1, THREADS, 0, st>>>(f, S, offset, stats);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_screen_batch(const BatchDesc* d, int count, double lambda, cudaStream_t st) {
+  screen_batch_kernel<<<count, THREADS, 0, st>>>(d, lambda);
   return cudaGetLastError();
 }
 

@@ -43,6 +43,26 @@ struct ubqp_q {
 
 namespace ubqp {
 
+// One instance of a batch (device-resident descriptor of the batched stages).
+struct BatchDesc {
+  const int8_t* Q8;
+  int64_t ldq;
+  int n, W;
+  int64_t S;
+  uint64_t* X;        // S x W starts
+  int64_t* f;         // S values
+  int32_t* idx;       // S passing indices
+  int64_t* count;     // 1
+  double* Tm;         // 2: T, Mean
+  int64_t* stats;     // 3: sum, max, argmax
+  int32_t* flips;     // S
+  const float* Y;     // start-up y = Q x (rows = passing starts), or null
+  int64_t ldy;
+  unsigned* err;
+  uint64_t* best_x;   // W
+  int64_t* best_f;    // 2: value, index
+};
+
 __host__ __device__ inline int64_t words_of(int64_t n) { return (n + 63) / 64; }
 
 // SplitMix64 (Steele, Lea & Flood 2014): the first output of the sequential
@@ -66,12 +86,18 @@ __host__ __device__ __forceinline__ uint64_t valid_mask(int64_t n, int64_t w) {
   return (1ULL << (n - lo)) - 1ULL;
 }
 
+// Records a one-line detail for ubqp_last_error() and returns status.
+int record_error(int status, const char* fmt, ...) __attribute__((format(printf, 2, 3)));
+
 // ---- launchers (each returns cudaError_t of its launch) --------------------
 cudaError_t launch_prepare(const int8_t* Q, int n, int64_t ldq_in, ubqp_q* h,
                            cudaStream_t st);
+// seed_dev: when not null the seed is read from device memory at run time
+// (lets a captured graph be replayed with a new seed).
 cudaError_t launch_diversify(const uint64_t* x0, int n, int mode, uint64_t seed,
                              uint64_t round, int64_t S_total, int64_t s_begin,
-                             int64_t S_local, int div_H, uint64_t* X, cudaStream_t st);
+                             int64_t S_local, int div_H, uint64_t* X, cudaStream_t st,
+                             const uint64_t* seed_dev = nullptr);
 cudaError_t launch_eval_plain(const ubqp_q* h, const uint64_t* X, int64_t S,
                               int64_t* f, cudaStream_t st);
 size_t eval_tc_workspace(const ubqp_q* h, int64_t S);
@@ -80,10 +106,15 @@ size_t eval_tc_static_capacity();
 size_t ascent_tc_workspace(const ubqp_q* h, int64_t S);
 cudaError_t launch_ascent_init_tc(const ubqp_q* h, const uint64_t* X, const int32_t* idx,
                                   const int64_t* count, int64_t S, void* ws, size_t ws_bytes,
-                                  float** Y_out, cudaStream_t st);
+                                  float** Y_out, cudaStream_t st,
+                                  const void* mapA_in = nullptr);
 cudaError_t eval_tc_static_scratch(void** out);
+// mapA_in: a TMA descriptor (128 bytes) of the unpacked starts in ws made by
+// eval_tc_map_A, or nullptr to build one per call.
 cudaError_t launch_eval_tc(const ubqp_q* h, const uint64_t* X, int64_t S, int64_t* f,
-                           void* ws, size_t ws_bytes, cudaStream_t st);
+                           void* ws, size_t ws_bytes, cudaStream_t st,
+                           const void* mapA_in = nullptr);
+bool eval_tc_map_A(void* out128, const void* Xe, int64_t S, int n_tc);
 cudaError_t launch_screen_stats(const int64_t* f, int64_t S, int64_t offset, int64_t* stats,
                                 cudaStream_t st);
 cudaError_t launch_screen_apply(const int64_t* f, int64_t S, const int64_t* gstats,
@@ -98,6 +129,16 @@ cudaError_t launch_search_update(const int64_t* cand, const uint64_t* X, int W,
                                  const int64_t* count, const int32_t* idx, const int32_t* flips,
                                  int64_t* inc_f, uint64_t* inc_x, int64_t* history,
                                  int64_t* stats, cudaStream_t st);
+// batched stages: one launch over all instances of a batch
+cudaError_t launch_screen_batch(const BatchDesc* d, int count, double lambda, cudaStream_t st);
+cudaError_t launch_batch_items(const BatchDesc* d, const int32_t* order, int count, int2* items,
+                               int64_t* n_items, cudaStream_t st);
+cudaError_t launch_ascent_batch(const BatchDesc* d, const int2* items, const int64_t* n_items,
+                                int T, int C, int32_t max_flips, int grid, cudaStream_t st);
+int ascent_batch_grid(int T, int C, int sm_count);
+bool ascent_batch_supported(int T, int C);
+cudaError_t launch_best_batch(const BatchDesc* d, int count, cudaStream_t st);
+cudaError_t launch_set_u64(uint64_t* dst, uint64_t v, cudaStream_t st);
 cudaError_t launch_solve_stats(const int64_t* count, const int32_t* idx,
                                const int32_t* flips, const double* Tm,
                                const int64_t* sstats, const int64_t* best,

@@ -28,7 +28,9 @@ EXPORTS = ["ubqp_strerror", "ubqp_last_error", "ubqp_abi_version", "ubqp_q_prepa
            "ubqp_diversify", "ubqp_diversify_range", "ubqp_eval_workspace_size", "ubqp_eval",
            "ubqp_eval_noalloc", "ubqp_screen", "ubqp_screen_stats", "ubqp_screen_apply",
            "ubqp_ascent_workspace_size", "ubqp_ascent", "ubqp_best", "ubqp_solve_workspace_size",
-           "ubqp_solve", "ubqp_search_workspace_size", "ubqp_search"]
+           "ubqp_solve", "ubqp_search_workspace_size", "ubqp_search", "ubqp_batch_create",
+           "ubqp_batch_destroy", "ubqp_batch_run", "ubqp_batch_tune", "ubqp_batch_capture",
+           "ubqp_batch_result", "ubqp_batch_get", "ubqp_batch_config"]
 
 
 class UbqpError(RuntimeError):
@@ -104,6 +106,14 @@ def load() -> ctypes.CDLL:
                                       P, sz, P]),
         "ubqp_search_workspace_size": (sz, [P, ctypes.POINTER(SearchParams)]),
         "ubqp_search": (ctypes.c_int, [P, ctypes.POINTER(SearchParams), P, P, P, P, P, sz, P]),
+        "ubqp_batch_create": (ctypes.c_int, [P, i32, ctypes.POINTER(Params), ctypes.POINTER(P)]),
+        "ubqp_batch_destroy": (None, [P]),
+        "ubqp_batch_run": (ctypes.c_int, [P, u64, P]),
+        "ubqp_batch_tune": (ctypes.c_int, [P, P]),
+        "ubqp_batch_capture": (ctypes.c_int, [P, P]),
+        "ubqp_batch_result": (ctypes.c_int, [P, i32, ctypes.POINTER(P), ctypes.POINTER(P)]),
+        "ubqp_batch_config": (ctypes.c_int, [P, P, P, P, P, P]),
+        "ubqp_batch_get": (ctypes.c_int, [P, i32, P, P, P]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -333,3 +343,51 @@ def search(inst: Instance, num_samples: int, starts_per_round: int, rounds: int,
     _check(load().ubqp_search(inst.handle, ctypes.byref(p), _ptr(bx), _ptr(bf), _ptr(hist),
                               _ptr(st), _ptr(ws), ws.numel(), _stream(stream)))
     return {"best_x": bx, "best_f": bf, "history": hist[:rounds], "stats": st}
+
+
+class Batch:
+    """A batch plan over prepared instances (ubqp_batch_*): one round for every
+    instance per run, identical per instance to ``solve``."""
+
+    def __init__(self, instances: list, params: Params):
+        self.instances = list(instances)  # keep the handles alive
+        arr = (ctypes.c_void_p * len(self.instances))(*[i.handle.value for i in self.instances])
+        h = ctypes.c_void_p()
+        _check(load().ubqp_batch_create(arr, len(self.instances), ctypes.byref(params),
+                                        ctypes.byref(h)))
+        self._h = h
+        self.device = self.instances[0].device
+
+    def close(self):
+        if getattr(self, "_h", None) is not None:
+            load().ubqp_batch_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def run(self, seed: int, stream=None):
+        _check(load().ubqp_batch_run(self._h, seed % 2**64, _stream(stream)))
+
+    def tune(self, stream=None):
+        _check(load().ubqp_batch_tune(self._h, _stream(stream)))
+
+    def capture(self, stream=None):
+        _check(load().ubqp_batch_capture(self._h, _stream(stream)))
+
+    def config(self) -> dict:
+        v = [ctypes.c_int32() for _ in range(5)]
+        _check(load().ubqp_batch_config(self._h, *[ctypes.byref(x) for x in v]))
+        return dict(zip(["asc_threads", "asc_chunks", "eval_path", "streams", "graph"],
+                        [x.value for x in v]))
+
+    def result(self, i: int, stream=None):
+        """(best_x words, {value, index}) of instance i, copied to new tensors."""
+        W = self.instances[i].words
+        bx = torch.empty(W, dtype=torch.int64, device=self.device)
+        bf = torch.empty(2, dtype=torch.int64, device=self.device)
+        _check(load().ubqp_batch_get(self._h, i, _ptr(bx), _ptr(bf), _stream(stream)))
+        return bx, bf

@@ -1,0 +1,79 @@
+"""Batches of uneven instances: every instance's result equals its single
+solve (and the oracle's), with the default, the autotuned and the captured-
+graph execution."""
+import numpy as np
+import pytest
+import torch
+
+import oracle as orc
+from paper_1706_00037_gb300 import synth, ubqp
+
+pytestmark = pytest.mark.gpu
+
+
+def make_batch(sizes, densities, seed0=100):
+    Qs, insts = [], []
+    for k, (n, d) in enumerate(zip(sizes, densities)):
+        Q = synth.make_instance(n, d, seed0 + k)
+        Qs.append(Q)
+        insts.append(ubqp.Instance(torch.from_numpy(Q).cuda()))
+    return Qs, insts
+
+
+def check_against_single(insts, batch, params, seed):
+    for i, inst in enumerate(insts):
+        bx, bf = batch.result(i)
+        p1 = ubqp.make_params(params.num_starts, params.lambda_, mode=params.mode, seed=seed,
+                              eval_path=params.eval_path)
+        sx, sf, _ = ubqp.solve(inst, p1, want_stats=False)
+        torch.cuda.synchronize()
+        assert torch.equal(bf, sf), (i, bf.tolist(), sf.tolist())
+        assert torch.equal(bx, sx), i
+
+
+SIZES = [60, 700, 2500, 300, 1025, 129, 2100, 513]
+DENS = [1.0, 0.1, 0.5, 1.0, 0.1, 0.5, 1.0, 0.1]
+
+
+@pytest.mark.parametrize("mode", [ubqp.DIVERSIFY, ubqp.RANDOM])
+def test_batch_equals_single_solves(mode):
+    Qs, insts = make_batch(SIZES, DENS)
+    p = ubqp.make_params(256, 0.5, mode=mode, seed=1)
+    b = ubqp.Batch(insts, p)
+    b.run(seed=5)
+    torch.cuda.synchronize()
+    check_against_single(insts, b, p, 5)
+    # the small instances against the oracle too
+    for i in (0, 5):
+        want = orc.solve(Qs[i], 256, 0.5, seed=5, mode=mode)
+        bx, bf = b.result(i)
+        assert int(bf[0]) == want["best_f"] and int(bf[1]) == want["best_index"]
+        assert np.array_equal(bx.cpu().numpy().view(np.uint64), want["best_x"])
+
+
+def test_batch_tune_and_graph_keep_results():
+    Qs, insts = make_batch(SIZES, DENS, seed0=300)
+    p = ubqp.make_params(300, 0.25, seed=2)
+    b = ubqp.Batch(insts, p)
+    b.tune()
+    cfg = b.config()
+    assert cfg["asc_threads"] * cfg["asc_chunks"] * 16 >= max(SIZES)
+    b.run(seed=7)
+    torch.cuda.synchronize()
+    check_against_single(insts, b, p, 7)
+    b.capture()
+    assert b.config()["graph"] == 1
+    for seed in (11, 12):  # replays with new seeds
+        b.run(seed=seed)
+        torch.cuda.synchronize()
+        check_against_single(insts, b, p, seed)
+
+
+def test_batch_plain_eval_path():
+    Qs, insts = make_batch([200, 900, 1500], [0.5, 1.0, 0.1], seed0=500)
+    p = ubqp.make_params(128, 0.5, seed=3, eval_path=ubqp.EVAL_PLAIN)
+    b = ubqp.Batch(insts, p)
+    assert b.config()["eval_path"] == ubqp.EVAL_PLAIN
+    b.run(seed=9)
+    torch.cuda.synchronize()
+    check_against_single(insts, b, p, 9)
