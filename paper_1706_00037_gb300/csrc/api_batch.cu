@@ -64,6 +64,7 @@ struct ubqp_batch {
   std::vector<cudaStream_t> streams;
   std::vector<cudaEvent_t> ev_join;
   cudaEvent_t ev_fork = nullptr;
+  cudaStream_t cap_stream = nullptr;     // capture stream (the legacy stream cannot capture)
   cudaGraphExec_t exec = nullptr;
   cudaGraph_t graph = nullptr;
 };
@@ -156,6 +157,7 @@ void ubqp_batch_destroy(ubqp_batch* b) {
   for (cudaStream_t s : b->streams) cudaStreamDestroy(s);
   for (cudaEvent_t e : b->ev_join) cudaEventDestroy(e);
   if (b->ev_fork) cudaEventDestroy(b->ev_fork);
+  if (b->cap_stream) cudaStreamDestroy(b->cap_stream);
   cudaFree(b->dmem);
   delete b;
 }
@@ -287,7 +289,8 @@ int ubqp_batch_create(const ubqp_q* const* qs, int32_t count, const ubqp_params*
       return bfail(UBQP_ERR_CUDA, "stream creation failed");
     }
   }
-  if (cudaEventCreateWithFlags(&b->ev_fork, cudaEventDisableTiming) != cudaSuccess) {
+  if (cudaEventCreateWithFlags(&b->ev_fork, cudaEventDisableTiming) != cudaSuccess ||
+      cudaStreamCreateWithFlags(&b->cap_stream, cudaStreamNonBlocking) != cudaSuccess) {
     ubqp_batch_destroy(b);
     return bfail(UBQP_ERR_CUDA, "event creation failed");
   }
@@ -325,10 +328,11 @@ int ubqp_batch_capture(ubqp_batch* b, void* stream) {
   int r = run_body(b, st);
   if (r) return r;
   UBQP_BCUDA(cudaStreamSynchronize(st));
-  UBQP_BCUDA(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
-  r = run_body(b, st);
+  cudaStream_t cs = b->cap_stream;
+  UBQP_BCUDA(cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal));
+  r = run_body(b, cs);
   cudaGraph_t g = nullptr;
-  cudaError_t e = cudaStreamEndCapture(st, &g);
+  cudaError_t e = cudaStreamEndCapture(cs, &g);
   if (r) {
     if (g) cudaGraphDestroy(g);
     return r;
