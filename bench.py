@@ -49,6 +49,9 @@ def parse():
     ap.add_argument("--eval-path", choices=["auto", "tc", "plain"], default="auto")
     ap.add_argument("--cpu-sample", type=int, default=160,
                     help="starts in the oracle's timed sample")
+    ap.add_argument("--workload", choices=["table1", "batch64", "serve"], default="table1",
+                    help="table1: the default line; batch64: 64 uneven instances, batched "
+                         "vs one at a time; serve: the request-serving loop")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     return ap.parse_args()
@@ -192,10 +195,90 @@ def run_reference(a):
 
 # --------------------------------------------------------------------- GPU arm
 
+def batch_instances(count=64, seed=4):
+    """64 instances: n ~ U[200, 2500], density in {0.1, 0.5, 1.0}, seeds 4000+k."""
+    from paper_1706_00037_gb300 import synth
+    r = np.random.default_rng(seed)
+    ns = r.integers(200, 2501, count)
+    ds = r.choice([0.1, 0.5, 1.0], count)
+    return [(int(n), float(d), synth.make_instance(int(n), float(d), 4000 + k))
+            for k, (n, d) in enumerate(zip(ns, ds))]
+
+
+def run_batch64(a):
+    """Solves/s for 64 uneven instances: the batch plan (autotuned, CUDA graph)
+    against solving the same instances one at a time through ubqp_solve."""
+    import torch
+    from paper_1706_00037_gb300 import ubqp
+    torch.cuda.set_device(0)
+    data = batch_instances()
+    insts = [ubqp.Instance(torch.from_numpy(Q).cuda()) for _, _, Q in data]
+    S, lam = 1024, 0.5
+    params = ubqp.make_params(S, lam, seed=0)
+    # one at a time, workspace reused
+    need = max(ubqp.solve_workspace_size(i, params) for i in insts)
+    ws = torch.empty(need, dtype=torch.uint8, device="cuda")
+    bx = [torch.empty(i.words, dtype=torch.int64, device="cuda") for i in insts]
+    bf = [torch.empty(2, dtype=torch.int64, device="cuda") for _ in insts]
+
+    def loop(seed):
+        for k, inst in enumerate(insts):
+            params.seed = seed
+            ubqp.solve(inst, params, ws=ws, best_x=bx[k], best_f=bf[k], want_stats=False)
+
+    for w in range(a.warmup):
+        loop(10 + w)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for k in range(a.steps):
+        loop(100 + k)
+    torch.cuda.synchronize()
+    t_loop = time.perf_counter() - t0
+    ref = [(bf[k].clone(), bx[k].clone()) for k in range(len(insts))]
+    # batched: tune, capture, replay
+    b = ubqp.Batch(insts, ubqp.make_params(S, lam, seed=0))
+    b.tune()
+    b.capture()
+    for w in range(a.warmup):
+        b.run(10 + w)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    t0 = time.perf_counter()
+    e0.record()
+    for k in range(a.steps):
+        b.run(100 + k)
+    e1.record()
+    torch.cuda.synchronize()
+    t_batch = time.perf_counter() - t0
+    same = all(torch.equal(b.result(k)[1], ref[k][0]) and torch.equal(b.result(k)[0], ref[k][1])
+               for k in range(len(insts)))
+    value = len(insts) * a.steps / t_batch
+    line = {"metric": "solves/s, 64 instances n~U[200,2500]", "value": value, "unit": "solves/s",
+            "n_gpus": 1, "steps": a.steps, "warmup": a.warmup,
+            "ms_per_step": 1e3 * t_batch / a.steps, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "int64", "data": "synthetic",
+            "config": {"workload": "batch64", "instances": len(insts),
+                       "n": [n for n, _, _ in data], "starts_per_instance": S, "lambda": lam,
+                       "batch_config": b.config()},
+            "per_instance_loop_solves_per_s": len(insts) * a.steps / t_loop,
+            "speedup_batched_vs_loop": t_loop / t_batch,
+            "device_ms_per_batch": e0.elapsed_time(e1) / a.steps,
+            "results_identical_to_loop": bool(same)}
+    print(json.dumps(line), flush=True)
+
+
+def run_serve(a):
+    raise SystemExit("the serving loop is added later")
+
+
 def main():
     a = parse()
     if a.impl == "reference":
         return run_reference(a)
+    if a.workload == "batch64":
+        return run_batch64(a)
+    if a.workload == "serve":
+        return run_serve(a)
 
     import torch
     import torch.distributed as dist
