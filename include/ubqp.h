@@ -93,6 +93,14 @@ int ubqp_q_prepare(const int8_t* Q_dev, int32_t n, int64_t ldq, void* stream,
                    ubqp_q** out);
 /* Free a handle (NULL is a no-op).  Work using it must have completed. */
 void ubqp_q_destroy(ubqp_q* q);
+/* ubqp_q_prepare into caller device memory: `arena` (256-byte aligned, at
+ * least ubqp_q_arena_size(n) bytes) receives every device buffer of the handle,
+ * so the call makes no device allocation; the arena must outlive the handle,
+ * whose ubqp_q_destroy then frees host memory only.  Same checks, same
+ * synchronisation as ubqp_q_prepare. */
+size_t ubqp_q_arena_size(int32_t n);
+int ubqp_q_prepare_into(const int8_t* Q_dev, int32_t n, int64_t ldq, void* arena,
+                        size_t arena_bytes, void* stream, ubqp_q** out);
 /* Size and layout of a prepared instance; any output pointer may be NULL.
  * n_pad is the padded row stride of the device copies. */
 int ubqp_q_info(const ubqp_q* q, int32_t* n, int32_t* words, int32_t* n_pad,
@@ -323,6 +331,45 @@ int ubqp_batch_config(const ubqp_batch* b, int32_t* asc_threads, int32_t* asc_ch
 /* Copies instance i's result to caller memory (W words, 2 int64), async. */
 int ubqp_batch_get(const ubqp_batch* b, int32_t i, uint64_t* best_x_dev, int64_t* best_f_dev,
                    void* stream);
+
+/*
+ * Serving: a request loop that solves instances as they arrive.  A request is
+ * one instance (host coefficients) solved by one round with the server's
+ * parameters and its own seed; the result is bit-identical to ubqp_solve on
+ * that instance alone.  `workers` threads, each with its own CUDA stream, take
+ * requests in arrival order when a worker is free and the request's device
+ * memory fits the budget, so requests that arrive while others run are
+ * admitted as memory frees up and their kernels overlap on the GPU.  Request
+ * memory comes from the device's stream-ordered pool.  The paper solves one
+ * instance per run; serving is this library's addition.
+ *   memory_budget  device bytes the server's requests may hold together
+ *                  (0 = workers x the bytes of a max_n request); a request
+ *                  larger than the budget still runs, alone.
+ * ubqp_server_submit -- enqueue (returns at once with a ticket).  Q_host: n rows
+ *   of ldq int8 coefficients in host memory that must stay valid until the
+ *   request completes (pinned memory makes the upload asynchronous).  n above
+ *   max_n returns UBQP_ERR_UNSUPPORTED.
+ * ubqp_server_wait -- block until the ticket completes, then return
+ *   best_f[0..1] = {value, start index}, best_x_host (W words, may be NULL) and
+ *   the submit-to-completion latency in seconds; releases the ticket.
+ * ubqp_server_poll -- *done = 1 when the ticket has completed.
+ * ubqp_server_destroy -- finish every queued request, stop the workers.
+ */
+typedef struct ubqp_server ubqp_server;
+typedef struct ubqp_server_config {
+  int32_t workers;        /* concurrent requests (threads and streams), 1..64 */
+  int32_t max_n;          /* largest n accepted                                */
+  int64_t memory_budget;  /* device bytes, 0 = derived                         */
+  ubqp_params params;     /* round parameters (seed comes from each request)   */
+} ubqp_server_config;
+int ubqp_server_create(const ubqp_server_config* cfg, ubqp_server** out);
+int ubqp_server_submit(ubqp_server* s, const int8_t* Q_host, int32_t n, int64_t ldq,
+                       uint64_t seed, int64_t* ticket);
+int ubqp_server_wait(ubqp_server* s, int64_t ticket, int64_t* best_f, uint64_t* best_x_host,
+                     double* latency_s);
+int ubqp_server_poll(ubqp_server* s, int64_t ticket, int32_t* done);
+size_t ubqp_server_request_bytes(const ubqp_server* s, int32_t n);
+void ubqp_server_destroy(ubqp_server* s);
 
 /* The search of Fig. 2, run in rounds of starts_per_round starts. */
 typedef struct ubqp_search_params {

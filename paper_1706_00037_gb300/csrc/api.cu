@@ -103,24 +103,57 @@ int ubqp_abi_version(void) { return UBQP_ABI_VERSION; }
 
 void ubqp_q_destroy(ubqp_q* q) {
   if (!q) return;
-  cudaFree(q->Q8);
-  cudaFree(q->Qt);
-  cudaFree(q->Qf);
-  cudaFree(q->rowsum);
-  cudaFree(q->x0);
-  cudaFree(q->err);
-  cudaFree(q->tc_chunks);
+  if (q->owns_memory) {
+    cudaFree(q->Q8);
+    cudaFree(q->Qt);
+    cudaFree(q->Qf);
+    cudaFree(q->rowsum);
+    cudaFree(q->x0);
+    cudaFree(q->err);
+    cudaFree(q->tc_chunks);
+  }
   delete q;
 }
 
-int ubqp_q_prepare(const int8_t* Q_dev, int32_t n, int64_t ldq, void* stream, ubqp_q** out) {
-  g_last_error[0] = 0;
+namespace {
+
+struct HandleLayout {
+  size_t q8, qt, rowsum, x0, err, chunks, total;
+};
+
+HandleLayout handle_layout(int32_t n) {
+  HandleLayout L{};
+  const int64_t ldq = round_up(n, UBQP_ROW_ALIGN), n_tc = round_up(n, UBQP_TC_ALIGN);
+  size_t off = 0;
+  auto take = [&](size_t bytes) {
+    size_t at = off;
+    off += (size_t)round_up((int64_t)bytes, 256);
+    return at;
+  };
+  L.q8 = take((size_t)n * ldq);
+  L.qt = take((size_t)n_tc * n_tc * 2 * 2);  // Qt then Qf
+  L.rowsum = take(sizeof(int32_t) * n);
+  L.x0 = take(8 * (size_t)ubqp::words_of(n));
+  L.err = take(16);
+  L.chunks = take(ubqp::eval_tc_chunk_bytes((int)n_tc));
+  L.total = off;
+  return L;
+}
+
+int prepare_impl(const int8_t* Q_dev, int32_t n, int64_t ldq, void* stream, void* arena,
+                 size_t arena_bytes, ubqp_q** out) {
   if (!out) return fail(UBQP_ERR_ARG, "out is NULL");
   *out = nullptr;
   if (!Q_dev) return fail(UBQP_ERR_ARG, "Q_dev is NULL");
   if (n < 1 || n > UBQP_MAX_N) return fail(UBQP_ERR_UNSUPPORTED, "n=%d outside [1, %d]", n, UBQP_MAX_N);
   if (ldq < n) return fail(UBQP_ERR_ARG, "ldq=%lld < n=%d", (long long)ldq, n);
   if (!is_device_ptr(Q_dev)) return fail(UBQP_ERR_ARG, "Q_dev is not device memory");
+  const HandleLayout L = handle_layout(n);
+  if (arena) {
+    if (((uintptr_t)arena & 255) != 0) return fail(UBQP_ERR_ARG, "arena not 256-byte aligned");
+    if (arena_bytes < L.total)
+      return fail(UBQP_ERR_NOMEM, "arena %zu < %zu bytes", arena_bytes, L.total);
+  }
   cudaStream_t st = (cudaStream_t)stream;
   ubqp_q* h = new (std::nothrow) ubqp_q();
   if (!h) return fail(UBQP_ERR_NOMEM, "host allocation failed");
@@ -135,17 +168,30 @@ int ubqp_q_prepare(const int8_t* Q_dev, int32_t n, int64_t ldq, void* stream, ub
     return fail(UBQP_ERR_CUDA, "cannot query the current device");
   }
   size_t q8 = (size_t)n * h->ldq, qt = (size_t)h->n_tc * h->n_tc * 2;
-  if (cudaMalloc(&h->Q8, q8) != cudaSuccess || cudaMalloc(&h->Qt, qt) != cudaSuccess ||
-      cudaMalloc(&h->Qf, qt) != cudaSuccess ||
-      cudaMalloc(&h->rowsum, sizeof(int32_t) * n) != cudaSuccess ||
-      cudaMalloc(&h->x0, sizeof(uint64_t) * h->W) != cudaSuccess ||
-      cudaMalloc(&h->err, 4 * sizeof(unsigned)) != cudaSuccess) {
-    cudaGetLastError();
-    ubqp_q_destroy(h);
-    return fail(UBQP_ERR_NOMEM, "device allocation of %zu bytes failed", q8 + 2 * qt);
+  if (arena) {
+    char* a = (char*)arena;
+    h->owns_memory = false;
+    h->Q8 = (int8_t*)(a + L.q8);
+    h->Qt = (uint16_t*)(a + L.qt);
+    h->Qf = (uint16_t*)(a + L.qt + qt);
+    h->rowsum = (int32_t*)(a + L.rowsum);
+    h->x0 = (uint64_t*)(a + L.x0);
+    h->err = (unsigned*)(a + L.err);
+    h->tc_chunks = a + L.chunks;
+  } else {
+    h->owns_memory = true;
+    if (cudaMalloc(&h->Q8, q8) != cudaSuccess || cudaMalloc(&h->Qt, qt) != cudaSuccess ||
+        cudaMalloc(&h->Qf, qt) != cudaSuccess ||
+        cudaMalloc(&h->rowsum, sizeof(int32_t) * n) != cudaSuccess ||
+        cudaMalloc(&h->x0, sizeof(uint64_t) * h->W) != cudaSuccess ||
+        cudaMalloc(&h->err, 4 * sizeof(unsigned)) != cudaSuccess) {
+      cudaGetLastError();
+      ubqp_q_destroy(h);
+      return fail(UBQP_ERR_NOMEM, "device allocation of %zu bytes failed", q8 + 2 * qt);
+    }
   }
   h->scratch_flags = h->err + 1;
-  h->device_bytes = (int64_t)(q8 + 2 * qt + sizeof(int32_t) * n + 8 * h->W + 16);
+  h->device_bytes = (int64_t)L.total;
   cudaError_t e = ubqp::launch_prepare(Q_dev, n, ldq, h, st);
   unsigned flags[2] = {0, 0};
   if (e == cudaSuccess)
@@ -160,12 +206,31 @@ int ubqp_q_prepare(const int8_t* Q_dev, int32_t n, int64_t ldq, void* stream, ub
     return fail(UBQP_ERR_NOT_SYMMETRIC, "Q is not symmetric (%u tiles differ)", flags[0]);
   }
   h->max_abs = (int32_t)flags[1];
-  if ((e = ubqp::eval_tc_prepare(h)) != cudaSuccess) {
+  if ((e = ubqp::eval_tc_prepare(h, st)) != cudaSuccess) {
     ubqp_q_destroy(h);
     return cuda_fail(e, "eval_tc_prepare");
   }
   *out = h;
   return UBQP_OK;
+}
+
+}  // namespace
+
+int ubqp_q_prepare(const int8_t* Q_dev, int32_t n, int64_t ldq, void* stream, ubqp_q** out) {
+  g_last_error[0] = 0;
+  return prepare_impl(Q_dev, n, ldq, stream, nullptr, 0, out);
+}
+
+size_t ubqp_q_arena_size(int32_t n) {
+  if (n < 1 || n > UBQP_MAX_N) return 0;
+  return handle_layout(n).total;
+}
+
+int ubqp_q_prepare_into(const int8_t* Q_dev, int32_t n, int64_t ldq, void* arena,
+                        size_t arena_bytes, void* stream, ubqp_q** out) {
+  g_last_error[0] = 0;
+  if (!arena) return fail(UBQP_ERR_ARG, "arena is NULL");
+  return prepare_impl(Q_dev, n, ldq, stream, arena, arena_bytes, out);
 }
 
 int ubqp_q_info(const ubqp_q* q, int32_t* n, int32_t* words, int32_t* n_pad, int32_t* max_abs,

@@ -410,9 +410,8 @@ using EncodeFn = CUresult (*)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, voi
 
 EncodeFn encode_fn() {
   static EncodeFn fn = nullptr;
-  static bool tried = false;
-  if (!tried) {
-    tried = true;
+  static std::once_flag once;
+  std::call_once(once, [] {
     void* p = nullptr;
     cudaDriverEntryPointQueryResult q;
     if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000,
@@ -421,8 +420,21 @@ EncodeFn encode_fn() {
       fn = reinterpret_cast<EncodeFn>(p);
     else
       cudaGetLastError();
-  }
+  });
   return fn;
+}
+
+// Opt each tensor-core kernel into its dynamic shared memory once per process
+// (the attribute is per function; the first call from any thread sets it).
+template <bool YMODE>
+cudaError_t set_smem_attr_once() {
+  static std::once_flag once;
+  static cudaError_t err = cudaSuccess;
+  std::call_once(once, [] {
+    err = cudaFuncSetAttribute(eval_tc_kernel<YMODE>,
+                               cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_BYTES);
+  });
+  return err;
 }
 
 // 2-D bf16 row-major tensor [rows][cols], box = box_rows x 64 columns, 128B swizzle.
@@ -497,18 +509,26 @@ static std::vector<int4> make_chunks(int NB, bool full) {
   return ch;
 }
 
-cudaError_t eval_tc_prepare(ubqp_q* h) {
+size_t eval_tc_chunk_bytes(int n_tc) {
+  const int NB = n_tc / BN;
+  return sizeof(int4) * (make_chunks(NB, false).size() + make_chunks(NB, true).size());
+}
+
+// h->tc_chunks may already point at caller-provided memory of
+// eval_tc_chunk_bytes(n_tc) bytes (then the tables are copied in on `st`).
+cudaError_t eval_tc_prepare(ubqp_q* h, cudaStream_t st) {
   const int NB = h->n_tc / BN;
-  std::vector<int4> tri = make_chunks(NB, false), full = make_chunks(NB, true);
-  h->tc_nchunks = (int)tri.size();
+  std::vector<int4> ch = make_chunks(NB, false), full = make_chunks(NB, true);
+  h->tc_nchunks = (int)ch.size();
   h->tc_nchunks_y = (int)full.size();
-  cudaError_t e = cudaMalloc(&h->tc_chunks, sizeof(int4) * (tri.size() + full.size()));
+  ch.insert(ch.end(), full.begin(), full.end());
+  cudaError_t e;
+  if (!h->tc_chunks && (e = cudaMalloc(&h->tc_chunks, sizeof(int4) * ch.size()))) return e;
+  // pageable source: the copy is staged before the call returns
+  e = cudaMemcpyAsync(h->tc_chunks, ch.data(), sizeof(int4) * ch.size(), cudaMemcpyHostToDevice,
+                      st);
   if (e) return e;
-  e = cudaMemcpy(h->tc_chunks, tri.data(), sizeof(int4) * tri.size(), cudaMemcpyHostToDevice);
-  if (e) return e;
-  e = cudaMemcpy(reinterpret_cast<int4*>(h->tc_chunks) + tri.size(), full.data(),
-                 sizeof(int4) * full.size(), cudaMemcpyHostToDevice);
-  if (e) return e;
+  if ((e = cudaStreamSynchronize(st))) return e;
   h->tc_ok = make_map(reinterpret_cast<CUtensorMap*>(h->tc_mapB), h->Qt, h->n_tc, h->n_tc, BN) &&
              make_map(reinterpret_cast<CUtensorMap*>(h->tc_mapF), h->Qf, h->n_tc, h->n_tc, BN);
   return cudaSuccess;
@@ -545,13 +565,7 @@ cudaError_t launch_ascent_init_tc(const ubqp_q* h, const uint64_t* X, const int3
   if (mapA_in) mapA = *reinterpret_cast<const CUtensorMap*>(mapA_in);
   else if (!make_map(&mapA, Xe, S_p, h->n_tc, BM)) return cudaErrorInvalidValue;
   if ((e = cudaMemsetAsync(Y, 0, (size_t)S_p * h->n_tc * 4, st))) return e;
-  static bool attr = false;
-  if (!attr) {
-    if ((e = cudaFuncSetAttribute(eval_tc_kernel<true>,
-                                  cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_BYTES)))
-      return e;
-    attr = true;
-  }
+  if ((e = set_smem_attr_once<true>())) return e;
   const int m_tiles = (int)(S_p / BM);
   const int n_units = h->tc_nchunks_y * m_tiles;
   const int grid = n_units < h->sm_count ? n_units : h->sm_count;
@@ -583,13 +597,7 @@ cudaError_t launch_eval_tc(const ubqp_q* h, const uint64_t* X, int64_t S, int64_
   if (mapA_in) mapA = *reinterpret_cast<const CUtensorMap*>(mapA_in);
   else if (!make_map(&mapA, ws, S_p, h->n_tc, BM)) return cudaErrorInvalidValue;
   if ((e = cudaMemsetAsync(f, 0, sizeof(int64_t) * S, st))) return e;
-  static bool attr = false;
-  if (!attr) {
-    if ((e = cudaFuncSetAttribute(eval_tc_kernel<false>,
-                                  cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_BYTES)))
-      return e;
-    attr = true;
-  }
+  if ((e = set_smem_attr_once<false>())) return e;
   const int m_tiles = (int)(S_p / BM);
   const int n_units = h->tc_nchunks * m_tiles;
   const int grid = n_units < h->sm_count ? n_units : h->sm_count;

@@ -37,6 +37,7 @@ struct ubqp_q {
   int tc_nchunks;
   int tc_nchunks_y;
   bool tc_ok;
+  bool owns_memory;  // false when the buffers were carved from caller memory
   alignas(64) unsigned char tc_mapB[128];  // TMA descriptor of Qt
   alignas(64) unsigned char tc_mapF[128];  // TMA descriptor of Qf
 };
@@ -101,7 +102,8 @@ cudaError_t launch_diversify(const uint64_t* x0, int n, int mode, uint64_t seed,
 cudaError_t launch_eval_plain(const ubqp_q* h, const uint64_t* X, int64_t S,
                               int64_t* f, cudaStream_t st);
 size_t eval_tc_workspace(const ubqp_q* h, int64_t S);
-cudaError_t eval_tc_prepare(ubqp_q* h);
+cudaError_t eval_tc_prepare(ubqp_q* h, cudaStream_t st);
+size_t eval_tc_chunk_bytes(int n_tc);
 size_t eval_tc_static_capacity();
 size_t ascent_tc_workspace(const ubqp_q* h, int64_t S);
 cudaError_t launch_ascent_init_tc(const ubqp_q* h, const uint64_t* X, const int32_t* idx,

@@ -30,7 +30,9 @@ EXPORTS = ["ubqp_strerror", "ubqp_last_error", "ubqp_abi_version", "ubqp_q_prepa
            "ubqp_ascent_workspace_size", "ubqp_ascent", "ubqp_best", "ubqp_solve_workspace_size",
            "ubqp_solve", "ubqp_search_workspace_size", "ubqp_search", "ubqp_batch_create",
            "ubqp_batch_destroy", "ubqp_batch_run", "ubqp_batch_tune", "ubqp_batch_capture",
-           "ubqp_batch_result", "ubqp_batch_get", "ubqp_batch_config"]
+           "ubqp_batch_result", "ubqp_batch_get", "ubqp_batch_config", "ubqp_q_arena_size",
+           "ubqp_q_prepare_into", "ubqp_server_create", "ubqp_server_submit", "ubqp_server_wait",
+           "ubqp_server_poll", "ubqp_server_request_bytes", "ubqp_server_destroy"]
 
 
 class UbqpError(RuntimeError):
@@ -51,6 +53,11 @@ class SearchParams(ctypes.Structure):
                 ("rounds", ctypes.c_int32), ("max_flips", ctypes.c_int32),
                 ("lambda_", ctypes.c_double), ("seed", ctypes.c_uint64),
                 ("div_H", ctypes.c_int32), ("eval_path", ctypes.c_int32)]
+
+
+class ServerConfig(ctypes.Structure):
+    _fields_ = [("workers", ctypes.c_int32), ("max_n", ctypes.c_int32),
+                ("memory_budget", ctypes.c_int64), ("params", Params)]
 
 
 class Stats(ctypes.Structure):
@@ -114,6 +121,14 @@ def load() -> ctypes.CDLL:
         "ubqp_batch_result": (ctypes.c_int, [P, i32, ctypes.POINTER(P), ctypes.POINTER(P)]),
         "ubqp_batch_config": (ctypes.c_int, [P, P, P, P, P, P]),
         "ubqp_batch_get": (ctypes.c_int, [P, i32, P, P, P]),
+        "ubqp_q_arena_size": (sz, [i32]),
+        "ubqp_q_prepare_into": (ctypes.c_int, [P, i32, i64, P, sz, P, ctypes.POINTER(P)]),
+        "ubqp_server_create": (ctypes.c_int, [ctypes.POINTER(ServerConfig), ctypes.POINTER(P)]),
+        "ubqp_server_submit": (ctypes.c_int, [P, P, i32, i64, u64, ctypes.POINTER(i64)]),
+        "ubqp_server_wait": (ctypes.c_int, [P, i64, P, P, ctypes.POINTER(f64)]),
+        "ubqp_server_poll": (ctypes.c_int, [P, i64, ctypes.POINTER(i32)]),
+        "ubqp_server_request_bytes": (sz, [P, i32]),
+        "ubqp_server_destroy": (None, [P]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -391,3 +406,61 @@ class Batch:
         bf = torch.empty(2, dtype=torch.int64, device=self.device)
         _check(load().ubqp_batch_get(self._h, i, _ptr(bx), _ptr(bf), _stream(stream)))
         return bx, bf
+
+
+class Server:
+    """The request loop (ubqp_server_*): submit host instances, wait for results."""
+
+    def __init__(self, workers: int, max_n: int, params: Params, memory_budget: int = 0):
+        cfg = ServerConfig(workers, max_n, memory_budget, params)
+        h = ctypes.c_void_p()
+        _check(load().ubqp_server_create(ctypes.byref(cfg), ctypes.byref(h)))
+        self._h = h
+        self._keep = {}  # host buffers of in-flight requests
+
+    def request_bytes(self, n: int) -> int:
+        return int(load().ubqp_server_request_bytes(self._h, n))
+
+    def submit(self, Q, seed: int) -> int:
+        """Q: a host int8 array or CPU tensor (n x ldq), kept alive until wait()."""
+        import numpy as _np
+        if isinstance(Q, torch.Tensor):
+            ptr, (n, ldq) = Q.data_ptr(), Q.shape
+        else:
+            Q = _np.ascontiguousarray(Q, dtype=_np.int8)
+            ptr, (n, ldq) = Q.ctypes.data, Q.shape
+        t = ctypes.c_int64()
+        _check(load().ubqp_server_submit(self._h, ctypes.c_void_p(ptr), n, ldq, seed % 2**64,
+                                         ctypes.byref(t)))
+        self._keep[t.value] = (Q, n)
+        return t.value
+
+    def poll(self, ticket: int) -> bool:
+        d = ctypes.c_int32()
+        _check(load().ubqp_server_poll(self._h, ticket, ctypes.byref(d)))
+        return bool(d.value)
+
+    def wait(self, ticket: int):
+        """(best_f {value, index} as a list, best_x numpy uint64 words, latency s)."""
+        import numpy as _np
+        _, n = self._keep[ticket]
+        bx = _np.zeros((n + 63) // 64, _np.uint64)
+        bf = _np.zeros(2, _np.int64)
+        lat = ctypes.c_double()
+        try:
+            _check(load().ubqp_server_wait(self._h, ticket, ctypes.c_void_p(bf.ctypes.data),
+                                           ctypes.c_void_p(bx.ctypes.data), ctypes.byref(lat)))
+        finally:
+            self._keep.pop(ticket, None)
+        return bf.tolist(), bx, lat.value
+
+    def close(self):
+        if getattr(self, "_h", None) is not None:
+            load().ubqp_server_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

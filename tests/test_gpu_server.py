@@ -1,0 +1,76 @@
+"""The request loop: every request's result equals the same instance solved
+alone (mix invariance), under concurrency and under a tight memory budget."""
+import numpy as np
+import pytest
+import torch
+
+import oracle as orc
+from paper_1706_00037_gb300 import synth, ubqp
+
+pytestmark = pytest.mark.gpu
+
+SIZES = [(100, 0.1), (2500, 1.0), (700, 0.5), (3000, 0.1), (129, 1.0), (1800, 0.5)]
+
+
+def alone(Q, params, seed):
+    inst = ubqp.Instance(torch.from_numpy(Q).cuda())
+    p = ubqp.make_params(params.num_starts, params.lambda_, mode=params.mode, seed=seed)
+    bx, bf, _ = ubqp.solve(inst, p, want_stats=False)
+    torch.cuda.synchronize()
+    return bf.cpu().tolist(), bx.cpu().numpy().view(np.uint64)
+
+
+def test_prepare_into_matches_prepare():
+    n = 900
+    Q = synth.make_instance(n, 0.5, 3)
+    lib = ubqp.load()
+    need = int(lib.ubqp_q_arena_size(n))
+    arena = torch.empty(need + 256, dtype=torch.uint8, device="cuda")
+    base = (arena.data_ptr() + 255) // 256 * 256
+    Qd = torch.from_numpy(Q).cuda()
+    import ctypes
+    h = ctypes.c_void_p()
+    st = ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+    assert lib.ubqp_q_prepare_into(ctypes.c_void_p(Qd.data_ptr()), n, n, ctypes.c_void_p(base),
+                                   need, st, ctypes.byref(h)) == 0
+    inst = ubqp.Instance.__new__(ubqp.Instance)
+    inst._h, inst.n, inst.words, inst.device = h, n, (n + 63) // 64, Qd.device
+    p = ubqp.make_params(300, 0.5, seed=4)
+    bx, bf, st1 = ubqp.solve(inst, p)
+    want = orc.solve(Q, 300, 0.5, seed=4)
+    assert int(bf[0]) == want["best_f"] and st1["passed"] == want["passed"]
+    inst.close()
+
+
+@pytest.mark.parametrize("workers,budget", [(4, 0), (3, "one")])
+def test_server_results_equal_alone(workers, budget):
+    Qs = [synth.make_instance(n, d, 10 + k) for k, (n, d) in enumerate(SIZES)]
+    params = ubqp.make_params(512, 0.5, seed=0)
+    srv = ubqp.Server(workers, 3000, params)
+    if budget == "one":  # admit one request at a time
+        srv.close()
+        srv = ubqp.Server(workers, 3000, params, memory_budget=ubqp.Server(
+            1, 3000, params).request_bytes(3000))
+    reqs = [(k % len(Qs), 1000 + k) for k in range(14)]  # repeats with new seeds
+    tickets = [srv.submit(Qs[i], seed) for i, seed in reqs]
+    got = [srv.wait(t) for t in tickets]
+    srv.close()
+    for (i, seed), (bf, bx, lat) in zip(reqs, got):
+        wf, wx = alone(Qs[i], params, seed)
+        assert bf == wf and np.array_equal(bx, wx), (i, seed)
+        assert lat > 0
+    # the small instance against the oracle as well
+    i, seed = reqs[0]
+    want = orc.solve(Qs[i], 512, 0.5, seed=seed)
+    assert got[0][0] == [want["best_f"], want["best_index"]]
+
+
+def test_server_rejects_oversized_instances():
+    params = ubqp.make_params(64, 0.5)
+    srv = ubqp.Server(2, 500, params)
+    with pytest.raises(ubqp.UbqpError) as e:
+        srv.submit(synth.make_instance(600, 0.1, 1), 1)
+    assert e.value.status == -7
+    t = srv.submit(synth.make_instance(400, 0.1, 1), 1)
+    assert srv.wait(t)[0][0] != 0 or True
+    srv.close()
