@@ -52,6 +52,10 @@ def parse():
     ap.add_argument("--workload", choices=["table1", "batch64", "serve"], default="table1",
                     help="table1: the default line; batch64: 64 uneven instances, batched "
                          "vs one at a time; serve: the request-serving loop")
+    ap.add_argument("--serve-seconds", type=float, default=None,
+                    help="seconds of Poisson arrivals (default 60 for --workload serve, 10 "
+                         "inside the default line)")
+    ap.add_argument("--no-serve", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     return ap.parse_args()
@@ -267,8 +271,86 @@ def run_batch64(a):
     print(json.dumps(line), flush=True)
 
 
+def serve_pool(count=24, seed=5):
+    """Request instances: n log-uniform in [500, 7000], density in {0.1, 1.0}."""
+    from paper_1706_00037_gb300 import synth
+    r = np.random.default_rng(seed)
+    ns = np.exp(r.uniform(np.log(500), np.log(7000), count)).astype(int)
+    ds = r.choice([0.1, 1.0], count)
+    return [(int(n), float(d), synth.make_instance(int(n), float(d), 5000 + k))
+            for k, (n, d) in enumerate(zip(ns, ds))]
+
+
+def serve_measure(duration_s: float, rate: float = 200.0, workers: int = 8, seed: int = 5,
+                  seq_requests: int = 300):
+    """Poisson arrivals at `rate` req/s for `duration_s` into the request loop;
+    returns served solves/s, latency percentiles and the one-at-a-time rate."""
+    import threading
+    import torch
+    from paper_1706_00037_gb300 import ubqp
+    pool = serve_pool()
+    pinned = [torch.from_numpy(Q).pin_memory() for _, _, Q in pool]
+    S, lam = 1024, 0.5
+    params = ubqp.make_params(S, lam, seed=0)
+    r = np.random.default_rng(seed)
+    gaps = r.exponential(1.0 / rate, int(rate * duration_s * 1.2) + 16)
+    t_arr = np.cumsum(gaps)
+    t_arr = t_arr[t_arr < duration_s]
+    which = r.integers(0, len(pool), t_arr.shape[0])
+    srv = ubqp.Server(workers, max(n for n, _, _ in pool), params)
+    for k in range(2 * workers):  # warm-up (module loading, pool growth)
+        srv.wait(srv.submit(pinned[k % len(pool)], 10**6 + k))
+    tickets = [None] * len(t_arr)
+    t0 = time.perf_counter()
+
+    def submitter():
+        for k, (ta, i) in enumerate(zip(t_arr, which)):
+            d = t0 + ta - time.perf_counter()
+            if d > 0:
+                time.sleep(d)
+            tickets[k] = srv.submit(pinned[i], k)
+
+    th = threading.Thread(target=submitter)
+    th.start()
+    th.join()
+    res = [srv.wait(t) for t in tickets]
+    t_end = time.perf_counter()
+    srv.close()
+    lat = np.array([x[2] for x in res]) * 1e3
+    # the same requests one at a time through the public API (upload, prepare, solve)
+    m = min(seq_requests, len(res))
+    out_x = torch.empty(111, dtype=torch.int64).pin_memory()
+    same = True
+    ts = time.perf_counter()
+    for k in range(m):
+        Qd = pinned[which[k]].to("cuda", non_blocking=True)
+        inst = ubqp.Instance(Qd)
+        params.seed = k
+        bx, bf, _ = ubqp.solve(inst, params, want_stats=False)
+        bfh = bf.cpu().tolist()
+        same = same and bfh == res[k][0]
+        inst.close()
+    t_seq = time.perf_counter() - ts
+    return {"served_solves_per_s": len(res) / (t_end - t0), "requests": len(res),
+            "offered_req_per_s": rate, "duration_s": duration_s, "workers": workers,
+            "p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99)),
+            "max_ms": float(lat.max()),
+            "sequential_solves_per_s": m / t_seq, "sequential_requests": m,
+            "results_identical_to_alone": bool(same),
+            "pool": {"instances": len(pool), "n": [n for n, _, _ in pool],
+                     "density": [d for _, d, _ in pool], "starts": S, "lambda": lam}}
+
+
 def run_serve(a):
-    raise SystemExit("the serving loop is added later")
+    import torch
+    torch.cuda.set_device(0)
+    m = serve_measure(a.serve_seconds)
+    line = {"metric": "served solves/s with p50/p99 latency (Poisson 200 req/s)",
+            "value": m["served_solves_per_s"], "unit": "solves/s", "n_gpus": 1,
+            "steps": m["requests"], "warmup": 16, "ms_per_step": 1e3 / m["served_solves_per_s"],
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int64",
+            "data": "synthetic", "config": {"workload": "serve", **m["pool"]}, "serve": m}
+    print(json.dumps(line), flush=True)
 
 
 def main():
@@ -278,6 +360,7 @@ def main():
     if a.workload == "batch64":
         return run_batch64(a)
     if a.workload == "serve":
+        a.serve_seconds = a.serve_seconds or 60.0
         return run_serve(a)
 
     import torch
@@ -498,6 +581,10 @@ def main():
                "what": "instance Q from pinned host memory, ubqp_q_prepare, ubqp_solve, "
                        "best solution and value back to host, per step"}
 
+    served = None
+    if rank == 0 and world == 1 and not a.no_serve:
+        served = serve_measure(a.serve_seconds or 10.0, seq_requests=150)
+
     cpu = None
     if rank == 0 and world == 1 and not a.no_cpu:
         import oracle as orc
@@ -525,6 +612,7 @@ def main():
                 "passed_per_step": passers / a.steps, "flips_per_step": flips_timed / a.steps,
                 "kernels": kernels, "roofline": roofline, "roofline_eval": roof_eval,
                 "roofline_ascent": roof_asc, "cpu_baseline": cpu, "e2e": e2e,
+                "served": served,
                 "clocks": clocks, "gpu_launches": launches_per_step * a.steps,
                 "wall_s_timed_region": t_wall}
         print(json.dumps(line), flush=True)
