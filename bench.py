@@ -315,6 +315,13 @@ def serve_measure(duration_s: float, rate: float = 200.0, workers: int = 8, seed
     th.join()
     res = [srv.wait(t) for t in tickets]
     t_end = time.perf_counter()
+    # capacity: the same request mix submitted at once (a saturating burst)
+    burst = min(len(t_arr), 1200)
+    tb = time.perf_counter()
+    bt = [srv.submit(pinned[which[k]], k) for k in range(burst)]
+    for t in bt:
+        srv.wait(t)
+    t_burst = time.perf_counter() - tb
     srv.close()
     lat = np.array([x[2] for x in res]) * 1e3
     # the same requests one at a time through the public API (upload, prepare, solve)
@@ -335,6 +342,7 @@ def serve_measure(duration_s: float, rate: float = 200.0, workers: int = 8, seed
             "offered_req_per_s": rate, "duration_s": duration_s, "workers": workers,
             "p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99)),
             "max_ms": float(lat.max()),
+            "saturated_solves_per_s": burst / t_burst, "saturating_burst": burst,
             "sequential_solves_per_s": m / t_seq, "sequential_requests": m,
             "results_identical_to_alone": bool(same),
             "pool": {"instances": len(pool), "n": [n for n, _, _ in pool],
