@@ -62,7 +62,7 @@ typedef enum ubqp_status {
 /* Start generation modes (see ubqp_diversify). */
 enum { UBQP_MODE_RANDOM = 0, UBQP_MODE_DIVERSIFY = 1 };
 /* Evaluation paths (see ubqp_eval). */
-enum { UBQP_EVAL_AUTO = 0, UBQP_EVAL_TC = 1, UBQP_EVAL_PLAIN = 2 };
+enum { UBQP_EVAL_AUTO = 0, UBQP_EVAL_TC = 1, UBQP_EVAL_PLAIN = 2, UBQP_EVAL_TC_STAGED = 3 };
 
 /* Opaque prepared instance: device-resident Q in the layouts the kernels use,
  * its row sums, max|Q|, the first-derivative start and an error word. */
@@ -148,9 +148,13 @@ int ubqp_diversify_range(const ubqp_q* q, const uint64_t* x0_dev, int32_t mode,
  *        diag(Q), f = sum_j x_j sum_{k<=j} Q'_jk x_k, so only the lower block
  *        triangle of X * Q'^t is formed (tcgen05 kind::f16, bf16 operands,
  *        fp32 accumulation in tensor memory, exact), and an int64 epilogue
- *        folds the row-dot with x without writing the product.  Needs
- *        ws_bytes >= ubqp_eval_workspace_size(q, S, path) of device scratch
- *        (16-byte aligned) for the unpacked solutions.
+ *        folds the row-dot with x without writing the product.  The 0/1
+ *        operand is built in shared memory straight from the bit-packed
+ *        solutions; needs no workspace.
+ *   path UBQP_EVAL_TC_STAGED: the same contraction with the solutions first
+ *        unpacked to bf16 in device scratch and both operands fed by TMA;
+ *        needs ws_bytes >= ubqp_eval_workspace_size(q, S, path) (16-byte
+ *        aligned).
  *   path UBQP_EVAL_PLAIN: one block per solution on the CUDA cores (dp4a);
  *        needs no workspace.
  *   path UBQP_EVAL_AUTO: UBQP_EVAL_TC.
@@ -161,9 +165,9 @@ int ubqp_eval(const ubqp_q* q, const uint64_t* X_dev, int64_t S, int64_t* f_dev,
               int32_t path, void* ws, size_t ws_bytes, void* stream);
 
 /*
- * ubqp_eval_noalloc -- the tensor-core evaluation of ubqp_eval (same results,
- * bit for bit) for callers that cannot allocate device memory or hand the
- * library a workspace: for example a host whose device memory is entirely
+ * ubqp_eval_noalloc -- the staged tensor-core evaluation of ubqp_eval
+ * (UBQP_EVAL_TC_STAGED; same results, bit for bit) for callers that cannot
+ * allocate device memory or hand the library a workspace: for example a host whose device memory is entirely
  * reserved by another allocator (a framework's caching pool, an application
  * with a fixed memory budget), or a latency-critical loop that must not run
  * cudaMalloc/cudaFree, which can synchronise the whole device.  The paper has

@@ -72,7 +72,7 @@ SolveLayout solve_layout(const ubqp_q* q, const ubqp_params* p) {
   L.flips = take((size_t)S * 4);
   L.small = take(kSmallBytes);
   const int path = resolve_path(p->eval_path);
-  const size_t ev = path == UBQP_EVAL_TC ? ubqp::eval_tc_workspace(q, S) : 0;
+  const size_t ev = path == UBQP_EVAL_TC_STAGED ? ubqp::eval_tc_workspace(q, S) : 0;
   const size_t as = ubqp::ascent_tc_workspace(q, S);
   L.eval = take(ev > as ? ev : as);
   L.total = off;
@@ -290,7 +290,7 @@ int ubqp_diversify(const ubqp_q* q, const uint64_t* x0_dev, int32_t mode, uint64
 
 size_t ubqp_eval_workspace_size(const ubqp_q* q, int64_t S, int32_t path) {
   if (!q || S < 0) return 0;
-  return resolve_path(path) == UBQP_EVAL_TC ? ubqp::eval_tc_workspace(q, S) : 0;
+  return resolve_path(path) == UBQP_EVAL_TC_STAGED ? ubqp::eval_tc_workspace(q, S) : 0;
 }
 
 int ubqp_eval(const ubqp_q* q, const uint64_t* X_dev, int64_t S, int64_t* f_dev, int32_t path,
@@ -298,7 +298,7 @@ int ubqp_eval(const ubqp_q* q, const uint64_t* X_dev, int64_t S, int64_t* f_dev,
   if (!q || !X_dev || !f_dev) return fail(UBQP_ERR_ARG, "NULL argument");
   if (S < 0) return fail(UBQP_ERR_ARG, "S < 0");
   path = resolve_path(path);
-  if (path != UBQP_EVAL_TC && path != UBQP_EVAL_PLAIN)
+  if (path != UBQP_EVAL_TC && path != UBQP_EVAL_PLAIN && path != UBQP_EVAL_TC_STAGED)
     return fail(UBQP_ERR_ARG, "unknown eval path %d", path);
   if (S == 0) return UBQP_OK;
   cudaStream_t st = (cudaStream_t)stream;
@@ -310,11 +310,12 @@ int ubqp_eval(const ubqp_q* q, const uint64_t* X_dev, int64_t S, int64_t* f_dev,
   if ((int64_t)2 * q->max_abs * q->n_tc >= (1 << 24))
     return fail(UBQP_ERR_RANGE, "2*max|Q|*n_pad = %lld >= 2^24",
                 (long long)2 * q->max_abs * q->n_tc);
-  const size_t need = ubqp::eval_tc_workspace(q, S);
+  const bool fused = path == UBQP_EVAL_TC;
+  const size_t need = fused ? 0 : ubqp::eval_tc_workspace(q, S);
   if (ws_bytes < need || (need && !ws))
     return fail(UBQP_ERR_NOMEM, "eval workspace %zu < %zu bytes", ws_bytes, need);
   if (((uintptr_t)ws & 15) != 0) return fail(UBQP_ERR_ARG, "workspace not 16-byte aligned");
-  cudaError_t e = ubqp::launch_eval_tc(q, X_dev, S, f_dev, ws, ws_bytes, st);
+  cudaError_t e = ubqp::launch_eval_tc(q, X_dev, S, f_dev, ws, ws_bytes, st, nullptr, fused);
   if (e == cudaErrorNotSupported)
     return fail(UBQP_ERR_UNSUPPORTED, "tensor-core evaluation not available for this size");
   if (e != cudaSuccess) return cuda_fail(e, "eval_tc");
@@ -339,7 +340,7 @@ int ubqp_eval_noalloc(const ubqp_q* q, const uint64_t* X_dev, int64_t S, int64_t
   cudaError_t e = ubqp::eval_tc_static_scratch(&scratch);
   if (e != cudaSuccess) return cuda_fail(e, "cudaGetSymbolAddress(eval scratch)");
   e = ubqp::launch_eval_tc(q, X_dev, S, f_dev, scratch, ubqp::eval_tc_static_capacity(),
-                           (cudaStream_t)stream);
+                           (cudaStream_t)stream, nullptr, /*fused=*/false);
   if (e == cudaErrorNotSupported)
     return fail(UBQP_ERR_UNSUPPORTED, "tensor-core evaluation not available for this size");
   if (e != cudaSuccess) return cuda_fail(e, "eval_tc (static scratch)");
@@ -500,7 +501,7 @@ SearchLayout search_layout(const ubqp_q* q, const ubqp_search_params* p) {
   L.cand_x = take((size_t)q->W * 8);
   const int path = resolve_path(p->eval_path);
   const int64_t big = S > NS ? S : NS;
-  const size_t ev = path == UBQP_EVAL_TC ? ubqp::eval_tc_workspace(q, big) : 0;
+  const size_t ev = path == UBQP_EVAL_TC_STAGED ? ubqp::eval_tc_workspace(q, big) : 0;
   const size_t as = ubqp::ascent_tc_workspace(q, S);
   L.scratch = take(ev > as ? ev : as);
   L.total = off;

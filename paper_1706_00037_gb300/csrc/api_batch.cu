@@ -95,7 +95,7 @@ int run_body(ubqp_batch* b, cudaStream_t st) {
                                       p.num_starts, p.div_H, d.X, s, b->d_seed));
     if (b->eval_path == UBQP_EVAL_TC) {
       UBQP_BCUDA(ubqp::launch_eval_tc(q, d.X, p.num_starts, d.f, b->scratch[i],
-                                      b->scratch_bytes[i], s, b->mapA[i].bytes));
+                                      b->scratch_bytes[i], s, b->mapA[i].bytes, true));
     } else {
       UBQP_BCUDA(ubqp::launch_eval_plain(q, d.X, p.num_starts, d.f, s));
     }
@@ -296,7 +296,7 @@ int ubqp_batch_create(const ubqp_q* const* qs, int32_t count, const ubqp_params*
   }
   pick_default_shape(b);
   b->nstreams = std::min(8, count);
-  b->eval_path = p->eval_path == UBQP_EVAL_PLAIN ? UBQP_EVAL_PLAIN : UBQP_EVAL_TC;
+  b->eval_path = p->eval_path == UBQP_EVAL_PLAIN ? UBQP_EVAL_PLAIN : UBQP_EVAL_TC;  // TC = fused
   for (int i = 0; i < count && b->eval_path == UBQP_EVAL_TC; ++i)
     if (!qs[i]->tc_ok) b->eval_path = UBQP_EVAL_PLAIN;
   int r = set_shape(b, b->asc_T, b->asc_C);

@@ -45,6 +45,11 @@ constexpr int KCH = 16;  // max K steps (of BK) per work unit
 constexpr int THREADS = 192;
 constexpr uint32_t TMEM_COLS = 512;
 constexpr int SMEM_BYTES = 1024 + STAGES * STAGE_BYTES + 256;
+// fused variant: two more warps build the A operand from the solution bits,
+// with a 256-entry byte -> 8 bf16 table in shared memory
+constexpr int THREADS_FUSED = THREADS + 64;
+constexpr int LUT_BYTES = 256 * 16;
+constexpr int SMEM_BYTES_FUSED = SMEM_BYTES + LUT_BYTES;
 constexpr uint64_t kWaitNs = 2000ull * 1000 * 1000;
 
 // Instruction descriptor, kind::f16: D fp32 (bits 4-5 = 1), A bf16 (7-9 = 1),
@@ -173,13 +178,27 @@ __device__ __forceinline__ Unit unit_of(const int4* __restrict__ chunks, int m_t
   return Unit{c.x, c.y, c.z, u % m_tiles};
 }
 
+__device__ __forceinline__ uint4 expand_byte(uint32_t b) {
+  uint32_t v[4];
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+    const uint32_t lo = ((b >> (2 * i)) & 1u) ? 0x3F80u : 0u;
+    const uint32_t hi = ((b >> (2 * i + 1)) & 1u) ? 0x3F80u : 0u;
+    v[i] = lo | (hi << 16);
+  }
+  return make_uint4(v[0], v[1], v[2], v[3]);
+}
+
 // YMODE = false: f_s += sum_j x_sj D_sj over the lower block triangle (Evaluate).
 // YMODE = true:  Y = Xe Qf^t over the full square, accumulated in fp32 (exact
 // integers) with vector atomics -- y = Q x for the starts an ascent climbs.
-template <bool YMODE>
-__global__ void __launch_bounds__(THREADS, 1)
+// FUSED (evaluation only): the A operand is written to shared memory directly
+// from the bit-packed solutions by warps 6-7 (no unpacked copy in global
+// memory); otherwise both operands arrive by TMA.
+template <bool YMODE, bool FUSED>
+__global__ void __launch_bounds__(FUSED ? THREADS_FUSED : THREADS, 1)
 eval_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
-               const uint64_t* __restrict__ X, int W, int64_t S, int m_tiles,
+               const uint64_t* __restrict__ X, int n, int W, int64_t S, int m_tiles,
                const int4* __restrict__ chunks, int n_chunks, int64_t* __restrict__ f,
                const int64_t* __restrict__ count, float* __restrict__ Y, int64_t ldy,
                unsigned* __restrict__ err) {
@@ -192,6 +211,9 @@ eval_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ 
   uint64_t* drain = tempty + 2;
   uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(drain + 1);
   volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
+  uint4* lut = reinterpret_cast<uint4*>(smem + STAGES * STAGE_BYTES + 256);
+  if (FUSED)
+    for (int b = threadIdx.x; b < 256; b += blockDim.x) lut[b] = expand_byte((uint32_t)b);
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   int64_t rows = S;
@@ -204,7 +226,7 @@ eval_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ 
 
   if (threadIdx.x == 0) {
     for (int s = 0; s < STAGES; ++s) {
-      mbar_init(&full[s], 1);
+      mbar_init(&full[s], FUSED ? 1 + 64 : 1);  // TMA arrival (+ the A writers)
       mbar_init(&empty[s], 1);
     }
     for (int a = 0; a < 2; ++a) {
@@ -230,7 +252,9 @@ eval_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ 
   if (warp == 0) {
     if (lane == 0) {
       // ---------------- TMA producer
-      asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&tmA)) : "memory");
+      if (!FUSED)
+        asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&tmA))
+                     : "memory");
       asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&tmB)) : "memory");
       int pending[STAGES];
       for (int s = 0; s < STAGES; ++s) pending[s] = -1;
@@ -245,9 +269,9 @@ eval_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ 
             break;
           }
           uint8_t* sa = smem + stage * STAGE_BYTES;
-          mbar_expect_tx(&full[stage], STAGE_BYTES);
+          mbar_expect_tx(&full[stage], FUSED ? B_BYTES : STAGE_BYTES);
           const int kx = (un.k0 + ks) * BK;
-          tma_load_2d(sa, &tmA, kx, un.mt * BM, &full[stage]);
+          if (!FUSED) tma_load_2d(sa, &tmA, kx, un.mt * BM, &full[stage]);
           tma_load_2d(sa + A_BYTES, &tmB, kx, un.nb * BN, &full[stage]);
           pending[stage] = (int)phase;
           if (++stage == STAGES) {
@@ -301,6 +325,45 @@ eval_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ 
       if (!ok) {  // wait for the MMAs already issued before TMEM is freed
         mma_commit(drain);
         mbar_drain(drain, 0);
+      }
+    }
+  } else if (FUSED && warp >= 6) {
+    // ---------------- A writers (warps 6-7): rows t and t + 64 of the A tile,
+    // one 64-bit word of solution bits per row and K step, expanded through the
+    // table into the 128-byte-swizzled K-major layout the MMA descriptor reads
+    const int t = threadIdx.x - THREADS;
+    int stage = 0;
+    uint32_t phase = 0;
+    bool ok = true;
+    for (int u = blockIdx.x; u < n_units && ok; u += gridDim.x) {
+      const Unit un = unit_of(chunks, m_tiles, u);
+      const int64_t s0 = (int64_t)un.mt * BM + t, s1 = s0 + 64;
+      const uint64_t* x0p = s0 < S ? X + s0 * W : nullptr;
+      const uint64_t* x1p = s1 < S ? X + s1 * W : nullptr;
+      for (int ks = 0; ks < un.nk; ++ks) {
+        const int kw = un.k0 + ks;
+        const uint64_t msk = kw < W ? valid_mask(n, kw) : 0ull;
+        const uint64_t w0 = (x0p && msk) ? (x0p[kw] & msk) : 0ull;
+        const uint64_t w1 = (x1p && msk) ? (x1p[kw] & msk) : 0ull;
+        if (!mbar_wait(&empty[stage], phase ^ 1u, abort_flag, err)) {
+          ok = false;
+          break;
+        }
+        uint8_t* sa = smem + stage * STAGE_BYTES;
+        uint8_t* r0 = sa + t * 128;
+        uint8_t* r1 = sa + (t + 64) * 128;
+#pragma unroll
+        for (int c = 0; c < 8; ++c) {
+          *reinterpret_cast<uint4*>(r0 + ((c ^ (t & 7)) << 4)) = lut[(w0 >> (8 * c)) & 0xFF];
+          *reinterpret_cast<uint4*>(r1 + ((c ^ (t & 7)) << 4)) = lut[(w1 >> (8 * c)) & 0xFF];
+        }
+        // make the generic-proxy writes visible to the tensor cores' reads
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        mbar_arrive(&full[stage]);
+        if (++stage == STAGES) {
+          stage = 0;
+          phase ^= 1u;
+        }
       }
     }
   } else {
@@ -426,13 +489,14 @@ EncodeFn encode_fn() {
 
 // Opt each tensor-core kernel into its dynamic shared memory once per process
 // (the attribute is per function; the first call from any thread sets it).
-template <bool YMODE>
+template <bool YMODE, bool FUSED>
 cudaError_t set_smem_attr_once() {
   static std::once_flag once;
   static cudaError_t err = cudaSuccess;
   std::call_once(once, [] {
-    err = cudaFuncSetAttribute(eval_tc_kernel<YMODE>,
-                               cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_BYTES);
+    err = cudaFuncSetAttribute(eval_tc_kernel<YMODE, FUSED>,
+                               cudaFuncAttributeMaxDynamicSharedMemorySize,
+                               FUSED ? SMEM_BYTES_FUSED : SMEM_BYTES);
   });
   return err;
 }
@@ -565,12 +629,12 @@ cudaError_t launch_ascent_init_tc(const ubqp_q* h, const uint64_t* X, const int3
   if (mapA_in) mapA = *reinterpret_cast<const CUtensorMap*>(mapA_in);
   else if (!make_map(&mapA, Xe, S_p, h->n_tc, BM)) return cudaErrorInvalidValue;
   if ((e = cudaMemsetAsync(Y, 0, (size_t)S_p * h->n_tc * 4, st))) return e;
-  if ((e = set_smem_attr_once<true>())) return e;
+  if ((e = set_smem_attr_once<true, false>())) return e;
   const int m_tiles = (int)(S_p / BM);
   const int n_units = h->tc_nchunks_y * m_tiles;
   const int grid = n_units < h->sm_count ? n_units : h->sm_count;
-  eval_tc_kernel<true><<<grid, THREADS, SMEM_BYTES, st>>>(
-      mapA, *reinterpret_cast<const CUtensorMap*>(h->tc_mapF), X, h->W, S, m_tiles,
+  eval_tc_kernel<true, false><<<grid, THREADS, SMEM_BYTES, st>>>(
+      mapA, *reinterpret_cast<const CUtensorMap*>(h->tc_mapF), X, h->n, h->W, S, m_tiles,
       reinterpret_cast<const int4*>(h->tc_chunks) + h->tc_nchunks, h->tc_nchunks_y, nullptr,
       count, Y, h->n_tc, h->err);
   if ((e = cudaGetLastError())) return e;
@@ -579,12 +643,15 @@ cudaError_t launch_ascent_init_tc(const ubqp_q* h, const uint64_t* X, const int3
 }
 
 cudaError_t launch_eval_tc(const ubqp_q* h, const uint64_t* X, int64_t S, int64_t* f, void* ws,
-                           size_t ws_bytes, cudaStream_t st, const void* mapA_in) {
+                           size_t ws_bytes, cudaStream_t st, const void* mapA_in, bool fused) {
   if (!h->tc_ok) return cudaErrorNotSupported;
   const int64_t S_p = padded_starts(S);
-  if (ws_bytes < eval_tc_workspace(h, S)) return cudaErrorInvalidValue;
   cudaError_t e;
-  {
+  alignas(64) CUtensorMap mapA;
+  if (fused) {
+    mapA = *reinterpret_cast<const CUtensorMap*>(h->tc_mapB);  // unused by the fused kernel
+  } else {
+    if (ws_bytes < eval_tc_workspace(h, S)) return cudaErrorInvalidValue;
     const int64_t total = S_p * (h->n_tc / 8);
     int64_t blocks = (total + 255) / 256;
     if (blocks > (int64_t)h->sm_count * 8) blocks = (int64_t)h->sm_count * 8;
@@ -592,19 +659,26 @@ cudaError_t launch_eval_tc(const ubqp_q* h, const uint64_t* X, int64_t S, int64_
                                                       S_p, h->n_tc,
                                                       reinterpret_cast<uint4*>(ws));
     if ((e = cudaGetLastError())) return e;
+    if (mapA_in) mapA = *reinterpret_cast<const CUtensorMap*>(mapA_in);
+    else if (!make_map(&mapA, ws, S_p, h->n_tc, BM)) return cudaErrorInvalidValue;
   }
-  alignas(64) CUtensorMap mapA;
-  if (mapA_in) mapA = *reinterpret_cast<const CUtensorMap*>(mapA_in);
-  else if (!make_map(&mapA, ws, S_p, h->n_tc, BM)) return cudaErrorInvalidValue;
   if ((e = cudaMemsetAsync(f, 0, sizeof(int64_t) * S, st))) return e;
-  if ((e = set_smem_attr_once<false>())) return e;
   const int m_tiles = (int)(S_p / BM);
   const int n_units = h->tc_nchunks * m_tiles;
   const int grid = n_units < h->sm_count ? n_units : h->sm_count;
-  eval_tc_kernel<false><<<grid, THREADS, SMEM_BYTES, st>>>(
-      mapA, *reinterpret_cast<const CUtensorMap*>(h->tc_mapB), X, h->W, S, m_tiles,
-      reinterpret_cast<const int4*>(h->tc_chunks), h->tc_nchunks, f, nullptr, nullptr, 0,
-      h->err);
+  const CUtensorMap& mapB = *reinterpret_cast<const CUtensorMap*>(h->tc_mapB);
+  const int4* ch = reinterpret_cast<const int4*>(h->tc_chunks);
+  if (fused) {
+    if ((e = set_smem_attr_once<false, true>())) return e;
+    eval_tc_kernel<false, true><<<grid, THREADS_FUSED, SMEM_BYTES_FUSED, st>>>(
+        mapA, mapB, X, h->n, h->W, S, m_tiles, ch, h->tc_nchunks, f, nullptr, nullptr, 0,
+        h->err);
+  } else {
+    if ((e = set_smem_attr_once<false, false>())) return e;
+    eval_tc_kernel<false, false><<<grid, THREADS, SMEM_BYTES, st>>>(
+        mapA, mapB, X, h->n, h->W, S, m_tiles, ch, h->tc_nchunks, f, nullptr, nullptr, 0,
+        h->err);
+  }
   return cudaGetLastError();
 }
 

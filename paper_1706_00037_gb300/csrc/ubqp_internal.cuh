@@ -113,9 +113,11 @@ cudaError_t launch_ascent_init_tc(const ubqp_q* h, const uint64_t* X, const int3
 cudaError_t eval_tc_static_scratch(void** out);
 // mapA_in: a TMA descriptor (128 bytes) of the unpacked starts in ws made by
 // eval_tc_map_A, or nullptr to build one per call.
+// fused: build the A operand in shared memory from the bits (no workspace);
+// otherwise unpack into ws first and feed both operands by TMA.
 cudaError_t launch_eval_tc(const ubqp_q* h, const uint64_t* X, int64_t S, int64_t* f,
                            void* ws, size_t ws_bytes, cudaStream_t st,
-                           const void* mapA_in = nullptr);
+                           const void* mapA_in = nullptr, bool fused = false);
 bool eval_tc_map_A(void* out128, const void* Xe, int64_t S, int n_tc);
 cudaError_t launch_screen_stats(const int64_t* f, int64_t S, int64_t offset, int64_t* stats,
                                 cudaStream_t st);

@@ -138,13 +138,24 @@ def test_eval_tc_workspace_errors():
     n, S = 300, 50
     Q, inst = instance(n, 0.5, 1)
     X = words_dev(synth.random_solutions(n, S, 1))
-    need = ubqp.eval_workspace_size(inst, S, ubqp.EVAL_TC)
+    need = ubqp.eval_workspace_size(inst, S, ubqp.EVAL_TC_STAGED)
     assert need == 128 * 512 * 2
     small = torch.empty(need - 16, dtype=torch.uint8, device="cuda")
     with pytest.raises(ubqp.UbqpError) as e:
-        ubqp.eval(inst, X, path=ubqp.EVAL_TC, ws=small)
+        ubqp.eval(inst, X, path=ubqp.EVAL_TC_STAGED, ws=small)
     assert e.value.status == -4
     assert ubqp.eval_workspace_size(inst, S, ubqp.EVAL_PLAIN) == 0
+    assert ubqp.eval_workspace_size(inst, S, ubqp.EVAL_TC) == 0
+
+
+@pytest.mark.parametrize("n", [1, 65, 257, 1000, 2100])
+@pytest.mark.parametrize("S", [1, 129, 300])
+def test_eval_tc_staged_matches_oracle(n, S):
+    Q, inst = instance(n, 0.6, n + 300)
+    X = synth.random_solutions(n, S, n + 2 * S)
+    f = ubqp.eval(inst, words_dev(X), path=ubqp.EVAL_TC_STAGED)
+    inst.sync()
+    assert np.array_equal(f.cpu().numpy(), orc.eval(Q, X))
 
 
 def test_eval_ignores_pad_bits():
@@ -153,7 +164,7 @@ def test_eval_ignores_pad_bits():
     X = synth.random_solutions(n, 9, 2)
     Xd = X.copy()
     Xd[:, -1] |= np.uint64(0xFFFF) << np.uint64(48)  # set bits >= n
-    for path in (ubqp.EVAL_PLAIN, ubqp.EVAL_TC):
+    for path in (ubqp.EVAL_PLAIN, ubqp.EVAL_TC, ubqp.EVAL_TC_STAGED):
         f = ubqp.eval(inst, words_dev(Xd), path=path)
         assert np.array_equal(f.cpu().numpy(), orc.eval(Q, X))
 
