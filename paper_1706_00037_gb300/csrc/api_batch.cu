@@ -94,8 +94,10 @@ int run_body(ubqp_batch* b, cudaStream_t st) {
     UBQP_BCUDA(ubqp::launch_diversify(q->x0, q->n, p.mode, p.seed, p.round, p.num_starts, 0,
                                       p.num_starts, p.div_H, d.X, s, b->d_seed));
     if (b->eval_path == UBQP_EVAL_TC) {
+      // fused operand build up to n_pad 4096, staged above (as UBQP_EVAL_AUTO)
       UBQP_BCUDA(ubqp::launch_eval_tc(q, d.X, p.num_starts, d.f, b->scratch[i],
-                                      b->scratch_bytes[i], s, b->mapA[i].bytes, true));
+                                      b->scratch_bytes[i], s, b->mapA[i].bytes,
+                                      q->n_tc <= 4096));
     } else {
       UBQP_BCUDA(ubqp::launch_eval_plain(q, d.X, p.num_starts, d.f, s));
     }

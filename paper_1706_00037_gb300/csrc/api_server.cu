@@ -70,7 +70,9 @@ size_t request_bytes(const ubqp_server_config& c, int32_t n) {
   const int64_t S = c.params.num_starts, W = (n + 63) / 64;
   const int64_t n_tc = rup(n, UBQP_TC_ALIGN), S_p = rup(S, 128);
   int64_t ws = rup(S * W * 8, 256) + rup(S * 8, 256) + 2 * rup(S * 4, 256) + 256;
-  const int64_t ev = c.params.eval_path == UBQP_EVAL_TC_STAGED ? S_p * n_tc * 2 : 0;
+  const bool staged = c.params.eval_path == UBQP_EVAL_TC_STAGED ||
+                      (c.params.eval_path == UBQP_EVAL_AUTO && n_tc > 4096);
+  const int64_t ev = staged ? S_p * n_tc * 2 : 0;
   ws += rup(std::max<int64_t>(ev, S_p * n_tc * 6), 256);
   return (size_t)(rup((int64_t)n * rup(n, 16), 256) + (int64_t)ubqp_q_arena_size(n) + ws +
                   rup(W * 8, 256) + 256);

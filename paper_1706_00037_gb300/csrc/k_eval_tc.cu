@@ -47,9 +47,9 @@ constexpr uint32_t TMEM_COLS = 512;
 constexpr int SMEM_BYTES = 1024 + STAGES * STAGE_BYTES + 256;
 // fused variant: two more warps build the A operand from the solution bits,
 // with a 256-entry byte -> 8 bf16 table in shared memory
-constexpr int THREADS_FUSED = THREADS + 64;
-constexpr int LUT_BYTES = 256 * 16;
-constexpr int SMEM_BYTES_FUSED = SMEM_BYTES + LUT_BYTES;
+constexpr int A_WRITERS = 128;  // one row of the A tile per thread
+constexpr int THREADS_FUSED = THREADS + A_WRITERS;
+constexpr int SMEM_BYTES_FUSED = SMEM_BYTES;
 constexpr uint64_t kWaitNs = 2000ull * 1000 * 1000;
 
 // Instruction descriptor, kind::f16: D fp32 (bits 4-5 = 1), A bf16 (7-9 = 1),
@@ -178,13 +178,14 @@ __device__ __forceinline__ Unit unit_of(const int4* __restrict__ chunks, int m_t
   return Unit{c.x, c.y, c.z, u % m_tiles};
 }
 
+// Eight bits -> eight bf16 values 0.0 / 1.0 (bit i = element i): bit pair
+// (2i, 2i+1) spread to the two 16-bit halves of word i, times 0x3F80 (1.0).
 __device__ __forceinline__ uint4 expand_byte(uint32_t b) {
   uint32_t v[4];
 #pragma unroll
   for (int i = 0; i < 4; ++i) {
-    const uint32_t lo = ((b >> (2 * i)) & 1u) ? 0x3F80u : 0u;
-    const uint32_t hi = ((b >> (2 * i + 1)) & 1u) ? 0x3F80u : 0u;
-    v[i] = lo | (hi << 16);
+    const uint32_t p = (b >> (2 * i)) & 3u;
+    v[i] = ((p & 1u) | ((p & 2u) << 15)) * 0x3F80u;
   }
   return make_uint4(v[0], v[1], v[2], v[3]);
 }
@@ -193,7 +194,7 @@ __device__ __forceinline__ uint4 expand_byte(uint32_t b) {
 // YMODE = true:  Y = Xe Qf^t over the full square, accumulated in fp32 (exact
 // integers) with vector atomics -- y = Q x for the starts an ascent climbs.
 // FUSED (evaluation only): the A operand is written to shared memory directly
-// from the bit-packed solutions by warps 6-7 (no unpacked copy in global
+// from the bit-packed solutions by warps 6-9 (no unpacked copy in global
 // memory); otherwise both operands arrive by TMA.
 template <bool YMODE, bool FUSED>
 __global__ void __launch_bounds__(FUSED ? THREADS_FUSED : THREADS, 1)
@@ -211,9 +212,6 @@ eval_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ 
   uint64_t* drain = tempty + 2;
   uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(drain + 1);
   volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
-  uint4* lut = reinterpret_cast<uint4*>(smem + STAGES * STAGE_BYTES + 256);
-  if (FUSED)
-    for (int b = threadIdx.x; b < 256; b += blockDim.x) lut[b] = expand_byte((uint32_t)b);
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   int64_t rows = S;
@@ -226,7 +224,7 @@ eval_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ 
 
   if (threadIdx.x == 0) {
     for (int s = 0; s < STAGES; ++s) {
-      mbar_init(&full[s], FUSED ? 1 + 64 : 1);  // TMA arrival (+ the A writers)
+      mbar_init(&full[s], FUSED ? 1 + A_WRITERS : 1);  // TMA arrival (+ the A writers)
       mbar_init(&empty[s], 1);
     }
     for (int a = 0; a < 2; ++a) {
@@ -327,36 +325,39 @@ eval_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ 
         mbar_drain(drain, 0);
       }
     }
-  } else if (FUSED && warp >= 6) {
-    // ---------------- A writers (warps 6-7): rows t and t + 64 of the A tile,
-    // one 64-bit word of solution bits per row and K step, expanded through the
-    // table into the 128-byte-swizzled K-major layout the MMA descriptor reads
+  } else if (FUSED && warp >= THREADS / 32) {
+    // ---------------- A writers (warps 6-9): row t of the A tile, one 64-bit
+    // word of solution bits per K step, expanded arithmetically into the
+    // 128-byte-swizzled K-major layout the MMA descriptor reads
     const int t = threadIdx.x - THREADS;
     int stage = 0;
     uint32_t phase = 0;
     bool ok = true;
     for (int u = blockIdx.x; u < n_units && ok; u += gridDim.x) {
       const Unit un = unit_of(chunks, m_tiles, u);
-      const int64_t s0 = (int64_t)un.mt * BM + t, s1 = s0 + 64;
+      const int64_t s0 = (int64_t)un.mt * BM + t;
       const uint64_t* x0p = s0 < S ? X + s0 * W : nullptr;
-      const uint64_t* x1p = s1 < S ? X + s1 * W : nullptr;
-      for (int ks = 0; ks < un.nk; ++ks) {
-        const int kw = un.k0 + ks;
-        const uint64_t msk = kw < W ? valid_mask(n, kw) : 0ull;
-        const uint64_t w0 = (x0p && msk) ? (x0p[kw] & msk) : 0ull;
-        const uint64_t w1 = (x1p && msk) ? (x1p[kw] & msk) : 0ull;
+      // all of this unit's solution words up front: one memory latency per unit
+      uint64_t wa[KCH];
+#pragma unroll
+      for (int i = 0; i < KCH; ++i) {
+        const int kw = un.k0 + i;
+        const bool in = i < un.nk && kw < W;
+        wa[i] = (x0p && in) ? (__ldg(x0p + kw) & valid_mask(n, kw)) : 0ull;
+      }
+#pragma unroll
+      for (int ks = 0; ks < KCH; ++ks) {
+        if (ks >= un.nk) break;
+        const uint64_t w0 = wa[ks];
         if (!mbar_wait(&empty[stage], phase ^ 1u, abort_flag, err)) {
           ok = false;
           break;
         }
-        uint8_t* sa = smem + stage * STAGE_BYTES;
-        uint8_t* r0 = sa + t * 128;
-        uint8_t* r1 = sa + (t + 64) * 128;
+        uint8_t* r0 = smem + stage * STAGE_BYTES + t * 128;
 #pragma unroll
-        for (int c = 0; c < 8; ++c) {
-          *reinterpret_cast<uint4*>(r0 + ((c ^ (t & 7)) << 4)) = lut[(w0 >> (8 * c)) & 0xFF];
-          *reinterpret_cast<uint4*>(r1 + ((c ^ (t & 7)) << 4)) = lut[(w1 >> (8 * c)) & 0xFF];
-        }
+        for (int c = 0; c < 8; ++c)
+          *reinterpret_cast<uint4*>(r0 + ((c ^ (t & 7)) << 4)) =
+              expand_byte((uint32_t)(w0 >> (8 * c)) & 0xFFu);
         // make the generic-proxy writes visible to the tensor cores' reads
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
         mbar_arrive(&full[stage]);
