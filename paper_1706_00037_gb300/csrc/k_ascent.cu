@@ -23,7 +23,10 @@
 // toggles the x bit of C_k.  Rows are read from L2 (the int8 Q of one
 // instance, e.g. 49 MB at n = 7000, stays resident there); nothing per move
 // goes to HBM.  The chain of moves is latency-bound: per move a dependent L2
-// row fetch, the update and a block-wide reduction.
+// row fetch, the update and a block-wide reduction.  The fetch is taken off
+// the chain when the move was predicted: every move also copies the row of
+// the reduction's runner-up into shared memory, and the next move is that
+// row often enough (about 40% at n = 7000) to pay for the copies.
 //
 // Start-up: y = Q x of every listed start comes from the tensor-core product of
 // the ascent workspace when given (exact integers in fp32), else each group
@@ -36,6 +39,16 @@ namespace ubqp {
 namespace {
 
 constexpr int64_t kTimeoutNs = 20ll * 1000 * 1000 * 1000;  // per start
+// Runner-up rows copied one move ahead.  Measured at n = 7000 / 2500 / 1500
+// (passing starts of 1000 random ones): one row is 3-13% faster than none;
+// two or more cost more in reductions and copies than their hits save.
+constexpr int kSpecRows = 1;
+// shared-memory slots (16 bytes each) of a group of T threads: two buffers of
+// R rows x C chunks per thread
+template <int T, int C, int R>
+constexpr int spec_slot_count() {
+  return R > 0 ? T * 2 * R * C : 1;
+}
 
 __device__ __forceinline__ uint64_t globaltimer() {
   uint64_t t;
@@ -49,6 +62,31 @@ __device__ __forceinline__ int byte_sel(int i, int d) {
   return (int)((unsigned)(d & 0xFF) << (8 * i));
 }
 
+// The R best entries (gain r.x, tag r.y) held one per lane across a warp,
+// excluding the entry tagged `first`: their tags in decreasing order of gain
+// (ties to the lower lane), INT_MAX where fewer entries remain.  One max
+// reduction per rank on gain * 32 + (31 - lane) (|gain| < 2^26), then one
+// shuffle per rank for the tags.
+template <int R>
+__device__ __forceinline__ void runners_up(int2 r, int first, int* cand) {
+  const int lane = threadIdx.x & 31;
+  int key = (r.y == first || r.y == INT_MAX) ? INT_MIN : r.x * 32 + (31 - lane);
+  int wl[R];
+  bool ok[R];
+#pragma unroll
+  for (int i = 0; i < R; ++i) {
+    const int m = __reduce_max_sync(0xffffffffu, key);
+    ok[i] = m != INT_MIN;
+    wl[i] = 31 - (m & 31);
+    if (lane == wl[i]) key = INT_MIN;
+  }
+#pragma unroll
+  for (int i = 0; i < R; ++i) {
+    const int t = __shfl_sync(0xffffffffu, r.y, wl[i]);
+    cand[i] = ok[i] ? t : INT_MAX;
+  }
+}
+
 template <int T>
 struct Group;
 
@@ -56,11 +94,18 @@ struct Group;
 template <>
 struct Group<32> {
   __device__ __forceinline__ int rank() const { return threadIdx.x & 31; }
+  int2 mine;  // this lane's entry of the last reduction
   // returns {max gain, 2k + x_k} over the group
   __device__ __forceinline__ int2 reduce(int gain, int jx) {
     const int m = __reduce_max_sync(0xffffffffu, gain);
     const int c = __reduce_min_sync(0xffffffffu, gain == m ? jx : INT_MAX);
+    mine = make_int2(gain, jx);
     return make_int2(m, c);
+  }
+  // runners-up of the last reduction among the lanes' own maxima
+  template <int R>
+  __device__ __forceinline__ void runners(int first, int* cand) const {
+    runners_up<R>(mine, first, cand);
   }
   __device__ __forceinline__ bool any(bool p) { return __any_sync(0xffffffffu, p); }
   __device__ __forceinline__ void sync() { __syncwarp(); }
@@ -73,6 +118,8 @@ struct Group {
   int2 (*rec)[NW];  // [2][NW] shared
   int parity;
   __device__ __forceinline__ int rank() const { return threadIdx.x; }
+  int2 mine;  // warp `lane`'s winner in the last reduction
+  // returns {max gain, 2k + x_k} over the group
   __device__ __forceinline__ int2 reduce(int gain, int jx) {
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int m = __reduce_max_sync(0xffffffffu, gain);
@@ -83,19 +130,26 @@ struct Group {
     const int m2 = __reduce_max_sync(0xffffffffu, r.x);
     const int c2 = __reduce_min_sync(0xffffffffu, r.x == m2 ? r.y : INT_MAX);
     parity ^= 1;
+    mine = r;
     return make_int2(m2, c2);
+  }
+  // runners-up of the last reduction among the warps' winners
+  template <int R>
+  __device__ __forceinline__ void runners(int first, int* cand) const {
+    runners_up<R>(mine, first, cand);
   }
   __device__ __forceinline__ bool any(bool p) { return __syncthreads_or(p) != 0; }
   __device__ __forceinline__ void sync() { __syncthreads(); }
 };
 
-template <int T, int C>
+template <int T, int C, int R>
 __device__ __forceinline__ void ascend_one(const int8_t* __restrict__ Q8, int64_t ldq,
                                            int64_t ldy, int n,
                                            int W, uint64_t* __restrict__ x_g,
                                            int64_t* __restrict__ f_s, int32_t max_flips,
                                            int32_t* __restrict__ flips_s,
                                            unsigned* __restrict__ err, uint64_t* xs,
+                                           uint4* spec_slots,
                                            const float* __restrict__ y_g, Group<T>& grp) {
   constexpr int E = 16 * C;
   constexpr int CW = 16 * T;  // indices per chunk
@@ -149,11 +203,11 @@ __device__ __forceinline__ void ascend_one(const int8_t* __restrict__ Q8, int64_
   for (int w = 0; w < W && !y_g; ++w) {
     uint64_t word = x_g[w] & valid_mask(n, w);
     while (word) {
-      constexpr int R = C == 1 ? 4 : 2;  // rows in flight
-      int ks[R];
+      constexpr int RF = C == 1 ? 4 : 2;  // rows in flight
+      int ks[RF];
       int nk = 0;
 #pragma unroll
-      for (int r = 0; r < R; ++r) {
+      for (int r = 0; r < RF; ++r) {
         ks[r] = 0;
         if (word) {
           ks[r] = w * 64 + __ffsll((long long)word) - 1;
@@ -161,9 +215,9 @@ __device__ __forceinline__ void ascend_one(const int8_t* __restrict__ Q8, int64_
           nk = r + 1;
         }
       }
-      uint4 q[R][C];
+      uint4 q[RF][C];
 #pragma unroll
-      for (int r = 0; r < R; ++r)
+      for (int r = 0; r < RF; ++r)
 #pragma unroll
         for (int c = 0; c < C; ++c) {
           const int j0 = c * CW + 16 * g;
@@ -172,7 +226,7 @@ __device__ __forceinline__ void ascend_one(const int8_t* __restrict__ Q8, int64_
                         : make_uint4(0, 0, 0, 0);
         }
 #pragma unroll
-      for (int r = 0; r < R; ++r)
+      for (int r = 0; r < RF; ++r)
 #pragma unroll
         for (int c = 0; c < C; ++c) {
           const int wv[4] = {(int)q[r][c].x, (int)q[r][c].y, (int)q[r][c].z, (int)q[r][c].w};
@@ -186,6 +240,20 @@ __device__ __forceinline__ void ascend_one(const int8_t* __restrict__ Q8, int64_
   int kmax = INT_MIN;
 #pragma unroll
   for (int e = 0; e < E; ++e) kmax = max(kmax, Ck[e] + S[e] * y[e]);
+  // Speculation: the next move is often the runner-up of the previous
+  // reduction (about 40% of moves at n = 7000), so each move copies this
+  // thread's chunks of the runner-up rows (prow) into its own shared-memory
+  // slots with cp.async; a hit reads them there instead of waiting for a
+  // dependent L2 round trip.  Two buffers alternate: the copies of move t go
+  // to buffer t % 2 and are read at move t + 1.  Each thread reads only the
+  // bytes it copied, so its own cp.async.wait_group orders them.
+  constexpr int RR = R > 0 ? R : 1;
+  int cand[RR], prow[RR];
+#pragma unroll
+  for (int i = 0; i < RR; ++i) prow[i] = -1;
+  const uint32_t slot0 =
+      (uint32_t)__cvta_generic_to_shared(spec_slots) + (uint32_t)g * (2 * RR * C * 16);
+  int buf = 0;
   auto reduce_key = [&](int kt) {
     const int gain = kt >> 6;
     const int e = 31 - ((kt >> 1) & 31);
@@ -212,12 +280,56 @@ __device__ __forceinline__ void ascend_one(const int8_t* __restrict__ Q8, int64_
     const int dsel[4] = {byte_sel(0, d), byte_sel(1, d), byte_sel(2, d), byte_sel(3, d)};
     fval += best.x;
     ++flips;
-    const int8_t* row = Q8 + (int64_t)k * ldq;
     uint4 q[C];
+    bool hit = false;
+    if constexpr (R > 0) {
+      int hi = -1;
 #pragma unroll
-    for (int c = 0; c < C; ++c) {
-      const int j0 = c * CW + 16 * g;
-      q[c] = j0 < ldq ? __ldg(reinterpret_cast<const uint4*>(row + j0)) : make_uint4(0, 0, 0, 0);
+      for (int i = 0; i < R; ++i)
+        if (prow[i] == k) hi = i;
+      if (hi >= 0) {
+        asm volatile("cp.async.wait_group 0;" ::: "memory");
+        const uint32_t a = slot0 + (uint32_t)((buf ^ 1) * RR * C + hi * C) * 16;
+#pragma unroll
+        for (int c = 0; c < C; ++c)
+          asm volatile("ld.shared.v4.u32 {%0, %1, %2, %3}, [%4];"
+                       : "=r"(q[c].x), "=r"(q[c].y), "=r"(q[c].z), "=r"(q[c].w)
+                       : "r"(a + 16 * c));
+        hit = true;
+      }
+    }
+    if (!hit) {
+      const int8_t* row = Q8 + (int64_t)k * ldq;
+#pragma unroll
+      for (int c = 0; c < C; ++c) {
+        const int j0 = c * CW + 16 * g;
+        q[c] = j0 < ldq ? __ldg(reinterpret_cast<const uint4*>(row + j0))
+                        : make_uint4(0, 0, 0, 0);
+      }
+    }
+    if constexpr (R > 0) {  // fetch the runners-up's rows for the next move
+      grp.template runners<R>(best.y, cand);
+      // the copies into this buffer two moves ago have landed
+      asm volatile("cp.async.wait_group 1;" ::: "memory");
+#pragma unroll
+      for (int i = 0; i < R; ++i) {
+        const int r = cand[i] >> 1;
+        prow[i] = r < n ? r : -1;
+#pragma unroll
+        for (int c = 0; c < C; ++c) {
+          const int j0 = c * CW + 16 * g;
+          // chunks at or beyond ldq are not copied: their elements have
+          // S = 0, so whatever the slot holds never changes a key
+          if (prow[i] >= 0 && j0 < ldq) {
+            const int8_t* src = Q8 + (int64_t)prow[i] * ldq + j0;
+            const uint32_t a = slot0 + (uint32_t)(buf * RR * C + i * C + c) * 16;
+            asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(a), "l"(src)
+                         : "memory");
+          }
+        }
+      }
+      asm volatile("cp.async.commit_group;" ::: "memory");
+      buf ^= 1;
     }
     // the owner of k flips x_k: negate S_k, toggle the x bit in C_k
     const int kc = k / CW, kr = k - kc * CW;
@@ -244,6 +356,8 @@ __device__ __forceinline__ void ascend_one(const int8_t* __restrict__ Q8, int64_
     kmax = max(max(km[0], km[1]), max(km[2], km[3]));
     best = reduce_key(kmax);
   }
+  // copies still in flight must land before the slots serve another start
+  if (R > 0) asm volatile("cp.async.wait_group 0;" ::: "memory");
   // ---- write back f, flips and x
   if (g == 0) {
     *f_s = fval;
@@ -265,7 +379,7 @@ __device__ __forceinline__ void ascend_one(const int8_t* __restrict__ Q8, int64_
   grp.sync();
 }
 
-template <int T, int C>
+template <int T, int C, int R>
 __global__ void __launch_bounds__(T, 1)
 ascent_block_kernel(const int8_t* __restrict__ Q8, int64_t ldq, int n, int W,
                     uint64_t* __restrict__ X, int64_t* __restrict__ f,
@@ -274,6 +388,7 @@ ascent_block_kernel(const int8_t* __restrict__ Q8, int64_t ldq, int n, int W,
                     const float* __restrict__ Y, int64_t ldy, unsigned* __restrict__ err) {
   __shared__ int2 rec[2][T / 32];
   __shared__ uint64_t xs[UBQP_MAX_N / 64];
+  __shared__ uint4 spec_slots[spec_slot_count<T, C, R>()];
   Group<T> grp{rec, 0};
   const int64_t cnt = *count;
   for (int64_t t = blockIdx.x; t < cnt; t += gridDim.x) {
@@ -282,19 +397,21 @@ ascent_block_kernel(const int8_t* __restrict__ Q8, int64_t ldq, int n, int W,
       if (threadIdx.x == 0) atomicOr(err, UBQP_DEVERR_BADIDX);
       continue;
     }
-    ascend_one<T, C>(Q8, ldq, ldy, n, W, X + (int64_t)s * W, f + s, max_flips,
-                     flips ? flips + s : nullptr, err, xs, Y ? Y + t * ldy : nullptr, grp);
+    ascend_one<T, C, R>(Q8, ldq, ldy, n, W, X + (int64_t)s * W, f + s, max_flips,
+                        flips ? flips + s : nullptr, err, xs, spec_slots,
+                        Y ? Y + t * ldy : nullptr, grp);
   }
 }
 
 // All passing starts of a batch of instances in one persistent launch: item
 // t = (instance, position in its passing list); every instance has n <= 16 T C.
-template <int T, int C>
+template <int T, int C, int R>
 __global__ void __launch_bounds__(T, 1)
 ascent_batch_kernel(const BatchDesc* __restrict__ d, const int2* __restrict__ items,
                     const int64_t* __restrict__ n_items, int32_t max_flips) {
   __shared__ int2 rec[2][T / 32];
   __shared__ uint64_t xs[UBQP_MAX_N / 64];
+  __shared__ uint4 spec_slots[spec_slot_count<T, C, R>()];
   Group<T> grp{rec, 0};
   const int64_t cnt = *n_items;
   for (int64_t t = blockIdx.x; t < cnt; t += gridDim.x) {
@@ -305,14 +422,14 @@ ascent_batch_kernel(const BatchDesc* __restrict__ d, const int2* __restrict__ it
       if (threadIdx.x == 0) atomicOr(b.err, UBQP_DEVERR_BADIDX);
       continue;
     }
-    ascend_one<T, C>(b.Q8, b.ldq, b.ldy, b.n, b.W, b.X + (int64_t)s * b.W, b.f + s, max_flips,
-                     b.flips ? b.flips + s : nullptr, b.err, xs,
+    ascend_one<T, C, R>(b.Q8, b.ldq, b.ldy, b.n, b.W, b.X + (int64_t)s * b.W, b.f + s, max_flips,
+                     b.flips ? b.flips + s : nullptr, b.err, xs, spec_slots,
                      b.Y ? b.Y + (int64_t)it.y * b.ldy : nullptr, grp);
   }
 }
 
 // Four independent warps per block, one start each (n <= 512).
-template <int C>
+template <int C, int R>
 __global__ void __launch_bounds__(128)
 ascent_warp_kernel(const int8_t* __restrict__ Q8, int64_t ldq, int n, int W,
                    uint64_t* __restrict__ X, int64_t* __restrict__ f,
@@ -320,6 +437,7 @@ ascent_warp_kernel(const int8_t* __restrict__ Q8, int64_t ldq, int n, int W,
                    int64_t S, int32_t max_flips, int32_t* __restrict__ flips,
                    const float* __restrict__ Y, int64_t ldy, unsigned* __restrict__ err) {
   __shared__ uint64_t xs_all[4][16];
+  __shared__ uint4 spec_slots[4 * spec_slot_count<32, C, R>()];
   Group<32> grp;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int64_t cnt = *count;
@@ -329,8 +447,9 @@ ascent_warp_kernel(const int8_t* __restrict__ Q8, int64_t ldq, int n, int W,
       if (lane == 0) atomicOr(err, UBQP_DEVERR_BADIDX);
       continue;
     }
-    ascend_one<32, C>(Q8, ldq, ldy, n, W, X + (int64_t)s * W, f + s, max_flips,
+    ascend_one<32, C, R>(Q8, ldq, ldy, n, W, X + (int64_t)s * W, f + s, max_flips,
                       flips ? flips + s : nullptr, err, xs_all[warp],
+                      spec_slots + warp * spec_slot_count<32, C, R>(),
                       Y ? Y + t * ldy : nullptr, grp);
   }
 }
@@ -351,10 +470,10 @@ template <int T, int C>
 cudaError_t launch_block(const ubqp_q* h, uint64_t* X, int64_t* f, const int32_t* idx,
                          const int64_t* count, int64_t S, int32_t max_flips, int32_t* flips,
                          const float* Y, cudaStream_t st) {
-  int grid = resident_grid(ascent_block_kernel<T, C>, T, h->sm_count);
+  int grid = resident_grid(ascent_block_kernel<T, C, kSpecRows>, T, h->sm_count);
   if ((int64_t)grid > S) grid = (int)S;
-  ascent_block_kernel<T, C><<<grid, T, 0, st>>>(h->Q8, h->ldq, h->n, h->W, X, f, idx, count,
-                                                S, max_flips, flips, Y, h->n_tc, h->err);
+  ascent_block_kernel<T, C, kSpecRows><<<grid, T, 0, st>>>(
+      h->Q8, h->ldq, h->n, h->W, X, f, idx, count, S, max_flips, flips, Y, h->n_tc, h->err);
   return cudaGetLastError();
 }
 
@@ -362,18 +481,18 @@ template <int C>
 cudaError_t launch_warp(const ubqp_q* h, uint64_t* X, int64_t* f, const int32_t* idx,
                         const int64_t* count, int64_t S, int32_t max_flips, int32_t* flips,
                         const float* Y, cudaStream_t st) {
-  int grid = resident_grid(ascent_warp_kernel<C>, 128, h->sm_count);
+  int grid = resident_grid(ascent_warp_kernel<C, kSpecRows>, 128, h->sm_count);
   const int64_t need = (S + 3) / 4;
   if ((int64_t)grid > need) grid = (int)need;
-  ascent_warp_kernel<C><<<grid, 128, 0, st>>>(h->Q8, h->ldq, h->n, h->W, X, f, idx, count, S,
-                                              max_flips, flips, Y, h->n_tc, h->err);
+  ascent_warp_kernel<C, kSpecRows><<<grid, 128, 0, st>>>(
+      h->Q8, h->ldq, h->n, h->W, X, f, idx, count, S, max_flips, flips, Y, h->n_tc, h->err);
   return cudaGetLastError();
 }
 
 template <int T, int C>
 cudaError_t launch_ascent_batch_tc(const BatchDesc* d, const int2* items, const int64_t* n_items,
                                    int32_t max_flips, int grid, cudaStream_t st) {
-  ascent_batch_kernel<T, C><<<grid, T, 0, st>>>(d, items, n_items, max_flips);
+  ascent_batch_kernel<T, C, kSpecRows><<<grid, T, 0, st>>>(d, items, n_items, max_flips);
   return cudaGetLastError();
 }
 
@@ -388,8 +507,8 @@ int ascent_batch_grid(int T, int C, int sm_count) {
   cudaError_t e = cudaErrorInvalidValue;
 #define UBQP_OCC(TT, CC)                                                                     \
   if (T == TT && C == CC)                                                                    \
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, ascent_batch_kernel<TT, CC>, \
-                                                      TT, 0);
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(                                       \
+        &per_sm, ascent_batch_kernel<TT, CC, kSpecRows>, TT, 0);
   UBQP_OCC(64, 1) UBQP_OCC(64, 2) UBQP_OCC(128, 1) UBQP_OCC(128, 2)
   UBQP_OCC(256, 1) UBQP_OCC(256, 2) UBQP_OCC(512, 1) UBQP_OCC(512, 2)
 #undef UBQP_OCC
@@ -419,7 +538,7 @@ cudaError_t launch_ascent(const ubqp_q* h, uint64_t* X, int64_t* f, const int32_
   if (n <= 1024) return launch_block<64, 1>(h, X, f, idx, count, S, max_flips, flips, Y, st);
   if (n <= 2048) return launch_block<128, 1>(h, X, f, idx, count, S, max_flips, flips, Y, st);
   if (n <= 4096) return launch_block<256, 1>(h, X, f, idx, count, S, max_flips, flips, Y, st);
-  if (n <= 8192) return launch_block<512, 1>(h, X, f, idx, count, S, max_flips, flips, Y, st);
+  if (n <= 8192) return launch_block<256, 2>(h, X, f, idx, count, S, max_flips, flips, Y, st);
   if (n <= 16384) return launch_block<512, 2>(h, X, f, idx, count, S, max_flips, flips, Y, st);
   return cudaErrorInvalidValue;
 }
