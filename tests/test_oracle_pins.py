@@ -416,3 +416,32 @@ def test_search_small_n_reaches_a_local_optimum_below_global():
         y = x.copy()
         y[i] ^= 1
         assert _f_np(Q, y) <= r["best_f"]
+
+
+def test_search_replays_the_rounds_of_fig2():
+    """The search is the loop of Fig. 2 in rounds: replayed here with numpy
+    objective values, a numpy screen and best-of, and the separately pinned
+    start generation and ascent."""
+    n, S, R, lam, seed, ns = 60, 16, 6, 0.5, 3, 200
+    Q = synth.make_instance(n, 0.4, 2)
+    r = orc.search(Q, num_samples=ns, S=S, rounds=R, lam=lam, seed=seed)
+    sample = synth.unpack_bits(orc.diversify(None, n, orc.RANDOM, seed, 0, ns), n)
+    mean = np.float64(sum(_f_np(Q, x) for x in sample)) / np.float64(ns)
+    inc = orc.first_derivative(Q)
+    inc_f = _f_np(Q, synth.unpack_bits(inc, n))
+    history, passed = [], 0
+    for rnd in range(R):
+        X = orc.diversify(inc, n, orc.DIVERSIFY, seed, rnd, S)
+        fv = [_f_np(Q, x) for x in synth.unpack_bits(X, n)]
+        T = mean + np.float64(lam) * (np.float64(inc_f) - mean)
+        for s in range(S):
+            if np.float64(fv[s]) > T:
+                X[s], fv[s], _, _ = orc.ascent1(Q, X[s], fv[s])
+                passed += 1
+        b = int(np.argmax(fv))  # first maximum: lowest index on ties
+        if fv[b] > inc_f:
+            inc, inc_f = X[b].copy(), fv[b]
+        history.append(inc_f)
+    assert list(r["history"]) == history
+    assert r["best_f"] == inc_f and np.array_equal(r["best_x"], inc)
+    assert r["passed"] == passed
