@@ -49,9 +49,11 @@ def parse():
     ap.add_argument("--eval-path", choices=["auto", "tc", "plain"], default="auto")
     ap.add_argument("--cpu-sample", type=int, default=160,
                     help="starts in the oracle's timed sample")
-    ap.add_argument("--workload", choices=["table1", "batch64", "serve"], default="table1",
+    ap.add_argument("--workload", choices=["table1", "batch64", "serve", "configs"],
+                    default="table1",
                     help="table1: the default line; batch64: 64 uneven instances, batched "
-                         "vs one at a time; serve: the request-serving loop")
+                         "vs one at a time; serve: the request-serving loop; configs: "
+                         "per-configuration measurements")
     ap.add_argument("--serve-seconds", type=float, default=None,
                     help="seconds of Poisson arrivals (default 60 for --workload serve, 10 "
                          "inside the default line)")
@@ -361,6 +363,133 @@ def run_serve(a):
     print(json.dumps(line), flush=True)
 
 
+def run_configs(a):
+    """The per-configuration measurements behind the headline: evals/s of each
+    evaluation path at the Table 1 sizes (with the oracle's rate on a bounded
+    sample), the n = 5000 density-0.1 solve over lambda, the n = 100 small-case
+    solve latency, and a multi-round search history (Fig. 3/4-style curve on a
+    synthetic ORLIB-shaped instance).  CUDA-event times, L2 flushed before
+    every timed call."""
+    import torch
+    from paper_1706_00037_gb300 import synth, ubqp
+    import oracle as orc
+    orc.build()
+    torch.cuda.set_device(0)
+    dev = torch.device("cuda", 0)
+    flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device=dev)
+    stream = torch.cuda.current_stream()
+
+    def timed(fn, reps, warm=2):
+        ts = []
+        for r in range(warm + reps):
+            flush.zero_()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            fn(r)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            if r >= warm:
+                ts.append(e0.elapsed_time(e1))
+        return statistics.median(ts)
+
+    peaks = {}
+    try:
+        peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except Exception:
+        pass
+    bf16_peak = float(peaks.get("bf16_tflops", 1858.6))
+    paper_gpu_s = {2500: 0.7, 5000: 2.0, 6000: 3.0, 7000: 3.5}  # Table 1, 1000 evals
+    table1 = {}
+    for n in (2500, 5000, 6000, 7000):
+        Qh = synth.make_instance(n, 1.0, n)
+        inst = ubqp.Instance(torch.from_numpy(Qh).to(dev))
+        S = 1000
+        X = ubqp.diversify(inst, S, mode=ubqp.RANDOM, seed=n + 1)
+        f = torch.empty(S, dtype=torch.int64, device=dev)
+        row = {}
+        ref = None
+        for name, path in (("auto", ubqp.EVAL_AUTO), ("tc_fused", ubqp.EVAL_TC),
+                           ("tc_staged", ubqp.EVAL_TC_STAGED), ("plain", ubqp.EVAL_PLAIN)):
+            ws = torch.empty(max(ubqp.eval_workspace_size(inst, S, path), 16),
+                             dtype=torch.uint8, device=dev)
+            ms = timed(lambda r: ubqp.eval(inst, X, path=path, out=f, ws=ws), 10)
+            if ref is None:
+                ref = f.clone()
+            assert torch.equal(f, ref), "evaluation paths disagree"
+            row[name] = {"ms_per_1000": ms, "evals_per_s": S / (ms / 1e3),
+                         "tflops": S * n * (n + 1) / (ms / 1e3) / 1e12}
+            if path != ubqp.EVAL_PLAIN:
+                row[name]["frac_of_bf16_burst"] = row[name]["tflops"] / bf16_peak
+        inst.sync()
+        # the oracle's rate on a bounded sample of the same starts
+        Xh = X[:8].cpu().numpy().view(np.uint64)
+        t0 = time.perf_counter()
+        fh = orc.eval(Qh, Xh)
+        dt = time.perf_counter() - t0
+        assert np.array_equal(fh, ref[:8].cpu().numpy())
+        row["oracle_1core"] = {"evals_per_s": 8 / dt, "sample": "8 starts"}
+        row["paper_gtx780ti_evals_per_s"] = 1000 / paper_gpu_s[n]
+        table1[n] = row
+        del inst
+
+    # n = 5000, density 0.1, 8192 DIVERSIFY starts, lambda sweep
+    Qh = synth.make_instance(5000, 0.1, 3)
+    inst = ubqp.Instance(torch.from_numpy(Qh).to(dev))
+    c3 = {}
+    for lam in (0.25, 0.5, 0.75):
+        params = ubqp.make_params(8192, lam, mode=ubqp.DIVERSIFY, seed=3)
+        ws = torch.empty(ubqp.solve_workspace_size(inst, params), dtype=torch.uint8, device=dev)
+        bx = torch.empty(inst.words, dtype=torch.int64, device=dev)
+        bf = torch.empty(2, dtype=torch.int64, device=dev)
+        ms = timed(lambda r: ubqp.solve(inst, params, ws=ws, best_x=bx, best_f=bf,
+                                        want_stats=False), 5)
+        _, bfv, st = ubqp.solve(inst, params, ws=ws)
+        c3[str(lam)] = {"solve_ms": ms, "evals_per_s": 8192 / (ms / 1e3),
+                        "passed": st["passed"], "flips": st["total_flips"],
+                        "moves_per_s": st["total_flips"] / (ms / 1e3),
+                        "best_f": int(bfv[0].item())}
+    inst.sync()
+    del inst
+
+    # n = 100 small case: latency of one whole solve (1000 DIVERSIFY starts)
+    Qh = synth.make_instance(100, 0.1, 0)
+    inst = ubqp.Instance(torch.from_numpy(Qh).to(dev))
+    params = ubqp.make_params(1000, 0.5, mode=ubqp.DIVERSIFY, seed=0)
+    ws = torch.empty(ubqp.solve_workspace_size(inst, params), dtype=torch.uint8, device=dev)
+    bx = torch.empty(inst.words, dtype=torch.int64, device=dev)
+    bf = torch.empty(2, dtype=torch.int64, device=dev)
+    ms = timed(lambda r: ubqp.solve(inst, params, ws=ws, best_x=bx, best_f=bf,
+                                    want_stats=False), 20)
+    ref = orc.solve(Qh, 1000, 0.5, 0, 0, orc.DIVERSIFY)
+    assert int(bf[0].item()) == ref["best_f"]
+    c1 = {"solve_us": ms * 1e3, "evals_per_s": 1000 / (ms / 1e3), "best_f": ref["best_f"],
+          "equals_oracle": True}
+    inst.sync()
+    del inst
+
+    # multi-round search on an ORLIB-shaped instance (n = 2500, density 0.1)
+    Qh = synth.make_instance(2500, 0.1, 25)
+    inst = ubqp.Instance(torch.from_numpy(Qh).to(dev))
+    rounds = 40
+    res = {}
+    ms = timed(lambda r: res.update(ubqp.search(inst, 1000, 1000, rounds, 0.5, seed=25)), 3,
+               warm=1)
+    hist = res["history"].cpu().tolist()
+    search = {"n": 2500, "density": 0.1, "starts_per_round": 1000, "rounds": rounds,
+              "num_samples": 1000, "lambda": 0.5, "ms_total": ms, "ms_per_round": ms / rounds,
+              "history": hist}
+    inst.sync()
+
+    line = {"metric": "per-configuration measurements (Table 1 sizes, n=5000 lambda sweep, "
+                      "n=100 latency, search history)",
+            "value": table1[7000]["auto"]["evals_per_s"], "unit": "evals/s (eval only, n=7000)",
+            "n_gpus": 1, "steps": 10, "warmup": 2, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "int64", "data": "synthetic",
+            "config": {"workload": "configs", "l2": "flushed before every timed call"},
+            "table1": table1, "n5000_d0.1_S8192": c3, "n100_solve": c1, "search": search}
+    print(json.dumps(line), flush=True)
+
+
 def main():
     a = parse()
     if a.impl == "reference":
@@ -370,6 +499,8 @@ def main():
     if a.workload == "serve":
         a.serve_seconds = a.serve_seconds or 60.0
         return run_serve(a)
+    if a.workload == "configs":
+        return run_configs(a)
 
     import torch
     import torch.distributed as dist
