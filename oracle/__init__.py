@@ -70,6 +70,8 @@ def _load():
         "orc_solve": (None, [P, i32, i64, i64, f64, i32, u64, i32, i32, P, P, P, P]),
         "orc_brute_force": (i64, [P, i32, i64, P]),
         "orc_search": (None, [P, i32, i64, i64, i64, i32, f64, i32, u64, i32, P, P, P, P]),
+        "orc_relink1": (i32, [P, i32, i64, P, P, P, P]),
+        "orc_relink": (None, [P, i32, i64, P, P, i64, P, P, P]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -227,6 +229,30 @@ def search(Q, num_samples: int, S: int, rounds: int, lam: float, max_flips: int 
                        seed & (2**64 - 1), div_H, _p(bx), _p(bf), _p(hist), _p(st))
     return {"best_x": bx, "best_f": int(bf[0]), "history": hist[:rounds].copy(),
             "passed": int(st[0]), "total_flips": int(st[1]), "sample_sum": int(st[2])}
+
+
+def relink1(Q, x, g):
+    """Path relinking from x toward g: (best intermediate x, its f, distance)."""
+    Q, n, ldq = _q(Q)
+    x = np.ascontiguousarray(x, dtype=np.uint64)
+    g = np.ascontiguousarray(g, dtype=np.uint64)
+    xb = np.zeros(words(n), np.uint64)
+    fb = np.zeros(1, np.int64)
+    d = _load().orc_relink1(_p(Q), n, ldq, _p(x), _p(g), _p(xb), _p(fb))
+    return xb, int(fb[0]), int(d)
+
+
+def relink(Q, X, G):
+    """relink1 over pairs (X[p], G[p]): (X_best, f_best, dist)."""
+    Q, n, ldq = _q(Q)
+    X = np.ascontiguousarray(X, dtype=np.uint64).reshape(-1, words(n))
+    G = np.ascontiguousarray(G, dtype=np.uint64).reshape(-1, words(n))
+    P = X.shape[0]
+    Xb = np.zeros_like(X)
+    fb = np.zeros(P, np.int64)
+    d = np.zeros(P, np.int32)
+    _load().orc_relink(_p(Q), n, ldq, _p(X), _p(G), P, _p(Xb), _p(fb), _p(d))
+    return Xb, fb, d
 
 
 def brute_force(Q):

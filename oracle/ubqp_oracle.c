@@ -401,3 +401,68 @@ void orc_search(const int8_t* Q, int32_t n, int64_t ldq, int64_t num_samples,
   free(f);
   free(flips);
 }
+
+/* Path relinking: the solution-polishing phase the Experiments section names
+ * for after the multi-start phase, and the Path Relinking phase of Glover's
+ * template (Glover 1998) that Fig. 1's concepts come from.  From the
+ * initiating solution x toward the guiding solution g: while x and g differ,
+ * flip the differing variable whose flip gains most (the 1-flip move value
+ * Q_kk + 2 (1 - 2 x_k) y_k; lowest index on ties), whether the gain is
+ * positive or not, until x = g.  Reading: the result is the best solution
+ * strictly between the endpoints (after 1 .. |D|-1 flips, the earliest on
+ * ties), since both endpoints are already known; with |D| < 2 there is none
+ * and the result is x itself.  Returns |D|, the Hamming distance. */
+int32_t orc_relink1(const int8_t* Q, int32_t n, int64_t ldq, const uint64_t* x_init,
+                    const uint64_t* g, uint64_t* x_best, int64_t* f_best) {
+  int64_t W = orc_words(n);
+  uint64_t* x = (uint64_t*)malloc(sizeof(uint64_t) * (size_t)W);
+  int64_t* y = (int64_t*)malloc(sizeof(int64_t) * (size_t)(n > 0 ? n : 1));
+  memcpy(x, x_init, sizeof(uint64_t) * (size_t)W);
+  for (int32_t i = 0; i < n; ++i) {
+    int64_t acc = 0;
+    for (int32_t j = 0; j < n; ++j)
+      if (orc_bit(x, j)) acc += Q[(int64_t)i * ldq + j];
+    y[i] = acc;
+  }
+  int64_t fx = orc_f(Q, n, ldq, x);
+  int32_t dist = 0;
+  for (int32_t j = 0; j < n; ++j) dist += orc_bit(x, j) != orc_bit(g, j);
+  memcpy(x_best, x, sizeof(uint64_t) * (size_t)W);
+  *f_best = fx;
+  int have = 0;
+  for (int32_t t = 1; t <= dist; ++t) {
+    int32_t k = -1;
+    int64_t dk = 0;
+    for (int32_t j = 0; j < n; ++j) {
+      if (orc_bit(x, j) == orc_bit(g, j)) continue;
+      int64_t dj = Q[(int64_t)j * ldq + j] + 2 * (1 - 2 * orc_bit(x, j)) * y[j];
+      if (k < 0 || dj > dk) {
+        k = j;
+        dk = dj;
+      }
+    }
+    /* flip k: y changes by (1 - 2 x_k) times column k */
+    int64_t d = 1 - 2 * orc_bit(x, k);
+    orc_set_bit(x, k, !orc_bit(x, k));
+    for (int32_t j = 0; j < n; ++j) y[j] += d * Q[(int64_t)j * ldq + k];
+    fx += dk;
+    if (t < dist && (!have || fx > *f_best)) {
+      have = 1;
+      *f_best = fx;
+      memcpy(x_best, x, sizeof(uint64_t) * (size_t)W);
+    }
+  }
+  free(x);
+  free(y);
+  return dist;
+}
+
+void orc_relink(const int8_t* Q, int32_t n, int64_t ldq, const uint64_t* X,
+                const uint64_t* G, int64_t P, uint64_t* X_best, int64_t* f_best,
+                int32_t* dist) {
+  int64_t W = orc_words(n);
+  for (int64_t p = 0; p < P; ++p) {
+    int32_t d = orc_relink1(Q, n, ldq, X + p * W, G + p * W, X_best + p * W, f_best + p);
+    if (dist) dist[p] = d;
+  }
+}

@@ -89,6 +89,18 @@ void orc_search(const int8_t* Q, int32_t n, int64_t ldq, int64_t num_samples,
                 uint64_t seed, int32_t div_H, uint64_t* best_x, int64_t* best_f,
                 int64_t* history, int64_t* stats);
 
+/* Path relinking from x toward g: flip, among the variables where they still
+ * differ, the one of largest 1-flip gain (lowest index on ties; negative gains
+ * included) until x = g.  x_best / *f_best receive the best solution strictly
+ * between the endpoints (the earliest on ties), or x itself when the distance
+ * is below 2.  Returns the Hamming distance. */
+int32_t orc_relink1(const int8_t* Q, int32_t n, int64_t ldq, const uint64_t* x,
+                    const uint64_t* g, uint64_t* x_best, int64_t* f_best);
+/* orc_relink1 for P pairs (X[p], G[p]); dist (may be NULL) gets the distances. */
+void orc_relink(const int8_t* Q, int32_t n, int64_t ldq, const uint64_t* X,
+                const uint64_t* G, int64_t P, uint64_t* X_best, int64_t* f_best,
+                int32_t* dist);
+
 /* Exhaustive search over all 2^n solutions (n <= 24): global maximum and the
  * lowest-numbered maximiser (solution number = its bit pattern). */
 int64_t orc_brute_force(const int8_t* Q, int32_t n, int64_t ldq,

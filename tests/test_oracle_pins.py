@@ -445,3 +445,75 @@ def test_search_replays_the_rounds_of_fig2():
     assert list(r["history"]) == history
     assert r["best_f"] == inc_f and np.array_equal(r["best_x"], inc)
     assert r["passed"] == passed
+
+
+# ------------------------------------------------------------ path relinking
+
+def _relink_np(Q, x, g):
+    """Path relinking replayed with brute-force gains f(x ^ e_j) - f(x)."""
+    x = np.array(x, dtype=np.int64)
+    g = np.asarray(g, dtype=np.int64)
+    fx = _f_np(Q, x)
+    D = int((x != g).sum())
+    best_x, best_f, have = x.copy(), fx, False
+    for t in range(1, D + 1):
+        gains = []
+        for j in np.flatnonzero(x != g):
+            y = x.copy()
+            y[j] ^= 1
+            gains.append((_f_np(Q, y) - fx, -j))
+        gain, negj = max(gains)  # largest gain, then lowest index
+        x[-negj] ^= 1
+        fx += gain
+        if t < D and (not have or fx > best_f):
+            best_x, best_f, have = x.copy(), fx, True
+    assert np.array_equal(x, g)  # the path ends at the guiding solution
+    return best_x, best_f, D
+
+
+def test_relink_hand_case():
+    # Q = [[1,-2,0],[-2,3,1],[0,1,-1]], from 000 toward 111: gains (1, 3, -1)
+    # -> flip 1 (f=3); then y = column 1 = (-2, 3, 1): gains x0: 1 - 4 = -3,
+    # x2: -1 + 2 = 1 -> flip 2 (f=4); then x0 (gain -3, f=1 = sum of Q).
+    # Intermediates 010 (3) and 011 (4): best 011, value 4, distance 3.
+    Q = np.array([[1, -2, 0], [-2, 3, 1], [0, 1, -1]], dtype=np.int8)
+    xb, fb, d = orc.relink1(Q, np.array([0], np.uint64), np.array([7], np.uint64))
+    assert (int(xb[0]), fb, d) == (0b110, 4, 3)
+
+
+@pytest.mark.parametrize("n,density,seed", [(9, 1.0, 1), (23, 0.5, 2), (64, 0.3, 3),
+                                            (70, 1.0, 4)])
+def test_relink_matches_bruteforce_replay(n, density, seed):
+    Q = synth.make_instance(n, density, seed)
+    rng = np.random.default_rng(seed)
+    for _ in range(4):
+        x = rng.integers(0, 2, n)
+        g = rng.integers(0, 2, n)
+        xb, fb, d = orc.relink1(Q, synth.pack_bits(x), synth.pack_bits(g))
+        ex, ef, ed = _relink_np(Q, x, g)
+        assert d == ed and fb == ef
+        assert np.array_equal(synth.unpack_bits(xb, n), ex)
+        assert fb == _f_np(Q, synth.unpack_bits(xb, n))
+
+
+def test_relink_short_distances_return_the_initiating_solution():
+    n = 40
+    Q = synth.make_instance(n, 0.5, 9)
+    x = np.random.default_rng(1).integers(0, 2, n)
+    for flip in ([], [17]):
+        g = x.copy()
+        g[flip] ^= 1
+        xb, fb, d = orc.relink1(Q, synth.pack_bits(x), synth.pack_bits(g))
+        assert d == len(flip)
+        assert np.array_equal(synth.unpack_bits(xb, n), x) and fb == _f_np(Q, x)
+
+
+def test_relink_batch_is_pairwise():
+    n = 50
+    Q = synth.make_instance(n, 0.6, 11)
+    X = orc.diversify(None, n, orc.RANDOM, 1, 0, 5)
+    G = orc.diversify(None, n, orc.RANDOM, 2, 0, 5)
+    Xb, fb, d = orc.relink(Q, X, G)
+    for p in range(5):
+        xb1, fb1, d1 = orc.relink1(Q, X[p], G[p])
+        assert np.array_equal(Xb[p], xb1) and fb[p] == fb1 and d[p] == d1
