@@ -46,7 +46,7 @@
 extern "C" {
 #endif
 
-#define UBQP_ABI_VERSION 2
+#define UBQP_ABI_VERSION 3
 
 typedef enum ubqp_status {
   UBQP_OK = 0,
@@ -375,6 +375,30 @@ int ubqp_server_wait(ubqp_server* s, int64_t ticket, int64_t* best_f, uint64_t* 
 int ubqp_server_poll(ubqp_server* s, int64_t ticket, int32_t* done);
 size_t ubqp_server_request_bytes(const ubqp_server* s, int32_t n);
 void ubqp_server_destroy(ubqp_server* s);
+
+/*
+ * Path relinking (intensification).  The Experiments section names path
+ * relinking as the polishing phase to follow the multi-start phase, and the
+ * Conclusions find the method short of intensification; Fig. 1's concepts
+ * come from Glover's (1998) template, whose second phase it is.  For each pair
+ * p < P: from the initiating solution X_dev[p] (value f_dev[p], as from
+ * ubqp_eval) toward the guiding solution G_dev[p], flip at each step, among the
+ * variables where the two still differ, the one of largest 1-flip gain
+ * Q_kk + 2 (1 - 2 x_k) y_k (lowest index on ties; negative gains are taken
+ * too), until the two agree.  Xbest_dev[p] (W words) receives the best solution
+ * strictly between the endpoints (the earliest on ties) and fbest_dev[p] its
+ * value; when the pair differs in fewer than 2 variables there is none and the
+ * result is X_dev[p] itself.  dist_dev[p] (may be NULL) receives the Hamming
+ * distance.  The results are typically polished with ubqp_ascent.
+ *   ws: at least ubqp_relink_workspace_size(q, P, 0) bytes (16-byte aligned;
+ *   a trace of the flipped indices); with ubqp_relink_workspace_size(q, P, 1)
+ *   bytes y = Qx of the initiating solutions is formed on the tensor cores.
+ *   Async on `stream`; errors as ubqp_ascent (UBQP_ERR_NOMEM: ws too small).
+ */
+size_t ubqp_relink_workspace_size(const ubqp_q* q, int64_t P, int32_t tensor_startup);
+int ubqp_relink(const ubqp_q* q, const uint64_t* X_dev, const int64_t* f_dev,
+                const uint64_t* G_dev, int64_t P, uint64_t* Xbest_dev, int64_t* fbest_dev,
+                int32_t* dist_dev, void* ws, size_t ws_bytes, void* stream);
 
 /* The search of Fig. 2, run in rounds of starts_per_round starts. */
 typedef struct ubqp_search_params {

@@ -386,10 +386,8 @@ int ubqp_screen(const int64_t* f_dev, int64_t S, double lambda, int32_t* idx_dev
   if (S < 1 || S >= ((int64_t)1 << 31)) return fail(UBQP_ERR_ARG, "S=%lld outside [1, 2^31)", (long long)S);
   if (!(lambda == lambda) || lambda > 1e300 || lambda < -1e300)
     return fail(UBQP_ERR_ARG, "lambda is not finite");
-  int r;
-  if ((r = ubqp_screen_stats(f_dev, S, 0, stats_dev, stream))) return r;
-  if ((r = ubqp_screen_apply(f_dev, S, stats_dev, S, lambda, idx_dev, count_dev, Tm_dev, stream)))
-    return r;
+  UBQP_CUDA(ubqp::launch_screen(f_dev, S, lambda, idx_dev, count_dev, Tm_dev, stats_dev,
+                                (cudaStream_t)stream));
   return UBQP_OK;
 }
 
@@ -417,6 +415,49 @@ int ubqp_ascent(const ubqp_q* q, uint64_t* X_dev, int64_t* f_dev, const int32_t*
   }
   UBQP_CUDA(ubqp::launch_ascent(q, X_dev, f_dev, idx_dev, count_dev, S, max_flips, flips_dev, Y,
                                 st));
+  return UBQP_OK;
+}
+
+// Relinking workspace: [trace: P rows of n rounded up to 8 uint16][pair count]
+// [tensor-core start-up of P starts, optional]
+static int64_t relink_trace_ld(const ubqp_q* q) { return ((int64_t)q->n + 7) / 8 * 8; }
+static size_t relink_base_bytes(const ubqp_q* q, int64_t P) {
+  return (size_t)((P * relink_trace_ld(q) * 2 + 255) / 256 * 256) + 256;
+}
+
+size_t ubqp_relink_workspace_size(const ubqp_q* q, int64_t P, int32_t tensor_startup) {
+  if (!q || P < 0) return 0;
+  return relink_base_bytes(q, P) + (tensor_startup ? ubqp::ascent_tc_workspace(q, P) : 0);
+}
+
+int ubqp_relink(const ubqp_q* q, const uint64_t* X_dev, const int64_t* f_dev,
+                const uint64_t* G_dev, int64_t P, uint64_t* Xbest_dev, int64_t* fbest_dev,
+                int32_t* dist_dev, void* ws, size_t ws_bytes, void* stream) {
+  if (!q || !X_dev || !f_dev || !G_dev || !Xbest_dev || !fbest_dev)
+    return fail(UBQP_ERR_ARG, "NULL argument");
+  if (P < 0 || P >= ((int64_t)1 << 31)) return fail(UBQP_ERR_ARG, "P outside [0, 2^31)");
+  if (P == 0) return UBQP_OK;
+  if (!ws || ((uintptr_t)ws & 15) != 0)
+    return fail(UBQP_ERR_ARG, "workspace NULL or not 16-byte aligned");
+  const size_t base = relink_base_bytes(q, P);
+  if (ws_bytes < base)
+    return fail(UBQP_ERR_NOMEM, "relink workspace of %zu bytes, need at least %zu", ws_bytes,
+                base);
+  cudaStream_t st = (cudaStream_t)stream;
+  uint16_t* trace = reinterpret_cast<uint16_t*>(ws);
+  int64_t* count = reinterpret_cast<int64_t*>(static_cast<char*>(ws) + base - 256);
+  float* Y = nullptr;
+  if (ws_bytes >= base + ubqp::ascent_tc_workspace(q, P) &&
+      (int64_t)q->max_abs * q->n_tc < (1 << 24)) {
+    UBQP_CUDA(ubqp::launch_set_u64(reinterpret_cast<uint64_t*>(count), (uint64_t)P, st));
+    cudaError_t e = ubqp::launch_ascent_init_tc(q, X_dev, nullptr, count, P,
+                                                static_cast<char*>(ws) + base, ws_bytes - base,
+                                                &Y, st);
+    if (e == cudaErrorNotSupported) Y = nullptr;
+    else if (e != cudaSuccess) return cuda_fail(e, "relink start-up (tensor cores)");
+  }
+  UBQP_CUDA(ubqp::launch_relink(q, X_dev, f_dev, G_dev, P, Xbest_dev, fbest_dev, dist_dev, trace,
+                                relink_trace_ld(q), Y, st));
   return UBQP_OK;
 }
 

@@ -109,6 +109,7 @@ struct Group<32> {
   }
   __device__ __forceinline__ bool any(bool p) { return __any_sync(0xffffffffu, p); }
   __device__ __forceinline__ void sync() { __syncwarp(); }
+  __device__ __forceinline__ int sum(int v) { return __reduce_add_sync(0xffffffffu, v); }
 };
 
 // One block per start.
@@ -140,9 +141,34 @@ struct Group {
   }
   __device__ __forceinline__ bool any(bool p) { return __syncthreads_or(p) != 0; }
   __device__ __forceinline__ void sync() { __syncthreads(); }
+  __device__ __forceinline__ int sum(int v) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int s = __reduce_add_sync(0xffffffffu, v);
+    if (lane == 0) rec[parity][warp] = make_int2(s, 0);
+    __syncthreads();
+    const int r = lane < NW ? rec[parity][lane].x : 0;
+    parity ^= 1;
+    return __reduce_add_sync(0xffffffffu, r);
+  }
 };
 
-template <int T, int C, int R>
+// Path relinking of one pair (see relink_block_kernel): the guiding solution,
+// the outputs and a trace of the flipped indices (n entries of scratch).
+struct RelinkArgs {
+  const uint64_t* g;
+  uint64_t* x_best;
+  int64_t* f_best;
+  int32_t* dist;
+  uint16_t* trace;
+};
+
+// RL = false: steepest ascent of x_g in place (f_s updated, flips to flips_s).
+// RL = true: path relinking from x_g (read only, value *f_s) toward rl->g --
+// the same move machinery, but only variables where x and g differ are
+// candidates, every step is taken whatever its gain, a flipped variable leaves
+// the candidate set, and the best solution strictly between the endpoints is
+// the result.
+template <int T, int C, int R, bool RL = false>
 __device__ __forceinline__ void ascend_one(const int8_t* __restrict__ Q8, int64_t ldq,
                                            int64_t ldy, int n,
                                            int W, uint64_t* __restrict__ x_g,
@@ -150,28 +176,36 @@ __device__ __forceinline__ void ascend_one(const int8_t* __restrict__ Q8, int64_
                                            int32_t* __restrict__ flips_s,
                                            unsigned* __restrict__ err, uint64_t* xs,
                                            uint4* spec_slots,
-                                           const float* __restrict__ y_g, Group<T>& grp) {
+                                           const float* __restrict__ y_g, Group<T>& grp,
+                                           const RelinkArgs* rl = nullptr) {
   constexpr int E = 16 * C;
   constexpr int CW = 16 * T;  // indices per chunk
   static_assert(E <= 32, "local index must fit 5 bits");
   const int g = grp.rank();
 
   int y[E], S[E], Ck[E];
+  int ndiff = 0;  // relinking: owned variables where x and g differ
   // ---- owned bits of x; C and S per element
 #pragma unroll
   for (int c = 0; c < C; ++c) {
     const int j0 = c * CW + 16 * g;
-    uint32_t nib = 0;
+    uint32_t nib = 0, diff = 0xFFFFu;
     if (j0 < n) {
       nib = (uint32_t)((x_g[j0 >> 6] >> (j0 & 63)) & 0xFFFFull);
       if (n - j0 < 16) nib &= (1u << (n - j0)) - 1u;
+      if (RL) {
+        uint32_t gn = (uint32_t)((rl->g[j0 >> 6] >> (j0 & 63)) & 0xFFFFull);
+        if (n - j0 < 16) gn &= (1u << (n - j0)) - 1u;
+        diff = nib ^ gn;
+        ndiff += __popc(diff);
+      }
     }
 #pragma unroll
     for (int o = 0; o < 16; ++o) {
       const int e = c * 16 + o, j = j0 + o;
       const int xb = (int)((nib >> o) & 1u);
       y[e] = 0;
-      if (j < n) {
+      if (j < n && ((diff >> o) & 1u)) {
         const int qjj = Q8[(int64_t)j * ldq + j];
         S[e] = xb ? -128 : 128;
         Ck[e] = 64 * qjj + 2 * (31 - e) + xb;
@@ -264,10 +298,18 @@ __device__ __forceinline__ void ascend_one(const int8_t* __restrict__ Q8, int64_
 
   int64_t fval = *f_s;
   int flips = 0;
+  // relinking: path length, best intermediate value and its step
+  const int dist = RL ? grp.sum(ndiff) : 0;
+  int64_t fbest = fval;
+  int tbest = 0;
   const uint64_t t0 = globaltimer();
   for (;;) {
-    if (max_flips > 0 && flips >= max_flips) break;
-    if (best.x <= 0) break;
+    if (RL) {
+      if (flips >= dist - 1) break;  // the last step only reaches g
+    } else {
+      if (max_flips > 0 && flips >= max_flips) break;
+      if (best.x <= 0) break;
+    }
     if ((flips & 1023) == 1023) {
       const bool late = (int64_t)(globaltimer() - t0) > kTimeoutNs;
       if (grp.any(late)) {
@@ -280,6 +322,13 @@ __device__ __forceinline__ void ascend_one(const int8_t* __restrict__ Q8, int64_
     const int dsel[4] = {byte_sel(0, d), byte_sel(1, d), byte_sel(2, d), byte_sel(3, d)};
     fval += best.x;
     ++flips;
+    if (RL) {
+      if (flips < dist && (tbest == 0 || fval > fbest)) {
+        fbest = fval;
+        tbest = flips;
+      }
+      if (g == 0) rl->trace[flips - 1] = (uint16_t)k;
+    }
     uint4 q[C];
     bool hit = false;
     if constexpr (R > 0) {
@@ -331,15 +380,16 @@ __device__ __forceinline__ void ascend_one(const int8_t* __restrict__ Q8, int64_
       asm volatile("cp.async.commit_group;" ::: "memory");
       buf ^= 1;
     }
-    // the owner of k flips x_k: negate S_k, toggle the x bit in C_k
+    // the owner of k flips x_k: negate S_k, toggle the x bit in C_k (when
+    // relinking, k leaves the candidates instead: S_k = 0, C_k = INT_MIN)
     const int kc = k / CW, kr = k - kc * CW;
     if ((kr >> 4) == g) {
       const int ek = kc * 16 + (kr & 15);
 #pragma unroll
       for (int e = 0; e < E; ++e)
         if (e == ek) {
-          S[e] = -S[e];
-          Ck[e] ^= 1;
+          S[e] = RL ? 0 : -S[e];
+          Ck[e] = RL ? INT_MIN : (Ck[e] ^ 1);
         }
     }
     int km[4] = {INT_MIN, INT_MIN, INT_MIN, INT_MIN};
@@ -358,6 +408,23 @@ __device__ __forceinline__ void ascend_one(const int8_t* __restrict__ Q8, int64_
   }
   // copies still in flight must land before the slots serve another start
   if (R > 0) asm volatile("cp.async.wait_group 0;" ::: "memory");
+  if constexpr (RL) {
+    // ---- the best intermediate: x with the first tbest traced flips applied
+    if (g == 0) {
+      *rl->f_best = fbest;
+      if (rl->dist) *rl->dist = dist;
+    }
+    for (int w = g; w < W; w += T) xs[w] = x_g[w];
+    grp.sync();
+    for (int t = g; t < tbest; t += T) {
+      const int k = rl->trace[t];
+      atomicXor(reinterpret_cast<unsigned long long*>(&xs[k >> 6]), 1ull << (k & 63));
+    }
+    grp.sync();
+    for (int w = g; w < W; w += T) rl->x_best[w] = xs[w];
+    grp.sync();
+    return;
+  }
   // ---- write back f, flips and x
   if (g == 0) {
     *f_s = fval;
@@ -454,6 +521,54 @@ ascent_warp_kernel(const int8_t* __restrict__ Q8, int64_t ldq, int n, int W,
   }
 }
 
+// Path relinking of pairs p < P: from X[p] (value f[p]) toward G[p]; the best
+// intermediate solution to Xb[p], its value to fb[p], the distance to dist[p]
+// (may be NULL).  trace: P rows of ldt uint16 scratch.  Y: y = Q X[p] rows from
+// the tensor-core start-up, or NULL.
+template <int T, int C, int R>
+__global__ void __launch_bounds__(T, 1)
+relink_block_kernel(const int8_t* __restrict__ Q8, int64_t ldq, int n, int W,
+                    const uint64_t* __restrict__ X, const int64_t* __restrict__ f,
+                    const uint64_t* __restrict__ G, int64_t P, uint64_t* __restrict__ Xb,
+                    int64_t* __restrict__ fb, int32_t* __restrict__ dist,
+                    uint16_t* __restrict__ trace, int64_t ldt, const float* __restrict__ Y,
+                    int64_t ldy, unsigned* __restrict__ err) {
+  __shared__ int2 rec[2][T / 32];
+  __shared__ uint64_t xs[UBQP_MAX_N / 64];
+  __shared__ uint4 spec_slots[spec_slot_count<T, C, R>()];
+  Group<T> grp{rec, 0};
+  for (int64_t p = blockIdx.x; p < P; p += gridDim.x) {
+    const RelinkArgs a{G + p * W, Xb + p * W, fb + p, dist ? dist + p : nullptr,
+                       trace + p * ldt};
+    int64_t f0 = f[p];
+    ascend_one<T, C, R, true>(Q8, ldq, ldy, n, W, const_cast<uint64_t*>(X + p * W), &f0, 0,
+                              nullptr, err, xs, spec_slots, Y ? Y + p * ldy : nullptr, grp, &a);
+  }
+}
+
+template <int C, int R>
+__global__ void __launch_bounds__(128)
+relink_warp_kernel(const int8_t* __restrict__ Q8, int64_t ldq, int n, int W,
+                   const uint64_t* __restrict__ X, const int64_t* __restrict__ f,
+                   const uint64_t* __restrict__ G, int64_t P, uint64_t* __restrict__ Xb,
+                   int64_t* __restrict__ fb, int32_t* __restrict__ dist,
+                   uint16_t* __restrict__ trace, int64_t ldt, const float* __restrict__ Y,
+                   int64_t ldy, unsigned* __restrict__ err) {
+  __shared__ uint64_t xs_all[4][16];
+  __shared__ uint4 spec_slots[4 * spec_slot_count<32, C, R>()];
+  Group<32> grp;
+  const int warp = threadIdx.x >> 5;
+  for (int64_t p = (int64_t)blockIdx.x * 4 + warp; p < P; p += (int64_t)gridDim.x * 4) {
+    const RelinkArgs a{G + p * W, Xb + p * W, fb + p, dist ? dist + p : nullptr,
+                       trace + p * ldt};
+    int64_t f0 = f[p];
+    ascend_one<32, C, R, true>(Q8, ldq, ldy, n, W, const_cast<uint64_t*>(X + p * W), &f0, 0,
+                               nullptr, err, xs_all[warp],
+                               spec_slots + warp * spec_slot_count<32, C, R>(),
+                               Y ? Y + p * ldy : nullptr, grp, &a);
+  }
+}
+
 template <class K>
 int resident_grid(K kernel, int threads, int sm_count) {
   int per_sm = 0;
@@ -496,7 +611,48 @@ cudaError_t launch_ascent_batch_tc(const BatchDesc* d, const int2* items, const 
   return cudaGetLastError();
 }
 
+template <int T, int C>
+cudaError_t launch_relink_block(const ubqp_q* h, const uint64_t* X, const int64_t* f,
+                                const uint64_t* G, int64_t P, uint64_t* Xb, int64_t* fb,
+                                int32_t* dist, uint16_t* trace, int64_t ldt, const float* Y,
+                                cudaStream_t st) {
+  int grid = resident_grid(relink_block_kernel<T, C, kSpecRows>, T, h->sm_count);
+  if ((int64_t)grid > P) grid = (int)P;
+  relink_block_kernel<T, C, kSpecRows><<<grid, T, 0, st>>>(
+      h->Q8, h->ldq, h->n, h->W, X, f, G, P, Xb, fb, dist, trace, ldt, Y, h->n_tc, h->err);
+  return cudaGetLastError();
+}
+
+template <int C>
+cudaError_t launch_relink_warp(const ubqp_q* h, const uint64_t* X, const int64_t* f,
+                               const uint64_t* G, int64_t P, uint64_t* Xb, int64_t* fb,
+                               int32_t* dist, uint16_t* trace, int64_t ldt, const float* Y,
+                               cudaStream_t st) {
+  int grid = resident_grid(relink_warp_kernel<C, kSpecRows>, 128, h->sm_count);
+  const int64_t need = (P + 3) / 4;
+  if ((int64_t)grid > need) grid = (int)need;
+  relink_warp_kernel<C, kSpecRows><<<grid, 128, 0, st>>>(
+      h->Q8, h->ldq, h->n, h->W, X, f, G, P, Xb, fb, dist, trace, ldt, Y, h->n_tc, h->err);
+  return cudaGetLastError();
+}
+
 }  // namespace
+
+cudaError_t launch_relink(const ubqp_q* h, const uint64_t* X, const int64_t* f, const uint64_t* G,
+                          int64_t P, uint64_t* Xb, int64_t* fb, int32_t* dist, uint16_t* trace,
+                          int64_t ldt, const float* Y, cudaStream_t st) {
+  const int n = h->n;
+#define UBQP_RL_ARGS h, X, f, G, P, Xb, fb, dist, trace, ldt, Y, st
+  if (n <= 256) return launch_relink_warp<1>(UBQP_RL_ARGS);
+  if (n <= 512) return launch_relink_warp<2>(UBQP_RL_ARGS);
+  if (n <= 1024) return launch_relink_block<64, 1>(UBQP_RL_ARGS);
+  if (n <= 2048) return launch_relink_block<128, 1>(UBQP_RL_ARGS);
+  if (n <= 4096) return launch_relink_block<256, 1>(UBQP_RL_ARGS);
+  if (n <= 8192) return launch_relink_block<256, 2>(UBQP_RL_ARGS);
+  if (n <= 16384) return launch_relink_block<512, 2>(UBQP_RL_ARGS);
+#undef UBQP_RL_ARGS
+  return cudaErrorInvalidValue;
+}
 
 bool ascent_batch_supported(int T, int C) {
   return (T == 64 || T == 128 || T == 256 || T == 512) && (C == 1 || C == 2);

@@ -3,8 +3,9 @@
 // f_b > T (Fig. 2).  Two single-block kernels: the statistics (an exact int64
 // sum and a max with its lowest index, by warp shuffles), and the threshold in
 // double with explicitly rounded operations (no FMA) followed by a block-wide
-// ballot/prefix-sum compaction.  The split lets a batch sharded over ranks
-// combine the statistics before the threshold.
+// ballot/prefix-sum compaction.  One launch runs both for a whole batch; the
+// split launches let a batch sharded over ranks combine the statistics before
+// the threshold.
 #include <climits>
 
 #include "ubqp_internal.cuh"
@@ -103,6 +104,15 @@ screen_apply_kernel(const int64_t* __restrict__ f, int64_t S, const int64_t* __r
   block_screen_apply(f, S, gstats, S_total, lambda, idx, count, Tm);
 }
 
+// The whole screen of one batch in one block (statistics, then threshold and
+// compaction): the unsharded ubqp_screen.
+__global__ void __launch_bounds__(THREADS)
+screen_kernel(const int64_t* __restrict__ f, int64_t S, double lambda, int32_t* __restrict__ idx,
+              int64_t* __restrict__ count, double* __restrict__ Tm, int64_t* __restrict__ stats) {
+  block_screen_stats(f, S, 0, stats);
+  block_screen_apply(f, S, stats, S, lambda, idx, count, Tm);
+}
+
 // One block per instance of a batch: the screen of ubqp_screen on its values.
 __global__ void __launch_bounds__(THREADS)
 screen_batch_kernel(const BatchDesc* __restrict__ d, double lambda) {
@@ -116,6 +126,12 @@ screen_batch_kernel(const BatchDesc* __restrict__ d, double lambda) {
 cudaError_t launch_screen_stats(const int64_t* f, int64_t S, int64_t offset, int64_t* stats,
                                 cudaStream_t st) {
   screen_stats_kernel<<<1, THREADS, 0, st>>>(f, S, offset, stats);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_screen(const int64_t* f, int64_t S, double lambda, int32_t* idx,
+                          int64_t* count, double* Tm, int64_t* stats, cudaStream_t st) {
+  screen_kernel<<<1, THREADS, 0, st>>>(f, S, lambda, idx, count, Tm, stats);
   return cudaGetLastError();
 }
 

@@ -124,6 +124,9 @@ cudaError_t launch_screen_stats(const int64_t* f, int64_t S, int64_t offset, int
 cudaError_t launch_screen_apply(const int64_t* f, int64_t S, const int64_t* gstats,
                                 int64_t S_total, double lambda, int32_t* idx, int64_t* count,
                                 double* Tm, cudaStream_t st);
+cudaError_t launch_relink(const ubqp_q* h, const uint64_t* X, const int64_t* f, const uint64_t* G,
+                          int64_t P, uint64_t* Xb, int64_t* fb, int32_t* dist, uint16_t* trace,
+                          int64_t ldt, const float* Y, cudaStream_t st);
 cudaError_t launch_ascent(const ubqp_q* h, uint64_t* X, int64_t* f, const int32_t* idx,
                           const int64_t* count, int64_t S, int32_t max_flips,
                           int32_t* flips, const float* Y, cudaStream_t st);
@@ -134,6 +137,8 @@ cudaError_t launch_search_update(const int64_t* cand, const uint64_t* X, int W,
                                  int64_t* inc_f, uint64_t* inc_x, int64_t* history,
                                  int64_t* stats, cudaStream_t st);
 // batched stages: one launch over all instances of a batch
+cudaError_t launch_screen(const int64_t* f, int64_t S, double lambda, int32_t* idx,
+                          int64_t* count, double* Tm, int64_t* stats, cudaStream_t st);
 cudaError_t launch_screen_batch(const BatchDesc* d, int count, double lambda, cudaStream_t st);
 cudaError_t launch_batch_items(const BatchDesc* d, const int32_t* order, int count, int2* items,
                                int64_t* n_items, cudaStream_t st);

@@ -32,7 +32,8 @@ EXPORTS = ["ubqp_strerror", "ubqp_last_error", "ubqp_abi_version", "ubqp_q_prepa
            "ubqp_batch_destroy", "ubqp_batch_run", "ubqp_batch_tune", "ubqp_batch_capture",
            "ubqp_batch_result", "ubqp_batch_get", "ubqp_batch_config", "ubqp_q_arena_size",
            "ubqp_q_prepare_into", "ubqp_server_create", "ubqp_server_submit", "ubqp_server_wait",
-           "ubqp_server_poll", "ubqp_server_request_bytes", "ubqp_server_destroy"]
+           "ubqp_server_poll", "ubqp_server_request_bytes", "ubqp_server_destroy",
+           "ubqp_relink_workspace_size", "ubqp_relink"]
 
 
 class UbqpError(RuntimeError):
@@ -108,6 +109,8 @@ def load() -> ctypes.CDLL:
         "ubqp_ascent_workspace_size": (sz, [P, i64]),
         "ubqp_ascent": (ctypes.c_int, [P, P, P, P, P, i64, i32, P, P, sz, P]),
         "ubqp_best": (ctypes.c_int, [P, P, i64, i32, P, P, P]),
+        "ubqp_relink_workspace_size": (sz, [P, i64, i32]),
+        "ubqp_relink": (ctypes.c_int, [P, P, P, P, i64, P, P, P, P, sz, P]),
         "ubqp_solve_workspace_size": (sz, [P, ctypes.POINTER(Params)]),
         "ubqp_solve": (ctypes.c_int, [P, ctypes.POINTER(Params), P, P, ctypes.POINTER(Stats),
                                       P, sz, P]),
@@ -307,6 +310,26 @@ def ascent(inst: Instance, X: torch.Tensor, f: torch.Tensor, idx: torch.Tensor,
     _check(load().ubqp_ascent(inst.handle, _ptr(X), _ptr(f), _ptr(idx), _ptr(count), S,
                               max_flips, _ptr(flips), _ptr(ws), nbytes, _stream(stream)))
     return flips
+
+
+def relink_workspace_size(inst: Instance, P: int, tensor_startup: bool = True) -> int:
+    return int(load().ubqp_relink_workspace_size(inst.handle, P, 1 if tensor_startup else 0))
+
+
+def relink(inst: Instance, X: torch.Tensor, f: torch.Tensor, G: torch.Tensor,
+           tensor_startup: bool = True, ws: torch.Tensor | None = None, stream=None):
+    """Path relinking of the pairs (X[p], G[p]) (ubqp_relink); f[p] = f(X[p]).
+    Returns (X_best, f_best, dist)."""
+    P = X.shape[0]
+    Xb = torch.empty_like(X)
+    fb = torch.empty(P, dtype=torch.int64, device=X.device)
+    dist = torch.empty(P, dtype=torch.int32, device=X.device)
+    if ws is None:
+        ws = torch.empty(max(relink_workspace_size(inst, P, tensor_startup), 16),
+                         dtype=torch.uint8, device=X.device)
+    _check(load().ubqp_relink(inst.handle, _ptr(X), _ptr(f), _ptr(G), P, _ptr(Xb), _ptr(fb),
+                              _ptr(dist), _ptr(ws), ws.numel(), _stream(stream)))
+    return Xb, fb, dist
 
 
 def best(f: torch.Tensor, X: torch.Tensor, stream=None):

@@ -34,7 +34,7 @@ def test_library_exports_every_declared_symbol():
 
 def test_strerror_and_version():
     lib = ubqp.load()
-    assert lib.ubqp_abi_version() == 2
+    assert lib.ubqp_abi_version() == 3
     for st, name in ubqp.STATUS_NAMES.items():
         assert lib.ubqp_strerror(st)
     assert lib.ubqp_strerror(0) == b"ok"
