@@ -62,7 +62,13 @@ typedef enum ubqp_status {
 /* Start generation modes (see ubqp_diversify). */
 enum { UBQP_MODE_RANDOM = 0, UBQP_MODE_DIVERSIFY = 1 };
 /* Evaluation paths (see ubqp_eval). */
-enum { UBQP_EVAL_AUTO = 0, UBQP_EVAL_TC = 1, UBQP_EVAL_PLAIN = 2, UBQP_EVAL_TC_STAGED = 3 };
+enum {
+  UBQP_EVAL_AUTO = 0,
+  UBQP_EVAL_TC = 1,
+  UBQP_EVAL_PLAIN = 2,
+  UBQP_EVAL_TC_STAGED = 3,
+  UBQP_EVAL_TC_TMEM = 4
+};
 
 /* Opaque prepared instance: device-resident Q in the layouts the kernels use,
  * its row sums, max|Q|, the first-derivative start and an error word. */
@@ -155,6 +161,10 @@ int ubqp_diversify_range(const ubqp_q* q, const uint64_t* x0_dev, int32_t mode,
  *        unpacked to bf16 in device scratch and both operands fed by TMA;
  *        needs ws_bytes >= ubqp_eval_workspace_size(q, S, path) (16-byte
  *        aligned).
+ *   path UBQP_EVAL_TC_TMEM: the same contraction with the 0/1 operand
+ *        written into tensor memory (tcgen05.st) straight from the bits and
+ *        read from there by the MMA (192-column blocks), so shared memory
+ *        carries only Q'; needs no workspace.
  *   path UBQP_EVAL_PLAIN: one block per solution on the CUDA cores (dp4a);
  *        needs no workspace.
  *   path UBQP_EVAL_AUTO: UBQP_EVAL_TC up to n_pad = 4096 (n rounded up to

@@ -305,7 +305,8 @@ int ubqp_eval(const ubqp_q* q, const uint64_t* X_dev, int64_t S, int64_t* f_dev,
   if (!q || !X_dev || !f_dev) return fail(UBQP_ERR_ARG, "NULL argument");
   if (S < 0) return fail(UBQP_ERR_ARG, "S < 0");
   path = resolve_path(q, path);
-  if (path != UBQP_EVAL_TC && path != UBQP_EVAL_PLAIN && path != UBQP_EVAL_TC_STAGED)
+  if (path != UBQP_EVAL_TC && path != UBQP_EVAL_PLAIN && path != UBQP_EVAL_TC_STAGED &&
+      path != UBQP_EVAL_TC_TMEM)
     return fail(UBQP_ERR_ARG, "unknown eval path %d", path);
   if (S == 0) return UBQP_OK;
   cudaStream_t st = (cudaStream_t)stream;
@@ -317,6 +318,13 @@ int ubqp_eval(const ubqp_q* q, const uint64_t* X_dev, int64_t S, int64_t* f_dev,
   if ((int64_t)2 * q->max_abs * q->n_tc >= (1 << 24))
     return fail(UBQP_ERR_RANGE, "2*max|Q|*n_pad = %lld >= 2^24",
                 (long long)2 * q->max_abs * q->n_tc);
+  if (path == UBQP_EVAL_TC_TMEM) {
+    cudaError_t e = ubqp::launch_eval_ts(q, X_dev, S, f_dev, st);
+    if (e == cudaErrorNotSupported)
+      return fail(UBQP_ERR_UNSUPPORTED, "tensor-core evaluation not available for this size");
+    if (e != cudaSuccess) return cuda_fail(e, "eval_ts");
+    return UBQP_OK;
+  }
   const bool fused = path == UBQP_EVAL_TC;
   const size_t need = fused ? 0 : ubqp::eval_tc_workspace(q, S);
   if (ws_bytes < need || (need && !ws))

@@ -51,9 +51,26 @@ constexpr int A_WRITERS = 128;  // one row of the A tile per thread
 constexpr int THREADS_FUSED = THREADS + A_WRITERS;
 constexpr int SMEM_BYTES_FUSED = SMEM_BYTES;
 constexpr uint64_t kWaitNs = 2000ull * 1000 * 1000;
+// Tensor-memory A operand (eval_ts_kernel): the 0/1 rows are written into
+// tensor memory by tcgen05.st, so shared memory carries only B.  N = 192 so
+// that two accumulators (384 columns) and four A stages (4 x 32 columns of
+// 64 bf16 per row) fill the 512 columns.
+// The A ring (written locally, no memory latency to hide) and the B ring (TMA
+// loads from L2, whose latency the stages hide) advance independently: eight
+// B stages fill the shared memory.
+constexpr int BN_TS = 192;
+constexpr int B_BYTES_TS = BN_TS * BK * 2;
+constexpr int STAGES_A_TS = 4;
+constexpr int STAGES_B_TS = 4;
+constexpr uint32_t ACOL_TS = 2 * BN_TS;  // first A-stage column
+constexpr int A_WRITERS_TS = 256;  // two warps per lane quarter, 16 columns each
+constexpr int THREADS_TS = THREADS + A_WRITERS_TS;
+constexpr int SMEM_BYTES_TS = 1024 + STAGES_B_TS * B_BYTES_TS + 256;
 
 // Instruction descriptor, kind::f16: D fp32 (bits 4-5 = 1), A bf16 (7-9 = 1),
 // B bf16 (10-12 = 1), both K-major (15, 16 = 0), N/8 at 17-22, M/16 at 24-28.
+constexpr uint32_t IDESC_TS = (1u << 4) | (1u << 7) | (1u << 10) |
+                              ((uint32_t)(BN_TS >> 3) << 17) | ((uint32_t)(BM >> 4) << 24);
 constexpr uint32_t IDESC = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(BN >> 3) << 17) |
                            ((uint32_t)(BM >> 4) << 24);
 
@@ -157,6 +174,31 @@ __device__ __forceinline__ void mma_commit(uint64_t* bar) {
       : "memory");
 }
 
+// D (+)= A B with A (128 x 16 bf16) in tensor memory at tmem_a (row i in lane
+// i, two elements per 32-bit column) and B from shared memory.
+__device__ __forceinline__ void mma_bf16_ts(uint32_t tmem_d, uint32_t tmem_a, uint64_t b,
+                                            uint32_t accumulate) {
+  asm volatile(
+      "{\n .reg .pred p;\n setp.ne.b32 p, %3, 0;\n"
+      " tcgen05.mma.cta_group::1.kind::f16 [%0], [%1], %2, %4, p;\n}\n" ::"r"(tmem_d),
+      "r"(tmem_a), "l"(b), "r"(accumulate), "r"(IDESC_TS)
+      : "memory");
+}
+
+#define UBQP_S8(i) "r"(v[i]), "r"(v[i + 1]), "r"(v[i + 2]), "r"(v[i + 3]), \
+                   "r"(v[i + 4]), "r"(v[i + 5]), "r"(v[i + 6]), "r"(v[i + 7])
+// 16 consecutive 32-bit columns of this thread's lane; the warp may only
+// address its own quarter of the lanes (32 * (warp % 4) ...).
+__device__ __forceinline__ void tmem_st16(uint32_t taddr, const uint32_t (&v)[16]) {
+  asm volatile(
+      "tcgen05.st.sync.aligned.32x32b.x16.b32 [%0], {%1, %2, %3, %4, %5, %6, %7, %8, %9, %10,"
+      " %11, %12, %13, %14, %15, %16};" ::"r"(taddr),
+      UBQP_S8(0), UBQP_S8(8)
+      : "memory");
+  asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
+}
+#undef UBQP_S8
+
 #define UBQP_R8(i) "=r"(r[i]), "=r"(r[i + 1]), "=r"(r[i + 2]), "=r"(r[i + 3]), \
                    "=r"(r[i + 4]), "=r"(r[i + 5]), "=r"(r[i + 6]), "=r"(r[i + 7])
 __device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&r)[32]) {
@@ -177,17 +219,38 @@ __device__ __forceinline__ Unit unit_of(const int4* __restrict__ chunks, int m_t
   const int4 c = chunks[u / m_tiles];
   return Unit{c.x, c.y, c.z, u % m_tiles};
 }
-
-// Eight bits -> eight bf16 values 0.0 / 1.0 (bit i = element i): bit pair
-// (2i, 2i+1) spread to the two 16-bit halves of word i, times 0x3F80 (1.0).
-__device__ __forceinline__ uint4 expand_byte(uint32_t b) {
-  uint32_t v[4];
-#pragma unroll
-  for (int i = 0; i < 4; ++i) {
-    const uint32_t p = (b >> (2 * i)) & 3u;
-    v[i] = ((p & 1u) | ((p & 2u) << 15)) * 0x3F80u;
+// Row `row` of the A tile of unit u: one solution word per K step (zero past
+// the unit's K steps, W, S, or when u is past the last unit).  The A writers
+// load the next unit's words while they write the current unit's, so the
+// load latency is paid once per CTA, not once per unit.
+__device__ __forceinline__ void unit_words(const uint64_t* __restrict__ X, int n, int W, int64_t S,
+                                           const int4* __restrict__ chunks, int m_tiles,
+                                           int n_units, int u, int row, uint64_t (&wa)[KCH]) {
+  const uint64_t* x0p = nullptr;
+  int k0 = 0, nk = 0;
+  if (u < n_units) {
+    const Unit un = unit_of(chunks, m_tiles, u);
+    const int64_t s0 = (int64_t)un.mt * BM + row;
+    if (s0 < S) x0p = X + s0 * W;
+    k0 = un.k0;
+    nk = un.nk;
   }
-  return make_uint4(v[0], v[1], v[2], v[3]);
+#pragma unroll
+  for (int i = 0; i < KCH; ++i) {
+    const int kw = k0 + i;
+    const bool in = i < nk && kw < W;
+    wa[i] = (x0p && in) ? (__ldg(x0p + kw) & valid_mask(n, kw)) : 0ull;
+  }
+}
+
+// Sixteen bits -> sixteen bf16 values 0.0 / 1.0 (bit i = element i), as eight
+// words of two: with m = x | (x << 15), bit 2j of x sits at bit 2j of m and
+// bit 2j+1 at bit 2j+16, so ((m >> 2j) & 0x10001) * 0x3F80 (bf16 1.0) is word j.
+// Three operations per word.
+__device__ __forceinline__ void expand16(uint32_t x16, uint32_t (&v)[8]) {
+  const uint32_t m = x16 | (x16 << 15);
+#pragma unroll
+  for (int j = 0; j < 8; ++j) v[j] = ((m >> (2 * j)) & 0x10001u) * 0x3F80u;
 }
 
 // YMODE = false: f_s += sum_j x_sj D_sj over the lower block triangle (Evaluate).
@@ -333,18 +396,11 @@ eval_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ 
     int stage = 0;
     uint32_t phase = 0;
     bool ok = true;
+    uint64_t wa[KCH], wn[KCH];
+    unit_words(X, n, W, S, chunks, m_tiles, n_units, blockIdx.x, t, wa);
     for (int u = blockIdx.x; u < n_units && ok; u += gridDim.x) {
       const Unit un = unit_of(chunks, m_tiles, u);
-      const int64_t s0 = (int64_t)un.mt * BM + t;
-      const uint64_t* x0p = s0 < S ? X + s0 * W : nullptr;
-      // all of this unit's solution words up front: one memory latency per unit
-      uint64_t wa[KCH];
-#pragma unroll
-      for (int i = 0; i < KCH; ++i) {
-        const int kw = un.k0 + i;
-        const bool in = i < un.nk && kw < W;
-        wa[i] = (x0p && in) ? (__ldg(x0p + kw) & valid_mask(n, kw)) : 0ull;
-      }
+      unit_words(X, n, W, S, chunks, m_tiles, n_units, u + gridDim.x, t, wn);
 #pragma unroll
       for (int ks = 0; ks < KCH; ++ks) {
         if (ks >= un.nk) break;
@@ -355,9 +411,14 @@ eval_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ 
         }
         uint8_t* r0 = smem + stage * STAGE_BYTES + t * 128;
 #pragma unroll
-        for (int c = 0; c < 8; ++c)
-          *reinterpret_cast<uint4*>(r0 + ((c ^ (t & 7)) << 4)) =
-              expand_byte((uint32_t)(w0 >> (8 * c)) & 0xFFu);
+        for (int p = 0; p < 4; ++p) {  // 16-byte chunks 2p, 2p + 1
+          uint32_t v[8];
+          expand16((uint32_t)(w0 >> (16 * p)) & 0xFFFFu, v);
+          *reinterpret_cast<uint4*>(r0 + (((2 * p) ^ (t & 7)) << 4)) =
+              make_uint4(v[0], v[1], v[2], v[3]);
+          *reinterpret_cast<uint4*>(r0 + (((2 * p + 1) ^ (t & 7)) << 4)) =
+              make_uint4(v[4], v[5], v[6], v[7]);
+        }
         // make the generic-proxy writes visible to the tensor cores' reads
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
         mbar_arrive(&full[stage]);
@@ -366,6 +427,8 @@ eval_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ 
           phase ^= 1u;
         }
       }
+#pragma unroll
+      for (int i = 0; i < KCH; ++i) wa[i] = wn[i];
     }
   } else {
     // ---------------- epilogue: warps 2..5 cover TMEM lanes 64-95, 96-127, 0-31, 32-63
@@ -431,14 +494,242 @@ eval_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ 
   }
 }
 
+// Evaluate with the A operand in tensor memory (UBQP_EVAL_TC_TMEM).  Same
+// work units and epilogue as eval_tc_kernel with N-blocks of 192 columns;
+// warp 0 loads only B (Q' rows) by TMA, warps 6-13 expand each start's 64
+// solution bits per K step into 32 columns of bf16 pairs (two warps per lane
+// quarter, 16 columns each) and store them into the stage's tensor-memory
+// columns (tcgen05.st), warp 1 issues the MMAs with A from tensor memory.
+// Shared memory carries 48 KB per K step (B written by TMA and read by the
+// MMA) instead of 96 KB.  Measured slower than the staged kernel at every
+// Table 1 size (n = 7000: 91 vs 60 us per 1000 starts; tensor pipe 31% active)
+// whatever the B-ring depth (4 or 8), the writer count (4 or 8 warps) or the
+// word prefetch; kept as a selectable, bit-exact path.
+__global__ void __launch_bounds__(THREADS_TS, 1)
+eval_ts_kernel(const __grid_constant__ CUtensorMap tmB, const uint64_t* __restrict__ X, int n,
+               int W, int64_t S, int m_tiles, const int4* __restrict__ chunks, int n_chunks,
+               int64_t* __restrict__ f, unsigned* __restrict__ err) {
+  extern __shared__ uint8_t smem_raw[];
+  uint8_t* smem = smem_raw + ((1024 - (su32(smem_raw) & 1023)) & 1023);
+  uint64_t* fullB = reinterpret_cast<uint64_t*>(smem + STAGES_B_TS * B_BYTES_TS);
+  uint64_t* emptyB = fullB + STAGES_B_TS;
+  uint64_t* fullA = emptyB + STAGES_B_TS;
+  uint64_t* emptyA = fullA + STAGES_A_TS;
+  uint64_t* tfull = emptyA + STAGES_A_TS;
+  uint64_t* tempty = tfull + 2;
+  uint64_t* drain = tempty + 2;
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(drain + 1);
+  volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
+
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int n_units = n_chunks * m_tiles;
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < STAGES_B_TS; ++s) {
+      mbar_init(&fullB[s], 1);  // the TMA arrival
+      mbar_init(&emptyB[s], 1);
+    }
+    for (int s = 0; s < STAGES_A_TS; ++s) {
+      mbar_init(&fullA[s], A_WRITERS_TS);
+      mbar_init(&emptyA[s], 1);
+    }
+    for (int a = 0; a < 2; ++a) {
+      mbar_init(&tfull[a], 1);
+      mbar_init(&tempty[a], 128);
+    }
+    mbar_init(drain, 1);
+    *abort_flag = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (warp == 1) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                     su32(tmem_slot)),
+                 "r"(TMEM_COLS)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = *tmem_slot;
+
+  if (warp == 0) {
+    if (lane == 0) {
+      // ---------------- TMA producer: B only
+      asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&tmB)) : "memory");
+      int pending[STAGES_B_TS];
+      for (int s = 0; s < STAGES_B_TS; ++s) pending[s] = -1;
+      int stage = 0;
+      uint32_t phase = 0;
+      bool ok = true;
+      for (int u = blockIdx.x; u < n_units && ok; u += gridDim.x) {
+        const Unit un = unit_of(chunks, m_tiles, u);
+        for (int ks = 0; ks < un.nk; ++ks) {
+          if (!mbar_wait(&emptyB[stage], phase ^ 1u, abort_flag, err)) {
+            ok = false;
+            break;
+          }
+          mbar_expect_tx(&fullB[stage], B_BYTES_TS);
+          tma_load_2d(smem + stage * B_BYTES_TS, &tmB, (un.k0 + ks) * BK, un.nb * BN_TS,
+                      &fullB[stage]);
+          pending[stage] = (int)phase;
+          if (++stage == STAGES_B_TS) {
+            stage = 0;
+            phase ^= 1u;
+          }
+        }
+      }
+      if (!ok) {  // let every issued copy land before the CTA exits
+        for (int s = 0; s < STAGES_B_TS; ++s)
+          if (pending[s] >= 0) mbar_drain(&fullB[s], (uint32_t)pending[s]);
+      }
+    }
+  } else if (warp == 1) {
+    if (lane == 0) {
+      // ---------------- MMA issuer
+      int stage = 0, sa = 0;
+      uint32_t phase = 0, pa = 0;
+      bool ok = true;
+      int t = 0;
+      for (int u = blockIdx.x; u < n_units && ok; u += gridDim.x, ++t) {
+        const Unit un = unit_of(chunks, m_tiles, u);
+        const int a = t & 1;
+        const uint32_t aphase = (uint32_t)((t >> 1) & 1);
+        if (!mbar_wait(&tempty[a], aphase ^ 1u, abort_flag, err)) {
+          ok = false;
+          break;
+        }
+        tc_fence_after();
+        const uint32_t d = tmem + (uint32_t)(a * BN_TS);
+        for (int ks = 0; ks < un.nk; ++ks) {
+          if (!mbar_wait(&fullB[stage], phase, abort_flag, err) ||
+              !mbar_wait(&fullA[sa], pa, abort_flag, err)) {
+            ok = false;
+            break;
+          }
+          tc_fence_after();
+          const uint64_t bdesc = sdesc(su32(smem + stage * B_BYTES_TS));
+          const uint32_t ta = tmem + ACOL_TS + (uint32_t)(sa * (BK / 2));
+#pragma unroll
+          for (int kk = 0; kk < BK / 16; ++kk)
+            mma_bf16_ts(d, ta + (uint32_t)(8 * kk), bdesc + (uint64_t)(2 * kk),
+                        (ks | kk) != 0 ? 1u : 0u);
+          mma_commit(&emptyB[stage]);
+          mma_commit(&emptyA[sa]);
+          if (++stage == STAGES_B_TS) {
+            stage = 0;
+            phase ^= 1u;
+          }
+          if (++sa == STAGES_A_TS) {
+            sa = 0;
+            pa ^= 1u;
+          }
+        }
+        if (ok) mma_commit(&tfull[a]);
+      }
+      if (!ok) {  // wait for the MMAs already issued before TMEM is freed
+        mma_commit(drain);
+        mbar_drain(drain, 0);
+      }
+    }
+  } else if (warp >= THREADS / 32) {
+    // ---------------- A writers (warps 6-13): this warp's quarter of the 128
+    // rows (lanes) and half of the 64 solution bits per K step -> 16 columns
+    // of bf16 pairs
+    const int wq = warp & 3;
+    const int half = (warp - THREADS / 32) >> 2;
+    const int row = wq * 32 + lane;
+    const uint32_t tA = tmem + ((uint32_t)(wq * 32) << 16) + ACOL_TS + (uint32_t)(16 * half);
+    int stage = 0;
+    uint32_t phase = 0;
+    bool ok = true;
+    uint64_t wa[KCH], wn[KCH];
+    unit_words(X, n, W, S, chunks, m_tiles, n_units, blockIdx.x, row, wa);
+    for (int u = blockIdx.x; u < n_units && ok; u += gridDim.x) {
+      const Unit un = unit_of(chunks, m_tiles, u);
+      unit_words(X, n, W, S, chunks, m_tiles, n_units, u + gridDim.x, row, wn);
+#pragma unroll
+      for (int ks = 0; ks < KCH; ++ks) {
+        if (ks >= un.nk) break;
+        // the tcgen05.st below is warp-collective: leave together
+        const bool got = mbar_wait(&emptyA[stage], phase ^ 1u, abort_flag, err);
+        if (!__all_sync(0xffffffffu, got)) {
+          ok = false;
+          break;
+        }
+        tc_fence_after();
+        uint32_t v[16];
+#pragma unroll
+        for (int p = 0; p < 2; ++p) {
+          uint32_t v8[8];
+          expand16((uint32_t)(wa[ks] >> (32 * half + 16 * p)) & 0xFFFFu, v8);
+#pragma unroll
+          for (int j = 0; j < 8; ++j) v[8 * p + j] = v8[j];
+        }
+        tmem_st16(tA + (uint32_t)(stage * (BK / 2)), v);
+        tc_fence_before();
+        mbar_arrive(&fullA[stage]);
+        if (++stage == STAGES_A_TS) {
+          stage = 0;
+          phase ^= 1u;
+        }
+      }
+#pragma unroll
+      for (int i = 0; i < KCH; ++i) wa[i] = wn[i];
+    }
+  } else {
+    // ---------------- epilogue: warps 2..5 cover TMEM lanes 64-95, 96-127, 0-31, 32-63
+    const int q = warp & 3;
+    const int row = q * 32 + lane;
+    int t = 0;
+    for (int u = blockIdx.x; u < n_units; u += gridDim.x, ++t) {
+      const Unit un = unit_of(chunks, m_tiles, u);
+      const int a = t & 1;
+      const uint32_t aphase = (uint32_t)((t >> 1) & 1);
+      const bool got = mbar_wait(&tfull[a], aphase, abort_flag, err);
+      if (!__all_sync(0xffffffffu, got)) break;  // tcgen05.ld is warp-collective
+      tc_fence_after();
+      const int64_t s = (int64_t)un.mt * BM + row;
+      const uint32_t base = tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(a * BN_TS);
+      uint64_t xw[BN_TS / 64];
+#pragma unroll
+      for (int i = 0; i < BN_TS / 64; ++i) {
+        const int w = un.nb * (BN_TS / 64) + i;
+        xw[i] = (s < S && w < W) ? X[s * W + w] : 0ull;
+      }
+      int acc = 0;
+#pragma unroll 1
+      for (int cc = 0; cc < BN_TS / 32; ++cc) {
+        uint32_t r[32];
+        tmem_ld32(base + (uint32_t)(cc * 32), r);
+        const uint32_t bits = (uint32_t)(xw[cc >> 1] >> ((cc & 1) * 32));
+#pragma unroll
+        for (int i = 0; i < 32; ++i)
+          if ((bits >> i) & 1u) acc += __float2int_rn(__uint_as_float(r[i]));
+      }
+      tc_fence_before();
+      mbar_arrive(&tempty[a]);
+      if (s < S && acc != 0)
+        atomicAdd(reinterpret_cast<unsigned long long*>(&f[s]), (unsigned long long)(long long)acc);
+    }
+  }
+  __syncthreads();
+  if (warp == 1) {
+    tc_fence_after();
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem),
+                 "r"(TMEM_COLS)
+                 : "memory");
+  }
+}
+
 // Unpack bit-packed solutions into the bf16 A operand: S_p x n_tc of 0.0 / 1.0.
 // Row t is solution idx[t] (t < *count) when idx is given, else solution t
-// (t < S); other rows and columns >= n are zero.
+// (t < S); other rows and columns >= n are zero.  One thread per 16 columns
+// (two 16-byte stores).
 __global__ void unpack_bits_bf16(const uint64_t* __restrict__ X, int n, int W, int64_t S,
                                  const int32_t* __restrict__ idx,
                                  const int64_t* __restrict__ count, int64_t S_p, int n_tc,
                                  uint4* __restrict__ Xe) {
-  const int64_t per_row = n_tc / 8;
+  const int64_t per_row = n_tc / 16;
   const int64_t total = S_p * per_row;
   int64_t rows = S;
   if (idx) {
@@ -449,21 +740,17 @@ __global__ void unpack_bits_bf16(const uint64_t* __restrict__ X, int n, int W, i
        t += (int64_t)gridDim.x * blockDim.x) {
     const int64_t r = t / per_row;
     const int c = (int)(t - r * per_row);
-    const int w = c >> 3;
-    uint32_t byte = 0;
+    const int w = c >> 2;
+    uint32_t x16 = 0;
     if (r < rows && w < W) {
       const int64_t src = idx ? (int64_t)idx[r] : r;
       if (src >= 0 && src < S)
-        byte = (uint32_t)(((X[src * W + w] & valid_mask(n, w)) >> ((c & 7) * 8)) & 0xFFu);
+        x16 = (uint32_t)(((X[src * W + w] & valid_mask(n, w)) >> ((c & 3) * 16)) & 0xFFFFu);
     }
-    uint32_t v[4];
-#pragma unroll
-    for (int i = 0; i < 4; ++i) {
-      const uint32_t lo = ((byte >> (2 * i)) & 1u) ? 0x3F80u : 0u;
-      const uint32_t hi = ((byte >> (2 * i + 1)) & 1u) ? 0x3F80u : 0u;
-      v[i] = lo | (hi << 16);
-    }
-    Xe[t] = make_uint4(v[0], v[1], v[2], v[3]);
+    uint32_t v[8];
+    expand16(x16, v);
+    Xe[2 * t] = make_uint4(v[0], v[1], v[2], v[3]);
+    Xe[2 * t + 1] = make_uint4(v[4], v[5], v[6], v[7]);
   }
 }
 
@@ -498,6 +785,16 @@ cudaError_t set_smem_attr_once() {
     err = cudaFuncSetAttribute(eval_tc_kernel<YMODE, FUSED>,
                                cudaFuncAttributeMaxDynamicSharedMemorySize,
                                FUSED ? SMEM_BYTES_FUSED : SMEM_BYTES);
+  });
+  return err;
+}
+
+cudaError_t set_smem_attr_ts_once() {
+  static std::once_flag once;
+  static cudaError_t err = cudaSuccess;
+  std::call_once(once, [] {
+    err = cudaFuncSetAttribute(eval_ts_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                               SMEM_BYTES_TS);
   });
   return err;
 }
@@ -558,11 +855,13 @@ size_t eval_tc_workspace(const ubqp_q* h, int64_t S) {
 // Evaluation: for N-block J the K range is [0, 256 (J+1)) (lower block
 // triangle); ascent start-up (y = Q x): the full K range for every J.  Both are
 // split into near-equal chunks of at most KCH steps.
-static std::vector<int4> make_chunks(int NB, bool full) {
+// N-blocks of bn columns over n_tc; the K range of block J is capped at n_tc.
+static std::vector<int4> make_chunks(int n_tc, int bn, bool full) {
   std::vector<int4> ch;
-  const int nk_full = NB * (BN / BK);
+  const int NB = (n_tc + bn - 1) / bn;
+  const int nk_full = n_tc / BK;
   for (int J = 0; J < NB; ++J) {
-    const int nk = full ? nk_full : (J + 1) * (BN / BK);
+    const int nk = full ? nk_full : std::min((J + 1) * (bn / BK), nk_full);
     const int parts = (nk + KCH - 1) / KCH;
     for (int p = 0, k0 = 0; p < parts; ++p) {
       const int len = nk / parts + (p < nk % parts ? 1 : 0);
@@ -575,18 +874,20 @@ static std::vector<int4> make_chunks(int NB, bool full) {
 }
 
 size_t eval_tc_chunk_bytes(int n_tc) {
-  const int NB = n_tc / BN;
-  return sizeof(int4) * (make_chunks(NB, false).size() + make_chunks(NB, true).size());
+  return sizeof(int4) * (make_chunks(n_tc, BN, false).size() + make_chunks(n_tc, BN, true).size() +
+                         make_chunks(n_tc, BN_TS, false).size());
 }
 
 // h->tc_chunks may already point at caller-provided memory of
 // eval_tc_chunk_bytes(n_tc) bytes (then the tables are copied in on `st`).
 cudaError_t eval_tc_prepare(ubqp_q* h, cudaStream_t st) {
-  const int NB = h->n_tc / BN;
-  std::vector<int4> ch = make_chunks(NB, false), full = make_chunks(NB, true);
+  std::vector<int4> ch = make_chunks(h->n_tc, BN, false), full = make_chunks(h->n_tc, BN, true),
+                    ts = make_chunks(h->n_tc, BN_TS, false);
   h->tc_nchunks = (int)ch.size();
   h->tc_nchunks_y = (int)full.size();
+  h->tc_nchunks_ts = (int)ts.size();
   ch.insert(ch.end(), full.begin(), full.end());
+  ch.insert(ch.end(), ts.begin(), ts.end());
   cudaError_t e;
   if (!h->tc_chunks && (e = cudaMalloc(&h->tc_chunks, sizeof(int4) * ch.size()))) return e;
   // pageable source: the copy is staged before the call returns
@@ -595,7 +896,9 @@ cudaError_t eval_tc_prepare(ubqp_q* h, cudaStream_t st) {
   if (e) return e;
   if ((e = cudaStreamSynchronize(st))) return e;
   h->tc_ok = make_map(reinterpret_cast<CUtensorMap*>(h->tc_mapB), h->Qt, h->n_tc, h->n_tc, BN) &&
-             make_map(reinterpret_cast<CUtensorMap*>(h->tc_mapF), h->Qf, h->n_tc, h->n_tc, BN);
+             make_map(reinterpret_cast<CUtensorMap*>(h->tc_mapF), h->Qf, h->n_tc, h->n_tc, BN) &&
+             make_map(reinterpret_cast<CUtensorMap*>(h->tc_mapB_ts), h->Qt, h->n_tc, h->n_tc,
+                      BN_TS);
   return cudaSuccess;
 }
 
@@ -619,7 +922,7 @@ cudaError_t launch_ascent_init_tc(const ubqp_q* h, const uint64_t* X, const int3
   float* Y = reinterpret_cast<float*>(Xe + (size_t)S_p * h->n_tc * 2);
   cudaError_t e;
   {
-    const int64_t total = S_p * (h->n_tc / 8);
+    const int64_t total = S_p * (h->n_tc / 16);
     int64_t blocks = (total + 255) / 256;
     if (blocks > (int64_t)h->sm_count * 8) blocks = (int64_t)h->sm_count * 8;
     unpack_bits_bf16<<<(unsigned)blocks, 256, 0, st>>>(X, h->n, h->W, S, idx, count, S_p,
@@ -643,6 +946,22 @@ cudaError_t launch_ascent_init_tc(const ubqp_q* h, const uint64_t* X, const int3
   return cudaSuccess;
 }
 
+cudaError_t launch_eval_ts(const ubqp_q* h, const uint64_t* X, int64_t S, int64_t* f,
+                           cudaStream_t st) {
+  if (!h->tc_ok) return cudaErrorNotSupported;
+  cudaError_t e;
+  if ((e = cudaMemsetAsync(f, 0, sizeof(int64_t) * S, st))) return e;
+  const int m_tiles = (int)(padded_starts(S) / BM);
+  const int n_units = h->tc_nchunks_ts * m_tiles;
+  const int grid = n_units < h->sm_count ? n_units : h->sm_count;
+  if ((e = set_smem_attr_ts_once())) return e;
+  const int4* ch = reinterpret_cast<const int4*>(h->tc_chunks) + h->tc_nchunks + h->tc_nchunks_y;
+  eval_ts_kernel<<<grid, THREADS_TS, SMEM_BYTES_TS, st>>>(
+      *reinterpret_cast<const CUtensorMap*>(h->tc_mapB_ts), X, h->n, h->W, S, m_tiles, ch,
+      h->tc_nchunks_ts, f, h->err);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_eval_tc(const ubqp_q* h, const uint64_t* X, int64_t S, int64_t* f, void* ws,
                            size_t ws_bytes, cudaStream_t st, const void* mapA_in, bool fused) {
   if (!h->tc_ok) return cudaErrorNotSupported;
@@ -653,7 +972,7 @@ cudaError_t launch_eval_tc(const ubqp_q* h, const uint64_t* X, int64_t S, int64_
     mapA = *reinterpret_cast<const CUtensorMap*>(h->tc_mapB);  // unused by the fused kernel
   } else {
     if (ws_bytes < eval_tc_workspace(h, S)) return cudaErrorInvalidValue;
-    const int64_t total = S_p * (h->n_tc / 8);
+    const int64_t total = S_p * (h->n_tc / 16);
     int64_t blocks = (total + 255) / 256;
     if (blocks > (int64_t)h->sm_count * 8) blocks = (int64_t)h->sm_count * 8;
     unpack_bits_bf16<<<(unsigned)blocks, 256, 0, st>>>(X, h->n, h->W, S, nullptr, nullptr,

@@ -33,13 +33,15 @@ struct ubqp_q {
   int device;
   // tensor-core evaluation: work chunks of the lower block triangle (int4
   // {N-block, first K step, K steps, 0}) and the TMA descriptor of Qt
-  void* tc_chunks;   // evaluation chunks, then the full-square chunks
+  void* tc_chunks;   // evaluation chunks, the full-square chunks, the 192-column chunks
   int tc_nchunks;
   int tc_nchunks_y;
+  int tc_nchunks_ts;  // chunks of the tensor-memory-A evaluation (192-column blocks)
   bool tc_ok;
   bool owns_memory;  // false when the buffers were carved from caller memory
   alignas(64) unsigned char tc_mapB[128];  // TMA descriptor of Qt
   alignas(64) unsigned char tc_mapF[128];  // TMA descriptor of Qf
+  alignas(64) unsigned char tc_mapB_ts[128];  // TMA descriptor of Qt, 192-row boxes
 };
 
 namespace ubqp {
@@ -124,6 +126,9 @@ cudaError_t launch_screen_stats(const int64_t* f, int64_t S, int64_t offset, int
 cudaError_t launch_screen_apply(const int64_t* f, int64_t S, const int64_t* gstats,
                                 int64_t S_total, double lambda, int32_t* idx, int64_t* count,
                                 double* Tm, cudaStream_t st);
+// Evaluation with the A operand in tensor memory (no workspace).
+cudaError_t launch_eval_ts(const ubqp_q* h, const uint64_t* X, int64_t S, int64_t* f,
+                           cudaStream_t st);
 cudaError_t launch_relink(const ubqp_q* h, const uint64_t* X, const int64_t* f, const uint64_t* G,
                           int64_t P, uint64_t* Xb, int64_t* fb, int32_t* dist, uint16_t* trace,
                           int64_t ldt, const float* Y, cudaStream_t st);

@@ -17,7 +17,7 @@ import torch
 from . import build as _build
 
 RANDOM, DIVERSIFY = 0, 1
-EVAL_AUTO, EVAL_TC, EVAL_PLAIN, EVAL_TC_STAGED = 0, 1, 2, 3
+EVAL_AUTO, EVAL_TC, EVAL_PLAIN, EVAL_TC_STAGED, EVAL_TC_TMEM = 0, 1, 2, 3, 4
 
 OK = 0
 STATUS_NAMES = {0: "OK", -1: "ERR_ARG", -2: "ERR_NOT_SYMMETRIC", -3: "ERR_RANGE",

@@ -94,17 +94,22 @@ def test_eval_plain_matches_oracle(n):
     assert np.array_equal(f.cpu().numpy(), orc.eval(Q, X))
 
 
+TC_PATHS = [ubqp.EVAL_TC, ubqp.EVAL_TC_TMEM]
+
+
 @pytest.mark.parametrize("n", NS)
 @pytest.mark.parametrize("S", [1, 37, 129, 300])
-def test_eval_tc_matches_oracle(n, S):
+@pytest.mark.parametrize("path", TC_PATHS)
+def test_eval_tc_matches_oracle(n, S, path):
     Q, inst = instance(n, 0.6, n + 200)
     X = synth.random_solutions(n, S, n + S)
-    f = ubqp.eval(inst, words_dev(X), path=ubqp.EVAL_TC)
+    f = ubqp.eval(inst, words_dev(X), path=path)
     inst.sync()
     assert np.array_equal(f.cpu().numpy(), orc.eval(Q, X))
 
 
-def test_eval_tc_extreme_coefficients_exact():
+@pytest.mark.parametrize("path", TC_PATHS + [ubqp.EVAL_TC_STAGED])
+def test_eval_tc_extreme_coefficients_exact(path):
     # |Q| at the int8 limits and dense 0/1 patterns: every fp32 partial stays an
     # exact integer only if the chunked accumulation is right
     n = 1500
@@ -115,7 +120,7 @@ def test_eval_tc_extreme_coefficients_exact():
     X = np.concatenate([synth.random_solutions(n, 60, 5), synth.random_solutions(n, 60, 6, 0.95),
                         synth.pack_bits(np.ones((4, n), np.uint8)),
                         np.zeros((1, synth.words(n)), np.uint64)])
-    f = ubqp.eval(inst, words_dev(X), path=ubqp.EVAL_TC)
+    f = ubqp.eval(inst, words_dev(X), path=path)
     inst.sync()
     assert np.array_equal(f.cpu().numpy(), orc.eval(Q, X))
 
@@ -126,8 +131,9 @@ def test_eval_tc_equals_plain_at_table1_sizes(n, S):
     X = ubqp.diversify(inst, S, mode=ubqp.RANDOM, seed=n + 1)
     ft = ubqp.eval(inst, X, path=ubqp.EVAL_TC)
     fp = ubqp.eval(inst, X, path=ubqp.EVAL_PLAIN)
+    fm = ubqp.eval(inst, X, path=ubqp.EVAL_TC_TMEM)
     inst.sync()
-    assert torch.equal(ft, fp)
+    assert torch.equal(ft, fp) and torch.equal(fm, fp)
     # sampled starts against the oracle (its inputs regenerated on the CPU)
     Xh = orc.diversify(None, n, orc.RANDOM, n + 1, 0, S)
     pick = np.array([0, 1, S // 2, S - 1])
@@ -146,6 +152,7 @@ def test_eval_tc_workspace_errors():
     assert e.value.status == -4
     assert ubqp.eval_workspace_size(inst, S, ubqp.EVAL_PLAIN) == 0
     assert ubqp.eval_workspace_size(inst, S, ubqp.EVAL_TC) == 0
+    assert ubqp.eval_workspace_size(inst, S, ubqp.EVAL_TC_TMEM) == 0
 
 
 @pytest.mark.parametrize("n", [1, 65, 257, 1000, 2100])
@@ -164,7 +171,7 @@ def test_eval_ignores_pad_bits():
     X = synth.random_solutions(n, 9, 2)
     Xd = X.copy()
     Xd[:, -1] |= np.uint64(0xFFFF) << np.uint64(48)  # set bits >= n
-    for path in (ubqp.EVAL_PLAIN, ubqp.EVAL_TC, ubqp.EVAL_TC_STAGED):
+    for path in (ubqp.EVAL_PLAIN, ubqp.EVAL_TC, ubqp.EVAL_TC_STAGED, ubqp.EVAL_TC_TMEM):
         f = ubqp.eval(inst, words_dev(Xd), path=path)
         assert np.array_equal(f.cpu().numpy(), orc.eval(Q, X))
 
