@@ -397,10 +397,12 @@ __device__ __forceinline__ void ascend_one(const int8_t* __restrict__ Q8, int64_
     for (int c = 0; c < C; ++c) {
       const int wv[4] = {(int)q[c].x, (int)q[c].y, (int)q[c].z, (int)q[c].w};
 #pragma unroll
-      for (int o = 0; o < 16; ++o) {
+      for (int o = 0; o < 16; o += 2) {
         const int e = c * 16 + o;
         y[e] = __dp4a(wv[o >> 2], dsel[o & 3], y[e]);
-        km[o & 3] = max(km[o & 3], Ck[e] + S[e] * y[e]);
+        y[e + 1] = __dp4a(wv[o >> 2], dsel[(o + 1) & 3], y[e + 1]);
+        km[(o >> 1) & 3] = __vimax3_s32(km[(o >> 1) & 3], Ck[e] + S[e] * y[e],
+                                        Ck[e + 1] + S[e + 1] * y[e + 1]);
       }
     }
     kmax = max(max(km[0], km[1]), max(km[2], km[3]));
