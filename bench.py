@@ -480,13 +480,48 @@ def run_configs(a):
               "history": hist}
     inst.sync()
 
+    # path relinking (intensification) between elite solutions: the ascended
+    # passers of one 1000-start batch, each relinked toward the next one
+    relink = {}
+    for n in (2500, 7000):
+        Qh = synth.make_instance(n, 1.0, n)
+        inst = ubqp.Instance(torch.from_numpy(Qh).to(dev))
+        S = 1000
+        X = ubqp.diversify(inst, S, mode=ubqp.RANDOM, seed=77)
+        f = ubqp.eval(inst, X)
+        idx = torch.arange(S, dtype=torch.int32, device=dev)
+        cnt = torch.full((1,), S, dtype=torch.int64, device=dev)
+        ubqp.ascent(inst, X, f, idx, cnt)  # 1000 local optima
+        order = torch.argsort(f, descending=True)[:256]
+        Xe, fe = X[order].contiguous(), f[order].contiguous()
+        Ge = torch.roll(Xe, 1, 0).contiguous()
+        ws = torch.empty(ubqp.relink_workspace_size(inst, 256), dtype=torch.uint8, device=dev)
+        out = {}
+        ms = timed(lambda r: out.update(zip(("x", "f", "d"),
+                                            ubqp.relink(inst, Xe, fe, Ge, ws=ws))), 5)
+        steps = int(out["d"].sum().item())
+        Xh, Gh = Xe[:2].cpu().numpy().view(np.uint64), Ge[:2].cpu().numpy().view(np.uint64)
+        t0 = time.perf_counter()
+        for p in range(2):
+            ex, ef, ed = orc.relink1(Qh, Xh[p], Gh[p])
+            assert ef == int(out["f"][p].item()) and ed == int(out["d"][p].item())
+        dt = time.perf_counter() - t0
+        relink[n] = {"pairs": 256, "ms": ms, "pairs_per_s": 256 / (ms / 1e3),
+                     "moves_per_s": steps / (ms / 1e3), "mean_distance": steps / 256,
+                     "improved_pairs": int((out["f"] > torch.maximum(fe, fe.roll(1, 0)))
+                                           .sum().item()),
+                     "oracle_1core_pairs_per_s": 2 / dt}
+        inst.sync()
+        del inst
+
     line = {"metric": "per-configuration measurements (Table 1 sizes, n=5000 lambda sweep, "
-                      "n=100 latency, search history)",
+                      "n=100 latency, search history, path relinking)",
             "value": table1[7000]["auto"]["evals_per_s"], "unit": "evals/s (eval only, n=7000)",
             "n_gpus": 1, "steps": 10, "warmup": 2, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "int64", "data": "synthetic",
             "config": {"workload": "configs", "l2": "flushed before every timed call"},
-            "table1": table1, "n5000_d0.1_S8192": c3, "n100_solve": c1, "search": search}
+            "table1": table1, "n5000_d0.1_S8192": c3, "n100_solve": c1, "search": search,
+            "relink": relink}
     print(json.dumps(line), flush=True)
 
 

@@ -78,3 +78,28 @@ def test_relink_rejects_small_workspace():
     small = torch.empty(64, dtype=torch.uint8, device="cuda")
     with pytest.raises(ubqp.UbqpError):
         ubqp.relink(inst, X, f, G, ws=small)
+
+
+@pytest.mark.parametrize("n,extreme", [(9000, False), (2000, True)],
+                         ids=["n9000_block512", "n2000_extreme_gains"])
+def test_relink_large_and_extreme(n, extreme):
+    """n = 9000 takes the 512-thread groups; |Q| = 127 dense makes the gains
+    (positive and negative) as wide as the keys allow."""
+    if extreme:
+        rng = np.random.default_rng(3)
+        Q = rng.choice(np.array([-127, 127], np.int8), size=(n, n))
+        Q = np.triu(Q) + np.triu(Q, 1).T
+    else:
+        Q = synth.make_instance(n, 0.3, 90)
+    inst = ubqp.Instance(torch.from_numpy(np.ascontiguousarray(Q)).cuda())
+    P = 6
+    Xh, Gh = pairs_for(n, P, n)
+    X = torch.from_numpy(Xh.view(np.int64)).cuda()
+    G = torch.from_numpy(Gh.view(np.int64)).cuda()
+    f = ubqp.eval(inst, X, path=ubqp.EVAL_PLAIN)
+    Xb, fb, dist = ubqp.relink(inst, X, f, G)
+    inst.sync()
+    for p in (1, 2, 4):
+        ex, ef, ed = orc.relink1(Q, Xh[p], Gh[p])
+        assert (int(fb[p].item()), int(dist[p].item())) == (ef, ed)
+        assert np.array_equal(host_words(Xb)[p], ex)
