@@ -10,47 +10,77 @@
 namespace ubqp {
 namespace {
 
-constexpr int TILE = 32;
-constexpr int ROWS = 8;  // block is TILE x ROWS threads, 4 rows per thread
+constexpr int PT = 64;        // tile edge
+constexpr int PTHREADS = 256;  // 4 threads per tile row, 16 columns each
 
-__global__ void __launch_bounds__(TILE* ROWS)
+// One 64 x 64 tile of the n_tc x n_tc square per block (rows j0.., columns
+// k0..): the tile and its transpose are staged in shared memory with byte
+// loads (the caller's row stride may have any alignment), then each thread
+// takes 16 consecutive columns of one row and writes them as 16-byte vectors:
+// the int8 copy (rows < n), Q' = 2 tril(Q,-1) + diag(Q) and Q in bf16
+// (zero outside n, so the padded squares need no separate clearing), and adds
+// its row's partial sum.  It also flags any asymmetric pair and tracks max|Q|.
+__global__ void __launch_bounds__(PTHREADS)
 prepare_tiles(const int8_t* __restrict__ Q, int n, int64_t ldq_in, int8_t* __restrict__ Q8,
               int64_t ldq, uint16_t* __restrict__ Qt, uint16_t* __restrict__ Qf, int n_tc,
-              int32_t* __restrict__ rowsum,
-              unsigned* __restrict__ flags) {
-  __shared__ int8_t tr[TILE][TILE + 4];
-  const int bj = blockIdx.y * TILE, bk = blockIdx.x * TILE;
-  const int tx = threadIdx.x, ty = threadIdx.y;
-  // transposed tile: rows bk.., cols bj..
-  for (int r = ty; r < TILE; r += ROWS) {
-    int row = bk + r, col = bj + tx;
-    tr[r][tx] = (row < n && col < n) ? Q[(int64_t)row * ldq_in + col] : (int8_t)0;
+              int32_t* __restrict__ rowsum, unsigned* __restrict__ flags) {
+  __shared__ int8_t a[PT][PT + 4];   // a[r][c] = Q[j0 + r][k0 + c]
+  __shared__ int8_t at[PT][PT + 4];  // at[r][c] = Q[k0 + r][j0 + c]
+  const int j0 = blockIdx.y * PT, k0 = blockIdx.x * PT;
+  const int t = threadIdx.x;
+  for (int i = t; i < PT * PT; i += PTHREADS) {
+    const int r = i / PT, c = i % PT;
+    const int j = j0 + r, k = k0 + c;
+    a[r][c] = (j < n && k < n) ? Q[(int64_t)j * ldq_in + k] : (int8_t)0;
+    const int jt = k0 + r, kt = j0 + c;
+    at[r][c] = (jt < n && kt < n) ? Q[(int64_t)jt * ldq_in + kt] : (int8_t)0;
   }
   __syncthreads();
+  const int r = t >> 2, c0 = (t & 3) * 16;
+  const int j = j0 + r;
   unsigned asym = 0;
-  int amax = 0;
-  for (int r = ty; r < TILE; r += ROWS) {
-    const int j = bj + r, k = bk + tx;
-    int v = 0;
-    if (j < n && k < n) {
-      v = Q[(int64_t)j * ldq_in + k];
-      if ((int8_t)v != tr[tx][r]) asym = 1;
-      Q8[(int64_t)j * ldq + k] = (int8_t)v;
-      int w = k < j ? 2 * v : (k == j ? v : 0);
-      Qt[(int64_t)j * n_tc + k] = __bfloat16_as_ushort(__float2bfloat16_rn((float)w));
-      Qf[(int64_t)j * n_tc + k] = __bfloat16_as_ushort(__float2bfloat16_rn((float)v));
-    }
-    amax = max(amax, abs(v));
-    // row partial sum over this tile's 32 columns
-    int s = v;
+  int amax = 0, sum = 0;
+  uint32_t b8[4] = {0, 0, 0, 0};
+  uint32_t ht[8], hf[8];
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-    if (tx == 0 && j < n && s != 0) atomicAdd(&rowsum[j], s);
+  for (int i = 0; i < 16; ++i) {
+    const int k = k0 + c0 + i;
+    const int v = a[r][c0 + i];
+    asym |= (unsigned)(v != at[c0 + i][r]);
+    amax = max(amax, abs(v));
+    sum += v;
+    b8[i >> 2] |= (uint32_t)(uint8_t)v << (8 * (i & 3));
+    const int w = k < j ? 2 * v : (k == j ? v : 0);
+    const uint32_t bt = __bfloat16_as_ushort(__float2bfloat16_rn((float)w));
+    const uint32_t bf = __bfloat16_as_ushort(__float2bfloat16_rn((float)v));
+    if (i & 1) {
+      ht[i >> 1] |= bt << 16;
+      hf[i >> 1] |= bf << 16;
+    } else {
+      ht[i >> 1] = bt;
+      hf[i >> 1] = bf;
+    }
   }
-  unsigned any = __ballot_sync(0xffffffffu, asym);
+  const int k = k0 + c0;
+  if (j < n && k < ldq)
+    *reinterpret_cast<uint4*>(Q8 + (int64_t)j * ldq + k) = make_uint4(b8[0], b8[1], b8[2], b8[3]);
+  if (j < n_tc && k < n_tc) {
+    uint4* dt = reinterpret_cast<uint4*>(Qt + (int64_t)j * n_tc + k);
+    uint4* df = reinterpret_cast<uint4*>(Qf + (int64_t)j * n_tc + k);
+    dt[0] = make_uint4(ht[0], ht[1], ht[2], ht[3]);
+    dt[1] = make_uint4(ht[4], ht[5], ht[6], ht[7]);
+    df[0] = make_uint4(hf[0], hf[1], hf[2], hf[3]);
+    df[1] = make_uint4(hf[4], hf[5], hf[6], hf[7]);
+  }
+  // the row's partial sum over this tile: the 4 threads of row r are lanes
+  // 4m .. 4m+3 of one warp
+  sum += __shfl_xor_sync(0xffffffffu, sum, 1);
+  sum += __shfl_xor_sync(0xffffffffu, sum, 2);
+  if ((t & 3) == 0 && j < n && sum != 0) atomicAdd(&rowsum[j], sum);
+  const unsigned any = __ballot_sync(0xffffffffu, asym);
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) amax = max(amax, __shfl_xor_sync(0xffffffffu, amax, o));
-  if (tx == 0) {
+  if ((t & 31) == 0) {
     if (any) atomicAdd(&flags[0], 1u);
     atomicMax(&flags[1], (unsigned)amax);
   }
@@ -73,15 +103,15 @@ __global__ void first_derivative_bits(const int32_t* __restrict__ rowsum, int n,
 cudaError_t launch_prepare(const int8_t* Q, int n, int64_t ldq_in, ubqp_q* h,
                            cudaStream_t st) {
   cudaError_t e;
-  if ((e = cudaMemsetAsync(h->Q8, 0, (size_t)h->n * h->ldq, st))) return e;
-  if ((e = cudaMemsetAsync(h->Qt, 0, (size_t)h->n_tc * h->n_tc * 2, st))) return e;
-  if ((e = cudaMemsetAsync(h->Qf, 0, (size_t)h->n_tc * h->n_tc * 2, st))) return e;
+  // Q8 columns from n_tc to ldq are outside the tiles: clear the copy first
+  if (h->ldq > h->n_tc && (e = cudaMemsetAsync(h->Q8, 0, (size_t)h->n * h->ldq, st))) return e;
   if ((e = cudaMemsetAsync(h->rowsum, 0, sizeof(int32_t) * n, st))) return e;
   if ((e = cudaMemsetAsync(h->scratch_flags, 0, 2 * sizeof(unsigned), st))) return e;
   if ((e = cudaMemsetAsync(h->err, 0, sizeof(unsigned), st))) return e;
-  dim3 grid((n + TILE - 1) / TILE, (n + TILE - 1) / TILE), block(TILE, ROWS);
-  prepare_tiles<<<grid, block, 0, st>>>(Q, n, ldq_in, h->Q8, h->ldq, h->Qt, h->Qf, h->n_tc,
-                                         h->rowsum, h->scratch_flags);
+  const int tiles = h->n_tc / PT;
+  dim3 grid(tiles, tiles);
+  prepare_tiles<<<grid, PTHREADS, 0, st>>>(Q, n, ldq_in, h->Q8, h->ldq, h->Qt, h->Qf, h->n_tc,
+                                           h->rowsum, h->scratch_flags);
   if ((e = cudaGetLastError())) return e;
   first_derivative_bits<<<(h->W + 127) / 128, 128, 0, st>>>(h->rowsum, n, h->W, h->x0);
   return cudaGetLastError();
