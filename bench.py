@@ -724,12 +724,13 @@ def main():
         out_x = torch.empty(W, dtype=torch.int64).pin_memory()
         out_f = torch.empty(2, dtype=torch.int64).pin_memory()
         Qdev = torch.empty_like(Qd)
+        arena = torch.empty(ubqp.arena_size(n), dtype=torch.uint8, device=dev)
         wsz = None
 
         def e2e_step(k):
             nonlocal wsz
             Qdev.copy_(Qpin, non_blocking=True)
-            i2 = ubqp.Instance(Qdev)
+            i2 = ubqp.Instance(Qdev, arena=arena)
             params.seed = 77 + k
             need = ubqp.solve_workspace_size(i2, params)
             if wsz is None or wsz.numel() < need:
@@ -752,8 +753,9 @@ def main():
         e2e = {"value": world * S * ke / dt, "unit": UNIT,
                "h2d_bytes_per_step": int(Qh.nbytes),
                "d2h_bytes_per_step": int(out_x.numel() * 8 + out_f.numel() * 8),
-               "what": "instance Q from pinned host memory, ubqp_q_prepare, ubqp_solve, "
-                       "best solution and value back to host, per step"}
+               "what": "instance Q from pinned host memory, ubqp_q_prepare_into (an arena "
+                       "allocated once), ubqp_solve, best solution and value back to host, "
+                       "per step"}
 
     served = None
     if rank == 0 and world == 1 and not a.no_serve:

@@ -166,16 +166,29 @@ def words(n: int) -> int:
     return (n + 63) // 64
 
 
+def arena_size(n: int) -> int:
+    """Device bytes ubqp_q_prepare_into needs for an instance of size n."""
+    return int(load().ubqp_q_arena_size(n))
+
+
 class Instance:
     """A prepared UBQP instance (device-resident Q); wraps ``ubqp_q*``."""
 
-    def __init__(self, Q: torch.Tensor, stream=None):
+    def __init__(self, Q: torch.Tensor, stream=None, arena: torch.Tensor | None = None):
+        """Prepare Q (ubqp_q_prepare); with `arena` (a uint8 CUDA tensor of at
+        least arena_size(n) bytes, kept alive by the caller) the prepared copies
+        are carved from it instead of new device allocations
+        (ubqp_q_prepare_into)."""
         if Q.dtype != torch.int8 or Q.dim() != 2 or not Q.is_cuda:
             raise ValueError("Q must be a 2-D int8 CUDA tensor")
         Q = Q.contiguous()
         n, ldq = Q.shape
         h = ctypes.c_void_p()
-        _check(load().ubqp_q_prepare(_ptr(Q), n, ldq, _stream(stream), ctypes.byref(h)))
+        if arena is None:
+            _check(load().ubqp_q_prepare(_ptr(Q), n, ldq, _stream(stream), ctypes.byref(h)))
+        else:
+            _check(load().ubqp_q_prepare_into(_ptr(Q), n, ldq, _ptr(arena), arena.numel(),
+                                              _stream(stream), ctypes.byref(h)))
         self._h = h
         vals = [ctypes.c_int32() for _ in range(4)] + [ctypes.c_int64()]
         _check(load().ubqp_q_info(h, *[ctypes.byref(v) for v in vals]))

@@ -387,3 +387,18 @@ def test_solve_pipeline_steps_match_oracle(lam):
     assert st["passed"] == sc["count"] and st["T"] == sc["T"]
     assert (int(bf[0].item()), int(bf[1].item())) == bw
     assert np.array_equal(words_host(bx), Xw[bw[1]])
+
+
+def test_instance_in_caller_arena_solves_identically():
+    n = 777
+    Q = synth.make_instance(n, 0.4, 31)
+    arena = torch.empty(ubqp.arena_size(n), dtype=torch.uint8, device="cuda")
+    a = ubqp.Instance(dev(Q))
+    b = ubqp.Instance(dev(Q), arena=arena)
+    p = ubqp.make_params(500, 0.5, seed=9)
+    xa, fa, sa = ubqp.solve(a, p)
+    xb, fb, sb = ubqp.solve(b, p)
+    assert torch.equal(xa, xb) and torch.equal(fa, fb) and sa == sb
+    small = torch.empty(ubqp.arena_size(n) - 256, dtype=torch.uint8, device="cuda")
+    with pytest.raises(ubqp.UbqpError):
+        ubqp.Instance(dev(Q), arena=small)
