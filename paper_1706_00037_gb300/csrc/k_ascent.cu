@@ -44,7 +44,7 @@ constexpr int64_t kTimeoutNs = 20ll * 1000 * 1000 * 1000;  // per start
 // two or more cost more in reductions and copies than their hits save.
 constexpr int kSpecRows = 1;
 // shared-memory slots (16 bytes each) of a group of T threads: two buffers of
-// R rows x C chunks per thread
+// R rows x C chunks per thread, laid out thread-minor
 template <int T, int C, int R>
 constexpr int spec_slot_count() {
   return R > 0 ? T * 2 * R * C : 1;
@@ -285,8 +285,10 @@ __device__ __forceinline__ void ascend_one(const int8_t* __restrict__ Q8, int64_
   int cand[RR], prow[RR];
 #pragma unroll
   for (int i = 0; i < RR; ++i) prow[i] = -1;
-  const uint32_t slot0 =
-      (uint32_t)__cvta_generic_to_shared(spec_slots) + (uint32_t)g * (2 * RR * C * 16);
+  // slot (buffer b, row i, chunk c) of thread g at plane ((b RR + i) C + c):
+  // planes of T x 16 bytes, threads side by side, so a warp's copies and
+  // reads cover all banks without conflicts
+  const uint32_t slot0 = (uint32_t)__cvta_generic_to_shared(spec_slots) + (uint32_t)g * 16;
   int buf = 0;
   auto reduce_key = [&](int kt) {
     const int gain = kt >> 6;
@@ -338,12 +340,12 @@ __device__ __forceinline__ void ascend_one(const int8_t* __restrict__ Q8, int64_
         if (prow[i] == k) hi = i;
       if (hi >= 0) {
         asm volatile("cp.async.wait_group 0;" ::: "memory");
-        const uint32_t a = slot0 + (uint32_t)((buf ^ 1) * RR * C + hi * C) * 16;
+        const uint32_t a = slot0 + (uint32_t)(((buf ^ 1) * RR + hi) * C) * (T * 16);
 #pragma unroll
         for (int c = 0; c < C; ++c)
           asm volatile("ld.shared.v4.u32 {%0, %1, %2, %3}, [%4];"
                        : "=r"(q[c].x), "=r"(q[c].y), "=r"(q[c].z), "=r"(q[c].w)
-                       : "r"(a + 16 * c));
+                       : "r"(a + (uint32_t)(c * T * 16)));
         hit = true;
       }
     }
@@ -371,7 +373,7 @@ __device__ __forceinline__ void ascend_one(const int8_t* __restrict__ Q8, int64_
           // S = 0, so whatever the slot holds never changes a key
           if (prow[i] >= 0 && j0 < ldq) {
             const int8_t* src = Q8 + (int64_t)prow[i] * ldq + j0;
-            const uint32_t a = slot0 + (uint32_t)(buf * RR * C + i * C + c) * 16;
+            const uint32_t a = slot0 + (uint32_t)((buf * RR + i) * C + c) * (T * 16);
             asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(a), "l"(src)
                          : "memory");
           }
