@@ -200,10 +200,11 @@ int prepare_impl(const int8_t* Q_dev, int32_t n, int64_t ldq, void* stream, void
   h->scratch_flags = h->err + 1;
   h->device_bytes = (int64_t)L.total;
   cudaError_t e = ubqp::launch_prepare(Q_dev, n, ldq, h, st);
+  if (e == cudaSuccess) e = ubqp::eval_tc_upload_tables(h, st);
   unsigned flags[2] = {0, 0};
   if (e == cudaSuccess)
     e = cudaMemcpyAsync(flags, h->scratch_flags, sizeof(flags), cudaMemcpyDeviceToHost, st);
-  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);  // the one synchronisation
   if (e != cudaSuccess) {
     ubqp_q_destroy(h);
     return cuda_fail(e, "prepare");

@@ -28,6 +28,7 @@
 #include <cuda.h>
 
 #include <algorithm>
+#include <map>
 #include <mutex>
 #include <vector>
 
@@ -878,23 +879,44 @@ size_t eval_tc_chunk_bytes(int n_tc) {
                          make_chunks(n_tc, BN_TS, false).size());
 }
 
-// h->tc_chunks may already point at caller-provided memory of
-// eval_tc_chunk_bytes(n_tc) bytes (then the tables are copied in on `st`).
-cudaError_t eval_tc_prepare(ubqp_q* h, cudaStream_t st) {
-  std::vector<int4> ch = make_chunks(h->n_tc, BN, false), full = make_chunks(h->n_tc, BN, true),
-                    ts = make_chunks(h->n_tc, BN_TS, false);
-  h->tc_nchunks = (int)ch.size();
-  h->tc_nchunks_y = (int)full.size();
-  h->tc_nchunks_ts = (int)ts.size();
-  ch.insert(ch.end(), full.begin(), full.end());
-  ch.insert(ch.end(), ts.begin(), ts.end());
+// The three chunk tables of one padded size, built once per process and size.
+struct ChunkTables {
+  std::vector<int4> all;  // evaluation, full square, 192-column evaluation
+  int n_eval = 0, n_full = 0, n_ts = 0;
+};
+static const ChunkTables& chunk_tables(int n_tc) {
+  static std::mutex mu;
+  static std::map<int, ChunkTables> cache;
+  std::lock_guard<std::mutex> lock(mu);
+  auto it = cache.find(n_tc);
+  if (it != cache.end()) return it->second;
+  ChunkTables t;
+  std::vector<int4> full = make_chunks(n_tc, BN, true), ts = make_chunks(n_tc, BN_TS, false);
+  t.all = make_chunks(n_tc, BN, false);
+  t.n_eval = (int)t.all.size();
+  t.n_full = (int)full.size();
+  t.n_ts = (int)ts.size();
+  t.all.insert(t.all.end(), full.begin(), full.end());
+  t.all.insert(t.all.end(), ts.begin(), ts.end());
+  return cache.emplace(n_tc, std::move(t)).first->second;
+}
+
+// Copy the chunk tables to the device (async on `st`; the host tables live in
+// a process-wide cache).  h->tc_chunks may already point at caller-provided
+// memory of eval_tc_chunk_bytes(n_tc) bytes.
+cudaError_t eval_tc_upload_tables(ubqp_q* h, cudaStream_t st) {
+  const ChunkTables& t = chunk_tables(h->n_tc);
+  h->tc_nchunks = t.n_eval;
+  h->tc_nchunks_y = t.n_full;
+  h->tc_nchunks_ts = t.n_ts;
   cudaError_t e;
-  if (!h->tc_chunks && (e = cudaMalloc(&h->tc_chunks, sizeof(int4) * ch.size()))) return e;
-  // pageable source: the copy is staged before the call returns
-  e = cudaMemcpyAsync(h->tc_chunks, ch.data(), sizeof(int4) * ch.size(), cudaMemcpyHostToDevice,
-                      st);
-  if (e) return e;
-  if ((e = cudaStreamSynchronize(st))) return e;
+  if (!h->tc_chunks && (e = cudaMalloc(&h->tc_chunks, sizeof(int4) * t.all.size()))) return e;
+  return cudaMemcpyAsync(h->tc_chunks, t.all.data(), sizeof(int4) * t.all.size(),
+                         cudaMemcpyHostToDevice, st);
+}
+
+// The TMA descriptors of the prepared operands (host only).
+cudaError_t eval_tc_prepare(ubqp_q* h, cudaStream_t) {
   h->tc_ok = make_map(reinterpret_cast<CUtensorMap*>(h->tc_mapB), h->Qt, h->n_tc, h->n_tc, BN) &&
              make_map(reinterpret_cast<CUtensorMap*>(h->tc_mapF), h->Qf, h->n_tc, h->n_tc, BN) &&
              make_map(reinterpret_cast<CUtensorMap*>(h->tc_mapB_ts), h->Qt, h->n_tc, h->n_tc,

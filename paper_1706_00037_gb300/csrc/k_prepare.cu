@@ -13,27 +13,41 @@ namespace {
 constexpr int PT = 64;        // tile edge
 constexpr int PTHREADS = 256;  // 4 threads per tile row, 16 columns each
 
+// Four bytes of row j from column k (zero at or beyond n): one 32-bit load
+// when the four are inside the row and W4 (4-byte aligned rows), else bytes.
+template <bool W4>
+__device__ __forceinline__ uint32_t row_word(const int8_t* __restrict__ Q, int64_t ldq_in, int n,
+                                             int j, int k) {
+  if (j >= n) return 0;
+  const int8_t* p = Q + (int64_t)j * ldq_in + k;
+  if (W4 && k + 3 < n) return *reinterpret_cast<const uint32_t*>(p);
+  uint32_t w = 0;
+#pragma unroll
+  for (int b = 0; b < 4; ++b)
+    if (k + b < n) w |= (uint32_t)(uint8_t)p[b] << (8 * b);
+  return w;
+}
+
 // One 64 x 64 tile of the n_tc x n_tc square per block (rows j0.., columns
-// k0..): the tile and its transpose are staged in shared memory with byte
-// loads (the caller's row stride may have any alignment), then each thread
+// k0..): the tile and its transpose are staged in shared memory four bytes
+// at a time (32-bit loads when the caller's rows are 4-byte aligned), then each thread
 // takes 16 consecutive columns of one row and writes them as 16-byte vectors:
 // the int8 copy (rows < n), Q' = 2 tril(Q,-1) + diag(Q) and Q in bf16
 // (zero outside n, so the padded squares need no separate clearing), and adds
 // its row's partial sum.  It also flags any asymmetric pair and tracks max|Q|.
+template <bool W4>
 __global__ void __launch_bounds__(PTHREADS)
 prepare_tiles(const int8_t* __restrict__ Q, int n, int64_t ldq_in, int8_t* __restrict__ Q8,
               int64_t ldq, uint16_t* __restrict__ Qt, uint16_t* __restrict__ Qf, int n_tc,
               int32_t* __restrict__ rowsum, unsigned* __restrict__ flags) {
-  __shared__ int8_t a[PT][PT + 4];   // a[r][c] = Q[j0 + r][k0 + c]
-  __shared__ int8_t at[PT][PT + 4];  // at[r][c] = Q[k0 + r][j0 + c]
+  __shared__ __align__(16) int8_t a[PT][PT + 4];   // a[r][c] = Q[j0 + r][k0 + c]
+  __shared__ __align__(16) int8_t at[PT][PT + 4];  // at[r][c] = Q[k0 + r][j0 + c]
   const int j0 = blockIdx.y * PT, k0 = blockIdx.x * PT;
   const int t = threadIdx.x;
-  for (int i = t; i < PT * PT; i += PTHREADS) {
-    const int r = i / PT, c = i % PT;
-    const int j = j0 + r, k = k0 + c;
-    a[r][c] = (j < n && k < n) ? Q[(int64_t)j * ldq_in + k] : (int8_t)0;
-    const int jt = k0 + r, kt = j0 + c;
-    at[r][c] = (jt < n && kt < n) ? Q[(int64_t)jt * ldq_in + kt] : (int8_t)0;
+  for (int i = t; i < PT * PT / 4; i += PTHREADS) {
+    const int r = i / (PT / 4), c = (i % (PT / 4)) * 4;
+    *reinterpret_cast<uint32_t*>(&a[r][c]) = row_word<W4>(Q, ldq_in, n, j0 + r, k0 + c);
+    *reinterpret_cast<uint32_t*>(&at[r][c]) = row_word<W4>(Q, ldq_in, n, k0 + r, j0 + c);
   }
   __syncthreads();
   const int r = t >> 2, c0 = (t & 3) * 16;
@@ -110,8 +124,12 @@ cudaError_t launch_prepare(const int8_t* Q, int n, int64_t ldq_in, ubqp_q* h,
   if ((e = cudaMemsetAsync(h->err, 0, sizeof(unsigned), st))) return e;
   const int tiles = h->n_tc / PT;
   dim3 grid(tiles, tiles);
-  prepare_tiles<<<grid, PTHREADS, 0, st>>>(Q, n, ldq_in, h->Q8, h->ldq, h->Qt, h->Qf, h->n_tc,
-                                           h->rowsum, h->scratch_flags);
+  if (((uintptr_t)Q & 3) == 0 && (ldq_in & 3) == 0)
+    prepare_tiles<true><<<grid, PTHREADS, 0, st>>>(Q, n, ldq_in, h->Q8, h->ldq, h->Qt, h->Qf,
+                                                   h->n_tc, h->rowsum, h->scratch_flags);
+  else
+    prepare_tiles<false><<<grid, PTHREADS, 0, st>>>(Q, n, ldq_in, h->Q8, h->ldq, h->Qt, h->Qf,
+                                                    h->n_tc, h->rowsum, h->scratch_flags);
   if ((e = cudaGetLastError())) return e;
   first_derivative_bits<<<(h->W + 127) / 128, 128, 0, st>>>(h->rowsum, n, h->W, h->x0);
   return cudaGetLastError();

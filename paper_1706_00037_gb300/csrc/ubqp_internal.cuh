@@ -104,6 +104,7 @@ cudaError_t launch_diversify(const uint64_t* x0, int n, int mode, uint64_t seed,
 cudaError_t launch_eval_plain(const ubqp_q* h, const uint64_t* X, int64_t S,
                               int64_t* f, cudaStream_t st);
 size_t eval_tc_workspace(const ubqp_q* h, int64_t S);
+cudaError_t eval_tc_upload_tables(ubqp_q* h, cudaStream_t st);
 cudaError_t eval_tc_prepare(ubqp_q* h, cudaStream_t st);
 size_t eval_tc_chunk_bytes(int n_tc);
 size_t eval_tc_static_capacity();
