@@ -113,6 +113,9 @@ void orc_first_derivative(const int8_t* Q, int32_t n, int64_t ldq, uint64_t* x0)
  * Random words come from orc_rng: RANDOM word w of start s uses stream s;
  * the partner of counter i uses stream 2^63 | i; mask word t of counter i uses
  * stream 2^62 | (8i + t).  Bits >= n are cleared.
+ * DIVERSIFY: parity unpinned against the paper (which prints no rule); the
+ * tests pin this reading's own structure -- hand-worked h-patterns, the
+ * blend's independence from the incumbent and its bit frequency 2^-m.
  */
 void orc_diversify(const uint64_t* x0, int32_t n, int32_t mode, uint64_t seed,
                    uint64_t round, int64_t S, int32_t div_H, uint64_t* X) {

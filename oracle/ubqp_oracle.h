@@ -43,7 +43,9 @@ void orc_eval(const int8_t* Q, int32_t n, int64_t ldq, const uint64_t* X,
 void orc_first_derivative(const int8_t* Q, int32_t n, int64_t ldq, uint64_t* x0);
 
 /* Start generation.  mode 0 = RANDOM (uniform bits), 1 = DIVERSIFY
- * (loop-counter-driven flips and breeding around x0). */
+ * (loop-counter-driven flips and breeding around x0).  DIVERSIFY is a reading
+ * of a rule the paper does not print: parity unpinned against the paper (its
+ * own structure is pinned). */
 void orc_diversify(const uint64_t* x0, int32_t n, int32_t mode, uint64_t seed,
                    uint64_t round, int64_t S, int32_t div_H, uint64_t* X);
 
