@@ -87,6 +87,20 @@ __device__ __forceinline__ void runners_up(int2 r, int first, int* cand) {
   }
 }
 
+// Negate S and toggle the x bit of element ek (relinking: freeze it) with a
+// binary decision on ek: about log2(E) branches instead of E predicated ops.
+template <int LO, int HI, int E, bool RL>
+__device__ __forceinline__ void flip_tree(int (&S)[E], int (&Ck)[E], int ek) {
+  if constexpr (HI - LO == 1) {
+    S[LO] = RL ? 0 : -S[LO];
+    Ck[LO] = RL ? INT_MIN : (Ck[LO] ^ 1);
+  } else {
+    constexpr int MID = (LO + HI) / 2;
+    if (ek < MID) flip_tree<LO, MID, E, RL>(S, Ck, ek);
+    else flip_tree<MID, HI, E, RL>(S, Ck, ek);
+  }
+}
+
 template <int T>
 struct Group;
 
@@ -387,12 +401,7 @@ __device__ __forceinline__ void ascend_one(const int8_t* __restrict__ Q8, int64_
     const int kc = k / CW, kr = k - kc * CW;
     if ((kr >> 4) == g) {
       const int ek = kc * 16 + (kr & 15);
-#pragma unroll
-      for (int e = 0; e < E; ++e)
-        if (e == ek) {
-          S[e] = RL ? 0 : -S[e];
-          Ck[e] = RL ? INT_MIN : (Ck[e] ^ 1);
-        }
+      flip_tree<0, E, E, RL>(S, Ck, ek);
     }
     int km[4] = {INT_MIN, INT_MIN, INT_MIN, INT_MIN};
 #pragma unroll
