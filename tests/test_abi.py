@@ -55,6 +55,20 @@ def test_host_side_argument_errors():
     assert lib.ubqp_eval_workspace_size(None, 10, 0) == 0
     assert lib.ubqp_q_info(None, None, None, None, None, None) == -1
     lib.ubqp_q_destroy(None)  # no-op
+    # relinking, search, batch plans and the server validate on the host too
+    assert lib.ubqp_relink(None, None, None, None, 4, None, None, None, None, 0, None) == -1
+    assert lib.ubqp_relink_workspace_size(None, 4, 1) == 0
+    sp = ubqp.SearchParams(100, 10, 2, 0, 0.5, 1, 64, 0)
+    assert lib.ubqp_search(None, ctypes.byref(sp), None, None, None, None, None, 0, None) == -1
+    b = ctypes.c_void_p()
+    assert lib.ubqp_batch_create(None, 1, ctypes.byref(p), ctypes.byref(b)) == -1
+    assert lib.ubqp_batch_create(None, 1, ctypes.byref(p), None) == -1
+    srv = ctypes.c_void_p()
+    assert lib.ubqp_server_create(None, ctypes.byref(srv)) == -1
+    assert lib.ubqp_server_create(None, None) == -1
+    assert lib.ubqp_server_request_bytes(None, 100) == 0
+    lib.ubqp_server_destroy(None)  # no-op
+    lib.ubqp_batch_destroy(None)  # no-op
 
 
 def test_params_layout_matches_header():
