@@ -442,7 +442,7 @@ def run_configs(a):
         bx = torch.empty(inst.words, dtype=torch.int64, device=dev)
         bf = torch.empty(2, dtype=torch.int64, device=dev)
         ms = timed(lambda r: ubqp.solve(inst, params, ws=ws, best_x=bx, best_f=bf,
-                                        want_stats=False), 5)
+                                        want_stats=False), 10)
         _, bfv, st = ubqp.solve(inst, params, ws=ws)
         c3[str(lam)] = {"solve_ms": ms, "evals_per_s": 8192 / (ms / 1e3),
                         "passed": st["passed"], "flips": st["total_flips"],
@@ -498,7 +498,7 @@ def run_configs(a):
         ws = torch.empty(ubqp.relink_workspace_size(inst, 256), dtype=torch.uint8, device=dev)
         out = {}
         ms = timed(lambda r: out.update(zip(("x", "f", "d"),
-                                            ubqp.relink(inst, Xe, fe, Ge, ws=ws))), 5)
+                                            ubqp.relink(inst, Xe, fe, Ge, ws=ws))), 10)
         steps = int(out["d"].sum().item())
         Xh, Gh = Xe[:2].cpu().numpy().view(np.uint64), Ge[:2].cpu().numpy().view(np.uint64)
         t0 = time.perf_counter()
