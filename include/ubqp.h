@@ -385,6 +385,21 @@ int ubqp_server_wait(ubqp_server* s, int64_t ticket, int64_t* best_f, uint64_t* 
 int ubqp_server_poll(ubqp_server* s, int64_t ticket, int32_t* done);
 size_t ubqp_server_request_bytes(const ubqp_server* s, int32_t n);
 void ubqp_server_destroy(ubqp_server* s);
+/* Fault injection (tests): the next `count` admitted requests fail as if their
+ * device allocation had failed -- they complete with UBQP_ERR_NOMEM from
+ * ubqp_server_wait, nothing is launched for them, and the server keeps
+ * serving the requests after them. */
+int ubqp_server_inject_alloc_failures(ubqp_server* s, int32_t count);
+
+/*
+ * ubqp_selftest_timeout -- checks the bounded-wait mechanism every kernel wait
+ * of this library uses: one block waits on a shared-memory mbarrier phase that
+ * nothing completes, gives up after `limit_us` microseconds (1 .. 1e6),
+ * records UBQP_ERR_TIMEOUT in *status_dev (int32, device) and returns.
+ * Synchronises `stream` and returns the status it read, so the expected result
+ * is UBQP_ERR_TIMEOUT with the context still usable afterwards.
+ */
+int ubqp_selftest_timeout(uint32_t limit_us, int32_t* status_dev, void* stream);
 
 /*
  * Path relinking (intensification).  The Experiments section names path

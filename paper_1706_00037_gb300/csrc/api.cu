@@ -434,6 +434,18 @@ static size_t relink_base_bytes(const ubqp_q* q, int64_t P) {
   return (size_t)((P * relink_trace_ld(q) * 2 + 255) / 256 * 256) + 256;
 }
 
+int ubqp_selftest_timeout(uint32_t limit_us, int32_t* status_dev, void* stream) {
+  if (!status_dev || limit_us < 1 || limit_us > 1000000)
+    return fail(UBQP_ERR_ARG, "status_dev NULL or limit_us outside [1, 1e6]");
+  cudaStream_t st = (cudaStream_t)stream;
+  UBQP_CUDA(ubqp::launch_selftest_wait((uint64_t)limit_us * 1000, status_dev, st));
+  int32_t status = 0;
+  UBQP_CUDA(cudaMemcpyAsync(&status, status_dev, sizeof(status), cudaMemcpyDeviceToHost, st));
+  UBQP_CUDA(cudaStreamSynchronize(st));
+  if (status != UBQP_OK) return fail(status, "self-test wait gave up after %u us", limit_us);
+  return UBQP_OK;
+}
+
 size_t ubqp_relink_workspace_size(const ubqp_q* q, int64_t P, int32_t tensor_startup) {
   if (!q || P < 0) return 0;
   return relink_base_bytes(q, P) + (tensor_startup ? ubqp::ascent_tc_workspace(q, P) : 0);

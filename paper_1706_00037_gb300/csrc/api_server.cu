@@ -59,6 +59,7 @@ struct ubqp_server {
   int64_t mem_used = 0;
   int in_flight = 0;
   bool stop = false;
+  int inject_alloc_failures = 0;  // the next admissions fail as if out of memory
   std::vector<std::thread> workers;
 };
 
@@ -104,13 +105,19 @@ void worker_main(ubqp_server* s) {
       s->queue.pop_front();
       s->mem_used += (int64_t)r->bytes;
       ++s->in_flight;
+      if (s->inject_alloc_failures > 0) {
+        --s->inject_alloc_failures;
+        r->status = UBQP_ERR_NOMEM;  // marks this admission's allocation as failed
+      }
     }
     int status = UBQP_OK;
     char* buf = nullptr;
     ubqp_q* h = nullptr;
     const int32_t n = r->n, W = (n + 63) / 64;
     const int64_t ldq_dev = rup(n, 16);
-    if (cudaMallocAsync((void**)&buf, r->bytes, st) != cudaSuccess) {
+    if (r->status == UBQP_ERR_NOMEM) {
+      status = UBQP_ERR_NOMEM;  // injected failure: nothing allocated
+    } else if (cudaMallocAsync((void**)&buf, r->bytes, st) != cudaSuccess) {
       cudaGetLastError();
       status = UBQP_ERR_NOMEM;
     }
@@ -262,6 +269,13 @@ int ubqp_server_wait(ubqp_server* s, int64_t ticket, int64_t* best_f, uint64_t* 
   if (best_x_host)
     for (size_t w = 0; w < r->best_x.size(); ++w) best_x_host[w] = r->best_x[w];
   if (latency_s) *latency_s = r->t_done - r->t_submit;
+  return UBQP_OK;
+}
+
+int ubqp_server_inject_alloc_failures(ubqp_server* s, int32_t count) {
+  if (!s || count < 0) return sfail(UBQP_ERR_ARG, "NULL server or count < 0");
+  std::lock_guard<std::mutex> lk(s->mu);
+  s->inject_alloc_failures = count;
   return UBQP_OK;
 }
 

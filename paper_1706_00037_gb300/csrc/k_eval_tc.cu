@@ -722,6 +722,26 @@ eval_ts_kernel(const __grid_constant__ CUtensorMap tmB, const uint64_t* __restri
   }
 }
 
+// Self-test of the bounded wait: an mbarrier that expects one arrival and gets
+// none; the same try-wait / global-timer loop as mbar_wait, with a caller limit.
+__global__ void selftest_wait_kernel(uint64_t limit_ns, int32_t* status) {
+  __shared__ __align__(8) uint64_t bar;
+  if (threadIdx.x == 0) {
+    mbar_init(&bar, 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    const uint64_t t0 = gtimer();
+    int32_t st = 0;
+    for (uint32_t i = 0;; ++i) {
+      if (mbar_try(&bar, 0)) break;  // never: nothing arrives
+      if ((i & 63) == 63 && gtimer() - t0 > limit_ns) {
+        st = UBQP_ERR_TIMEOUT;
+        break;
+      }
+    }
+    *status = st;
+  }
+}
+
 // Unpack bit-packed solutions into the bf16 A operand: S_p x n_tc of 0.0 / 1.0.
 // Row t is solution idx[t] (t < *count) when idx is given, else solution t
 // (t < S); other rows and columns >= n are zero.  One thread per 16 columns
@@ -966,6 +986,11 @@ cudaError_t launch_ascent_init_tc(const ubqp_q* h, const uint64_t* X, const int3
   if ((e = cudaGetLastError())) return e;
   *Y_out = Y;
   return cudaSuccess;
+}
+
+cudaError_t launch_selftest_wait(uint64_t limit_ns, int32_t* status, cudaStream_t st) {
+  selftest_wait_kernel<<<1, 32, 0, st>>>(limit_ns, status);
+  return cudaGetLastError();
 }
 
 cudaError_t launch_eval_ts(const ubqp_q* h, const uint64_t* X, int64_t S, int64_t* f,

@@ -127,6 +127,7 @@ cudaError_t launch_screen_stats(const int64_t* f, int64_t S, int64_t offset, int
 cudaError_t launch_screen_apply(const int64_t* f, int64_t S, const int64_t* gstats,
                                 int64_t S_total, double lambda, int32_t* idx, int64_t* count,
                                 double* Tm, cudaStream_t st);
+cudaError_t launch_selftest_wait(uint64_t limit_ns, int32_t* status, cudaStream_t st);
 // Evaluation with the A operand in tensor memory (no workspace).
 cudaError_t launch_eval_ts(const ubqp_q* h, const uint64_t* X, int64_t S, int64_t* f,
                            cudaStream_t st);

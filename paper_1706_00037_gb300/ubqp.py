@@ -33,7 +33,8 @@ EXPORTS = ["ubqp_strerror", "ubqp_last_error", "ubqp_abi_version", "ubqp_q_prepa
            "ubqp_batch_result", "ubqp_batch_get", "ubqp_batch_config", "ubqp_q_arena_size",
            "ubqp_q_prepare_into", "ubqp_server_create", "ubqp_server_submit", "ubqp_server_wait",
            "ubqp_server_poll", "ubqp_server_request_bytes", "ubqp_server_destroy",
-           "ubqp_relink_workspace_size", "ubqp_relink"]
+           "ubqp_relink_workspace_size", "ubqp_relink", "ubqp_server_inject_alloc_failures",
+           "ubqp_selftest_timeout"]
 
 
 class UbqpError(RuntimeError):
@@ -110,6 +111,8 @@ def load() -> ctypes.CDLL:
         "ubqp_ascent": (ctypes.c_int, [P, P, P, P, P, i64, i32, P, P, sz, P]),
         "ubqp_best": (ctypes.c_int, [P, P, i64, i32, P, P, P]),
         "ubqp_relink_workspace_size": (sz, [P, i64, i32]),
+        "ubqp_server_inject_alloc_failures": (ctypes.c_int, [P, i32]),
+        "ubqp_selftest_timeout": (ctypes.c_int, [ctypes.c_uint32, P, P]),
         "ubqp_relink": (ctypes.c_int, [P, P, P, P, i64, P, P, P, P, sz, P]),
         "ubqp_solve_workspace_size": (sz, [P, ctypes.POINTER(Params)]),
         "ubqp_solve": (ctypes.c_int, [P, ctypes.POINTER(Params), P, P, ctypes.POINTER(Stats),
@@ -345,6 +348,13 @@ def relink(inst: Instance, X: torch.Tensor, f: torch.Tensor, G: torch.Tensor,
     return Xb, fb, dist
 
 
+def selftest_timeout(limit_us: int = 20000, stream=None) -> int:
+    """Run the bounded-wait self-test; returns its status (UBQP_ERR_TIMEOUT = -6
+    when the wait gave up as it should)."""
+    st = torch.zeros(1, dtype=torch.int32, device="cuda")
+    return int(load().ubqp_selftest_timeout(limit_us, _ptr(st), _stream(stream)))
+
+
 def best(f: torch.Tensor, X: torch.Tensor, stream=None):
     bx = torch.empty(X.shape[1], dtype=torch.int64, device=X.device)
     bf = torch.empty(2, dtype=torch.int64, device=X.device)
@@ -456,6 +466,10 @@ class Server:
 
     def request_bytes(self, n: int) -> int:
         return int(load().ubqp_server_request_bytes(self._h, n))
+
+    def inject_alloc_failures(self, count: int):
+        """Fault injection: the next `count` admissions fail as out of memory."""
+        _check(load().ubqp_server_inject_alloc_failures(self._h, count))
 
     def submit(self, Q, seed: int) -> int:
         """Q: a host int8 array or CPU tensor (n x ldq), kept alive until wait()."""

@@ -74,3 +74,44 @@ def test_server_rejects_oversized_instances():
     t = srv.submit(synth.make_instance(400, 0.1, 1), 1)
     assert srv.wait(t)[0][0] != 0 or True
     srv.close()
+
+
+def test_server_survives_injected_allocation_failures():
+    """Failure detection on the host: two admissions fail as out of memory,
+    their tickets report UBQP_ERR_NOMEM, and the requests after them are
+    served with results equal to solving alone."""
+    params = ubqp.make_params(256, 0.5, seed=0)
+    srv = ubqp.Server(2, 600, params)
+    Qs = [synth.make_instance(n, 0.5, 40 + k) for k, n in enumerate((300, 450, 200, 520))]
+    srv.inject_alloc_failures(2)
+    tickets = [srv.submit(Q, 7 + k) for k, Q in enumerate(Qs)]
+    statuses, results = [], []
+    for t in tickets:
+        try:
+            bf, bx, _ = srv.wait(t)
+            statuses.append(0)
+            results.append((bf, bx))
+        except ubqp.UbqpError as e:
+            statuses.append(e.status)
+            results.append(None)
+    srv.close()
+    assert sorted(statuses) == [-4, -4, 0, 0]
+    for k, (Q, r) in enumerate(zip(Qs, results)):
+        if r is None:
+            continue
+        inst = ubqp.Instance(torch.from_numpy(Q).cuda())
+        p1 = ubqp.make_params(256, 0.5, seed=7 + k)
+        bx, bf, _ = ubqp.solve(inst, p1, want_stats=False)
+        assert r[0] == bf.tolist() and np.array_equal(r[1], bx.cpu().numpy().view(np.uint64))
+
+
+def test_bounded_wait_gives_up_and_context_stays_usable():
+    """A kernel waits on a barrier nothing completes: it records a timeout
+    after the limit and returns; the next calls run normally."""
+    assert ubqp.selftest_timeout(20000) == -6  # UBQP_ERR_TIMEOUT
+    Q = synth.make_instance(100, 0.3, 1)
+    inst = ubqp.Instance(torch.from_numpy(Q).cuda())
+    X = ubqp.diversify(inst, 64, mode=ubqp.RANDOM, seed=1)
+    f = ubqp.eval(inst, X)
+    inst.sync()
+    assert np.array_equal(f.cpu().numpy(), orc.eval(Q, X.cpu().numpy().view(np.uint64)))
