@@ -457,6 +457,20 @@ size_t ubqp_search_workspace_size(const ubqp_q* q, const ubqp_search_params* p);
 int ubqp_search(const ubqp_q* q, const ubqp_search_params* p, uint64_t* best_x_dev,
                 int64_t* best_f_dev, int64_t* history_dev, int64_t* stats_dev,
                 void* ws, size_t ws_bytes, void* stream);
+/*
+ * ubqp_search_resume -- checkpoint/resume of the search: continues a search
+ * whose state is (best_x_dev, best_f_dev[0], stats_dev[0..2]) as ubqp_search or
+ * an earlier resumption left it, running rounds first_round .. first_round +
+ * p->rounds - 1 (loop counters as ubqp_search's) with the same parameters; the
+ * state is updated in place (stats accumulate; stats_dev[2], the sample sum
+ * behind Mean, is read, not recomputed) and history_dev[i] gets the incumbent
+ * value after round first_round + i.  ubqp_search with R1 + R2 rounds equals
+ * ubqp_search with R1 rounds followed by this call with first_round R1 and
+ * R2 rounds, bit for bit.  Same workspace and errors as ubqp_search.
+ */
+int ubqp_search_resume(const ubqp_q* q, const ubqp_search_params* p, int32_t first_round,
+                       uint64_t* best_x_dev, int64_t* best_f_dev, int64_t* history_dev,
+                       int64_t* stats_dev, void* ws, size_t ws_bytes, void* stream);
 
 #ifdef __cplusplus
 }

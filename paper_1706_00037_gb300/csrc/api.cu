@@ -582,9 +582,21 @@ size_t ubqp_search_workspace_size(const ubqp_q* q, const ubqp_search_params* p) 
   return search_layout(q, p).total;
 }
 
-int ubqp_search(const ubqp_q* q, const ubqp_search_params* p, uint64_t* best_x_dev,
-                int64_t* best_f_dev, int64_t* history_dev, int64_t* stats_dev, void* ws,
-                size_t ws_bytes, void* stream) {
+namespace {
+
+// Validation and workspace carving shared by ubqp_search and its resumption.
+struct SearchBufs {
+  uint64_t *Xs, *X, *inc_x, *cand_x;
+  int64_t *fs, *f, *count, *gstats, *sstats, *cand;
+  int32_t *idx, *flips;
+  double* Tm;
+  void* scratch;
+  size_t scratch_bytes;
+};
+
+int search_check(const ubqp_q* q, const ubqp_search_params* p, uint64_t* best_x_dev,
+                 int64_t* best_f_dev, int64_t* history_dev, int64_t* stats_dev, void* ws,
+                 size_t ws_bytes, SearchBufs* b) {
   if (!q || !p || !best_x_dev || !best_f_dev || !stats_dev || !ws)
     return fail(UBQP_ERR_ARG, "NULL argument");
   if (p->starts_per_round < 1 || p->starts_per_round >= ((int64_t)1 << 31) ||
@@ -596,52 +608,98 @@ int ubqp_search(const ubqp_q* q, const ubqp_search_params* p, uint64_t* best_x_d
   const SearchLayout L = search_layout(q, p);
   if (ws_bytes < L.total) return fail(UBQP_ERR_NOMEM, "workspace %zu < %zu bytes", ws_bytes, L.total);
   char* base = (char*)ws;
-  uint64_t* Xs = (uint64_t*)(base + L.Xs);
-  int64_t* fs = (int64_t*)(base + L.fs);
-  uint64_t* X = (uint64_t*)(base + L.X);
-  int64_t* f = (int64_t*)(base + L.f);
-  int32_t* idx = (int32_t*)(base + L.idx);
-  int32_t* flips = (int32_t*)(base + L.flips);
-  int64_t* count = (int64_t*)(base + L.small);
-  double* Tm = (double*)(base + L.small + 8);
-  int64_t* gstats = (int64_t*)(base + L.small + 24);
-  int64_t* sstats = (int64_t*)(base + L.small + 48);
-  int64_t* cand = (int64_t*)(base + L.small + 72);
-  uint64_t* inc_x = (uint64_t*)(base + L.inc_x);
-  uint64_t* cand_x = (uint64_t*)(base + L.cand_x);
-  void* scratch = base + L.scratch;
-  const size_t scratch_bytes = L.total - L.scratch;
+  b->Xs = (uint64_t*)(base + L.Xs);
+  b->fs = (int64_t*)(base + L.fs);
+  b->X = (uint64_t*)(base + L.X);
+  b->f = (int64_t*)(base + L.f);
+  b->idx = (int32_t*)(base + L.idx);
+  b->flips = (int32_t*)(base + L.flips);
+  b->count = (int64_t*)(base + L.small);
+  b->Tm = (double*)(base + L.small + 8);
+  b->gstats = (int64_t*)(base + L.small + 24);
+  b->sstats = (int64_t*)(base + L.small + 48);
+  b->cand = (int64_t*)(base + L.small + 72);
+  b->inc_x = (uint64_t*)(base + L.inc_x);
+  b->cand_x = (uint64_t*)(base + L.cand_x);
+  b->scratch = base + L.scratch;
+  b->scratch_bytes = L.total - L.scratch;
+  return UBQP_OK;
+}
+
+// Rounds first_round .. first_round + p->rounds - 1 of the loop of Fig. 2 around
+// the incumbent b.inc_x / best_f_dev, with gstats[0] holding the sample sum.
+int search_rounds(const ubqp_q* q, const ubqp_search_params* p, int32_t first_round,
+                  const SearchBufs& b, int64_t* best_f_dev, int64_t* history_dev,
+                  int64_t* stats_dev, void* stream) {
   const int64_t S = p->starts_per_round, NS = p->num_samples;
   cudaStream_t st = (cudaStream_t)stream;
   int r;
-  // EvaluateRandomStarts: the sample's sum gives Mean
-  if ((r = ubqp_diversify(q, nullptr, UBQP_MODE_RANDOM, p->seed, 0, NS, p->div_H, Xs, stream)))
+  for (int32_t i = 0; i < p->rounds; ++i) {
+    const uint64_t rd = (uint64_t)first_round + (uint64_t)i;
+    if ((r = ubqp_diversify(q, b.inc_x, UBQP_MODE_DIVERSIFY, p->seed, rd, S, p->div_H, b.X,
+                            stream)))
+      return r;
+    if ((r = ubqp_eval(q, b.X, S, b.f, p->eval_path, b.scratch, b.scratch_bytes, stream)))
+      return r;
+    UBQP_CUDA(cudaMemcpyAsync(b.gstats + 1, best_f_dev, 8, cudaMemcpyDeviceToDevice, st));
+    if ((r = ubqp_screen_apply(b.f, S, b.gstats, NS, p->lambda, b.idx, b.count, b.Tm, stream)))
+      return r;
+    UBQP_CUDA(cudaMemsetAsync(b.flips, 0, sizeof(int32_t) * S, st));
+    if ((r = ubqp_ascent(q, b.X, b.f, b.idx, b.count, S, p->max_flips, b.flips, b.scratch,
+                         b.scratch_bytes, stream)))
+      return r;
+    if ((r = ubqp_best(b.f, b.X, S, q->W, b.cand_x, b.cand, stream))) return r;
+    UBQP_CUDA(ubqp::launch_search_update(b.cand, b.X, q->W, b.count, b.idx, b.flips, best_f_dev,
+                                         b.inc_x, history_dev + i, stats_dev, st));
+  }
+  return UBQP_OK;
+}
+
+}  // namespace
+
+int ubqp_search(const ubqp_q* q, const ubqp_search_params* p, uint64_t* best_x_dev,
+                int64_t* best_f_dev, int64_t* history_dev, int64_t* stats_dev, void* ws,
+                size_t ws_bytes, void* stream) {
+  SearchBufs b;
+  int r;
+  if ((r = search_check(q, p, best_x_dev, best_f_dev, history_dev, stats_dev, ws, ws_bytes, &b)))
     return r;
-  if ((r = ubqp_eval(q, Xs, NS, fs, p->eval_path, scratch, scratch_bytes, stream))) return r;
-  if ((r = ubqp_screen_stats(fs, NS, 0, sstats, stream))) return r;
-  UBQP_CUDA(cudaMemcpyAsync(gstats, sstats, 8, cudaMemcpyDeviceToDevice, st));
+  const int64_t NS = p->num_samples;
+  cudaStream_t st = (cudaStream_t)stream;
+  // EvaluateRandomStarts: the sample's sum gives Mean
+  if ((r = ubqp_diversify(q, nullptr, UBQP_MODE_RANDOM, p->seed, 0, NS, p->div_H, b.Xs, stream)))
+    return r;
+  if ((r = ubqp_eval(q, b.Xs, NS, b.fs, p->eval_path, b.scratch, b.scratch_bytes, stream)))
+    return r;
+  if ((r = ubqp_screen_stats(b.fs, NS, 0, b.sstats, stream))) return r;
+  UBQP_CUDA(cudaMemcpyAsync(b.gstats, b.sstats, 8, cudaMemcpyDeviceToDevice, st));
   // CalculateFirstDerivativeSolution: the incumbent and the initial Max
-  UBQP_CUDA(cudaMemcpyAsync(inc_x, q->x0, 8 * (size_t)q->W, cudaMemcpyDeviceToDevice, st));
-  if ((r = ubqp_eval(q, inc_x, 1, best_f_dev, p->eval_path, scratch, scratch_bytes, stream)))
+  UBQP_CUDA(cudaMemcpyAsync(b.inc_x, q->x0, 8 * (size_t)q->W, cudaMemcpyDeviceToDevice, st));
+  if ((r = ubqp_eval(q, b.inc_x, 1, best_f_dev, p->eval_path, b.scratch, b.scratch_bytes,
+                     stream)))
     return r;
   UBQP_CUDA(cudaMemsetAsync(stats_dev, 0, 3 * sizeof(int64_t), st));
-  for (int32_t rd = 0; rd < p->rounds; ++rd) {
-    if ((r = ubqp_diversify(q, inc_x, UBQP_MODE_DIVERSIFY, p->seed, (uint64_t)rd, S, p->div_H,
-                            X, stream)))
-      return r;
-    if ((r = ubqp_eval(q, X, S, f, p->eval_path, scratch, scratch_bytes, stream))) return r;
-    UBQP_CUDA(cudaMemcpyAsync(gstats + 1, best_f_dev, 8, cudaMemcpyDeviceToDevice, st));
-    if ((r = ubqp_screen_apply(f, S, gstats, NS, p->lambda, idx, count, Tm, stream))) return r;
-    UBQP_CUDA(cudaMemsetAsync(flips, 0, sizeof(int32_t) * S, st));
-    if ((r = ubqp_ascent(q, X, f, idx, count, S, p->max_flips, flips, scratch, scratch_bytes,
-                         stream)))
-      return r;
-    if ((r = ubqp_best(f, X, S, q->W, cand_x, cand, stream))) return r;
-    UBQP_CUDA(ubqp::launch_search_update(cand, X, q->W, count, idx, flips, best_f_dev, inc_x,
-                                         history_dev + rd, stats_dev, st));
-  }
-  UBQP_CUDA(cudaMemcpyAsync(stats_dev + 2, sstats, 8, cudaMemcpyDeviceToDevice, st));
-  UBQP_CUDA(cudaMemcpyAsync(best_x_dev, inc_x, 8 * (size_t)q->W, cudaMemcpyDeviceToDevice, st));
+  if ((r = search_rounds(q, p, 0, b, best_f_dev, history_dev, stats_dev, stream))) return r;
+  UBQP_CUDA(cudaMemcpyAsync(stats_dev + 2, b.sstats, 8, cudaMemcpyDeviceToDevice, st));
+  UBQP_CUDA(cudaMemcpyAsync(best_x_dev, b.inc_x, 8 * (size_t)q->W, cudaMemcpyDeviceToDevice, st));
+  return UBQP_OK;
+}
+
+int ubqp_search_resume(const ubqp_q* q, const ubqp_search_params* p, int32_t first_round,
+                       uint64_t* best_x_dev, int64_t* best_f_dev, int64_t* history_dev,
+                       int64_t* stats_dev, void* ws, size_t ws_bytes, void* stream) {
+  SearchBufs b;
+  int r;
+  if ((r = search_check(q, p, best_x_dev, best_f_dev, history_dev, stats_dev, ws, ws_bytes, &b)))
+    return r;
+  if (first_round < 0) return fail(UBQP_ERR_ARG, "first_round < 0");
+  cudaStream_t st = (cudaStream_t)stream;
+  // the saved state: incumbent, its value, and the sample sum behind Mean
+  UBQP_CUDA(cudaMemcpyAsync(b.inc_x, best_x_dev, 8 * (size_t)q->W, cudaMemcpyDeviceToDevice, st));
+  UBQP_CUDA(cudaMemcpyAsync(b.gstats, stats_dev + 2, 8, cudaMemcpyDeviceToDevice, st));
+  if ((r = search_rounds(q, p, first_round, b, best_f_dev, history_dev, stats_dev, stream)))
+    return r;
+  UBQP_CUDA(cudaMemcpyAsync(best_x_dev, b.inc_x, 8 * (size_t)q->W, cudaMemcpyDeviceToDevice, st));
   return UBQP_OK;
 }
 

@@ -34,7 +34,7 @@ EXPORTS = ["ubqp_strerror", "ubqp_last_error", "ubqp_abi_version", "ubqp_q_prepa
            "ubqp_q_prepare_into", "ubqp_server_create", "ubqp_server_submit", "ubqp_server_wait",
            "ubqp_server_poll", "ubqp_server_request_bytes", "ubqp_server_destroy",
            "ubqp_relink_workspace_size", "ubqp_relink", "ubqp_server_inject_alloc_failures",
-           "ubqp_selftest_timeout"]
+           "ubqp_selftest_timeout", "ubqp_search_resume"]
 
 
 class UbqpError(RuntimeError):
@@ -119,6 +119,8 @@ def load() -> ctypes.CDLL:
                                       P, sz, P]),
         "ubqp_search_workspace_size": (sz, [P, ctypes.POINTER(SearchParams)]),
         "ubqp_search": (ctypes.c_int, [P, ctypes.POINTER(SearchParams), P, P, P, P, P, sz, P]),
+        "ubqp_search_resume": (ctypes.c_int, [P, ctypes.POINTER(SearchParams), i32, P, P, P, P,
+                                              P, sz, P]),
         "ubqp_batch_create": (ctypes.c_int, [P, i32, ctypes.POINTER(Params), ctypes.POINTER(P)]),
         "ubqp_batch_destroy": (None, [P]),
         "ubqp_batch_run": (ctypes.c_int, [P, u64, P]),
@@ -403,6 +405,25 @@ def search(inst: Instance, num_samples: int, starts_per_round: int, rounds: int,
     st = torch.empty(3, dtype=torch.int64, device=inst.device)
     _check(load().ubqp_search(inst.handle, ctypes.byref(p), _ptr(bx), _ptr(bf), _ptr(hist),
                               _ptr(st), _ptr(ws), ws.numel(), _stream(stream)))
+    return {"best_x": bx, "best_f": bf, "history": hist[:rounds], "stats": st}
+
+
+def search_resume(inst: Instance, state: dict, first_round: int, num_samples: int,
+                  starts_per_round: int, rounds: int, lam: float, max_flips: int = 0,
+                  seed: int = 0, div_H: int = 64, eval_path: int = EVAL_AUTO,
+                  stream=None) -> dict:
+    """Continue a search from `state` (the dict search or search_resume
+    returned) with rounds first_round .. first_round + rounds - 1
+    (ubqp_search_resume); returns the new state."""
+    p = SearchParams(num_samples, starts_per_round, rounds, max_flips, float(lam),
+                     seed % 2**64, div_H, eval_path)
+    need = int(load().ubqp_search_workspace_size(inst.handle, ctypes.byref(p)))
+    ws = torch.empty(max(need, 16), dtype=torch.uint8, device=inst.device)
+    bx, bf, st = state["best_x"].clone(), state["best_f"].clone(), state["stats"].clone()
+    hist = torch.empty(max(rounds, 1), dtype=torch.int64, device=inst.device)
+    _check(load().ubqp_search_resume(inst.handle, ctypes.byref(p), first_round, _ptr(bx),
+                                     _ptr(bf), _ptr(hist), _ptr(st), _ptr(ws), ws.numel(),
+                                     _stream(stream)))
     return {"best_x": bx, "best_f": bf, "history": hist[:rounds], "stats": st}
 
 

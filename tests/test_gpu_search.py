@@ -33,3 +33,22 @@ def test_search_zero_rounds_returns_first_derivative_start():
     x0 = orc.first_derivative(Q)
     assert np.array_equal(got["best_x"].cpu().numpy().view(np.uint64), x0)
     assert int(got["best_f"].item()) == orc.f(Q, x0)
+
+
+@pytest.mark.parametrize("split", [0, 3, 7])
+def test_search_resume_equals_one_search(split):
+    """Checkpoint/resume: rounds 0..R-1 in one call equal rounds 0..split-1
+    followed by a resumption from the saved state for the rest."""
+    n, S, R = 300, 256, 7
+    Q = synth.make_instance(n, 0.5, 12)
+    inst = ubqp.Instance(torch.from_numpy(Q).cuda())
+    kw = dict(num_samples=500, starts_per_round=S, lam=0.4, seed=21)
+    whole = ubqp.search(inst, rounds=R, **kw)
+    first = ubqp.search(inst, rounds=split, **kw)
+    rest = ubqp.search_resume(inst, first, split, rounds=R - split, **kw)
+    inst.sync()
+    assert torch.equal(rest["best_x"], whole["best_x"])
+    assert torch.equal(rest["best_f"], whole["best_f"])
+    assert torch.equal(rest["stats"], whole["stats"])
+    hist = torch.cat([first["history"], rest["history"]])
+    assert torch.equal(hist, whole["history"])
