@@ -225,6 +225,7 @@ int prepare_impl(const int8_t* Q_dev, int32_t n, int64_t ldq, void* stream, void
 }  // namespace
 
 int ubqp_q_prepare(const int8_t* Q_dev, int32_t n, int64_t ldq, void* stream, ubqp_q** out) {
+  UBQP_RANGE("ubqp:q_prepare");
   g_last_error[0] = 0;
   return prepare_impl(Q_dev, n, ldq, stream, nullptr, 0, out);
 }
@@ -236,6 +237,7 @@ size_t ubqp_q_arena_size(int32_t n) {
 
 int ubqp_q_prepare_into(const int8_t* Q_dev, int32_t n, int64_t ldq, void* arena,
                         size_t arena_bytes, void* stream, ubqp_q** out) {
+  UBQP_RANGE("ubqp:q_prepare_into");
   g_last_error[0] = 0;
   if (!arena) return fail(UBQP_ERR_ARG, "arena is NULL");
   return prepare_impl(Q_dev, n, ldq, stream, arena, arena_bytes, out);
@@ -276,6 +278,7 @@ int ubqp_first_derivative(const ubqp_q* q, uint64_t* x0_dev, void* stream) {
 int ubqp_diversify_range(const ubqp_q* q, const uint64_t* x0_dev, int32_t mode, uint64_t seed,
                          uint64_t round, int64_t S_total, int64_t s_begin, int64_t S_local,
                          int32_t div_H, uint64_t* X_dev, void* stream) {
+  UBQP_RANGE("ubqp:diversify");
   if (!q || !X_dev) return fail(UBQP_ERR_ARG, "NULL argument");
   if (S_total < 0 || s_begin < 0 || S_local < 0 || s_begin + S_local > S_total)
     return fail(UBQP_ERR_ARG, "range [%lld, %lld) outside a batch of %lld", (long long)s_begin,
@@ -303,6 +306,7 @@ size_t ubqp_eval_workspace_size(const ubqp_q* q, int64_t S, int32_t path) {
 
 int ubqp_eval(const ubqp_q* q, const uint64_t* X_dev, int64_t S, int64_t* f_dev, int32_t path,
               void* ws, size_t ws_bytes, void* stream) {
+  UBQP_RANGE("ubqp:eval");
   if (!q || !X_dev || !f_dev) return fail(UBQP_ERR_ARG, "NULL argument");
   if (S < 0) return fail(UBQP_ERR_ARG, "S < 0");
   path = resolve_path(q, path);
@@ -340,6 +344,7 @@ int ubqp_eval(const ubqp_q* q, const uint64_t* X_dev, int64_t S, int64_t* f_dev,
 
 int ubqp_eval_noalloc(const ubqp_q* q, const uint64_t* X_dev, int64_t S, int64_t* f_dev,
                       void* stream) {
+  UBQP_RANGE("ubqp:eval_noalloc");
   if (!q || !X_dev || !f_dev) return fail(UBQP_ERR_ARG, "NULL argument");
   if (S < 0) return fail(UBQP_ERR_ARG, "S < 0");
   if (S == 0) return UBQP_OK;
@@ -390,6 +395,7 @@ int ubqp_screen_apply(const int64_t* f_dev, int64_t S, const int64_t* gstats_dev
 
 int ubqp_screen(const int64_t* f_dev, int64_t S, double lambda, int32_t* idx_dev,
                 int64_t* count_dev, double* Tm_dev, int64_t* stats_dev, void* stream) {
+  UBQP_RANGE("ubqp:screen");
   if (!f_dev || !idx_dev || !count_dev || !Tm_dev || !stats_dev)
     return fail(UBQP_ERR_ARG, "NULL argument");
   if (S < 1 || S >= ((int64_t)1 << 31)) return fail(UBQP_ERR_ARG, "S=%lld outside [1, 2^31)", (long long)S);
@@ -408,6 +414,7 @@ size_t ubqp_ascent_workspace_size(const ubqp_q* q, int64_t S) {
 int ubqp_ascent(const ubqp_q* q, uint64_t* X_dev, int64_t* f_dev, const int32_t* idx_dev,
                 const int64_t* count_dev, int64_t S, int32_t max_flips, int32_t* flips_dev,
                 void* ws, size_t ws_bytes, void* stream) {
+  UBQP_RANGE("ubqp:ascent");
   if (!q || !X_dev || !f_dev || !idx_dev || !count_dev) return fail(UBQP_ERR_ARG, "NULL argument");
   if (S < 0 || S >= ((int64_t)1 << 31)) return fail(UBQP_ERR_ARG, "S outside [0, 2^31)");
   if (max_flips < 0) return fail(UBQP_ERR_ARG, "max_flips < 0");
@@ -454,6 +461,7 @@ size_t ubqp_relink_workspace_size(const ubqp_q* q, int64_t P, int32_t tensor_sta
 int ubqp_relink(const ubqp_q* q, const uint64_t* X_dev, const int64_t* f_dev,
                 const uint64_t* G_dev, int64_t P, uint64_t* Xbest_dev, int64_t* fbest_dev,
                 int32_t* dist_dev, void* ws, size_t ws_bytes, void* stream) {
+  UBQP_RANGE("ubqp:relink");
   if (!q || !X_dev || !f_dev || !G_dev || !Xbest_dev || !fbest_dev)
     return fail(UBQP_ERR_ARG, "NULL argument");
   if (P < 0 || P >= ((int64_t)1 << 31)) return fail(UBQP_ERR_ARG, "P outside [0, 2^31)");
@@ -484,6 +492,7 @@ int ubqp_relink(const ubqp_q* q, const uint64_t* X_dev, const int64_t* f_dev,
 
 int ubqp_best(const int64_t* f_dev, const uint64_t* X_dev, int64_t S, int32_t words,
               uint64_t* best_x_dev, int64_t* best_f_dev, void* stream) {
+  UBQP_RANGE("ubqp:best");
   if (!f_dev || !X_dev || !best_x_dev || !best_f_dev) return fail(UBQP_ERR_ARG, "NULL argument");
   if (S < 1 || words < 1) return fail(UBQP_ERR_ARG, "S < 1 or words < 1");
   UBQP_CUDA(ubqp::launch_best(f_dev, X_dev, S, words, best_x_dev, best_f_dev,
@@ -498,6 +507,7 @@ size_t ubqp_solve_workspace_size(const ubqp_q* q, const ubqp_params* p) {
 
 int ubqp_solve(const ubqp_q* q, const ubqp_params* p, uint64_t* best_x_dev, int64_t* best_f_dev,
                ubqp_stats* stats_host, void* ws, size_t ws_bytes, void* stream) {
+  UBQP_RANGE("ubqp:solve");
   if (!q || !p || !best_x_dev || !best_f_dev || !ws) return fail(UBQP_ERR_ARG, "NULL argument");
   if (p->num_starts < 1 || p->num_starts >= ((int64_t)1 << 31))
     return fail(UBQP_ERR_ARG, "num_starts outside [1, 2^31)");
@@ -660,6 +670,7 @@ int search_rounds(const ubqp_q* q, const ubqp_search_params* p, int32_t first_ro
 int ubqp_search(const ubqp_q* q, const ubqp_search_params* p, uint64_t* best_x_dev,
                 int64_t* best_f_dev, int64_t* history_dev, int64_t* stats_dev, void* ws,
                 size_t ws_bytes, void* stream) {
+  UBQP_RANGE("ubqp:search");
   SearchBufs b;
   int r;
   if ((r = search_check(q, p, best_x_dev, best_f_dev, history_dev, stats_dev, ws, ws_bytes, &b)))
@@ -688,6 +699,7 @@ int ubqp_search(const ubqp_q* q, const ubqp_search_params* p, uint64_t* best_x_d
 int ubqp_search_resume(const ubqp_q* q, const ubqp_search_params* p, int32_t first_round,
                        uint64_t* best_x_dev, int64_t* best_f_dev, int64_t* history_dev,
                        int64_t* stats_dev, void* ws, size_t ws_bytes, void* stream) {
+  UBQP_RANGE("ubqp:search_resume");
   SearchBufs b;
   int r;
   if ((r = search_check(q, p, best_x_dev, best_f_dev, history_dev, stats_dev, ws, ws_bytes, &b)))

@@ -44,7 +44,20 @@ struct ubqp_q {
   alignas(64) unsigned char tc_mapB_ts[128];  // TMA descriptor of Qt, 192-row boxes
 };
 
+#include <nvtx3/nvToolsExt.h>
+
 namespace ubqp {
+
+// An NVTX range named after the API call, for timeline tools (a no-op
+// without one attached).
+struct NvtxRange {
+  explicit NvtxRange(const char* name) { nvtxRangePushA(name); }
+  ~NvtxRange() { nvtxRangePop(); }
+  NvtxRange(const NvtxRange&) = delete;
+  NvtxRange& operator=(const NvtxRange&) = delete;
+};
+#define UBQP_RANGE(name) ::ubqp::NvtxRange ubqp_nvtx_range_(name)
+
 
 // One instance of a batch (device-resident descriptor of the batched stages).
 struct BatchDesc {

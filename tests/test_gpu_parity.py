@@ -402,3 +402,21 @@ def test_instance_in_caller_arena_solves_identically():
     small = torch.empty(ubqp.arena_size(n) - 256, dtype=torch.uint8, device="cuda")
     with pytest.raises(ubqp.UbqpError):
         ubqp.Instance(dev(Q), arena=small)
+
+
+@pytest.mark.parametrize("path", [ubqp.EVAL_PLAIN, ubqp.EVAL_TC, ubqp.EVAL_TC_STAGED,
+                                  ubqp.EVAL_TC_TMEM])
+def test_eval_all_solutions_of_a_small_instance(path):
+    """Every one of the 2^14 solutions: the evaluation against a numpy product,
+    its maximum and first maximiser against the oracle's exhaustive search."""
+    n = 14
+    Q = synth.make_instance(n, 0.8, 77)
+    inst = ubqp.Instance(dev(Q))
+    k = np.arange(2 ** n, dtype=np.uint64)
+    X = k.reshape(-1, 1)  # solution number = its bit pattern, one word each
+    f = ubqp.eval(inst, words_dev(X), path=path).cpu().numpy()
+    bits = ((k[:, None] >> np.arange(n, dtype=np.uint64)) & np.uint64(1)).astype(np.int64)
+    Qn = Q[:, :n].astype(np.int64)
+    assert np.array_equal(f, np.einsum("si,ij,sj->s", bits, Qn, bits))
+    gmax, gx = orc.brute_force(Q)
+    assert f.max() == gmax and int(np.argmax(f)) == gx
