@@ -84,8 +84,12 @@ int ubqp_abi_version(void);
 /*
  * ubqp_q_prepare -- copy Q to the device once (the one large host/device
  * transfer of Fig. 2's MoveQtoGPU, Pseudocode section) and prepare it.
- *   Q_dev   n rows of int8 coefficients, row stride ldq >= n bytes, device
- *           memory; bytes beyond column n of a row are ignored.  Not retained.
+ *   Q_dev   n rows of int8 coefficients, row stride ldq >= n bytes, in device
+ *           memory or in page-locked host memory (cudaHostAlloc or
+ *           cudaHostRegister), which the preparing kernel then reads in place
+ *           over the host link instead of a separate copy; pageable host
+ *           memory is rejected (UBQP_ERR_ARG).  Bytes beyond column n of a row
+ *           are ignored.  Not retained.
  *   n       1 <= n <= 16384.
  *   out     receives the handle (NULL on failure).
  * Checks that Q is symmetric (UBQP_ERR_NOT_SYMMETRIC otherwise), records max|Q|,

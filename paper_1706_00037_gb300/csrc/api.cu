@@ -38,13 +38,18 @@ int cuda_fail(cudaError_t e, const char* what) {
 
 int64_t round_up(int64_t v, int64_t a) { return (v + a - 1) / a * a; }
 
-bool is_device_ptr(const void* p) {
+// The address a kernel reads Q through: device or managed memory as given,
+// page-locked host memory through its device mapping; NULL otherwise.
+const int8_t* kernel_readable(const int8_t* p) {
   cudaPointerAttributes a;
   if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
     cudaGetLastError();
-    return false;
+    return nullptr;
   }
-  return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+  if (a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged) return p;
+  if (a.type == cudaMemoryTypeHost && a.devicePointer)
+    return static_cast<const int8_t*>(a.devicePointer);
+  return nullptr;
 }
 
 // AUTO: the fused tensor-core evaluation up to n_pad 4096, the staged one above
@@ -154,7 +159,8 @@ int prepare_impl(const int8_t* Q_dev, int32_t n, int64_t ldq, void* stream, void
   if (!Q_dev) return fail(UBQP_ERR_ARG, "Q_dev is NULL");
   if (n < 1 || n > UBQP_MAX_N) return fail(UBQP_ERR_UNSUPPORTED, "n=%d outside [1, %d]", n, UBQP_MAX_N);
   if (ldq < n) return fail(UBQP_ERR_ARG, "ldq=%lld < n=%d", (long long)ldq, n);
-  if (!is_device_ptr(Q_dev)) return fail(UBQP_ERR_ARG, "Q_dev is not device memory");
+  const int8_t* Q_k = kernel_readable(Q_dev);
+  if (!Q_k) return fail(UBQP_ERR_ARG, "Q_dev is neither device nor page-locked host memory");
   const HandleLayout L = handle_layout(n);
   if (arena) {
     if (((uintptr_t)arena & 255) != 0) return fail(UBQP_ERR_ARG, "arena not 256-byte aligned");
@@ -199,7 +205,7 @@ int prepare_impl(const int8_t* Q_dev, int32_t n, int64_t ldq, void* stream, void
   }
   h->scratch_flags = h->err + 1;
   h->device_bytes = (int64_t)L.total;
-  cudaError_t e = ubqp::launch_prepare(Q_dev, n, ldq, h, st);
+  cudaError_t e = ubqp::launch_prepare(Q_k, n, ldq, h, st);
   if (e == cudaSuccess) e = ubqp::eval_tc_upload_tables(h, st);
   unsigned flags[2] = {0, 0};
   if (e == cudaSuccess)

@@ -157,10 +157,10 @@ def _stream(stream=None):
     return ctypes.c_void_p(s.cuda_stream)
 
 
-def _ptr(t: torch.Tensor | None):
+def _ptr(t: torch.Tensor | None, pinned_ok: bool = False):
     if t is None:
         return None
-    if not t.is_cuda:
+    if not (t.is_cuda or (pinned_ok and t.is_pinned())):
         raise ValueError("expected a CUDA tensor")
     if not t.is_contiguous():
         raise ValueError("expected a contiguous tensor")
@@ -183,23 +183,26 @@ class Instance:
         """Prepare Q (ubqp_q_prepare); with `arena` (a uint8 CUDA tensor of at
         least arena_size(n) bytes, kept alive by the caller) the prepared copies
         are carved from it instead of new device allocations
-        (ubqp_q_prepare_into)."""
-        if Q.dtype != torch.int8 or Q.dim() != 2 or not Q.is_cuda:
-            raise ValueError("Q must be a 2-D int8 CUDA tensor")
+        (ubqp_q_prepare_into).  Q may be a CUDA tensor or a pinned CPU tensor,
+        which the preparing kernel reads in place."""
+        if Q.dtype != torch.int8 or Q.dim() != 2 or not (Q.is_cuda or Q.is_pinned()):
+            raise ValueError("Q must be a 2-D int8 CUDA tensor or pinned CPU tensor")
         Q = Q.contiguous()
         n, ldq = Q.shape
         h = ctypes.c_void_p()
         if arena is None:
-            _check(load().ubqp_q_prepare(_ptr(Q), n, ldq, _stream(stream), ctypes.byref(h)))
+            _check(load().ubqp_q_prepare(_ptr(Q, pinned_ok=True), n, ldq, _stream(stream),
+                                         ctypes.byref(h)))
         else:
-            _check(load().ubqp_q_prepare_into(_ptr(Q), n, ldq, _ptr(arena), arena.numel(),
+            _check(load().ubqp_q_prepare_into(_ptr(Q, pinned_ok=True), n, ldq, _ptr(arena),
+                                              arena.numel(),
                                               _stream(stream), ctypes.byref(h)))
         self._h = h
         vals = [ctypes.c_int32() for _ in range(4)] + [ctypes.c_int64()]
         _check(load().ubqp_q_info(h, *[ctypes.byref(v) for v in vals]))
         self.n, self.words, self.n_pad, self.max_abs = (v.value for v in vals[:4])
         self.device_bytes = vals[4].value
-        self.device = Q.device
+        self.device = Q.device if Q.is_cuda else torch.device("cuda", torch.cuda.current_device())
 
     @property
     def handle(self):

@@ -75,3 +75,13 @@ def test_params_layout_matches_header():
     # ubqp_params: int64, double, int32, int32, uint64, uint64, int32, int32
     assert ctypes.sizeof(ubqp.Params) == 48
     assert ctypes.sizeof(ubqp.Stats) == 64
+
+
+def test_binding_refuses_pageable_host_q():
+    """The binding takes Q on the device or in pinned host memory only."""
+    import torch
+    Q = torch.zeros((8, 8), dtype=torch.int8)
+    with pytest.raises(ValueError):
+        ubqp.Instance(Q)
+    with pytest.raises(ValueError):
+        ubqp.Instance(torch.zeros((8, 8), dtype=torch.int16))

@@ -404,6 +404,36 @@ def test_instance_in_caller_arena_solves_identically():
         ubqp.Instance(dev(Q), arena=small)
 
 
+def test_instance_from_pinned_host_memory_solves_identically():
+    """Q in page-locked host memory is read in place by the preparing kernel:
+    the same instance (max |Q|, first-derivative start, solve) as from a device
+    copy, with and without an arena; asymmetry is still caught; pageable host
+    memory is refused by the library itself."""
+    import ctypes
+    n, ldq = 777, 800
+    Q = synth.make_instance(n, 0.4, 31, ldq=ldq)
+    a = ubqp.Instance(dev(Q))
+    pinned = torch.from_numpy(Q).pin_memory()
+    arena = torch.empty(ubqp.arena_size(n), dtype=torch.uint8, device="cuda")
+    p = ubqp.make_params(500, 0.5, seed=9)
+    xa, fa, sa = ubqp.solve(a, p)
+    for b in (ubqp.Instance(pinned), ubqp.Instance(pinned, arena=arena)):
+        assert b.max_abs == a.max_abs
+        assert torch.equal(ubqp.first_derivative(b), ubqp.first_derivative(a))
+        xb, fb, sb = ubqp.solve(b, p)
+        assert torch.equal(xa, xb) and torch.equal(fa, fb) and sa == sb
+    bad = Q.copy()
+    bad[3, 60] = bad[60, 3] + 1
+    with pytest.raises(ubqp.UbqpError) as e:
+        ubqp.Instance(torch.from_numpy(bad).pin_memory())
+    assert e.value.status == -2
+    pageable = np.ascontiguousarray(Q)
+    h = ctypes.c_void_p()
+    assert ubqp.load().ubqp_q_prepare(pageable.ctypes.data_as(ctypes.c_void_p), n, ldq, None,
+                                      ctypes.byref(h)) == -1
+    assert not h.value
+
+
 @pytest.mark.parametrize("path", [ubqp.EVAL_PLAIN, ubqp.EVAL_TC, ubqp.EVAL_TC_STAGED,
                                   ubqp.EVAL_TC_TMEM])
 def test_eval_all_solutions_of_a_small_instance(path):
