@@ -22,7 +22,9 @@ struct ubqp_q {
   int32_t n_tc;     // n rounded up to UBQP_TC_ALIGN (rows/cols of Qt)
   int32_t max_abs;  // max |Q_ij|
   int8_t* Q8;       // n x ldq int8, zero beyond column n
-  uint16_t* Qt;     // n_tc x n_tc bf16 bits of Q' = 2 tril(Q,-1) + diag(Q)
+  uint16_t* Qt;     // n_tc x n_tc bf16 bits of Q' = 2 tril(Q,-1) + diag(Q); only the
+                    // tiles the evaluation reads (row j: columns below the end of
+                    // its 256- and 192-row blocks) are written
   uint16_t* Qf;     // n_tc x n_tc bf16 bits of Q (full, for y = Q x)
   int32_t* rowsum;  // n
   uint64_t* x0;     // W words: first-derivative start
