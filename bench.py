@@ -170,6 +170,40 @@ def cpu_sample(a, Q, S_cpu, seed):
     return time.perf_counter() - t0, int(flips.sum())
 
 
+_ORACLE_Q = {}
+
+
+def _oracle_worker_init(n, density, seed):
+    from paper_1706_00037_gb300 import synth
+    _ORACLE_Q[n] = synth.make_instance(n, density, seed)
+
+
+def _oracle_eval_chunk(args):
+    """Evaluate a chunk of starts with the oracle in a pool worker; returns
+    (values, seconds)."""
+    import oracle as orc
+    n, Xh = args
+    t0 = time.perf_counter()
+    f = orc.eval(_ORACLE_Q[n], Xh)
+    return f, time.perf_counter() - t0
+
+
+def oracle_eval_all_cores(n, density, seed, Xh):
+    """The oracle's evaluation of the rows of Xh split over every host core
+    (one spawned process per core, each holding its own copy of the seeded
+    instance); returns (values, wall seconds of the evaluation, processes)."""
+    import multiprocessing as mp
+    procs = os.cpu_count() or 1
+    ctx = mp.get_context("spawn")
+    parts = np.array_split(Xh, procs)
+    with ctx.Pool(procs, initializer=_oracle_worker_init, initargs=(n, density, seed)) as pool:
+        pool.map(_oracle_eval_chunk, [(n, p[:1]) for p in parts])  # every worker ready
+        t0 = time.perf_counter()
+        out = pool.map(_oracle_eval_chunk, [(n, p) for p in parts])
+        dt = time.perf_counter() - t0
+    return np.concatenate([o[0] for o in out]), dt, procs
+
+
 def run_reference(a):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
@@ -428,6 +462,12 @@ def run_configs(a):
         dt = time.perf_counter() - t0
         assert np.array_equal(fh, ref[:8].cpu().numpy())
         row["oracle_1core"] = {"evals_per_s": 8 / dt, "sample": "8 starts"}
+        if not a.no_cpu:
+            Xa = X[:256].cpu().numpy().view(np.uint64)
+            fa, dta, procs = oracle_eval_all_cores(n, 1.0, n, Xa)
+            assert np.array_equal(fa, ref[:256].cpu().numpy())
+            row["oracle_all_cores"] = {"evals_per_s": 256 / dta, "processes": procs,
+                                       "sample": "256 starts split over the processes"}
         row["paper_gtx780ti_evals_per_s"] = 1000 / paper_gpu_s[n]
         table1[n] = row
         del inst
