@@ -763,53 +763,72 @@ def main():
         params = ubqp.make_params(S, a.lam, mode=ubqp.RANDOM, seed=5, eval_path=path)
         out_x = torch.empty(W, dtype=torch.int64).pin_memory()
         out_f = torch.empty(2, dtype=torch.int64).pin_memory()
-        Qdev = torch.empty_like(Qd)
-        arena = torch.empty(ubqp.arena_size(n), dtype=torch.uint8, device=dev)
+        Qdev = torch.empty_like(Qd)  # staging buffer of the copied Q
+        arenas = [torch.empty(ubqp.arena_size(n), dtype=torch.uint8, device=dev)
+                  for _ in range(2)]
         wsz = None
-        copy_stream = torch.cuda.Stream()
-        copied = torch.cuda.Event()
+        main = torch.cuda.current_stream()
+        copy_stream, prep_stream = torch.cuda.Stream(), torch.cuda.Stream()
+        ev_copied = torch.cuda.Event()
+        ev_prepared = [torch.cuda.Event(), torch.cuda.Event()]
+        ev_solved = [torch.cuda.Event(), torch.cuda.Event()]
 
-        def upload():
-            # Q of the next step, on a copy stream: the previous prepare has
-            # finished reading Qdev (ubqp_q_prepare_into synchronises)
+        def prepare(k, first):
+            # step k's Q: copied from pinned host memory into the staging
+            # buffer once the previous preparation has read it, then prepared
+            # into arena k % 2 once the solve two steps back is done; both on
+            # side streams, nothing waits on the host
+            b = k & 1
+            if k > first:
+                copy_stream.wait_event(ev_prepared[(k - 1) & 1])
             with torch.cuda.stream(copy_stream):
                 Qdev.copy_(Qpin, non_blocking=True)
-                copied.record(copy_stream)
+            ev_copied.record(copy_stream)
+            prep_stream.wait_event(ev_copied)
+            if k - 2 >= first:
+                prep_stream.wait_event(ev_solved[b])
+            inst = ubqp.Instance(Qdev, stream=prep_stream, arena=arenas[b],
+                                 defer_validation=True)
+            ev_prepared[b].record(prep_stream)
+            return inst
 
-        def e2e_step(k, upload_next):
+        def solve(k, inst):
             nonlocal wsz
-            torch.cuda.current_stream().wait_event(copied)
-            i2 = ubqp.Instance(Qdev, arena=arena)
+            b = k & 1
+            main.wait_event(ev_prepared[b])
             params.seed = 77 + k
-            need = ubqp.solve_workspace_size(i2, params)
+            need = ubqp.solve_workspace_size(inst, params)
             if wsz is None or wsz.numel() < need:
                 wsz = torch.empty(need, dtype=torch.uint8, device=dev)
-            bx2, bf2, _ = ubqp.solve(i2, params, ws=wsz, want_stats=False)
-            if upload_next:
-                upload()  # overlaps this step's solve
+            bx2, bf2, _ = ubqp.solve(inst, params, ws=wsz, want_stats=False)
             out_x.copy_(bx2, non_blocking=True)
             out_f.copy_(bf2, non_blocking=True)
-            torch.cuda.synchronize()
-            i2.close()
+            ev_solved[b].record(main)
 
-        ke = max(2, min(a.steps, 5))
-        upload()
-        for k in range(2):
-            e2e_step(k, k < 1)
+        def run(first, count):
+            inst = prepare(first, first)
+            for k in range(first, first + count):
+                solve(k, inst)
+                nxt = prepare(k + 1, first) if k + 1 < first + count else None
+                inst.sync(main)  # this step's result is back; validation and errors
+                inst.close()
+                inst = nxt
+
+        ke = max(2, min(a.steps, 20))
+        run(0, 2)
         torch.cuda.synchronize()
         t0 = time.perf_counter()
-        upload()  # the first timed step's copy is not overlapped
-        for k in range(ke):
-            e2e_step(100 + k, k < ke - 1)
+        run(100, ke)
         torch.cuda.synchronize()
         dt = time.perf_counter() - t0
         e2e = {"value": world * S * ke / dt, "unit": UNIT,
                "h2d_bytes_per_step": int(Qh.nbytes),
                "d2h_bytes_per_step": int(out_x.numel() * 8 + out_f.numel() * 8),
-               "what": "per step: instance Q copied from pinned host memory (on a copy "
-                       "stream, overlapping the previous step's solve; the first step's "
-                       "copy is not overlapped), ubqp_q_prepare_into (an arena allocated "
-                       "once), ubqp_solve, best solution and value back to host"}
+               "what": "per step: instance Q copied from pinned host memory and "
+                       "prepared into one of two arenas (ubqp_q_prepare_into_async) on "
+                       "side streams, overlapping the previous step's solve (the first "
+                       "step's are not overlapped); ubqp_solve; best solution and value "
+                       "back to host; ubqp_sync reports the step's validation and errors"}
 
     served = None
     if rank == 0 and world == 1 and not a.no_serve:

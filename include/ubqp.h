@@ -46,7 +46,7 @@
 extern "C" {
 #endif
 
-#define UBQP_ABI_VERSION 3
+#define UBQP_ABI_VERSION 4
 
 typedef enum ubqp_status {
   UBQP_OK = 0,
@@ -111,6 +111,19 @@ void ubqp_q_destroy(ubqp_q* q);
 size_t ubqp_q_arena_size(int32_t n);
 int ubqp_q_prepare_into(const int8_t* Q_dev, int32_t n, int64_t ldq, void* arena,
                         size_t arena_bytes, void* stream, ubqp_q** out);
+/* ubqp_q_prepare_into without the synchronisation: the preparation is only
+ * enqueued on `stream` and the handle returned at once, so the host can go on
+ * (e.g. prepare the next instance while the current one is solved).  Argument
+ * errors return synchronously as before; the symmetry check and max|Q| are
+ * read by the first ubqp_sync on the handle: it returns UBQP_ERR_NOT_SYMMETRIC
+ * for an asymmetric Q, and so does every later ubqp_sync (whatever ran on the
+ * handle in between computed on the asymmetric Q and is meaningless).  Until
+ * then ubqp_q_info reports max_abs = -1 and the exactness checks assume the
+ * int8 bound 128.  Work on another stream must be ordered after `stream`, and
+ * the stream given to that first ubqp_sync must be `stream` or one ordered
+ * after it.  Q_dev must not change until the preparation has run. */
+int ubqp_q_prepare_into_async(const int8_t* Q_dev, int32_t n, int64_t ldq, void* arena,
+                              size_t arena_bytes, void* stream, ubqp_q** out);
 /* Size and layout of a prepared instance; any output pointer may be NULL.
  * n_pad is the padded row stride of the device copies. */
 int ubqp_q_info(const ubqp_q* q, int32_t* n, int32_t* words, int32_t* n_pad,

@@ -38,6 +38,10 @@ int cuda_fail(cudaError_t e, const char* what) {
 
 int64_t round_up(int64_t v, int64_t a) { return (v + a - 1) / a * a; }
 
+// max |Q| for the exactness checks: the int8 bound while a deferred
+// validation is unread
+int64_t coeff_bound(const ubqp_q* q) { return q->max_abs >= 0 ? q->max_abs : 128; }
+
 // The address a kernel reads Q through: device or managed memory as given,
 // page-locked host memory through its device mapping; NULL otherwise.
 const int8_t* kernel_readable(const int8_t* p) {
@@ -153,7 +157,7 @@ HandleLayout handle_layout(int32_t n) {
 }
 
 int prepare_impl(const int8_t* Q_dev, int32_t n, int64_t ldq, void* stream, void* arena,
-                 size_t arena_bytes, ubqp_q** out) {
+                 size_t arena_bytes, ubqp_q** out, bool deferred = false) {
   if (!out) return fail(UBQP_ERR_ARG, "out is NULL");
   *out = nullptr;
   if (!Q_dev) return fail(UBQP_ERR_ARG, "Q_dev is NULL");
@@ -207,6 +211,17 @@ int prepare_impl(const int8_t* Q_dev, int32_t n, int64_t ldq, void* stream, void
   h->device_bytes = (int64_t)L.total;
   cudaError_t e = ubqp::launch_prepare(Q_k, n, ldq, h, st);
   if (e == cudaSuccess) e = ubqp::eval_tc_upload_tables(h, st);
+  if (deferred) {  // no synchronisation: ubqp_sync reads the verdict
+    if (e == cudaSuccess) e = ubqp::eval_tc_prepare(h, st);
+    if (e != cudaSuccess) {
+      ubqp_q_destroy(h);
+      return cuda_fail(e, "prepare");
+    }
+    h->max_abs = -1;
+    h->deferred = true;
+    *out = h;
+    return UBQP_OK;
+  }
   unsigned flags[2] = {0, 0};
   if (e == cudaSuccess)
     e = cudaMemcpyAsync(flags, h->scratch_flags, sizeof(flags), cudaMemcpyDeviceToHost, st);
@@ -249,6 +264,14 @@ int ubqp_q_prepare_into(const int8_t* Q_dev, int32_t n, int64_t ldq, void* arena
   return prepare_impl(Q_dev, n, ldq, stream, arena, arena_bytes, out);
 }
 
+int ubqp_q_prepare_into_async(const int8_t* Q_dev, int32_t n, int64_t ldq, void* arena,
+                              size_t arena_bytes, void* stream, ubqp_q** out) {
+  UBQP_RANGE("ubqp:q_prepare_into_async");
+  g_last_error[0] = 0;
+  if (!arena) return fail(UBQP_ERR_ARG, "arena is NULL");
+  return prepare_impl(Q_dev, n, ldq, stream, arena, arena_bytes, out, true);
+}
+
 int ubqp_q_info(const ubqp_q* q, int32_t* n, int32_t* words, int32_t* n_pad, int32_t* max_abs,
                 int64_t* device_bytes) {
   if (!q) return fail(UBQP_ERR_ARG, "q is NULL");
@@ -264,6 +287,14 @@ int ubqp_sync(const ubqp_q* q, void* stream) {
   if (!q) return fail(UBQP_ERR_ARG, "q is NULL");
   cudaStream_t st = (cudaStream_t)stream;
   UBQP_CUDA(cudaStreamSynchronize(st));
+  if (q->deferred) {  // the validation of ubqp_q_prepare_into_async
+    unsigned flags[2] = {0, 0};
+    UBQP_CUDA(cudaMemcpy(flags, q->scratch_flags, sizeof(flags), cudaMemcpyDeviceToHost));
+    q->deferred = false;
+    q->asymmetric = flags[0] != 0;
+    const_cast<ubqp_q*>(q)->max_abs = (int32_t)flags[1];
+  }
+  if (q->asymmetric) return fail(UBQP_ERR_NOT_SYMMETRIC, "Q is not symmetric");
   unsigned e = 0;
   UBQP_CUDA(cudaMemcpy(&e, q->err, sizeof(unsigned), cudaMemcpyDeviceToHost));
   if (e) {
@@ -326,9 +357,9 @@ int ubqp_eval(const ubqp_q* q, const uint64_t* X_dev, int64_t S, int64_t* f_dev,
     return UBQP_OK;
   }
   // bf16 operands: |2 Q_jk| <= 256 is exact; fp32 partial sums stay below 2^24
-  if ((int64_t)2 * q->max_abs * q->n_tc >= (1 << 24))
+  if ((int64_t)2 * coeff_bound(q) * q->n_tc >= (1 << 24))
     return fail(UBQP_ERR_RANGE, "2*max|Q|*n_pad = %lld >= 2^24",
-                (long long)2 * q->max_abs * q->n_tc);
+                (long long)2 * coeff_bound(q) * q->n_tc);
   if (path == UBQP_EVAL_TC_TMEM) {
     cudaError_t e = ubqp::launch_eval_ts(q, X_dev, S, f_dev, st);
     if (e == cudaErrorNotSupported)
@@ -354,9 +385,9 @@ int ubqp_eval_noalloc(const ubqp_q* q, const uint64_t* X_dev, int64_t S, int64_t
   if (!q || !X_dev || !f_dev) return fail(UBQP_ERR_ARG, "NULL argument");
   if (S < 0) return fail(UBQP_ERR_ARG, "S < 0");
   if (S == 0) return UBQP_OK;
-  if ((int64_t)2 * q->max_abs * q->n_tc >= (1 << 24))
+  if ((int64_t)2 * coeff_bound(q) * q->n_tc >= (1 << 24))
     return fail(UBQP_ERR_RANGE, "2*max|Q|*n_pad = %lld >= 2^24",
-                (long long)2 * q->max_abs * q->n_tc);
+                (long long)2 * coeff_bound(q) * q->n_tc);
   const size_t need = ubqp::eval_tc_workspace(q, S);
   if (need > ubqp::eval_tc_static_capacity())
     return fail(UBQP_ERR_UNSUPPORTED,
@@ -429,7 +460,7 @@ int ubqp_ascent(const ubqp_q* q, uint64_t* X_dev, int64_t* f_dev, const int32_t*
   cudaStream_t st = (cudaStream_t)stream;
   float* Y = nullptr;
   if (ws && ws_bytes >= ubqp::ascent_tc_workspace(q, S) &&
-      (int64_t)q->max_abs * q->n_tc < (1 << 24)) {
+      (int64_t)coeff_bound(q) * q->n_tc < (1 << 24)) {
     cudaError_t e = ubqp::launch_ascent_init_tc(q, X_dev, idx_dev, count_dev, S, ws, ws_bytes,
                                                 &Y, st);
     if (e == cudaErrorNotSupported) Y = nullptr;
@@ -483,7 +514,7 @@ int ubqp_relink(const ubqp_q* q, const uint64_t* X_dev, const int64_t* f_dev,
   int64_t* count = reinterpret_cast<int64_t*>(static_cast<char*>(ws) + base - 256);
   float* Y = nullptr;
   if (ws_bytes >= base + ubqp::ascent_tc_workspace(q, P) &&
-      (int64_t)q->max_abs * q->n_tc < (1 << 24)) {
+      (int64_t)coeff_bound(q) * q->n_tc < (1 << 24)) {
     UBQP_CUDA(ubqp::launch_set_u64(reinterpret_cast<uint64_t*>(count), (uint64_t)P, st));
     cudaError_t e = ubqp::launch_ascent_init_tc(q, X_dev, nullptr, count, P,
                                                 static_cast<char*>(ws) + base, ws_bytes - base,

@@ -20,7 +20,7 @@ struct ubqp_q {
   int32_t W;        // words per solution
   int64_t ldq;      // row stride of Q8 (multiple of UBQP_ROW_ALIGN)
   int32_t n_tc;     // n rounded up to UBQP_TC_ALIGN (rows/cols of Qt)
-  int32_t max_abs;  // max |Q_ij|
+  int32_t max_abs;  // max |Q_ij|; -1 while a deferred validation is unread
   int8_t* Q8;       // n x ldq int8, zero beyond column n
   uint16_t* Qt;     // n_tc x n_tc bf16 bits of Q' = 2 tril(Q,-1) + diag(Q); only the
                     // tiles the evaluation reads (row j: columns below the end of
@@ -41,6 +41,10 @@ struct ubqp_q {
   int tc_nchunks_ts;  // chunks of the tensor-memory-A evaluation (192-column blocks)
   bool tc_ok;
   bool owns_memory;  // false when the buffers were carved from caller memory
+  // deferred validation (ubqp_q_prepare_into_async): the symmetry verdict and
+  // max |Q| stay in scratch_flags until the first ubqp_sync reads them
+  mutable bool deferred;
+  mutable bool asymmetric;
   alignas(64) unsigned char tc_mapB[128];  // TMA descriptor of Qt
   alignas(64) unsigned char tc_mapF[128];  // TMA descriptor of Qf
   alignas(64) unsigned char tc_mapB_ts[128];  // TMA descriptor of Qt, 192-row boxes

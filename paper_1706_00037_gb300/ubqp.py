@@ -34,7 +34,7 @@ EXPORTS = ["ubqp_strerror", "ubqp_last_error", "ubqp_abi_version", "ubqp_q_prepa
            "ubqp_q_prepare_into", "ubqp_server_create", "ubqp_server_submit", "ubqp_server_wait",
            "ubqp_server_poll", "ubqp_server_request_bytes", "ubqp_server_destroy",
            "ubqp_relink_workspace_size", "ubqp_relink", "ubqp_server_inject_alloc_failures",
-           "ubqp_selftest_timeout", "ubqp_search_resume"]
+           "ubqp_selftest_timeout", "ubqp_search_resume", "ubqp_q_prepare_into_async"]
 
 
 class UbqpError(RuntimeError):
@@ -131,6 +131,7 @@ def load() -> ctypes.CDLL:
         "ubqp_batch_get": (ctypes.c_int, [P, i32, P, P, P]),
         "ubqp_q_arena_size": (sz, [i32]),
         "ubqp_q_prepare_into": (ctypes.c_int, [P, i32, i64, P, sz, P, ctypes.POINTER(P)]),
+        "ubqp_q_prepare_into_async": (ctypes.c_int, [P, i32, i64, P, sz, P, ctypes.POINTER(P)]),
         "ubqp_server_create": (ctypes.c_int, [ctypes.POINTER(ServerConfig), ctypes.POINTER(P)]),
         "ubqp_server_submit": (ctypes.c_int, [P, P, i32, i64, u64, ctypes.POINTER(i64)]),
         "ubqp_server_wait": (ctypes.c_int, [P, i64, P, P, ctypes.POINTER(f64)]),
@@ -179,12 +180,18 @@ def arena_size(n: int) -> int:
 class Instance:
     """A prepared UBQP instance (device-resident Q); wraps ``ubqp_q*``."""
 
-    def __init__(self, Q: torch.Tensor, stream=None, arena: torch.Tensor | None = None):
+    def __init__(self, Q: torch.Tensor, stream=None, arena: torch.Tensor | None = None,
+                 defer_validation: bool = False):
         """Prepare Q (ubqp_q_prepare); with `arena` (a uint8 CUDA tensor of at
         least arena_size(n) bytes, kept alive by the caller) the prepared copies
         are carved from it instead of new device allocations
         (ubqp_q_prepare_into).  Q may be a CUDA tensor or a pinned CPU tensor,
-        which the preparing kernel reads in place."""
+        which the preparing kernel reads in place.  defer_validation (with an
+        arena): ubqp_q_prepare_into_async -- nothing waits for the preparation;
+        the symmetry check is reported by the first sync() (max_abs is -1
+        until then)."""
+        if defer_validation and arena is None:
+            raise ValueError("defer_validation needs an arena")
         if Q.dtype != torch.int8 or Q.dim() != 2 or not (Q.is_cuda or Q.is_pinned()):
             raise ValueError("Q must be a 2-D int8 CUDA tensor or pinned CPU tensor")
         Q = Q.contiguous()
@@ -194,9 +201,10 @@ class Instance:
             _check(load().ubqp_q_prepare(_ptr(Q, pinned_ok=True), n, ldq, _stream(stream),
                                          ctypes.byref(h)))
         else:
-            _check(load().ubqp_q_prepare_into(_ptr(Q, pinned_ok=True), n, ldq, _ptr(arena),
-                                              arena.numel(),
-                                              _stream(stream), ctypes.byref(h)))
+            fn = load().ubqp_q_prepare_into_async if defer_validation else \
+                load().ubqp_q_prepare_into
+            _check(fn(_ptr(Q, pinned_ok=True), n, ldq, _ptr(arena), arena.numel(),
+                      _stream(stream), ctypes.byref(h)))
         self._h = h
         vals = [ctypes.c_int32() for _ in range(4)] + [ctypes.c_int64()]
         _check(load().ubqp_q_info(h, *[ctypes.byref(v) for v in vals]))
@@ -222,7 +230,13 @@ class Instance:
             pass
 
     def sync(self, stream=None):
+        """ubqp_sync: wait for `stream`, report kernel errors and a deferred
+        validation (then max_abs is known)."""
         _check(load().ubqp_sync(self.handle, _stream(stream)))
+        if self.max_abs < 0:
+            m = ctypes.c_int32()
+            _check(load().ubqp_q_info(self.handle, None, None, None, ctypes.byref(m), None))
+            self.max_abs = m.value
 
 
 def first_derivative(inst: Instance, stream=None) -> torch.Tensor:

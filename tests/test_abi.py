@@ -34,7 +34,7 @@ def test_library_exports_every_declared_symbol():
 
 def test_strerror_and_version():
     lib = ubqp.load()
-    assert lib.ubqp_abi_version() == 3
+    assert lib.ubqp_abi_version() == 4
     for st, name in ubqp.STATUS_NAMES.items():
         assert lib.ubqp_strerror(st)
     assert lib.ubqp_strerror(0) == b"ok"
@@ -49,6 +49,9 @@ def test_host_side_argument_errors():
     assert lib.ubqp_q_prepare(ctypes.c_void_p(16), 10, 5, None, ctypes.byref(h)) == -1
     assert lib.ubqp_q_prepare(ctypes.c_void_p(16), 10, 10, None, None) == -1
     assert b"out" in lib.ubqp_last_error()
+    assert lib.ubqp_q_prepare_into_async(ctypes.c_void_p(16), 10, 10, None, 0, None,
+                                         ctypes.byref(h)) == -1
+    assert b"arena" in lib.ubqp_last_error()
     assert lib.ubqp_screen(None, 10, 0.5, None, None, None, None, None) == -1
     p = ubqp.Params(0, 0.5, 0, 1, 0, 0, 64, 0)
     assert lib.ubqp_solve(None, ctypes.byref(p), None, None, None, None, 0, None) == -1

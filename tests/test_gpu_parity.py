@@ -434,6 +434,37 @@ def test_instance_from_pinned_host_memory_solves_identically():
     assert not h.value
 
 
+def test_deferred_validation_instance():
+    """ubqp_q_prepare_into_async: the same instance without a synchronisation;
+    the first sync reports the symmetry check and max |Q|, and every later sync
+    keeps reporting an asymmetric Q."""
+    n = 777
+    Q = synth.make_instance(n, 0.4, 31)
+    a = ubqp.Instance(dev(Q))
+    arena = torch.empty(ubqp.arena_size(n), dtype=torch.uint8, device="cuda")
+    Qd = dev(Q)  # must live until the preparation has run
+    b = ubqp.Instance(Qd, arena=arena, defer_validation=True)
+    assert b.max_abs == -1
+    p = ubqp.make_params(500, 0.5, seed=9)
+    xa, fa, sa = ubqp.solve(a, p)
+    xb, fb, sb = ubqp.solve(b, p)
+    b.sync()
+    assert b.max_abs == a.max_abs
+    assert torch.equal(xa, xb) and torch.equal(fa, fb) and sa == sb
+    b.close()
+    bad = Q.copy()
+    bad[3, 60] = bad[60, 3] + 1
+    Qbad = dev(bad)
+    c = ubqp.Instance(Qbad, arena=arena, defer_validation=True)
+    for _ in range(2):
+        with pytest.raises(ubqp.UbqpError) as e:
+            c.sync()
+        assert e.value.status == -2
+    c.close()
+    with pytest.raises(ValueError):
+        ubqp.Instance(Qd, defer_validation=True)  # needs an arena
+
+
 @pytest.mark.parametrize("path", [ubqp.EVAL_PLAIN, ubqp.EVAL_TC, ubqp.EVAL_TC_STAGED,
                                   ubqp.EVAL_TC_TMEM])
 def test_eval_all_solutions_of_a_small_instance(path):
