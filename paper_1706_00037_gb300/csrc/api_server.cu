@@ -141,7 +141,7 @@ void worker_main(ubqp_server* s) {
         status = UBQP_ERR_CUDA;
       }
       if (status == UBQP_OK)
-        status = ubqp_q_prepare_into(Qd, n, ldq_dev, arena, arena_bytes, st, &h);
+        status = ubqp_q_prepare_into_async(Qd, n, ldq_dev, arena, arena_bytes, st, &h);
       ubqp_params prm = s->cfg.params;
       prm.seed = r->seed;
       if (status == UBQP_OK) status = ubqp_solve(h, &prm, bx, bf, nullptr, ws, ws_bytes, st);

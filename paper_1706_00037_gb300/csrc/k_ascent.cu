@@ -470,6 +470,7 @@ ascent_block_kernel(const int8_t* __restrict__ Q8, int64_t ldq, int n, int W,
   __shared__ uint64_t xs[UBQP_MAX_N / 64];
   __shared__ uint4 spec_slots[spec_slot_count<T, C, R>()];
   Group<T> grp{rec, 0};
+  if (err[1] != 0) return;  // Q failed its symmetry check: no climb
   const int64_t cnt = *count;
   for (int64_t t = blockIdx.x; t < cnt; t += gridDim.x) {
     const int s = idx[t];
@@ -497,6 +498,7 @@ ascent_batch_kernel(const BatchDesc* __restrict__ d, const int2* __restrict__ it
   for (int64_t t = blockIdx.x; t < cnt; t += gridDim.x) {
     const int2 it = items[t];
     const BatchDesc& b = d[it.x];
+    if (b.err[1] != 0) continue;  // Q failed its symmetry check: no climb
     const int s = b.idx[it.y];
     if (s < 0 || s >= b.S) {
       if (threadIdx.x == 0) atomicOr(b.err, UBQP_DEVERR_BADIDX);
@@ -520,6 +522,7 @@ ascent_warp_kernel(const int8_t* __restrict__ Q8, int64_t ldq, int n, int W,
   __shared__ uint4 spec_slots[4 * spec_slot_count<32, C, R>()];
   Group<32> grp;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  if (err[1] != 0) return;  // Q failed its symmetry check: no climb
   const int64_t cnt = *count;
   for (int64_t t = (int64_t)blockIdx.x * 4 + warp; t < cnt; t += (int64_t)gridDim.x * 4) {
     const int s = idx[t];
@@ -550,6 +553,7 @@ relink_block_kernel(const int8_t* __restrict__ Q8, int64_t ldq, int n, int W,
   __shared__ uint64_t xs[UBQP_MAX_N / 64];
   __shared__ uint4 spec_slots[spec_slot_count<T, C, R>()];
   Group<T> grp{rec, 0};
+  if (err[1] != 0) return;  // Q failed its symmetry check: no walk
   for (int64_t p = blockIdx.x; p < P; p += gridDim.x) {
     const RelinkArgs a{G + p * W, Xb + p * W, fb + p, dist ? dist + p : nullptr,
                        trace + p * ldt};
@@ -571,6 +575,7 @@ relink_warp_kernel(const int8_t* __restrict__ Q8, int64_t ldq, int n, int W,
   __shared__ uint4 spec_slots[4 * spec_slot_count<32, C, R>()];
   Group<32> grp;
   const int warp = threadIdx.x >> 5;
+  if (err[1] != 0) return;  // Q failed its symmetry check: no walk
   for (int64_t p = (int64_t)blockIdx.x * 4 + warp; p < P; p += (int64_t)gridDim.x * 4) {
     const RelinkArgs a{G + p * W, Xb + p * W, fb + p, dist ? dist + p : nullptr,
                        trace + p * ldt};

@@ -105,6 +105,33 @@ def test_server_survives_injected_allocation_failures():
         assert r[0] == bf.tolist() and np.array_equal(r[1], bx.cpu().numpy().view(np.uint64))
 
 
+def test_server_reports_an_asymmetric_instance_promptly():
+    """The server prepares without synchronising: an asymmetric request's
+    ticket reports UBQP_ERR_NOT_SYMMETRIC at its one synchronisation, its
+    climb is skipped (no run to the watchdog), and the requests around it are
+    served with results equal to solving alone."""
+    import time
+    params = ubqp.make_params(256, 0.5, seed=0)
+    srv = ubqp.Server(2, 2000, params)
+    good = [synth.make_instance(n, 0.5, 60 + k) for k, n in enumerate((300, 1500))]
+    bad = synth.make_instance(1500, 1.0, 62)
+    bad[5, 700] = bad[700, 5] + 1
+    t0 = time.perf_counter()
+    tickets = [srv.submit(good[0], 3), srv.submit(bad, 4), srv.submit(good[1], 5)]
+    res = []
+    for t in tickets:
+        try:
+            res.append(srv.wait(t))
+        except ubqp.UbqpError as e:
+            res.append(e.status)
+    assert time.perf_counter() - t0 < 10.0
+    srv.close()
+    assert res[1] == -2
+    for Q, seed, r in ((good[0], 3, res[0]), (good[1], 5, res[2])):
+        wf, wx = alone(Q, params, seed)
+        assert r[0] == wf and np.array_equal(r[1], wx)
+
+
 def test_bounded_wait_gives_up_and_context_stays_usable():
     """A kernel waits on a barrier nothing completes: it records a timeout
     after the limit and returns; the next calls run normally."""
