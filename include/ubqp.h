@@ -271,8 +271,11 @@ int ubqp_screen_apply(const int64_t* f_dev, int64_t S, const int64_t* gstats_dev
  *   ws / ws_bytes: device scratch (16-byte aligned) of at least
  *   ubqp_ascent_workspace_size(q, S) bytes lets the start-up y = Q x of all
  *   listed starts run as one tensor-core product (bf16 Q, fp32 accumulation,
- *   exact); with ws NULL or smaller the start-up sums the rows of Q on the
- *   CUDA cores instead.  Results are identical either way.
+ *   exact), and the groups take the listed starts one at a time from a
+ *   counter there as they finish (so long and short climbs even out over the
+ *   SMs); with ws NULL or smaller the start-up sums the rows of Q on the CUDA
+ *   cores and the starts are dealt round robin.  Results are identical either
+ *   way.
  */
 size_t ubqp_ascent_workspace_size(const ubqp_q* q, int64_t S);
 int ubqp_ascent(const ubqp_q* q, uint64_t* X_dev, int64_t* f_dev,

@@ -466,8 +466,14 @@ int ubqp_ascent(const ubqp_q* q, uint64_t* X_dev, int64_t* f_dev, const int32_t*
     if (e == cudaErrorNotSupported) Y = nullptr;
     else if (e != cudaSuccess) return cuda_fail(e, "ascent start-up (tensor cores)");
   }
+  // the start counter in the workspace's last 256 bytes (round robin without)
+  const size_t as = ubqp::ascent_tc_workspace(q, S);
+  unsigned long long* next =
+      ws && ws_bytes >= as
+          ? reinterpret_cast<unsigned long long*>(static_cast<char*>(ws) + as - 256)
+          : nullptr;
   UBQP_CUDA(ubqp::launch_ascent(q, X_dev, f_dev, idx_dev, count_dev, S, max_flips, flips_dev, Y,
-                                st));
+                                next, st));
   return UBQP_OK;
 }
 

@@ -74,7 +74,7 @@ size_t request_bytes(const ubqp_server_config& c, int32_t n) {
   const bool staged = c.params.eval_path == UBQP_EVAL_TC_STAGED ||
                       (c.params.eval_path == UBQP_EVAL_AUTO && n_tc > 4096);
   const int64_t ev = staged ? S_p * n_tc * 2 : 0;
-  ws += rup(std::max<int64_t>(ev, S_p * n_tc * 6), 256);
+  ws += rup(std::max<int64_t>(ev, S_p * n_tc * 6 + 256), 256);  // + the ascent's start counter
   return (size_t)(rup((int64_t)n * rup(n, 16), 256) + (int64_t)ubqp_q_arena_size(n) + ws +
                   rup(W * 8, 256) + 256);
 }

@@ -459,20 +459,35 @@ __device__ __forceinline__ void ascend_one(const int8_t* __restrict__ Q8, int64_
   grp.sync();
 }
 
+// The first wave of listed starts goes one per group in launch order (the
+// block scheduler spreads them over the SMs); the rest are taken from the
+// counter *next (zero at launch) one at a time as groups finish, so the long
+// and short climbs even out over the SMs.  next == NULL: round robin.
 template <int T, int C, int R>
 __global__ void __launch_bounds__(T, 1)
 ascent_block_kernel(const int8_t* __restrict__ Q8, int64_t ldq, int n, int W,
                     uint64_t* __restrict__ X, int64_t* __restrict__ f,
                     const int32_t* __restrict__ idx, const int64_t* __restrict__ count,
                     int64_t S, int32_t max_flips, int32_t* __restrict__ flips,
-                    const float* __restrict__ Y, int64_t ldy, unsigned* __restrict__ err) {
+                    const float* __restrict__ Y, int64_t ldy, unsigned* __restrict__ err,
+                    unsigned long long* __restrict__ next) {
   __shared__ int2 rec[2][T / 32];
   __shared__ uint64_t xs[UBQP_MAX_N / 64];
   __shared__ uint4 spec_slots[spec_slot_count<T, C, R>()];
+  __shared__ unsigned long long ticket;
   Group<T> grp{rec, 0};
   if (err[1] != 0) return;  // Q failed its symmetry check: no climb
   const int64_t cnt = *count;
-  for (int64_t t = blockIdx.x; t < cnt; t += gridDim.x) {
+  auto take = [&](int64_t t) -> int64_t {  // the block's next start
+    if (t < 0) return blockIdx.x;
+    if (!next) return t + gridDim.x;
+    if (threadIdx.x == 0) ticket = atomicAdd(next, 1ull);
+    __syncthreads();
+    const int64_t v = (int64_t)gridDim.x + (int64_t)ticket;
+    __syncthreads();
+    return v;
+  };
+  for (int64_t t = take(-1); t < cnt; t = take(t)) {
     const int s = idx[t];
     if (s < 0 || s >= S) {
       if (threadIdx.x == 0) atomicOr(err, UBQP_DEVERR_BADIDX);
@@ -517,14 +532,22 @@ ascent_warp_kernel(const int8_t* __restrict__ Q8, int64_t ldq, int n, int W,
                    uint64_t* __restrict__ X, int64_t* __restrict__ f,
                    const int32_t* __restrict__ idx, const int64_t* __restrict__ count,
                    int64_t S, int32_t max_flips, int32_t* __restrict__ flips,
-                   const float* __restrict__ Y, int64_t ldy, unsigned* __restrict__ err) {
+                   const float* __restrict__ Y, int64_t ldy, unsigned* __restrict__ err,
+                   unsigned long long* __restrict__ next) {
   __shared__ uint64_t xs_all[4][16];
   __shared__ uint4 spec_slots[4 * spec_slot_count<32, C, R>()];
   Group<32> grp;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   if (err[1] != 0) return;  // Q failed its symmetry check: no climb
   const int64_t cnt = *count;
-  for (int64_t t = (int64_t)blockIdx.x * 4 + warp; t < cnt; t += (int64_t)gridDim.x * 4) {
+  auto take = [&](int64_t t) -> int64_t {  // the warp's next start (see the block kernel)
+    if (t < 0) return (int64_t)blockIdx.x * 4 + warp;
+    if (!next) return t + (int64_t)gridDim.x * 4;
+    unsigned long long v = 0;
+    if (lane == 0) v = atomicAdd(next, 1ull);
+    return (int64_t)gridDim.x * 4 + (int64_t)__shfl_sync(0xffffffffu, v, 0);
+  };
+  for (int64_t t = take(-1); t < cnt; t = take(t)) {
     const int s = idx[t];
     if (s < 0 || s >= S) {
       if (lane == 0) atomicOr(err, UBQP_DEVERR_BADIDX);
@@ -602,23 +625,25 @@ int resident_grid(K kernel, int threads, int sm_count) {
 template <int T, int C>
 cudaError_t launch_block(const ubqp_q* h, uint64_t* X, int64_t* f, const int32_t* idx,
                          const int64_t* count, int64_t S, int32_t max_flips, int32_t* flips,
-                         const float* Y, cudaStream_t st) {
+                         const float* Y, unsigned long long* next, cudaStream_t st) {
   int grid = resident_grid(ascent_block_kernel<T, C, kSpecRows>, T, h->sm_count);
   if ((int64_t)grid > S) grid = (int)S;
   ascent_block_kernel<T, C, kSpecRows><<<grid, T, 0, st>>>(
-      h->Q8, h->ldq, h->n, h->W, X, f, idx, count, S, max_flips, flips, Y, h->n_tc, h->err);
+      h->Q8, h->ldq, h->n, h->W, X, f, idx, count, S, max_flips, flips, Y, h->n_tc, h->err,
+      next);
   return cudaGetLastError();
 }
 
 template <int C>
 cudaError_t launch_warp(const ubqp_q* h, uint64_t* X, int64_t* f, const int32_t* idx,
                         const int64_t* count, int64_t S, int32_t max_flips, int32_t* flips,
-                        const float* Y, cudaStream_t st) {
+                        const float* Y, unsigned long long* next, cudaStream_t st) {
   int grid = resident_grid(ascent_warp_kernel<C, kSpecRows>, 128, h->sm_count);
   const int64_t need = (S + 3) / 4;
   if ((int64_t)grid > need) grid = (int)need;
   ascent_warp_kernel<C, kSpecRows><<<grid, 128, 0, st>>>(
-      h->Q8, h->ldq, h->n, h->W, X, f, idx, count, S, max_flips, flips, Y, h->n_tc, h->err);
+      h->Q8, h->ldq, h->n, h->W, X, f, idx, count, S, max_flips, flips, Y, h->n_tc, h->err,
+      next);
   return cudaGetLastError();
 }
 
@@ -705,15 +730,21 @@ cudaError_t launch_ascent_batch(const BatchDesc* d, const int2* items, const int
 
 cudaError_t launch_ascent(const ubqp_q* h, uint64_t* X, int64_t* f, const int32_t* idx,
                           const int64_t* count, int64_t S, int32_t max_flips, int32_t* flips,
-                          const float* Y, cudaStream_t st) {
+                          const float* Y, unsigned long long* next, cudaStream_t st) {
   const int n = h->n;
-  if (n <= 256) return launch_warp<1>(h, X, f, idx, count, S, max_flips, flips, Y, st);
-  if (n <= 512) return launch_warp<2>(h, X, f, idx, count, S, max_flips, flips, Y, st);
-  if (n <= 1024) return launch_block<64, 1>(h, X, f, idx, count, S, max_flips, flips, Y, st);
-  if (n <= 2048) return launch_block<128, 1>(h, X, f, idx, count, S, max_flips, flips, Y, st);
-  if (n <= 4096) return launch_block<256, 1>(h, X, f, idx, count, S, max_flips, flips, Y, st);
-  if (n <= 8192) return launch_block<256, 2>(h, X, f, idx, count, S, max_flips, flips, Y, st);
-  if (n <= 16384) return launch_block<512, 2>(h, X, f, idx, count, S, max_flips, flips, Y, st);
+  if (next) {
+    cudaError_t e = cudaMemsetAsync(next, 0, sizeof(unsigned long long), st);
+    if (e != cudaSuccess) return e;
+  }
+#define UBQP_ASC_ARGS h, X, f, idx, count, S, max_flips, flips, Y, next, st
+  if (n <= 256) return launch_warp<1>(UBQP_ASC_ARGS);
+  if (n <= 512) return launch_warp<2>(UBQP_ASC_ARGS);
+  if (n <= 1024) return launch_block<64, 1>(UBQP_ASC_ARGS);
+  if (n <= 2048) return launch_block<128, 1>(UBQP_ASC_ARGS);
+  if (n <= 4096) return launch_block<256, 1>(UBQP_ASC_ARGS);
+  if (n <= 8192) return launch_block<256, 2>(UBQP_ASC_ARGS);
+  if (n <= 16384) return launch_block<512, 2>(UBQP_ASC_ARGS);
+#undef UBQP_ASC_ARGS
   return cudaErrorInvalidValue;
 }
 

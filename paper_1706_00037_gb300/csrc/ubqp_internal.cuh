@@ -153,9 +153,12 @@ cudaError_t launch_eval_ts(const ubqp_q* h, const uint64_t* X, int64_t S, int64_
 cudaError_t launch_relink(const ubqp_q* h, const uint64_t* X, const int64_t* f, const uint64_t* G,
                           int64_t P, uint64_t* Xb, int64_t* fb, int32_t* dist, uint16_t* trace,
                           int64_t ldt, const float* Y, cudaStream_t st);
+// next: a device counter the launch zeroes and the groups take starts from
+// (NULL: round robin).
 cudaError_t launch_ascent(const ubqp_q* h, uint64_t* X, int64_t* f, const int32_t* idx,
                           const int64_t* count, int64_t S, int32_t max_flips,
-                          int32_t* flips, const float* Y, cudaStream_t st);
+                          int32_t* flips, const float* Y, unsigned long long* next,
+                          cudaStream_t st);
 cudaError_t launch_best(const int64_t* f, const uint64_t* X, int64_t S, int W,
                         uint64_t* best_x, int64_t* best_f, cudaStream_t st);
 cudaError_t launch_search_update(const int64_t* cand, const uint64_t* X, int W,
