@@ -127,8 +127,11 @@ int run_body(ubqp_batch* b, cudaStream_t st) {
   // ---- one launch each: work list, every climb, every best
   UBQP_BCUDA(ubqp::launch_batch_items(b->d_desc, b->d_order, b->count, b->d_items, b->d_nitems,
                                       st));
+  // the item counter: the second word of the 16-byte item-count slot
   UBQP_BCUDA(ubqp::launch_ascent_batch(b->d_desc, b->d_items, b->d_nitems, b->asc_T, b->asc_C,
-                                       p.max_flips, b->asc_grid, st));
+                                       p.max_flips, b->asc_grid,
+                                       reinterpret_cast<unsigned long long*>(b->d_nitems + 1),
+                                       st));
   UBQP_BCUDA(ubqp::launch_best_batch(b->d_desc, b->count, st));
   return UBQP_OK;
 }

@@ -504,13 +504,26 @@ ascent_block_kernel(const int8_t* __restrict__ Q8, int64_t ldq, int n, int W,
 template <int T, int C, int R>
 __global__ void __launch_bounds__(T, 1)
 ascent_batch_kernel(const BatchDesc* __restrict__ d, const int2* __restrict__ items,
-                    const int64_t* __restrict__ n_items, int32_t max_flips) {
+                    const int64_t* __restrict__ n_items, int32_t max_flips,
+                    unsigned long long* __restrict__ next) {
   __shared__ int2 rec[2][T / 32];
   __shared__ uint64_t xs[UBQP_MAX_N / 64];
   __shared__ uint4 spec_slots[spec_slot_count<T, C, R>()];
+  __shared__ unsigned long long ticket;
   Group<T> grp{rec, 0};
   const int64_t cnt = *n_items;
-  for (int64_t t = blockIdx.x; t < cnt; t += gridDim.x) {
+  // the first wave one item per block, the rest from the counter (as in
+  // ascent_block_kernel)
+  auto take = [&](int64_t t) -> int64_t {
+    if (t < 0) return blockIdx.x;
+    if (!next) return t + gridDim.x;
+    if (threadIdx.x == 0) ticket = atomicAdd(next, 1ull);
+    __syncthreads();
+    const int64_t v = (int64_t)gridDim.x + (int64_t)ticket;
+    __syncthreads();
+    return v;
+  };
+  for (int64_t t = take(-1); t < cnt; t = take(t)) {
     const int2 it = items[t];
     const BatchDesc& b = d[it.x];
     if (b.err[1] != 0) continue;  // Q failed its symmetry check: no climb
@@ -649,8 +662,13 @@ cudaError_t launch_warp(const ubqp_q* h, uint64_t* X, int64_t* f, const int32_t*
 
 template <int T, int C>
 cudaError_t launch_ascent_batch_tc(const BatchDesc* d, const int2* items, const int64_t* n_items,
-                                   int32_t max_flips, int grid, cudaStream_t st) {
-  ascent_batch_kernel<T, C, kSpecRows><<<grid, T, 0, st>>>(d, items, n_items, max_flips);
+                                   int32_t max_flips, int grid, unsigned long long* next,
+                                   cudaStream_t st) {
+  if (next) {
+    cudaError_t e = cudaMemsetAsync(next, 0, sizeof(unsigned long long), st);
+    if (e != cudaSuccess) return e;
+  }
+  ascent_batch_kernel<T, C, kSpecRows><<<grid, T, 0, st>>>(d, items, n_items, max_flips, next);
   return cudaGetLastError();
 }
 
@@ -719,9 +737,11 @@ int ascent_batch_grid(int T, int C, int sm_count) {
 }
 
 cudaError_t launch_ascent_batch(const BatchDesc* d, const int2* items, const int64_t* n_items,
-                                int T, int C, int32_t max_flips, int grid, cudaStream_t st) {
-#define UBQP_ASC(TT, CC) \
-  if (T == TT && C == CC) return launch_ascent_batch_tc<TT, CC>(d, items, n_items, max_flips, grid, st);
+                                int T, int C, int32_t max_flips, int grid,
+                                unsigned long long* next, cudaStream_t st) {
+#define UBQP_ASC(TT, CC)                                                                      \
+  if (T == TT && C == CC)                                                                     \
+    return launch_ascent_batch_tc<TT, CC>(d, items, n_items, max_flips, grid, next, st);
   UBQP_ASC(64, 1) UBQP_ASC(64, 2) UBQP_ASC(128, 1) UBQP_ASC(128, 2)
   UBQP_ASC(256, 1) UBQP_ASC(256, 2) UBQP_ASC(512, 1) UBQP_ASC(512, 2)
 #undef UBQP_ASC

@@ -171,8 +171,10 @@ cudaError_t launch_screen(const int64_t* f, int64_t S, double lambda, int32_t* i
 cudaError_t launch_screen_batch(const BatchDesc* d, int count, double lambda, cudaStream_t st);
 cudaError_t launch_batch_items(const BatchDesc* d, const int32_t* order, int count, int2* items,
                                int64_t* n_items, cudaStream_t st);
+// next: as in launch_ascent (zeroed here; NULL: round robin)
 cudaError_t launch_ascent_batch(const BatchDesc* d, const int2* items, const int64_t* n_items,
-                                int T, int C, int32_t max_flips, int grid, cudaStream_t st);
+                                int T, int C, int32_t max_flips, int grid,
+                                unsigned long long* next, cudaStream_t st);
 int ascent_batch_grid(int T, int C, int sm_count);
 bool ascent_batch_supported(int T, int C);
 cudaError_t launch_best_batch(const BatchDesc* d, int count, cudaStream_t st);
