@@ -517,7 +517,10 @@ int ubqp_relink(const ubqp_q* q, const uint64_t* X_dev, const int64_t* f_dev,
                 base);
   cudaStream_t st = (cudaStream_t)stream;
   uint16_t* trace = reinterpret_cast<uint16_t*>(ws);
+  // the base's last 256 bytes: the pair count of the start-up, then the
+  // counter the walks take pairs from
   int64_t* count = reinterpret_cast<int64_t*>(static_cast<char*>(ws) + base - 256);
+  unsigned long long* next = reinterpret_cast<unsigned long long*>(count + 1);
   float* Y = nullptr;
   if (ws_bytes >= base + ubqp::ascent_tc_workspace(q, P) &&
       (int64_t)coeff_bound(q) * q->n_tc < (1 << 24)) {
@@ -529,7 +532,7 @@ int ubqp_relink(const ubqp_q* q, const uint64_t* X_dev, const int64_t* f_dev,
     else if (e != cudaSuccess) return cuda_fail(e, "relink start-up (tensor cores)");
   }
   UBQP_CUDA(ubqp::launch_relink(q, X_dev, f_dev, G_dev, P, Xbest_dev, fbest_dev, dist_dev, trace,
-                                relink_trace_ld(q), Y, st));
+                                relink_trace_ld(q), Y, next, st));
   return UBQP_OK;
 }
 

@@ -584,13 +584,26 @@ relink_block_kernel(const int8_t* __restrict__ Q8, int64_t ldq, int n, int W,
                     const uint64_t* __restrict__ G, int64_t P, uint64_t* __restrict__ Xb,
                     int64_t* __restrict__ fb, int32_t* __restrict__ dist,
                     uint16_t* __restrict__ trace, int64_t ldt, const float* __restrict__ Y,
-                    int64_t ldy, unsigned* __restrict__ err) {
+                    int64_t ldy, unsigned* __restrict__ err,
+                    unsigned long long* __restrict__ next) {
   __shared__ int2 rec[2][T / 32];
   __shared__ uint64_t xs[UBQP_MAX_N / 64];
   __shared__ uint4 spec_slots[spec_slot_count<T, C, R>()];
+  __shared__ unsigned long long ticket;
   Group<T> grp{rec, 0};
   if (err[1] != 0) return;  // Q failed its symmetry check: no walk
-  for (int64_t p = blockIdx.x; p < P; p += gridDim.x) {
+  // the first wave one pair per block, the rest from the counter (as in
+  // ascent_block_kernel)
+  auto take = [&](int64_t t) -> int64_t {
+    if (t < 0) return blockIdx.x;
+    if (!next) return t + gridDim.x;
+    if (threadIdx.x == 0) ticket = atomicAdd(next, 1ull);
+    __syncthreads();
+    const int64_t v = (int64_t)gridDim.x + (int64_t)ticket;
+    __syncthreads();
+    return v;
+  };
+  for (int64_t p = take(-1); p < P; p = take(p)) {
     const RelinkArgs a{G + p * W, Xb + p * W, fb + p, dist ? dist + p : nullptr,
                        trace + p * ldt};
     int64_t f0 = f[p];
@@ -606,13 +619,21 @@ relink_warp_kernel(const int8_t* __restrict__ Q8, int64_t ldq, int n, int W,
                    const uint64_t* __restrict__ G, int64_t P, uint64_t* __restrict__ Xb,
                    int64_t* __restrict__ fb, int32_t* __restrict__ dist,
                    uint16_t* __restrict__ trace, int64_t ldt, const float* __restrict__ Y,
-                   int64_t ldy, unsigned* __restrict__ err) {
+                   int64_t ldy, unsigned* __restrict__ err,
+                   unsigned long long* __restrict__ next) {
   __shared__ uint64_t xs_all[4][16];
   __shared__ uint4 spec_slots[4 * spec_slot_count<32, C, R>()];
   Group<32> grp;
-  const int warp = threadIdx.x >> 5;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   if (err[1] != 0) return;  // Q failed its symmetry check: no walk
-  for (int64_t p = (int64_t)blockIdx.x * 4 + warp; p < P; p += (int64_t)gridDim.x * 4) {
+  auto take = [&](int64_t t) -> int64_t {  // the warp's next pair (see the block kernel)
+    if (t < 0) return (int64_t)blockIdx.x * 4 + warp;
+    if (!next) return t + (int64_t)gridDim.x * 4;
+    unsigned long long v = 0;
+    if (lane == 0) v = atomicAdd(next, 1ull);
+    return (int64_t)gridDim.x * 4 + (int64_t)__shfl_sync(0xffffffffu, v, 0);
+  };
+  for (int64_t p = take(-1); p < P; p = take(p)) {
     const RelinkArgs a{G + p * W, Xb + p * W, fb + p, dist ? dist + p : nullptr,
                        trace + p * ldt};
     int64_t f0 = f[p];
@@ -676,11 +697,12 @@ template <int T, int C>
 cudaError_t launch_relink_block(const ubqp_q* h, const uint64_t* X, const int64_t* f,
                                 const uint64_t* G, int64_t P, uint64_t* Xb, int64_t* fb,
                                 int32_t* dist, uint16_t* trace, int64_t ldt, const float* Y,
-                                cudaStream_t st) {
+                                unsigned long long* next, cudaStream_t st) {
   int grid = resident_grid(relink_block_kernel<T, C, kSpecRows>, T, h->sm_count);
   if ((int64_t)grid > P) grid = (int)P;
   relink_block_kernel<T, C, kSpecRows><<<grid, T, 0, st>>>(
-      h->Q8, h->ldq, h->n, h->W, X, f, G, P, Xb, fb, dist, trace, ldt, Y, h->n_tc, h->err);
+      h->Q8, h->ldq, h->n, h->W, X, f, G, P, Xb, fb, dist, trace, ldt, Y, h->n_tc, h->err,
+      next);
   return cudaGetLastError();
 }
 
@@ -688,12 +710,13 @@ template <int C>
 cudaError_t launch_relink_warp(const ubqp_q* h, const uint64_t* X, const int64_t* f,
                                const uint64_t* G, int64_t P, uint64_t* Xb, int64_t* fb,
                                int32_t* dist, uint16_t* trace, int64_t ldt, const float* Y,
-                               cudaStream_t st) {
+                               unsigned long long* next, cudaStream_t st) {
   int grid = resident_grid(relink_warp_kernel<C, kSpecRows>, 128, h->sm_count);
   const int64_t need = (P + 3) / 4;
   if ((int64_t)grid > need) grid = (int)need;
   relink_warp_kernel<C, kSpecRows><<<grid, 128, 0, st>>>(
-      h->Q8, h->ldq, h->n, h->W, X, f, G, P, Xb, fb, dist, trace, ldt, Y, h->n_tc, h->err);
+      h->Q8, h->ldq, h->n, h->W, X, f, G, P, Xb, fb, dist, trace, ldt, Y, h->n_tc, h->err,
+      next);
   return cudaGetLastError();
 }
 
@@ -701,9 +724,14 @@ cudaError_t launch_relink_warp(const ubqp_q* h, const uint64_t* X, const int64_t
 
 cudaError_t launch_relink(const ubqp_q* h, const uint64_t* X, const int64_t* f, const uint64_t* G,
                           int64_t P, uint64_t* Xb, int64_t* fb, int32_t* dist, uint16_t* trace,
-                          int64_t ldt, const float* Y, cudaStream_t st) {
+                          int64_t ldt, const float* Y, unsigned long long* next,
+                          cudaStream_t st) {
   const int n = h->n;
-#define UBQP_RL_ARGS h, X, f, G, P, Xb, fb, dist, trace, ldt, Y, st
+  if (next) {
+    cudaError_t e = cudaMemsetAsync(next, 0, sizeof(unsigned long long), st);
+    if (e != cudaSuccess) return e;
+  }
+#define UBQP_RL_ARGS h, X, f, G, P, Xb, fb, dist, trace, ldt, Y, next, st
   if (n <= 256) return launch_relink_warp<1>(UBQP_RL_ARGS);
   if (n <= 512) return launch_relink_warp<2>(UBQP_RL_ARGS);
   if (n <= 1024) return launch_relink_block<64, 1>(UBQP_RL_ARGS);

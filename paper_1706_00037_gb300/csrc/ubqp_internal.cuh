@@ -150,9 +150,11 @@ cudaError_t launch_selftest_wait(uint64_t limit_ns, int32_t* status, cudaStream_
 // Evaluation with the A operand in tensor memory (no workspace).
 cudaError_t launch_eval_ts(const ubqp_q* h, const uint64_t* X, int64_t S, int64_t* f,
                            cudaStream_t st);
+// next: as in launch_ascent (zeroed here; NULL: round robin)
 cudaError_t launch_relink(const ubqp_q* h, const uint64_t* X, const int64_t* f, const uint64_t* G,
                           int64_t P, uint64_t* Xb, int64_t* fb, int32_t* dist, uint16_t* trace,
-                          int64_t ldt, const float* Y, cudaStream_t st);
+                          int64_t ldt, const float* Y, unsigned long long* next,
+                          cudaStream_t st);
 // next: a device counter the launch zeroes and the groups take starts from
 // (NULL: round robin).
 cudaError_t launch_ascent(const ubqp_q* h, uint64_t* X, int64_t* f, const int32_t* idx,
