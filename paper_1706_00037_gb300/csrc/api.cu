@@ -42,6 +42,12 @@ int64_t round_up(int64_t v, int64_t a) { return (v + a - 1) / a * a; }
 // validation is unread
 int64_t coeff_bound(const ubqp_q* q) { return q->max_abs >= 0 ? q->max_abs : 128; }
 
+// Workspace of ubqp_ascent: the tensor-core start-up's scratch, then 256
+// bytes holding the counter the climbs take starts from.
+size_t ascent_ws_bytes(const ubqp_q* q, int64_t S) {
+  return ubqp::ascent_tc_workspace(q, S) + 256;
+}
+
 // The address a kernel reads Q through: device or managed memory as given,
 // page-locked host memory through its device mapping; NULL otherwise.
 const int8_t* kernel_readable(const int8_t* p) {
@@ -89,7 +95,7 @@ SolveLayout solve_layout(const ubqp_q* q, const ubqp_params* p) {
   L.small = take(kSmallBytes);
   const int path = resolve_path(q, p->eval_path);
   const size_t ev = path == UBQP_EVAL_TC_STAGED ? ubqp::eval_tc_workspace(q, S) : 0;
-  const size_t as = ubqp::ascent_tc_workspace(q, S);
+  const size_t as = ascent_ws_bytes(q, S);
   L.eval = take(ev > as ? ev : as);
   L.total = off;
   return L;
@@ -445,7 +451,7 @@ int ubqp_screen(const int64_t* f_dev, int64_t S, double lambda, int32_t* idx_dev
 
 size_t ubqp_ascent_workspace_size(const ubqp_q* q, int64_t S) {
   if (!q || S < 0) return 0;
-  return ubqp::ascent_tc_workspace(q, S);
+  return ascent_ws_bytes(q, S);
 }
 
 int ubqp_ascent(const ubqp_q* q, uint64_t* X_dev, int64_t* f_dev, const int32_t* idx_dev,
@@ -467,7 +473,7 @@ int ubqp_ascent(const ubqp_q* q, uint64_t* X_dev, int64_t* f_dev, const int32_t*
     else if (e != cudaSuccess) return cuda_fail(e, "ascent start-up (tensor cores)");
   }
   // the start counter in the workspace's last 256 bytes (round robin without)
-  const size_t as = ubqp::ascent_tc_workspace(q, S);
+  const size_t as = ascent_ws_bytes(q, S);
   unsigned long long* next =
       ws && ws_bytes >= as
           ? reinterpret_cast<unsigned long long*>(static_cast<char*>(ws) + as - 256)
@@ -627,7 +633,7 @@ SearchLayout search_layout(const ubqp_q* q, const ubqp_search_params* p) {
   const int path = resolve_path(q, p->eval_path);
   const int64_t big = S > NS ? S : NS;
   const size_t ev = path == UBQP_EVAL_TC_STAGED ? ubqp::eval_tc_workspace(q, big) : 0;
-  const size_t as = ubqp::ascent_tc_workspace(q, S);
+  const size_t as = ascent_ws_bytes(q, S);
   L.scratch = take(ev > as ? ev : as);
   L.total = off;
   return L;

@@ -944,9 +944,8 @@ cudaError_t eval_tc_prepare(ubqp_q* h, cudaStream_t) {
   return cudaSuccess;
 }
 
-// the unpacked starts, Y, and (last 256 bytes) the ascent's start counter
 size_t ascent_tc_workspace(const ubqp_q* h, int64_t S) {
-  return (size_t)padded_starts(S) * (size_t)h->n_tc * (2 + 4) + 256;
+  return (size_t)padded_starts(S) * (size_t)h->n_tc * (2 + 4);
 }
 
 // y = Q x for the starts idx[0 .. *count) into Y (fp32, row t = idx[t], stride
