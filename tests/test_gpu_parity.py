@@ -278,6 +278,28 @@ def test_ascent_large_n_paths(n, extreme):
         assert np.array_equal(words_host(Xd), Xw)
 
 
+@pytest.mark.parametrize("n,S", [(200, 20000), (700, 3000)],
+                         ids=["warp_groups", "block64_groups"])
+def test_ascent_more_starts_than_the_first_wave(n, S):
+    """Every start climbed, many more than the persistent groups (four warps
+    per block at n = 200, 64-thread blocks at n = 700): the starts beyond the
+    first wave come from the workspace's counter, each exactly once, and every
+    value, flip count and solution equals the oracle's."""
+    Q = synth.make_instance(n, 0.5, n + 1)
+    inst = ubqp.Instance(dev(Q))
+    X = synth.random_solutions(n, S, 5)
+    fv = orc.eval(Q, X)
+    Xw, fw, flw = orc.ascent(Q, X, fv, np.arange(S, dtype=np.int32))
+    Xd, fd = words_dev(X), dev(fv)
+    flips = torch.zeros(S, dtype=torch.int32, device="cuda")
+    ubqp.ascent(inst, Xd, fd, dev(np.arange(S, dtype=np.int32)), dev(np.array([S], np.int64)),
+                0, flips, use_ws=True)
+    inst.sync()
+    assert np.array_equal(flips.cpu().numpy(), flw)
+    assert np.array_equal(fd.cpu().numpy(), fw)
+    assert np.array_equal(words_host(Xd), Xw)
+
+
 def test_ascent_startup_extreme_coefficients():
     # |Q| at the int8 limits: the tensor-core start-up y = Q x must stay exact
     n, S = 1200, 30
