@@ -26,6 +26,7 @@ import torch
 import torch.distributed as dist
 
 INT64_MAX = 2**63 - 1
+INT64_MIN = -2**63
 
 
 def shard(S_total: int, world: int, rank: int) -> tuple[int, int]:
@@ -107,6 +108,14 @@ def round_phase1(inst, params, world: int, rank: int) -> RankState:
     from . import ubqp
     S = params.num_starts
     begin, count = shard(S, world, rank)
+    if count == 0:
+        # more ranks than starts: one placeholder start that can neither pass
+        # the screen nor be the best, and the neutral statistics
+        X = torch.zeros((1, inst.words), dtype=torch.int64, device=inst.device)
+        f = torch.full((1,), INT64_MIN, dtype=torch.int64, device=inst.device)
+        st = torch.tensor([0, INT64_MIN, INT64_MAX], dtype=torch.int64, device=inst.device)
+        return RankState(begin, 0, X, f, st, torch.empty(16, dtype=torch.uint8,
+                                                         device=inst.device))
     X = ubqp.diversify_range(inst, S, begin, count, mode=params.mode, seed=params.seed,
                              round_=params.round, div_H=params.div_H)
     ws_bytes = max(ubqp.eval_workspace_size(inst, count, params.eval_path),

@@ -9,7 +9,8 @@ from paper_1706_00037_gb300 import parallel, synth, ubqp
 pytestmark = pytest.mark.gpu
 
 
-@pytest.mark.parametrize("mode,n,S", [(ubqp.DIVERSIFY, 300, 777), (ubqp.RANDOM, 2100, 500)])
+@pytest.mark.parametrize("mode,n,S", [(ubqp.DIVERSIFY, 300, 777), (ubqp.RANDOM, 2100, 500),
+                                      (ubqp.RANDOM, 300, 2)])
 @pytest.mark.parametrize("world", [2, 3])
 def test_sharded_round_equals_single_round(mode, n, S, world):
     Q = synth.make_instance(n, 0.3, 5)

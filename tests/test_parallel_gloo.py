@@ -76,3 +76,12 @@ def test_pure_combinations():
     st = [torch.tensor([10, 7, 3]), torch.tensor([-4, 7, 1]), torch.tensor([5, 2, 9])]
     assert parallel.combine_screen_stats(st).tolist() == [11, 7, 1]
     assert parallel.combine_best([(5, 8), (9, 4), (9, 2)]) == (9, 2)
+
+
+def test_a_rank_without_starts_is_neutral():
+    # more ranks than starts: the empty rank's triple and best change nothing
+    empty = torch.tensor([0, parallel.INT64_MIN, parallel.INT64_MAX])
+    st = [torch.tensor([-30, -7, 1]), empty, torch.tensor([-5, -2, 2])]
+    assert parallel.combine_screen_stats(st).tolist() == [-35, -2, 2]
+    assert parallel.combine_best([(-3, 0), (parallel.INT64_MIN, 3), (-3, 1)]) == (-3, 0)
+    assert [parallel.shard(2, 3, r) for r in range(3)] == [(0, 1), (1, 1), (2, 0)]
