@@ -217,7 +217,7 @@ int prepare_impl(const int8_t* Q_dev, int32_t n, int64_t ldq, void* stream, void
   h->device_bytes = (int64_t)L.total;
   cudaError_t e = ubqp::launch_prepare(Q_k, n, ldq, h, st);
   if (e == cudaSuccess) e = ubqp::eval_tc_upload_tables(h, st);
-  if (deferred) {  // no synchronisation: ubqp_sync reads the verdict
+  if (deferred) {  // no synchronisation: ubqp_sync reads the check
     if (e == cudaSuccess) e = ubqp::eval_tc_prepare(h, st);
     if (e != cudaSuccess) {
       ubqp_q_destroy(h);

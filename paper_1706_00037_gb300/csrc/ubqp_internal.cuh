@@ -41,7 +41,7 @@ struct ubqp_q {
   int tc_nchunks_ts;  // chunks of the tensor-memory-A evaluation (192-column blocks)
   bool tc_ok;
   bool owns_memory;  // false when the buffers were carved from caller memory
-  // deferred validation (ubqp_q_prepare_into_async): the symmetry verdict and
+  // deferred validation (ubqp_q_prepare_into_async): the symmetry check and
   // max |Q| stay in scratch_flags until the first ubqp_sync reads them
   mutable bool deferred;
   mutable bool asymmetric;

@@ -218,7 +218,8 @@ def test_diversify_round_counter_continues():
     x0 = synth.random_solutions(n, 1, 8)[0]
     big = orc.diversify(x0, n, orc.DIVERSIFY, 3, 0, 2 * S)
     r1 = orc.diversify(x0, n, orc.DIVERSIFY, 3, 1, S)
-    # starts of round 1 with S per round are the loop counters S..2S-1
+    # the starts of the second search round (round index 1, S per round) are the
+    # loop counters S..2S-1
     assert np.array_equal(r1, big[S:])
 
 
