@@ -369,6 +369,40 @@ def test_solve_consistency():
     assert r["passed"] >= 1
 
 
+@pytest.mark.parametrize("n,S,density,lam,max_flips,seed,mode", [
+    (100, 200, 0.1, 0.5, 0, 0, 1),
+    (100, 1000, 0.1, 0.5, 0, 0, 1),   # the n = 100 workload in full
+    (73, 300, 0.6, 0.25, 0, 7, 1),
+    (73, 300, 0.6, 0.75, 3, 7, 1),    # capped climbs
+    (130, 257, 1.0, 0.5, 0, 11, 0),   # uniform random starts
+])
+def test_solve_is_the_round_recomposed_from_its_pinned_steps(n, S, density, lam, max_flips,
+                                                             seed, mode):
+    # One round of the loop body of Fig. 2 in its order: the first-derivative
+    # start, start generation around it, evaluation, the screen, the ascent of
+    # the passing starts, then the best over every start's final value.  Each
+    # step is pinned on its own above; this pins their composition, so a solve
+    # that took the best-of before the ascent, climbed the wrong starts or
+    # screened the climbed values fails here.
+    Q = synth.make_instance(n, density, seed)
+    r = orc.solve(Q, S, lam, max_flips=max_flips, seed=seed, mode=mode)
+    x0 = orc.first_derivative(Q)
+    X = orc.diversify(x0, n, mode, seed, 0, S)
+    fv = orc.eval(Q, X)
+    sc = orc.screen(fv, lam)
+    Xa, fa, flips = orc.ascent(Q, X, fv, sc["idx"], max_flips)
+    bf, bi = orc.best(fa)
+    assert r["best_f"] == bf and r["best_index"] == bi
+    assert np.array_equal(r["best_x"], Xa[bi])
+    assert r["passed"] == sc["count"] and r["batch_max"] == sc["max"]
+    assert r["sum"] == int(fv.sum()) and r["T"] == sc["T"] and r["mean"] == sc["mean"]
+    assert r["total_flips"] == int(flips.sum())
+    assert r["max_flips_seen"] == int(flips.max(initial=0))
+    # the climb matters on every case: the best-of taken before the ascent
+    # would give a strictly smaller value
+    assert bf > int(fv.max())
+
+
 # ---------------------------------------------------------------- instance generator
 
 def test_instance_generator_shape_and_density():
