@@ -32,7 +32,7 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 METRIC = "xQx evals/s and 1-flip moves/s at n=7000; served solves/s with p50/p99 latency"
-UNIT = "evals/s"
+UNIT = "starts/s"  # starts taken through the whole round per second
 L2_FLUSH_BYTES = 256 << 20
 
 

@@ -46,7 +46,7 @@
 extern "C" {
 #endif
 
-#define UBQP_ABI_VERSION 4
+#define UBQP_ABI_VERSION 5
 
 typedef enum ubqp_status {
   UBQP_OK = 0,
@@ -203,17 +203,24 @@ int ubqp_eval(const ubqp_q* q, const uint64_t* X_dev, int64_t S, int64_t* f_dev,
  * cudaMalloc/cudaFree, which can synchronise the whole device.  The paper has
  * no counterpart; this is an interface convenience only.
  *   The scratch for the unpacked solutions is a static device array of
- *   UBQP_EVAL_NOALLOC_MAX_BYTES built into the library, present on every GPU
- *   that loads the library until the process exits.  A call needs
- *   ceil(S/128)*128 * n_tc * 2 bytes of it (n_tc = n rounded up to 256); larger
- *   requests return UBQP_ERR_UNSUPPORTED (e.g. 1000 starts fit up to n = 8192).
- *   The call allocates nothing and calls no cudaMalloc/cudaFree.  The first
- *   call on a device looks up the array's device address
- *   (cudaGetSymbolAddress) with that device current; make that first call
- *   before any stream capture.  All calls share the one array and it keeps the
- *   last call's contents (each call overwrites the part it uses): calls whose
- *   work overlaps on the GPU -- concurrent streams, or several host threads --
- *   race on it and must be serialised by the caller.  Async on `stream`.
+ *   UBQP_EVAL_NOALLOC_MAX_BYTES built into the library.  CUDA places it on a
+ *   device when it loads the library's evaluation module there, which with
+ *   CUDA's default lazy module loading is the first evaluation (any path) or
+ *   the first call of this entry point on that device -- not the loading of
+ *   the library -- and it stays there until the process exits.  A caller that
+ *   is about to hand the rest of a device's memory to another allocator should
+ *   therefore make one call (or one ubqp_q_prepare and ubqp_eval) first.
+ *   A call needs ceil(S/128)*128 * n_tc * 2 bytes of it (n_tc = n rounded up
+ *   to 256); larger requests return UBQP_ERR_UNSUPPORTED (e.g. 1000 starts fit
+ *   up to n = 8192, which uses all of it).  The call allocates nothing and
+ *   calls no cudaMalloc/cudaFree.  The array's device address is looked up
+ *   (cudaGetSymbolAddress) with the device current on the first call in each
+ *   CUDA context of a device (again after a cudaDeviceReset); make that first
+ *   call before any stream capture.  All calls share the one array and it
+ *   keeps the last call's contents (each call overwrites the part it uses):
+ *   calls whose work overlaps on the GPU -- concurrent streams, or several
+ *   host threads -- race on it and must be serialised by the caller.  Async
+ *   on `stream`.
  */
 #define UBQP_EVAL_NOALLOC_MAX_BYTES (16u << 20)
 int ubqp_eval_noalloc(const ubqp_q* q, const uint64_t* X_dev, int64_t S,
@@ -282,6 +289,23 @@ int ubqp_ascent(const ubqp_q* q, uint64_t* X_dev, int64_t* f_dev,
                 const int32_t* idx_dev, const int64_t* count_dev, int64_t S,
                 int32_t max_flips, int32_t* flips_dev, void* ws, size_t ws_bytes,
                 void* stream);
+/*
+ * ubqp_ascent_trace -- ubqp_ascent with a record of its moves: the same climb
+ * (identical X, f and flips), and the flipped indices of each listed start s,
+ * in the order PerformSteepestAscent of Fig. 2 takes them (largest 1-flip gain,
+ * lowest index on ties), written to trace_dev[s*ldt + t] for t < min(flips,
+ * ldt).  Moves beyond ldt are made but not recorded; entries at or beyond a
+ * start's flip count and the rows of starts not listed are left untouched.
+ *   trace_dev  S rows of ldt uint16 (n <= 16384 < 2^16), device memory.
+ *   ldt        >= 1; a row of n entries records every move of a start that
+ *              flips each variable at most once, 4n is ample in practice.
+ * Same arguments, workspace and errors otherwise (UBQP_ERR_ARG: trace_dev NULL
+ * or ldt < 1).  A testing and analysis aid: the record costs one store per move.
+ */
+int ubqp_ascent_trace(const ubqp_q* q, uint64_t* X_dev, int64_t* f_dev,
+                      const int32_t* idx_dev, const int64_t* count_dev, int64_t S,
+                      int32_t max_flips, int32_t* flips_dev, uint16_t* trace_dev,
+                      int64_t ldt, void* ws, size_t ws_bytes, void* stream);
 
 /*
  * ubqp_best -- UpdateBestAndT's bookkeeping (Fig. 2): the largest of the S

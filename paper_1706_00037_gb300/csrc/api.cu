@@ -454,10 +454,12 @@ size_t ubqp_ascent_workspace_size(const ubqp_q* q, int64_t S) {
   return ascent_ws_bytes(q, S);
 }
 
-int ubqp_ascent(const ubqp_q* q, uint64_t* X_dev, int64_t* f_dev, const int32_t* idx_dev,
-                const int64_t* count_dev, int64_t S, int32_t max_flips, int32_t* flips_dev,
-                void* ws, size_t ws_bytes, void* stream) {
-  UBQP_RANGE("ubqp:ascent");
+// ubqp_ascent and ubqp_ascent_trace: the tensor-core start-up when the
+// workspace allows, then one ascent launch (traced when trace_dev is given).
+static int ascent_impl(const ubqp_q* q, uint64_t* X_dev, int64_t* f_dev, const int32_t* idx_dev,
+                       const int64_t* count_dev, int64_t S, int32_t max_flips,
+                       int32_t* flips_dev, uint16_t* trace_dev, int64_t ldt, void* ws,
+                       size_t ws_bytes, void* stream) {
   if (!q || !X_dev || !f_dev || !idx_dev || !count_dev) return fail(UBQP_ERR_ARG, "NULL argument");
   if (S < 0 || S >= ((int64_t)1 << 31)) return fail(UBQP_ERR_ARG, "S outside [0, 2^31)");
   if (max_flips < 0) return fail(UBQP_ERR_ARG, "max_flips < 0");
@@ -478,9 +480,31 @@ int ubqp_ascent(const ubqp_q* q, uint64_t* X_dev, int64_t* f_dev, const int32_t*
       ws && ws_bytes >= as
           ? reinterpret_cast<unsigned long long*>(static_cast<char*>(ws) + as - 256)
           : nullptr;
-  UBQP_CUDA(ubqp::launch_ascent(q, X_dev, f_dev, idx_dev, count_dev, S, max_flips, flips_dev, Y,
-                                next, st));
+  if (trace_dev)
+    UBQP_CUDA(ubqp::launch_ascent_traced(q, X_dev, f_dev, idx_dev, count_dev, S, max_flips,
+                                         flips_dev, Y, next, trace_dev, ldt, st));
+  else
+    UBQP_CUDA(ubqp::launch_ascent(q, X_dev, f_dev, idx_dev, count_dev, S, max_flips, flips_dev,
+                                  Y, next, st));
   return UBQP_OK;
+}
+
+int ubqp_ascent(const ubqp_q* q, uint64_t* X_dev, int64_t* f_dev, const int32_t* idx_dev,
+                const int64_t* count_dev, int64_t S, int32_t max_flips, int32_t* flips_dev,
+                void* ws, size_t ws_bytes, void* stream) {
+  UBQP_RANGE("ubqp:ascent");
+  return ascent_impl(q, X_dev, f_dev, idx_dev, count_dev, S, max_flips, flips_dev, nullptr, 0,
+                     ws, ws_bytes, stream);
+}
+
+int ubqp_ascent_trace(const ubqp_q* q, uint64_t* X_dev, int64_t* f_dev, const int32_t* idx_dev,
+                      const int64_t* count_dev, int64_t S, int32_t max_flips, int32_t* flips_dev,
+                      uint16_t* trace_dev, int64_t ldt, void* ws, size_t ws_bytes,
+                      void* stream) {
+  UBQP_RANGE("ubqp:ascent_trace");
+  if (!trace_dev || ldt < 1) return fail(UBQP_ERR_ARG, "trace_dev is NULL or ldt < 1");
+  return ascent_impl(q, X_dev, f_dev, idx_dev, count_dev, S, max_flips, flips_dev, trace_dev,
+                     ldt, ws, ws_bytes, stream);
 }
 
 // Relinking workspace: [trace: P rows of n rounded up to 8 uint16][pair count]

@@ -838,12 +838,44 @@ int64_t padded_starts(int64_t S) { return (S + BM - 1) / BM * BM; }
 
 // Scratch of the allocation-free evaluation (ubqp_eval_noalloc): the unpacked
 // solutions live in this file-scope device array instead of caller workspace.
-// Every GPU that loads the library holds it until the process exits.
+// CUDA places it on a device when it loads this file's module there (lazily by
+// default: the first launch of a kernel of this file or the first address
+// lookup below) and keeps it until the process exits.
 static __device__ __align__(256) uint8_t g_eval_scratch[UBQP_EVAL_NOALLOC_MAX_BYTES];
 
 constexpr int kMaxDevices = 64;
 std::mutex g_scratch_mu;
-void* g_scratch_addr[kMaxDevices];  // device address of g_eval_scratch, per device
+// device address of g_eval_scratch per device, with the id of the CUDA context
+// it was looked up in (a cudaDeviceReset ends that context and the address
+// with it)
+void* g_scratch_addr[kMaxDevices];
+unsigned long long g_scratch_ctx[kMaxDevices];
+
+using CtxGetCurrentFn = CUresult (*)(CUcontext*);
+using CtxGetIdFn = CUresult (*)(CUcontext, unsigned long long*);
+
+// Unique id (for the life of the process) of the context current on this
+// thread; false when there is none or the driver cannot say.
+bool current_context_id(unsigned long long* id) {
+  static CtxGetCurrentFn get_cur = nullptr;
+  static CtxGetIdFn get_id = nullptr;
+  static std::once_flag once;
+  std::call_once(once, [] {
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &p, 12000, cudaEnableDefault, &q) ==
+            cudaSuccess && q == cudaDriverEntryPointSuccess)
+      get_cur = reinterpret_cast<CtxGetCurrentFn>(p);
+    p = nullptr;
+    if (cudaGetDriverEntryPointByVersion("cuCtxGetId", &p, 12000, cudaEnableDefault, &q) ==
+            cudaSuccess && q == cudaDriverEntryPointSuccess)
+      get_id = reinterpret_cast<CtxGetIdFn>(p);
+    cudaGetLastError();
+  });
+  CUcontext ctx = nullptr;
+  if (!get_cur || !get_id || get_cur(&ctx) != CUDA_SUCCESS || !ctx) return false;
+  return get_id(ctx, id) == CUDA_SUCCESS;
+}
 
 }  // namespace
 
@@ -851,18 +883,29 @@ size_t eval_tc_static_capacity() { return (size_t)UBQP_EVAL_NOALLOC_MAX_BYTES; }
 
 // Device address of the static scratch on the current device.  The host-side
 // name g_eval_scratch is only a stand-in; the real address comes from
-// cudaGetSymbolAddress, looked up once per device with that device current.
+// cudaGetSymbolAddress with the device current, looked up on the first call in
+// each context of the device and kept for the later calls in that context.
+// (The lookup loads this file's module if CUDA has not yet, which places the
+// array on the device.)  Without a context id from the driver every call
+// looks the address up.
 cudaError_t eval_tc_static_scratch(void** out) {
   int dev = 0;
   cudaError_t e = cudaGetDevice(&dev);
   if (e) return e;
   if (dev < 0 || dev >= kMaxDevices) return cudaErrorInvalidDevice;
+  unsigned long long id = 0;
+  bool have_id = current_context_id(&id);
   std::lock_guard<std::mutex> lock(g_scratch_mu);
-  if (!g_scratch_addr[dev]) {
+  if (!g_scratch_addr[dev] || !have_id || id != g_scratch_ctx[dev]) {
     void* p = nullptr;
     e = cudaGetSymbolAddress(&p, g_eval_scratch);
     if (e) return e;
-    g_scratch_addr[dev] = p;
+    // the lookup has made the device's context current: key the address by it
+    have_id = current_context_id(&id);
+    g_scratch_addr[dev] = have_id ? p : nullptr;
+    g_scratch_ctx[dev] = have_id ? id : 0;
+    *out = p;
+    return cudaSuccess;
   }
   *out = g_scratch_addr[dev];
   return cudaSuccess;

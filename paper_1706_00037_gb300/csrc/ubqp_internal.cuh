@@ -161,6 +161,12 @@ cudaError_t launch_ascent(const ubqp_q* h, uint64_t* X, int64_t* f, const int32_
                           const int64_t* count, int64_t S, int32_t max_flips,
                           int32_t* flips, const float* Y, unsigned long long* next,
                           cudaStream_t st);
+// launch_ascent that also writes start s's flipped indices, in order, to
+// trace[s * ldt ...] (the first ldt of them).
+cudaError_t launch_ascent_traced(const ubqp_q* h, uint64_t* X, int64_t* f, const int32_t* idx,
+                                 const int64_t* count, int64_t S, int32_t max_flips,
+                                 int32_t* flips, const float* Y, unsigned long long* next,
+                                 uint16_t* trace, int64_t ldt, cudaStream_t st);
 cudaError_t launch_best(const int64_t* f, const uint64_t* X, int64_t S, int W,
                         uint64_t* best_x, int64_t* best_f, cudaStream_t st);
 cudaError_t launch_search_update(const int64_t* cand, const uint64_t* X, int W,

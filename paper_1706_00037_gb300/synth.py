@@ -90,3 +90,37 @@ def random_solutions(n: int, S: int, seed: int, p_one: float = 0.5) -> np.ndarra
     """S arbitrary bit-packed solutions (test inputs; bits >= n are zero)."""
     r = np.random.default_rng(seed)
     return pack_bits((r.random((S, n)) < p_one).astype(np.uint8))
+
+
+# ---------------------------------------------------------------- workloads
+# The seeded instance sets of the multi-instance and serving workloads, shared
+# by the benchmark and the tests so that both run the same inputs.
+
+def batch_specs(count: int = 64, seed: int = 4) -> list[tuple[int, float, int]]:
+    """(n, density, instance seed) of the multi-instance batch: n uniform on
+    [200, 2500], density drawn from {0.1, 0.5, 1.0}, instance seeds 1000*seed + k."""
+    r = np.random.default_rng(seed)
+    ns = r.integers(200, 2501, count)
+    ds = r.choice([0.1, 0.5, 1.0], count)
+    return [(int(n), float(d), 1000 * seed + k) for k, (n, d) in enumerate(zip(ns, ds))]
+
+
+SERVE_MASTER_N = 8192
+
+
+def serve_master(density: float, seed: int = 5) -> np.ndarray:
+    """The master instance request instances are cut from (n = 8192)."""
+    return make_instance(SERVE_MASTER_N, density, 5000 + seed + (0 if density < 0.5 else 1))
+
+
+def serve_requests(count: int, seed: int = 5) -> list[tuple[int, float, int]]:
+    """(n, density, offset) of `count` requests: n log-uniform on [500, 7000],
+    density in {0.1, 1.0}, and the request's instance the principal submatrix
+    M[o:o+n, o:o+n] of the master M of that density at an offset o uniform on
+    [0, 8192 - n] -- a symmetric instance of the same recipe for every
+    request, drawn without building one matrix per request."""
+    r = np.random.default_rng(seed)
+    ns = np.exp(r.uniform(np.log(500), np.log(7000), count)).astype(int)
+    ds = r.choice([0.1, 1.0], count)
+    offs = [int(r.integers(0, SERVE_MASTER_N - int(n) + 1)) for n in ns]
+    return [(int(n), float(d), o) for n, d, o in zip(ns, ds, offs)]

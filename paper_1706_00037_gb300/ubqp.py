@@ -34,7 +34,8 @@ EXPORTS = ["ubqp_strerror", "ubqp_last_error", "ubqp_abi_version", "ubqp_q_prepa
            "ubqp_q_prepare_into", "ubqp_server_create", "ubqp_server_submit", "ubqp_server_wait",
            "ubqp_server_poll", "ubqp_server_request_bytes", "ubqp_server_destroy",
            "ubqp_relink_workspace_size", "ubqp_relink", "ubqp_server_inject_alloc_failures",
-           "ubqp_selftest_timeout", "ubqp_search_resume", "ubqp_q_prepare_into_async"]
+           "ubqp_selftest_timeout", "ubqp_search_resume", "ubqp_q_prepare_into_async",
+           "ubqp_ascent_trace"]
 
 
 class UbqpError(RuntimeError):
@@ -109,6 +110,7 @@ def load() -> ctypes.CDLL:
         "ubqp_screen_apply": (ctypes.c_int, [P, i64, P, i64, f64, P, P, P, P]),
         "ubqp_ascent_workspace_size": (sz, [P, i64]),
         "ubqp_ascent": (ctypes.c_int, [P, P, P, P, P, i64, i32, P, P, sz, P]),
+        "ubqp_ascent_trace": (ctypes.c_int, [P, P, P, P, P, i64, i32, P, P, i64, P, sz, P]),
         "ubqp_best": (ctypes.c_int, [P, P, i64, i32, P, P, P]),
         "ubqp_relink_workspace_size": (sz, [P, i64, i32]),
         "ubqp_server_inject_alloc_failures": (ctypes.c_int, [P, i32]),
@@ -347,6 +349,28 @@ def ascent(inst: Instance, X: torch.Tensor, f: torch.Tensor, idx: torch.Tensor,
     return flips
 
 
+def ascent_trace(inst: Instance, X: torch.Tensor, f: torch.Tensor, idx: torch.Tensor,
+                 count: torch.Tensor, ldt: int, max_flips: int = 0,
+                 flips: torch.Tensor | None = None, trace: torch.Tensor | None = None,
+                 ws: torch.Tensor | None = None, stream=None):
+    """ubqp_ascent_trace: the ascent of X[idx[:count]] in place, with start s's
+    flipped indices in order in trace[s, :min(flips[s], ldt)] (uint16 values
+    held in an int16 tensor of S x ldt; read them with .view(torch.uint16) or
+    numpy's .view(np.uint16)).  Returns (flips, trace)."""
+    S = X.shape[0]
+    if flips is None:
+        flips = torch.zeros(S, dtype=torch.int32, device=X.device)
+    if trace is None:
+        trace = torch.zeros((S, ldt), dtype=torch.int16, device=X.device)
+    if ws is None:
+        ws = torch.empty(max(ascent_workspace_size(inst, S), 16), dtype=torch.uint8,
+                         device=X.device)
+    _check(load().ubqp_ascent_trace(inst.handle, _ptr(X), _ptr(f), _ptr(idx), _ptr(count), S,
+                                    max_flips, _ptr(flips), _ptr(trace), ldt, _ptr(ws),
+                                    ws.numel(), _stream(stream)))
+    return flips, trace
+
+
 def relink_workspace_size(inst: Instance, P: int, tensor_startup: bool = True) -> int:
     return int(load().ubqp_relink_workspace_size(inst.handle, P, 1 if tensor_startup else 0))
 
@@ -509,14 +533,22 @@ class Server:
         """Fault injection: the next `count` admissions fail as out of memory."""
         _check(load().ubqp_server_inject_alloc_failures(self._h, count))
 
-    def submit(self, Q, seed: int) -> int:
-        """Q: a host int8 array or CPU tensor (n x ldq), kept alive until wait()."""
+    def submit(self, Q, seed: int, n: int | None = None, offset: int = 0) -> int:
+        """Q: a host int8 array or CPU tensor (rows x ldq), kept alive until
+        wait().  With n (and offset) the request's instance is the principal
+        submatrix Q[offset:offset+n, offset:offset+n], passed in place (row
+        stride ldq, no copy)."""
         import numpy as _np
         if isinstance(Q, torch.Tensor):
-            ptr, (n, ldq) = Q.data_ptr(), Q.shape
+            assert Q.dtype == torch.int8 and Q.dim() == 2 and Q.stride(1) == 1
+            ptr, rows, ldq = Q.data_ptr(), Q.shape[0], Q.stride(0)
         else:
             Q = _np.ascontiguousarray(Q, dtype=_np.int8)
-            ptr, (n, ldq) = Q.ctypes.data, Q.shape
+            ptr, (rows, ldq) = Q.ctypes.data, Q.shape
+        n = rows if n is None else int(n)
+        if offset < 0 or offset + n > min(rows, ldq):
+            raise ValueError("principal submatrix outside Q")
+        ptr += offset * ldq + offset
         t = ctypes.c_int64()
         _check(load().ubqp_server_submit(self._h, ctypes.c_void_p(ptr), n, ldq, seed % 2**64,
                                          ctypes.byref(t)))

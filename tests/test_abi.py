@@ -34,7 +34,7 @@ def test_library_exports_every_declared_symbol():
 
 def test_strerror_and_version():
     lib = ubqp.load()
-    assert lib.ubqp_abi_version() == 4
+    assert lib.ubqp_abi_version() == 5
     for st, name in ubqp.STATUS_NAMES.items():
         assert lib.ubqp_strerror(st)
     assert lib.ubqp_strerror(0) == b"ok"
@@ -57,6 +57,9 @@ def test_host_side_argument_errors():
     assert lib.ubqp_solve(None, ctypes.byref(p), None, None, None, None, 0, None) == -1
     assert lib.ubqp_eval_workspace_size(None, 10, 0) == 0
     assert lib.ubqp_q_info(None, None, None, None, None, None) == -1
+    assert lib.ubqp_ascent_trace(None, None, None, None, None, 1, 0, None, None, 4, None, 0,
+                                 None) == -1
+    assert b"trace" in lib.ubqp_last_error()
     lib.ubqp_q_destroy(None)  # no-op
     # relinking, search, batch plans and the server validate on the host too
     assert lib.ubqp_relink(None, None, None, None, 4, None, None, None, None, 0, None) == -1
