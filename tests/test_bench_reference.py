@@ -23,7 +23,7 @@ def test_reference_arm_prints_one_line():
     assert len(lines) == 1
     d = json.loads(lines[0])
     assert d["impl"] == "reference" and d["value"] > 0 and d["higher_is_better"] is True
-    assert d["steps"] == 2 and d["warmup"] == 1 and d["unit"] == "evals/s"
+    assert d["steps"] == 2 and d["warmup"] == 1 and d["unit"] == "starts/s"
     cb = d["cpu_baseline"]
     assert cb["kind"] == "oracle" and cb["cores"] == (os.cpu_count() or 1)
     assert cb["value"] == d["value"]
