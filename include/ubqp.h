@@ -518,6 +518,31 @@ int ubqp_search_resume(const ubqp_q* q, const ubqp_search_params* p, int32_t fir
                        uint64_t* best_x_dev, int64_t* best_f_dev, int64_t* history_dev,
                        int64_t* stats_dev, void* ws, size_t ws_bytes, void* stream);
 
+/*
+ * Measurement helpers: the two rates the ascent's roofline is made of, measured
+ * on the device the library runs on (not part of the method; the paper has no
+ * counterpart).  The steepest ascent reads one int8 row of Q (n bytes) per move
+ * from L2 and does about 3n integer operations per move (the gain update, the
+ * key and the comparison of each element), so its moves/s are bounded by
+ * min(L2 read rate / n, integer rate / 3n).  Each call only enqueues one
+ * kernel on `stream`; the caller times it (CUDA events) and divides.
+ * ubqp_peak_l2_read -- `reps` passes of 16-byte reads (cached in L2, not L1)
+ *   over the caller's device buffer (16-byte aligned, `bytes` >= 16; a buffer
+ *   well below the L2 size stays resident there after the first pass), every
+ *   SM taking part.  Bytes read = reps * (bytes rounded down to 16).
+ *   sink_dev: one uint32 of device memory, written only for a buffer whose
+ *   words xor to a particular value (use a zero-filled buffer).
+ * ubqp_peak_int32 -- kind 0: independent int32 multiply-add chains (the int32
+ *   instruction rate); kind 1: the ascent's per-element update (dp4a gain
+ *   update, multiply-add key, three-way max), counted as 3 operations per
+ *   element.  ubqp_peak_int32_ops gives the operations one call performs on
+ *   the current device (0 for bad arguments).
+ */
+int ubqp_peak_l2_read(const void* buf_dev, size_t bytes, int32_t reps, uint32_t* sink_dev,
+                      void* stream);
+int64_t ubqp_peak_int32_ops(int32_t kind, int64_t iters);
+int ubqp_peak_int32(int32_t kind, int64_t iters, uint32_t* sink_dev, void* stream);
+
 #ifdef __cplusplus
 }
 #endif

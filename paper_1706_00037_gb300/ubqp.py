@@ -35,7 +35,7 @@ EXPORTS = ["ubqp_strerror", "ubqp_last_error", "ubqp_abi_version", "ubqp_q_prepa
            "ubqp_server_poll", "ubqp_server_request_bytes", "ubqp_server_destroy",
            "ubqp_relink_workspace_size", "ubqp_relink", "ubqp_server_inject_alloc_failures",
            "ubqp_selftest_timeout", "ubqp_search_resume", "ubqp_q_prepare_into_async",
-           "ubqp_ascent_trace"]
+           "ubqp_ascent_trace", "ubqp_peak_l2_read", "ubqp_peak_int32_ops", "ubqp_peak_int32"]
 
 
 class UbqpError(RuntimeError):
@@ -140,6 +140,9 @@ def load() -> ctypes.CDLL:
         "ubqp_server_poll": (ctypes.c_int, [P, i64, ctypes.POINTER(i32)]),
         "ubqp_server_request_bytes": (sz, [P, i32]),
         "ubqp_server_destroy": (None, [P]),
+        "ubqp_peak_l2_read": (ctypes.c_int, [P, sz, i32, P, P]),
+        "ubqp_peak_int32_ops": (i64, [i32, i64]),
+        "ubqp_peak_int32": (ctypes.c_int, [i32, i64, P, P]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -584,3 +587,32 @@ class Server:
             self.close()
         except Exception:
             pass
+
+
+def measure_peaks(l2_bytes: int = 64 << 20, reps: int = 20, int_iters: int = 200_000) -> dict:
+    """The ascent's roofline rates on the current device (ubqp_peak_*), timed
+    with CUDA events after one untimed warm-up launch each: L2 read GB/s over
+    an L2-resident buffer, the int32 multiply-add rate and the ascent's
+    element-update rate in Tops/s."""
+    lib = load()
+    dev = torch.cuda.current_device()
+    buf = torch.zeros(l2_bytes, dtype=torch.uint8, device=dev)
+    sink = torch.zeros(1, dtype=torch.int32, device=dev)
+    st = torch.cuda.current_stream()
+
+    def timed(fn):
+        fn()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(st)
+        fn()
+        e1.record(st)
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1) / 1e3
+
+    s = timed(lambda: _check(lib.ubqp_peak_l2_read(_ptr(buf), l2_bytes, reps, _ptr(sink),
+                                                   _stream())))
+    out = {"l2_read_gbs": l2_bytes // 16 * 16 * reps / s / 1e9, "l2_buffer_bytes": l2_bytes}
+    for kind, key in ((0, "int32_imad_tops"), (1, "ascent_update_tops")):
+        s = timed(lambda: _check(lib.ubqp_peak_int32(kind, int_iters, _ptr(sink), _stream())))
+        out[key] = lib.ubqp_peak_int32_ops(kind, int_iters) / s / 1e12
+    return out
