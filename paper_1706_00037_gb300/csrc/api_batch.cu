@@ -10,10 +10,15 @@
 //   join   one launch builds the work list (largest instances first), one
 //          persistent launch climbs every passing start of every instance,
 //          one launch takes each instance's best.
+// The climb is either one start per group of the plan's shape, or packed: a
+// 256-thread block climbs up to four starts of one instance at once in
+// sub-groups of 64 or 128 threads when the instance's n fits them.
 // The whole run can be captured into a CUDA graph and replayed (the seed lives
-// in device memory so a replay can use a new one).  An autotuner times the
-// candidate ascent group shapes, evaluation paths and stream counts on the
-// batch itself and keeps the fastest; every choice gives identical results.
+// in device memory so a replay can use a new one).  An autotuner times, on the
+// batch itself, the candidate ascent group shapes (plain and packed), the
+// evaluation path, the evaluation's schedule (K steps per work chunk: 16, 12
+// or 8) and the stream count, and keeps the fastest; every choice gives
+// identical results.
 #include <algorithm>
 #include <cstring>
 #include <new>
@@ -57,9 +62,18 @@ struct ubqp_batch {
   std::vector<void*> scratch;            // per instance: unpacked starts, then y
   std::vector<size_t> scratch_bytes;
   std::vector<TmaDesc> mapA;             // TMA descriptor of each scratch
+  int4* d_units = nullptr;               // packed ascent: units of up to 4 items
+  int64_t* d_nunits = nullptr;           // 16 bytes: unit count, then the unit counter
+  // evaluation schedules: per instance, chunk tables of at most 8 and 12 K steps
+  // (the handle's own table has 16)
+  static constexpr int kAltKch[2] = {8, 12};
+  std::vector<int4*> alt_chunks[2];
+  std::vector<int> alt_nchunks[2];
   // configuration (autotuned)
   int asc_T = 256, asc_C = 1, eval_path = UBQP_EVAL_TC, nstreams = 8;
   int asc_grid = 0;
+  bool packed = false;                   // packed ascent (sub-groups by n)
+  int eval_kch = 16;                     // K steps per evaluation chunk
   int max_n = 0;
   std::vector<cudaStream_t> streams;
   std::vector<cudaEvent_t> ev_join;
@@ -95,9 +109,12 @@ int run_body(ubqp_batch* b, cudaStream_t st) {
                                       p.num_starts, p.div_H, d.X, s, b->d_seed));
     if (b->eval_path == UBQP_EVAL_TC) {
       // fused operand build up to n_pad 4096, staged above (as UBQP_EVAL_AUTO)
+      const int alt = b->eval_kch == ubqp_batch::kAltKch[0] ? 0
+                      : b->eval_kch == ubqp_batch::kAltKch[1] ? 1 : -1;
       UBQP_BCUDA(ubqp::launch_eval_tc(q, d.X, p.num_starts, d.f, b->scratch[i],
                                       b->scratch_bytes[i], s, b->mapA[i].bytes,
-                                      q->n_tc <= 4096));
+                                      q->n_tc <= 4096, alt >= 0 ? b->alt_chunks[alt][i] : nullptr,
+                                      alt >= 0 ? b->alt_nchunks[alt][i] : 0));
     } else {
       UBQP_BCUDA(ubqp::launch_eval_plain(q, d.X, p.num_starts, d.f, s));
     }
@@ -125,13 +142,22 @@ int run_body(ubqp_batch* b, cudaStream_t st) {
     UBQP_BCUDA(cudaStreamWaitEvent(st, b->ev_join[k], 0));
   }
   // ---- one launch each: work list, every climb, every best
-  UBQP_BCUDA(ubqp::launch_batch_items(b->d_desc, b->d_order, b->count, b->d_items, b->d_nitems,
-                                      st));
-  // the item counter: the second word of the 16-byte item-count slot
-  UBQP_BCUDA(ubqp::launch_ascent_batch(b->d_desc, b->d_items, b->d_nitems, b->asc_T, b->asc_C,
-                                       p.max_flips, b->asc_grid,
-                                       reinterpret_cast<unsigned long long*>(b->d_nitems + 1),
-                                       st));
+  if (b->packed) {
+    UBQP_BCUDA(ubqp::launch_batch_units(b->d_desc, b->d_order, b->count, b->asc_T, b->asc_C,
+                                        b->d_items, b->d_units, b->d_nunits, st));
+    // the unit counter: the second word of the 16-byte unit-count slot
+    UBQP_BCUDA(ubqp::launch_ascent_batch_packed(
+        b->d_desc, b->d_items, b->d_units, b->d_nunits, b->asc_T, b->asc_C, p.max_flips,
+        b->asc_grid, reinterpret_cast<unsigned long long*>(b->d_nunits + 1), st));
+  } else {
+    UBQP_BCUDA(ubqp::launch_batch_items(b->d_desc, b->d_order, b->count, b->d_items,
+                                        b->d_nitems, st));
+    // the item counter: the second word of the 16-byte item-count slot
+    UBQP_BCUDA(ubqp::launch_ascent_batch(b->d_desc, b->d_items, b->d_nitems, b->asc_T, b->asc_C,
+                                         p.max_flips, b->asc_grid,
+                                         reinterpret_cast<unsigned long long*>(b->d_nitems + 1),
+                                         st));
+  }
   UBQP_BCUDA(ubqp::launch_best_batch(b->d_desc, b->count, st));
   return UBQP_OK;
 }
@@ -143,12 +169,16 @@ void drop_graph(ubqp_batch* b) {
   b->graph = nullptr;
 }
 
-int set_shape(ubqp_batch* b, int T, int C) {
-  if (!ubqp::ascent_batch_supported(T, C) || 16 * T * C < b->max_n)
+int set_shape(ubqp_batch* b, int T, int C, bool packed = false) {
+  if (packed ? !ubqp::ascent_packed_supported(T, C) : !ubqp::ascent_batch_supported(T, C))
+    return bfail(UBQP_ERR_UNSUPPORTED, "ascent shape %dx%d not built", T, C);
+  if (16 * T * C < b->max_n)
     return bfail(UBQP_ERR_UNSUPPORTED, "ascent shape %dx%d cannot hold n=%d", T, C, b->max_n);
   b->asc_T = T;
   b->asc_C = C;
-  b->asc_grid = ubqp::ascent_batch_grid(T, C, b->sm_count);
+  b->packed = packed;
+  b->asc_grid = packed ? ubqp::ascent_packed_grid(T, C, b->sm_count)
+                       : ubqp::ascent_batch_grid(T, C, b->sm_count);
   return UBQP_OK;
 }
 
@@ -211,7 +241,20 @@ int ubqp_batch_create(const ubqp_q* const* qs, int32_t count, const ubqp_params*
   const size_t o_order = take(sizeof(int32_t) * count);
   const size_t o_items = take(sizeof(int2) * (size_t)S * count);
   const size_t o_nitems = take(16);
+  const size_t o_units = take(sizeof(int4) * (size_t)S * count);
+  const size_t o_nunits = take(16);
   const size_t o_seed = take(16);
+  // the alternative evaluation schedules of each instance
+  std::vector<std::vector<int4>> alt_tab[2];
+  std::vector<size_t> o_alt[2];
+  for (int a = 0; a < 2; ++a) {
+    for (int i = 0; i < count; ++i) {
+      alt_tab[a].push_back(qs[i]->tc_ok ? ubqp::eval_tc_chunks(qs[i]->n_tc,
+                                                               ubqp_batch::kAltKch[a])
+                                        : std::vector<int4>());
+      o_alt[a].push_back(take(sizeof(int4) * std::max<size_t>(alt_tab[a][i].size(), 1)));
+    }
+  }
   struct Off {
     size_t X, f, idx, count, Tm, stats, flips, bx, bf, scratch, scratch_bytes;
   };
@@ -242,6 +285,20 @@ int ubqp_batch_create(const ubqp_q* const* qs, int32_t count, const ubqp_params*
   b->d_order = (int32_t*)(b->dmem + o_order);
   b->d_items = (int2*)(b->dmem + o_items);
   b->d_nitems = (int64_t*)(b->dmem + o_nitems);
+  b->d_units = (int4*)(b->dmem + o_units);
+  b->d_nunits = (int64_t*)(b->dmem + o_nunits);
+  for (int a = 0; a < 2; ++a) {
+    for (int i = 0; i < count; ++i) {
+      b->alt_chunks[a].push_back((int4*)(b->dmem + o_alt[a][i]));
+      b->alt_nchunks[a].push_back((int)alt_tab[a][i].size());
+      if (!alt_tab[a][i].empty() &&
+          cudaMemcpy(b->alt_chunks[a][i], alt_tab[a][i].data(),
+                     sizeof(int4) * alt_tab[a][i].size(), cudaMemcpyHostToDevice) != cudaSuccess) {
+        ubqp_batch_destroy(b);
+        return bfail(UBQP_ERR_CUDA, "schedule upload failed");
+      }
+    }
+  }
   b->d_seed = (uint64_t*)(b->dmem + o_seed);
   b->h_desc.resize(count);
   b->scratch.resize(count);
@@ -384,15 +441,25 @@ int ubqp_batch_tune(ubqp_batch* b, void* stream) {
     const int shapes[8][2] = {{64, 1}, {64, 2}, {128, 1}, {128, 2},
                               {256, 1}, {256, 2}, {512, 1}, {512, 2}};
     int bt = b->asc_T, bc = b->asc_C;
+    bool bp = b->packed;
     for (auto& sh : shapes) {
-      if (16 * sh[0] * sh[1] < b->max_n || (sh[0] == bt && sh[1] == bc)) continue;
+      if (16 * sh[0] * sh[1] < b->max_n || (!bp && sh[0] == bt && sh[1] == bc)) continue;
       if (16 * sh[0] * sh[1] > 4 * std::max(b->max_n, 1024)) continue;  // far too wide
       if ((r = set_shape(b, sh[0], sh[1]))) goto done;
       float t = 0;
       if ((r = time_run(&t))) goto done;
-      if (t < cur) { cur = t; bt = sh[0]; bc = sh[1]; }
+      if (t < cur) { cur = t; bt = sh[0]; bc = sh[1]; bp = false; }
     }
     if ((r = set_shape(b, bt, bc))) goto done;
+    // the packed ascent (sub-groups of 256, 128 or 64 threads by n)
+    for (int c : {1, 2}) {
+      if (16 * 256 * c < b->max_n || 16 * 256 * c > 4 * std::max(b->max_n, 1024)) continue;
+      if ((r = set_shape(b, 256, c, true))) goto done;
+      float t = 0;
+      if ((r = time_run(&t))) goto done;
+      if (t < cur) { cur = t; bt = 256; bc = c; bp = true; }
+    }
+    if ((r = set_shape(b, bt, bc, bp))) goto done;
   }
   {  // evaluation path
     bool all_tc = true;
@@ -404,6 +471,18 @@ int ubqp_batch_tune(ubqp_batch* b, void* stream) {
       if ((r = time_run(&t))) goto done;
       if (t < cur) cur = t; else b->eval_path = keep;
     }
+  }
+  if (b->eval_path == UBQP_EVAL_TC) {  // evaluation schedule: K steps per work chunk
+    const int keep = b->eval_kch;
+    int bestk = keep;
+    for (int k : {16, ubqp_batch::kAltKch[1], ubqp_batch::kAltKch[0]}) {
+      if (k == keep) continue;
+      b->eval_kch = k;
+      float t = 0;
+      if ((r = time_run(&t))) goto done;
+      if (t < cur) { cur = t; bestk = k; }
+    }
+    b->eval_kch = bestk;
   }
   {  // fork/join streams
     const int keep = b->nstreams;
@@ -431,6 +510,25 @@ int ubqp_batch_config(const ubqp_batch* b, int32_t* asc_threads, int32_t* asc_ch
   if (eval_path) *eval_path = b->eval_path;
   if (streams) *streams = b->nstreams;
   if (graph) *graph = b->exec != nullptr;
+  return UBQP_OK;
+}
+
+int ubqp_batch_set(ubqp_batch* b, int32_t asc_threads, int32_t asc_chunks, int32_t packed,
+                   int32_t eval_kch) {
+  if (!b) return bfail(UBQP_ERR_ARG, "batch is NULL");
+  if (eval_kch != 16 && eval_kch != ubqp_batch::kAltKch[0] && eval_kch != ubqp_batch::kAltKch[1])
+    return bfail(UBQP_ERR_ARG, "eval_kch must be 8, 12 or 16");
+  const int r = set_shape(b, asc_threads, asc_chunks, packed != 0);
+  if (r) return r;
+  drop_graph(b);
+  b->eval_kch = eval_kch;
+  return UBQP_OK;
+}
+
+int ubqp_batch_schedule(const ubqp_batch* b, int32_t* packed, int32_t* eval_kch) {
+  if (!b) return bfail(UBQP_ERR_ARG, "batch is NULL");
+  if (packed) *packed = b->packed ? 1 : 0;
+  if (eval_kch) *eval_kch = b->eval_kch;
   return UBQP_OK;
 }
 

@@ -138,6 +138,63 @@ struct Group {
   }
 };
 
+// TS consecutive threads of a larger block owning one start (TS >= 64, a
+// multiple of 32): the block-group operations of Group<TS> on the named
+// barrier `bar` (1..15) instead of the block-wide one, so that several
+// sub-groups of one block climb different starts independently.
+__device__ __forceinline__ void named_sync(int bar, int count) {
+  asm volatile("bar.sync %0, %1;" ::"r"(bar), "r"(count) : "memory");
+}
+__device__ __forceinline__ bool named_or(int bar, int count, bool p) {
+  uint32_t out;
+  asm volatile(
+      "{\n .reg .pred pi, po;\n setp.ne.u32 pi, %1, 0;\n"
+      " bar.red.or.pred po, %2, %3, pi;\n selp.u32 %0, 1, 0, po;\n}\n"
+      : "=r"(out)
+      : "r"((uint32_t)p), "r"(bar), "r"(count)
+      : "memory");
+  return out != 0;
+}
+
+template <int TS>
+struct SubGroup {
+  static constexpr int NW = TS / 32;
+  int2 (*rec)[NW];  // [2][NW] shared, this sub-group's
+  int parity;
+  int base;  // first thread of the sub-group
+  int bar;   // its named barrier
+  __device__ __forceinline__ int rank() const { return (int)threadIdx.x - base; }
+  int2 mine;
+  __device__ __forceinline__ int2 reduce(int gain, int jx) {
+    const int lane = threadIdx.x & 31, warp = rank() >> 5;
+    const int m = __reduce_max_sync(0xffffffffu, gain);
+    const int c = __reduce_min_sync(0xffffffffu, gain == m ? jx : INT_MAX);
+    if (lane == 0) rec[parity][warp] = make_int2(m, c);
+    named_sync(bar, TS);
+    const int2 r = lane < NW ? rec[parity][lane] : make_int2(INT_MIN, INT_MAX);
+    const int m2 = __reduce_max_sync(0xffffffffu, r.x);
+    const int c2 = __reduce_min_sync(0xffffffffu, r.x == m2 ? r.y : INT_MAX);
+    parity ^= 1;
+    mine = r;
+    return make_int2(m2, c2);
+  }
+  template <int R>
+  __device__ __forceinline__ void runners(int first, int* cand) const {
+    runners_up<R>(mine, first, cand);
+  }
+  __device__ __forceinline__ bool any(bool p) { return named_or(bar, TS, p); }
+  __device__ __forceinline__ void sync() { named_sync(bar, TS); }
+  __device__ __forceinline__ int sum(int v) {
+    const int lane = threadIdx.x & 31, warp = rank() >> 5;
+    const int sv = __reduce_add_sync(0xffffffffu, v);
+    if (lane == 0) rec[parity][warp] = make_int2(sv, 0);
+    named_sync(bar, TS);
+    const int r = lane < NW ? rec[parity][lane].x : 0;
+    parity ^= 1;
+    return __reduce_add_sync(0xffffffffu, r);
+  }
+};
+
 // Path relinking of one pair (see relink_block_kernel): the guiding solution,
 // the outputs and a trace of the flipped indices (n entries of scratch).
 struct RelinkArgs {
@@ -154,7 +211,7 @@ struct RelinkArgs {
 // candidates, every step is taken whatever its gain, a flipped variable leaves
 // the candidate set, and the best solution strictly between the endpoints is
 // the result.
-template <int T, int C, int R, bool RL = false, bool TR = false>
+template <int T, int C, int R, bool RL = false, bool TR = false, class G = Group<T>>
 __device__ __forceinline__ void ascend_one(const int8_t* __restrict__ Q8, int64_t ldq,
                                            int64_t ldy, int n,
                                            int W, uint64_t* __restrict__ x_g,
@@ -162,7 +219,7 @@ __device__ __forceinline__ void ascend_one(const int8_t* __restrict__ Q8, int64_
                                            int32_t* __restrict__ flips_s,
                                            unsigned* __restrict__ err, uint64_t* xs,
                                            uint4* spec_slots,
-                                           const float* __restrict__ y_g, Group<T>& grp,
+                                           const float* __restrict__ y_g, G& grp,
                                            const RelinkArgs* rl = nullptr,
                                            uint16_t* __restrict__ trace_row = nullptr,
                                            int64_t trace_cap = 0) {
@@ -521,6 +578,74 @@ ascent_batch_kernel(const BatchDesc* __restrict__ d, const int2* __restrict__ it
     ascend_one<T, C, R>(b.Q8, b.ldq, b.ldy, b.n, b.W, b.X + (int64_t)s * b.W, b.f + s, max_flips,
                      b.flips ? b.flips + s : nullptr, b.err, xs, spec_slots,
                      b.Y ? b.Y + (int64_t)it.y * b.ldy : nullptr, grp);
+  }
+}
+
+// All passing starts of a batch of instances in one persistent launch, packed
+// by size: a work unit is up to 2^cls starts of one instance (cls 0, 1, 2),
+// climbed together by the block's 2^cls sub-groups of T >> cls threads (the
+// smallest sub-group whose 16 (T >> cls) C elements hold the instance's n), so
+// that a block climbs four small starts at once instead of one with mostly
+// idle elements.  Units run largest instances first: the first wave one per
+// block, the rest from the counter *next.
+template <int T, int C, int R, int TS>
+__device__ __forceinline__ void climb_packed(const BatchDesc* __restrict__ d,
+                                             const int2* __restrict__ items, int4 un,
+                                             int32_t max_flips, int2* rec_flat, uint64_t* xs,
+                                             uint4* spec_slots) {
+  constexpr int K = T / TS;  // sub-groups per block
+  const int sg = (int)threadIdx.x / TS;
+  if (sg >= un.z) return;
+  const int2 it = items[un.y + sg];
+  const BatchDesc& b = d[it.x];
+  if (b.err[1] != 0) return;  // Q failed its symmetry check: no climb
+  const int s = b.idx[it.y];
+  if (s < 0 || s >= b.S) {
+    if ((int)threadIdx.x == sg * TS) atomicOr(b.err, UBQP_DEVERR_BADIDX);
+    return;
+  }
+  if constexpr (K == 1) {
+    Group<T> grp{reinterpret_cast<int2 (*)[T / 32]>(rec_flat), 0};
+    ascend_one<T, C, R>(b.Q8, b.ldq, b.ldy, b.n, b.W, b.X + (int64_t)s * b.W, b.f + s, max_flips,
+                        b.flips ? b.flips + s : nullptr, b.err, xs, spec_slots,
+                        b.Y ? b.Y + (int64_t)it.y * b.ldy : nullptr, grp);
+  } else {
+    SubGroup<TS> grp{reinterpret_cast<int2 (*)[TS / 32]>(rec_flat + sg * 2 * (TS / 32)), 0,
+                     sg * TS, 1 + sg};
+    ascend_one<TS, C, R>(b.Q8, b.ldq, b.ldy, b.n, b.W, b.X + (int64_t)s * b.W, b.f + s,
+                         max_flips, b.flips ? b.flips + s : nullptr, b.err,
+                         xs + sg * (TS * C / 4), spec_slots + sg * spec_slot_count<TS, C, R>(),
+                         b.Y ? b.Y + (int64_t)it.y * b.ldy : nullptr, grp);
+  }
+}
+
+template <int T, int C, int R>
+__global__ void __launch_bounds__(T, 2)
+ascent_batch_packed_kernel(const BatchDesc* __restrict__ d, const int2* __restrict__ items,
+                           const int4* __restrict__ units, const int64_t* __restrict__ n_units,
+                           int32_t max_flips, unsigned long long* __restrict__ next) {
+  static_assert(T / 4 >= 64, "sub-groups of at least two warps");
+  __shared__ int2 rec_flat[2 * (T / 32)];
+  __shared__ uint64_t xs[T * C / 4];
+  __shared__ uint4 spec_slots[spec_slot_count<T, C, R>()];
+  __shared__ unsigned long long ticket;
+  const int64_t cnt = *n_units;
+  auto take = [&](int64_t t) -> int64_t {
+    if (t < 0) return blockIdx.x;
+    if (!next) return t + gridDim.x;
+    if (threadIdx.x == 0) ticket = atomicAdd(next, 1ull);
+    __syncthreads();
+    const int64_t v = (int64_t)gridDim.x + (int64_t)ticket;
+    __syncthreads();
+    return v;
+  };
+  for (int64_t t = take(-1); t < cnt; t = take(t)) {
+    const int4 un = units[t];
+    if (un.x == 0) climb_packed<T, C, R, T>(d, items, un, max_flips, rec_flat, xs, spec_slots);
+    else if (un.x == 1)
+      climb_packed<T, C, R, T / 2>(d, items, un, max_flips, rec_flat, xs, spec_slots);
+    else climb_packed<T, C, R, T / 4>(d, items, un, max_flips, rec_flat, xs, spec_slots);
+    __syncthreads();  // every sub-group done before the block takes the next unit
   }
 }
 

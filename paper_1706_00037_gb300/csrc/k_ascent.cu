@@ -89,6 +89,42 @@ cudaError_t launch_ascent_batch(const BatchDesc* d, const int2* items, const int
   return cudaErrorInvalidValue;
 }
 
+bool ascent_packed_supported(int T, int C) { return T == 256 && (C == 1 || C == 2); }
+
+int ascent_packed_grid(int T, int C, int sm_count) {
+  int per_sm = 0;
+  cudaError_t e = cudaErrorInvalidValue;
+  if (T == 256 && C == 1)
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(
+        &per_sm, ascent_batch_packed_kernel<256, 1, kSpecRows>, 256, 0);
+  if (T == 256 && C == 2)
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(
+        &per_sm, ascent_batch_packed_kernel<256, 2, kSpecRows>, 256, 0);
+  if (e != cudaSuccess || per_sm < 1) {
+    cudaGetLastError();
+    per_sm = 1;
+  }
+  return per_sm * sm_count;
+}
+
+cudaError_t launch_ascent_batch_packed(const BatchDesc* d, const int2* items, const int4* units,
+                                       const int64_t* n_units, int T, int C, int32_t max_flips,
+                                       int grid, unsigned long long* next, cudaStream_t st) {
+  if (next) {
+    cudaError_t e = cudaMemsetAsync(next, 0, sizeof(unsigned long long), st);
+    if (e != cudaSuccess) return e;
+  }
+  if (T == 256 && C == 1)
+    ascent_batch_packed_kernel<256, 1, kSpecRows><<<grid, 256, 0, st>>>(d, items, units, n_units,
+                                                                         max_flips, next);
+  else if (T == 256 && C == 2)
+    ascent_batch_packed_kernel<256, 2, kSpecRows><<<grid, 256, 0, st>>>(d, items, units, n_units,
+                                                                         max_flips, next);
+  else
+    return cudaErrorInvalidValue;
+  return cudaGetLastError();
+}
+
 cudaError_t launch_ascent(const ubqp_q* h, uint64_t* X, int64_t* f, const int32_t* idx,
                           const int64_t* count, int64_t S, int32_t max_flips, int32_t* flips,
                           const float* Y, unsigned long long* next, cudaStream_t st) {

@@ -70,6 +70,34 @@ batch_items_kernel(const BatchDesc* __restrict__ d, const int32_t* __restrict__ 
   if (threadIdx.x == 0) *n_items = base;
 }
 
+// The work list of the packed batch ascent: the items as batch_items_kernel
+// writes them, and units {cls, first item, items in the unit, 0} of up to
+// 2^cls items of one instance, cls the largest of 0, 1, 2 whose sub-group of
+// T >> cls threads (16 (T >> cls) C elements) holds the instance's n.
+__global__ void __launch_bounds__(THREADS)
+batch_units_kernel(const BatchDesc* __restrict__ d, const int32_t* __restrict__ order, int count,
+                   int T, int C, int2* __restrict__ items, int4* __restrict__ units,
+                   int64_t* __restrict__ n_units) {
+  int64_t base = 0, ubase = 0;
+  for (int k = 0; k < count; ++k) {
+    const int i = order[k];
+    const int64_t c = *d[i].count;
+    const int n = d[i].n;
+    const int cls = n <= 16 * (T >> 2) * C ? 2 : n <= 16 * (T >> 1) * C ? 1 : 0;
+    const int64_t per = (int64_t)1 << cls;
+    const int64_t nu = (c + per - 1) / per;
+    for (int64_t t = threadIdx.x; t < c; t += THREADS) items[base + t] = make_int2(i, (int)t);
+    for (int64_t u = threadIdx.x; u < nu; u += THREADS) {
+      const int64_t first = u * per;
+      const int64_t m = c - first < per ? c - first : per;
+      units[ubase + u] = make_int4(cls, (int)(base + first), (int)m, 0);
+    }
+    base += c;
+    ubase += nu;
+  }
+  if (threadIdx.x == 0) *n_units = ubase;
+}
+
 // out = {passed, total flips, max flips of one start, batch max, best index, sum}
 __global__ void __launch_bounds__(THREADS)
 solve_stats_kernel(const int64_t* __restrict__ count, const int32_t* __restrict__ idx,
@@ -166,6 +194,12 @@ cudaError_t launch_best_batch(const BatchDesc* d, int count, cudaStream_t st) {
 cudaError_t launch_batch_items(const BatchDesc* d, const int32_t* order, int count, int2* items,
                                int64_t* n_items, cudaStream_t st) {
   batch_items_kernel<<<1, THREADS, 0, st>>>(d, order, count, items, n_items);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_batch_units(const BatchDesc* d, const int32_t* order, int count, int T, int C,
+                               int2* items, int4* units, int64_t* n_units, cudaStream_t st) {
+  batch_units_kernel<<<1, THREADS, 0, st>>>(d, order, count, T, C, items, units, n_units);
   return cudaGetLastError();
 }
 

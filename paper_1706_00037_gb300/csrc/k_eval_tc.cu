@@ -288,12 +288,13 @@ eval_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ 
 
   if (threadIdx.x == 0) {
     for (int s = 0; s < STAGES; ++s) {
-      mbar_init(&full[s], FUSED ? 1 + A_WRITERS : 1);  // TMA arrival (+ the A writers)
+      // the TMA arrival (+ one arrival per A-writer warp)
+      mbar_init(&full[s], FUSED ? 1 + A_WRITERS / 32 : 1);
       mbar_init(&empty[s], 1);
     }
     for (int a = 0; a < 2; ++a) {
       mbar_init(&tfull[a], 1);
-      mbar_init(&tempty[a], 128);
+      mbar_init(&tempty[a], 4);  // one arrival per epilogue warp
     }
     mbar_init(drain, 1);
     *abort_flag = 0;
@@ -406,7 +407,9 @@ eval_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ 
       for (int ks = 0; ks < KCH; ++ks) {
         if (ks >= un.nk) break;
         const uint64_t w0 = wa[ks];
-        if (!mbar_wait(&empty[stage], phase ^ 1u, abort_flag, err)) {
+        // the warp arrives as one below: leave together
+        const bool got = mbar_wait(&empty[stage], phase ^ 1u, abort_flag, err);
+        if (!__all_sync(0xffffffffu, got)) {
           ok = false;
           break;
         }
@@ -420,9 +423,11 @@ eval_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ 
           *reinterpret_cast<uint4*>(r0 + (((2 * p + 1) ^ (t & 7)) << 4)) =
               make_uint4(v[4], v[5], v[6], v[7]);
         }
-        // make the generic-proxy writes visible to the tensor cores' reads
+        // make the generic-proxy writes visible to the tensor cores' reads,
+        // then one arrival for the warp's 32 rows
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-        mbar_arrive(&full[stage]);
+        __syncwarp();
+        if (lane == 0) mbar_arrive(&full[stage]);
         if (++stage == STAGES) {
           stage = 0;
           phase ^= 1u;
@@ -440,7 +445,9 @@ eval_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ 
       const Unit un = unit_of(chunks, m_tiles, u);
       const int a = t & 1;
       const uint32_t aphase = (uint32_t)((t >> 1) & 1);
-      if (!mbar_wait(&tfull[a], aphase, abort_flag, err)) break;
+      // the warp arrives as one on tempty below: leave together
+      const bool got = mbar_wait(&tfull[a], aphase, abort_flag, err);
+      if (!__all_sync(0xffffffffu, got)) break;
       tc_fence_after();
       const int64_t s = (int64_t)un.mt * BM + row;
       const uint32_t base = tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(a * BN);
@@ -460,7 +467,8 @@ eval_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ 
           }
         }
         tc_fence_before();
-        mbar_arrive(&tempty[a]);
+        __syncwarp();
+        if (lane == 0) mbar_arrive(&tempty[a]);
       } else {
         uint64_t xw[4];
 #pragma unroll
@@ -479,7 +487,8 @@ eval_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ 
             if ((bits >> i) & 1u) acc += __float2int_rn(__uint_as_float(r[i]));
         }
         tc_fence_before();
-        mbar_arrive(&tempty[a]);
+        __syncwarp();
+        if (lane == 0) mbar_arrive(&tempty[a]);
         if (s < S && acc != 0)
           atomicAdd(reinterpret_cast<unsigned long long*>(&f[s]),
                     (unsigned long long)(long long)acc);
@@ -530,12 +539,12 @@ eval_ts_kernel(const __grid_constant__ CUtensorMap tmB, const uint64_t* __restri
       mbar_init(&emptyB[s], 1);
     }
     for (int s = 0; s < STAGES_A_TS; ++s) {
-      mbar_init(&fullA[s], A_WRITERS_TS);
+      mbar_init(&fullA[s], A_WRITERS_TS / 32);  // one arrival per writer warp
       mbar_init(&emptyA[s], 1);
     }
     for (int a = 0; a < 2; ++a) {
       mbar_init(&tfull[a], 1);
-      mbar_init(&tempty[a], 128);
+      mbar_init(&tempty[a], 4);  // one arrival per epilogue warp
     }
     mbar_init(drain, 1);
     *abort_flag = 0;
@@ -668,7 +677,8 @@ eval_ts_kernel(const __grid_constant__ CUtensorMap tmB, const uint64_t* __restri
         }
         tmem_st16(tA + (uint32_t)(stage * (BK / 2)), v);
         tc_fence_before();
-        mbar_arrive(&fullA[stage]);
+        __syncwarp();
+        if (lane == 0) mbar_arrive(&fullA[stage]);
         if (++stage == STAGES_A_TS) {
           stage = 0;
           phase ^= 1u;
@@ -708,7 +718,8 @@ eval_ts_kernel(const __grid_constant__ CUtensorMap tmB, const uint64_t* __restri
           if ((bits >> i) & 1u) acc += __float2int_rn(__uint_as_float(r[i]));
       }
       tc_fence_before();
-      mbar_arrive(&tempty[a]);
+      __syncwarp();
+      if (lane == 0) mbar_arrive(&tempty[a]);
       if (s < S && acc != 0)
         atomicAdd(reinterpret_cast<unsigned long long*>(&f[s]), (unsigned long long)(long long)acc);
     }
@@ -920,13 +931,13 @@ size_t eval_tc_workspace(const ubqp_q* h, int64_t S) {
 // triangle); ascent start-up (y = Q x): the full K range for every J.  Both are
 // split into near-equal chunks of at most KCH steps.
 // N-blocks of bn columns over n_tc; the K range of block J is capped at n_tc.
-static std::vector<int4> make_chunks(int n_tc, int bn, bool full) {
+static std::vector<int4> make_chunks(int n_tc, int bn, bool full, int kch = KCH) {
   std::vector<int4> ch;
   const int NB = (n_tc + bn - 1) / bn;
   const int nk_full = n_tc / BK;
   for (int J = 0; J < NB; ++J) {
     const int nk = full ? nk_full : std::min((J + 1) * (bn / BK), nk_full);
-    const int parts = (nk + KCH - 1) / KCH;
+    const int parts = (nk + kch - 1) / kch;
     for (int p = 0, k0 = 0; p < parts; ++p) {
       const int len = nk / parts + (p < nk % parts ? 1 : 0);
       ch.push_back(make_int4(J, k0, len, 0));
@@ -935,6 +946,12 @@ static std::vector<int4> make_chunks(int n_tc, int bn, bool full) {
   }
   std::stable_sort(ch.begin(), ch.end(), [](const int4& a, const int4& b) { return a.z > b.z; });
   return ch;
+}
+
+// The evaluation's work chunks with at most kch (1..16) K steps of 64 each
+// (the handle's own table uses 16): a schedule a batch plan may tune.
+std::vector<int4> eval_tc_chunks(int n_tc, int kch) {
+  return make_chunks(n_tc, BN, false, std::max(1, std::min(kch, KCH)));
 }
 
 size_t eval_tc_chunk_bytes(int n_tc) {
@@ -1053,7 +1070,8 @@ cudaError_t launch_eval_ts(const ubqp_q* h, const uint64_t* X, int64_t S, int64_
 }
 
 cudaError_t launch_eval_tc(const ubqp_q* h, const uint64_t* X, int64_t S, int64_t* f, void* ws,
-                           size_t ws_bytes, cudaStream_t st, const void* mapA_in, bool fused) {
+                           size_t ws_bytes, cudaStream_t st, const void* mapA_in, bool fused,
+                           const int4* chunks_in, int nchunks_in) {
   if (!h->tc_ok) return cudaErrorNotSupported;
   const int64_t S_p = padded_starts(S);
   cudaError_t e;
@@ -1074,19 +1092,20 @@ cudaError_t launch_eval_tc(const ubqp_q* h, const uint64_t* X, int64_t S, int64_
   }
   if ((e = cudaMemsetAsync(f, 0, sizeof(int64_t) * S, st))) return e;
   const int m_tiles = (int)(S_p / BM);
-  const int n_units = h->tc_nchunks * m_tiles;
+  const int4* ch = chunks_in ? chunks_in : reinterpret_cast<const int4*>(h->tc_chunks);
+  const int nch = chunks_in ? nchunks_in : h->tc_nchunks;
+  const int n_units = nch * m_tiles;
   const int grid = n_units < h->sm_count ? n_units : h->sm_count;
   const CUtensorMap& mapB = *reinterpret_cast<const CUtensorMap*>(h->tc_mapB);
-  const int4* ch = reinterpret_cast<const int4*>(h->tc_chunks);
   if (fused) {
     if ((e = set_smem_attr_once<false, true>())) return e;
     eval_tc_kernel<false, true><<<grid, THREADS_FUSED, SMEM_BYTES_FUSED, st>>>(
-        mapA, mapB, X, h->n, h->W, S, m_tiles, ch, h->tc_nchunks, f, nullptr, nullptr, 0,
+        mapA, mapB, X, h->n, h->W, S, m_tiles, ch, nch, f, nullptr, nullptr, 0,
         h->err);
   } else {
     if ((e = set_smem_attr_once<false, false>())) return e;
     eval_tc_kernel<false, false><<<grid, THREADS, SMEM_BYTES, st>>>(
-        mapA, mapB, X, h->n, h->W, S, m_tiles, ch, h->tc_nchunks, f, nullptr, nullptr, 0,
+        mapA, mapB, X, h->n, h->W, S, m_tiles, ch, nch, f, nullptr, nullptr, 0,
         h->err);
   }
   return cudaGetLastError();

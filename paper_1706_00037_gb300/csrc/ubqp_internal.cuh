@@ -5,6 +5,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <vector>
+
 #include "../../include/ubqp.h"
 
 #define UBQP_ROW_ALIGN 1024  // row stride of the int8 copy (ascent rows)
@@ -126,6 +128,7 @@ size_t eval_tc_workspace(const ubqp_q* h, int64_t S);
 cudaError_t eval_tc_upload_tables(ubqp_q* h, cudaStream_t st);
 cudaError_t eval_tc_prepare(ubqp_q* h, cudaStream_t st);
 size_t eval_tc_chunk_bytes(int n_tc);
+std::vector<int4> eval_tc_chunks(int n_tc, int kch);
 size_t eval_tc_static_capacity();
 size_t ascent_tc_workspace(const ubqp_q* h, int64_t S);
 cudaError_t launch_ascent_init_tc(const ubqp_q* h, const uint64_t* X, const int32_t* idx,
@@ -137,9 +140,12 @@ cudaError_t eval_tc_static_scratch(void** out);
 // eval_tc_map_A, or nullptr to build one per call.
 // fused: build the A operand in shared memory from the bits (no workspace);
 // otherwise unpack into ws first and feed both operands by TMA.
+// chunks_in / nchunks_in: a work-chunk table in device memory (as
+// eval_tc_chunks makes) in place of the handle's own.
 cudaError_t launch_eval_tc(const ubqp_q* h, const uint64_t* X, int64_t S, int64_t* f,
                            void* ws, size_t ws_bytes, cudaStream_t st,
-                           const void* mapA_in = nullptr, bool fused = false);
+                           const void* mapA_in = nullptr, bool fused = false,
+                           const int4* chunks_in = nullptr, int nchunks_in = 0);
 bool eval_tc_map_A(void* out128, const void* Xe, int64_t S, int n_tc);
 cudaError_t launch_screen_stats(const int64_t* f, int64_t S, int64_t offset, int64_t* stats,
                                 cudaStream_t st);
@@ -183,6 +189,15 @@ cudaError_t launch_batch_items(const BatchDesc* d, const int32_t* order, int cou
 cudaError_t launch_ascent_batch(const BatchDesc* d, const int2* items, const int64_t* n_items,
                                 int T, int C, int32_t max_flips, int grid,
                                 unsigned long long* next, cudaStream_t st);
+// packed batch ascent: units of up to 4 starts of one instance per block of T
+// threads (sub-groups of T, T/2 or T/4 threads by n)
+cudaError_t launch_batch_units(const BatchDesc* d, const int32_t* order, int count, int T, int C,
+                               int2* items, int4* units, int64_t* n_units, cudaStream_t st);
+cudaError_t launch_ascent_batch_packed(const BatchDesc* d, const int2* items, const int4* units,
+                                       const int64_t* n_units, int T, int C, int32_t max_flips,
+                                       int grid, unsigned long long* next, cudaStream_t st);
+bool ascent_packed_supported(int T, int C);
+int ascent_packed_grid(int T, int C, int sm_count);
 int ascent_batch_grid(int T, int C, int sm_count);
 bool ascent_batch_supported(int T, int C);
 cudaError_t launch_best_batch(const BatchDesc* d, int count, cudaStream_t st);

@@ -35,7 +35,8 @@ EXPORTS = ["ubqp_strerror", "ubqp_last_error", "ubqp_abi_version", "ubqp_q_prepa
            "ubqp_server_poll", "ubqp_server_request_bytes", "ubqp_server_destroy",
            "ubqp_relink_workspace_size", "ubqp_relink", "ubqp_server_inject_alloc_failures",
            "ubqp_selftest_timeout", "ubqp_search_resume", "ubqp_q_prepare_into_async",
-           "ubqp_ascent_trace", "ubqp_peak_l2_read", "ubqp_peak_int32_ops", "ubqp_peak_int32"]
+           "ubqp_ascent_trace", "ubqp_peak_l2_read", "ubqp_peak_int32_ops", "ubqp_peak_int32",
+           "ubqp_batch_schedule", "ubqp_batch_set"]
 
 
 class UbqpError(RuntimeError):
@@ -130,6 +131,8 @@ def load() -> ctypes.CDLL:
         "ubqp_batch_capture": (ctypes.c_int, [P, P]),
         "ubqp_batch_result": (ctypes.c_int, [P, i32, ctypes.POINTER(P), ctypes.POINTER(P)]),
         "ubqp_batch_config": (ctypes.c_int, [P, P, P, P, P, P]),
+        "ubqp_batch_schedule": (ctypes.c_int, [P, P, P]),
+        "ubqp_batch_set": (ctypes.c_int, [P, i32, i32, i32, i32]),
         "ubqp_batch_get": (ctypes.c_int, [P, i32, P, P, P]),
         "ubqp_q_arena_size": (sz, [i32]),
         "ubqp_q_prepare_into": (ctypes.c_int, [P, i32, i64, P, sz, P, ctypes.POINTER(P)]),
@@ -501,14 +504,22 @@ class Batch:
     def tune(self, stream=None):
         _check(load().ubqp_batch_tune(self._h, _stream(stream)))
 
+    def set(self, asc_threads: int, asc_chunks: int, packed: bool = False, eval_kch: int = 16):
+        """Pin the configuration (ubqp_batch_set) instead of tuning it."""
+        _check(load().ubqp_batch_set(self._h, asc_threads, asc_chunks, int(packed), eval_kch))
+
     def capture(self, stream=None):
         _check(load().ubqp_batch_capture(self._h, _stream(stream)))
 
     def config(self) -> dict:
         v = [ctypes.c_int32() for _ in range(5)]
         _check(load().ubqp_batch_config(self._h, *[ctypes.byref(x) for x in v]))
-        return dict(zip(["asc_threads", "asc_chunks", "eval_path", "streams", "graph"],
-                        [x.value for x in v]))
+        out = dict(zip(["asc_threads", "asc_chunks", "eval_path", "streams", "graph"],
+                       [x.value for x in v]))
+        pk, kch = ctypes.c_int32(), ctypes.c_int32()
+        _check(load().ubqp_batch_schedule(self._h, ctypes.byref(pk), ctypes.byref(kch)))
+        out.update(packed=pk.value, eval_kch=kch.value)
+        return out
 
     def result(self, i: int, stream=None):
         """(best_x words, {value, index}) of instance i, copied to new tensors."""

@@ -77,3 +77,43 @@ def test_batch_plain_eval_path():
     b.run(seed=9)
     torch.cuda.synchronize()
     check_against_single(insts, b, p, 9)
+
+
+@pytest.mark.parametrize("shape,packed,kch", [((256, 1), True, 16), ((256, 2), True, 8),
+                                              ((256, 1), False, 12), ((128, 2), False, 8)])
+def test_batch_pinned_schedules_equal_single_solves(shape, packed, kch):
+    # packed climbs (sub-groups of 64 / 128 / 256 threads by n, several starts
+    # of one instance per block) and every evaluation schedule give the same
+    # results as single solves, with the graph too
+    sizes = [60, 700, 2500, 300, 1025, 129, 2100, 513, 1024, 1023, 2048, 2049]
+    dens = [1.0, 0.1, 0.5, 1.0, 0.1, 0.5, 1.0, 0.1, 0.5, 1.0, 0.1, 0.5]
+    Qs, insts = make_batch(sizes, dens, seed0=700)
+    p = ubqp.make_params(257, 0.3, seed=4)
+    b = ubqp.Batch(insts, p)
+    b.set(shape[0], shape[1], packed=packed, eval_kch=kch)
+    cfg = b.config()
+    assert (cfg["asc_threads"], cfg["asc_chunks"], cfg["packed"], cfg["eval_kch"]) == \
+        (shape[0], shape[1], int(packed), kch)
+    b.run(seed=21)
+    torch.cuda.synchronize()
+    check_against_single(insts, b, p, 21)
+    b.capture()
+    b.run(seed=22)
+    torch.cuda.synchronize()
+    check_against_single(insts, b, p, 22)
+    for i in (0, 3):
+        want = orc.solve(Qs[i], 257, 0.3, seed=22)
+        bx, bf = b.result(i)
+        assert int(bf[0]) == want["best_f"] and int(bf[1]) == want["best_index"]
+        assert np.array_equal(bx.cpu().numpy().view(np.uint64), want["best_x"])
+
+
+def test_batch_set_rejects_shapes_that_cannot_hold_n():
+    Qs, insts = make_batch([3000, 100], [0.5, 0.5], seed0=900)
+    b = ubqp.Batch(insts, ubqp.make_params(64, 0.5, seed=1))
+    with pytest.raises(ubqp.UbqpError):
+        b.set(128, 1)          # 2048 elements < 3000
+    with pytest.raises(ubqp.UbqpError):
+        b.set(128, 2, packed=True)  # packed blocks are 256 threads
+    with pytest.raises(ubqp.UbqpError):
+        b.set(256, 1, eval_kch=5)
