@@ -292,13 +292,9 @@ def run_reference(a):
 # --------------------------------------------------------------------- GPU arm
 
 def batch_instances(count=64, seed=4):
-    """64 instances: n ~ U[200, 2500], density in {0.1, 0.5, 1.0}, seeds 4000+k."""
+    """64 instances: n ~ U[200, 2500], density in {0.1, 0.5, 1.0} (synth.batch_specs)."""
     from paper_1706_00037_gb300 import synth
-    r = np.random.default_rng(seed)
-    ns = r.integers(200, 2501, count)
-    ds = r.choice([0.1, 0.5, 1.0], count)
-    return [(int(n), float(d), synth.make_instance(int(n), float(d), 4000 + k))
-            for k, (n, d) in enumerate(zip(ns, ds))]
+    return [(n, d, synth.make_instance(n, d, s)) for n, d, s in synth.batch_specs(count, seed)]
 
 
 def run_batch64(a):
@@ -363,82 +359,91 @@ def run_batch64(a):
     print(json.dumps(line), flush=True)
 
 
-def serve_pool(count=24, seed=5):
-    """Request instances: n log-uniform in [500, 7000], density in {0.1, 1.0}."""
-    from paper_1706_00037_gb300 import synth
-    r = np.random.default_rng(seed)
-    ns = np.exp(r.uniform(np.log(500), np.log(7000), count)).astype(int)
-    ds = r.choice([0.1, 1.0], count)
-    return [(int(n), float(d), synth.make_instance(int(n), float(d), 5000 + k))
-            for k, (n, d) in enumerate(zip(ns, ds))]
-
-
-def serve_measure(duration_s: float, rate: float = 200.0, workers: int = 8, seed: int = 5,
-                  seq_requests: int = 300):
-    """Poisson arrivals at `rate` req/s for `duration_s` into the request loop;
-    returns served solves/s, latency percentiles and the one-at-a-time rate."""
+def serve_measure(duration_s: float, rate: float = 200.0, workers: int = 4, seed: int = 5,
+                  seq_requests: int = 100, max_batch: int = 16):
+    """Poisson arrivals at `rate` req/s for `duration_s` into the request loop,
+    each request its own instance (synth.serve_requests: n log-uniform on
+    [500, 7000], density in {0.1, 1.0}, a principal submatrix of a seeded
+    n = 8192 master passed in place); returns served solves/s, latency
+    percentiles, the saturated rate and the one-at-a-time rate."""
     import threading
     import torch
-    from paper_1706_00037_gb300 import ubqp
-    pool = serve_pool()
-    pinned = [torch.from_numpy(Q).pin_memory() for _, _, Q in pool]
+    from paper_1706_00037_gb300 import synth, ubqp
+    masters_np = {d: synth.serve_master(d) for d in (0.1, 1.0)}
+    masters = {d: torch.from_numpy(M).pin_memory() for d, M in masters_np.items()}
     S, lam = 1024, 0.5
     params = ubqp.make_params(S, lam, seed=0)
     r = np.random.default_rng(seed)
     gaps = r.exponential(1.0 / rate, int(rate * duration_s * 1.2) + 16)
     t_arr = np.cumsum(gaps)
     t_arr = t_arr[t_arr < duration_s]
-    which = r.integers(0, len(pool), t_arr.shape[0])
-    srv = ubqp.Server(workers, max(n for n, _, _ in pool), params)
-    for k in range(2 * workers):  # warm-up (module loading, pool growth)
-        srv.wait(srv.submit(pinned[k % len(pool)], 10**6 + k))
+    reqs = synth.serve_requests(len(t_arr) + 1200, seed)
+    srv = ubqp.Server(workers, synth.SERVE_MASTER_N, params, max_batch=max_batch)
+    for k in range(4 * workers):  # warm-up (module loading, pool growth)
+        n, d, o = reqs[-1 - k]
+        srv.wait(srv.submit(masters[d], 10**6 + k, n=n, offset=o))
     tickets = [None] * len(t_arr)
     t0 = time.perf_counter()
 
     def submitter():
-        for k, (ta, i) in enumerate(zip(t_arr, which)):
-            d = t0 + ta - time.perf_counter()
-            if d > 0:
-                time.sleep(d)
-            tickets[k] = srv.submit(pinned[i], k)
+        for k, ta in enumerate(t_arr):
+            dly = t0 + ta - time.perf_counter()
+            if dly > 0:
+                time.sleep(dly)
+            n, d, o = reqs[k]
+            tickets[k] = srv.submit(masters[d], k, n=n, offset=o)
 
+    st0 = srv.stats()
     th = threading.Thread(target=submitter)
     th.start()
     th.join()
     res = [srv.wait(t) for t in tickets]
     t_end = time.perf_counter()
-    # capacity: the same request mix submitted at once (a saturating burst)
-    burst = min(len(t_arr), 1200)
+    st1 = srv.stats()
+    # capacity: the next requests of the mix submitted at once (a saturating burst)
+    burst = 1200
     tb = time.perf_counter()
-    bt = [srv.submit(pinned[which[k]], k) for k in range(burst)]
+    bt = [srv.submit(masters[d], 2 * 10**6 + k, n=n, offset=o)
+          for k, (n, d, o) in enumerate(reqs[len(t_arr):len(t_arr) + burst])]
     for t in bt:
         srv.wait(t)
     t_burst = time.perf_counter() - tb
+    st2 = srv.stats()
     srv.close()
     lat = np.array([x[2] for x in res]) * 1e3
-    # the same requests one at a time through the public API (upload, prepare, solve)
+    # the first requests one at a time through the public API (upload,
+    # prepare, ubqp_solve, result back), each from a contiguous pinned copy
     m = min(seq_requests, len(res))
-    out_x = torch.empty(111, dtype=torch.int64).pin_memory()
+    copies = [torch.from_numpy(np.ascontiguousarray(masters_np[d][o:o + n, o:o + n])).pin_memory()
+              for n, d, o in reqs[:m]]
     same = True
     ts = time.perf_counter()
     for k in range(m):
-        Qd = pinned[which[k]].to("cuda", non_blocking=True)
-        inst = ubqp.Instance(Qd)
+        inst = ubqp.Instance(copies[k].to("cuda", non_blocking=True))
         params.seed = k
         bx, bf, _ = ubqp.solve(inst, params, want_stats=False)
         bfh = bf.cpu().tolist()
-        same = same and bfh == res[k][0]
+        same = same and bfh == res[k][0] and np.array_equal(
+            bx.cpu().numpy().view(np.uint64), res[k][1])
         inst.close()
     t_seq = time.perf_counter() - ts
+    ns = [n for n, _, _ in reqs[:len(t_arr)]]
     return {"served_solves_per_s": len(res) / (t_end - t0), "requests": len(res),
-            "offered_req_per_s": rate, "duration_s": duration_s, "workers": workers,
+            "offered_req_per_s": rate, "duration_s": duration_s, "lanes": workers,
+            "max_batch": max_batch,
+            "mean_batch_served": (st1["requests"] - st0["requests"]) /
+                                 max(st1["batches"] - st0["batches"], 1),
+            "mean_batch_saturated": (st2["requests"] - st1["requests"]) /
+                                    max(st2["batches"] - st1["batches"], 1),
             "p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99)),
             "max_ms": float(lat.max()),
             "saturated_solves_per_s": burst / t_burst, "saturating_burst": burst,
             "sequential_solves_per_s": m / t_seq, "sequential_requests": m,
             "results_identical_to_alone": bool(same),
-            "pool": {"instances": len(pool), "n": [n for n, _, _ in pool],
-                     "density": [d for _, d, _ in pool], "starts": S, "lambda": lam}}
+            "requests_mix": {"instances": "one per request: principal submatrix of a seeded "
+                                          "n=8192 master at a random offset",
+                             "n_mean": float(np.mean(ns)), "n_min": int(min(ns)),
+                             "n_max": int(max(ns)), "starts": S, "lambda": lam}}
 
 
 def run_serve(a):
@@ -449,7 +454,8 @@ def run_serve(a):
             "value": m["served_solves_per_s"], "unit": "solves/s", "n_gpus": 1,
             "steps": m["requests"], "warmup": 16, "ms_per_step": 1e3 / m["served_solves_per_s"],
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int64",
-            "data": "synthetic", "config": {"workload": "serve", **m["pool"]}, "serve": m}
+            "data": "synthetic", "config": {"workload": "serve", **m["requests_mix"]},
+            "serve": m}
     print(json.dumps(line), flush=True)
 
 
@@ -909,7 +915,7 @@ def main():
 
     served = None
     if rank == 0 and world == 1 and not a.no_serve:
-        served = serve_measure(a.serve_seconds or 10.0, seq_requests=150)
+        served = serve_measure(a.serve_seconds or 60.0)
 
     cpu = None
     if rank == 0 and world == 1 and not a.no_cpu:

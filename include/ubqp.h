@@ -407,18 +407,25 @@ int ubqp_batch_get(const ubqp_batch* b, int32_t i, uint64_t* best_x_dev, int64_t
                    void* stream);
 
 /*
- * Serving: a request loop that solves instances as they arrive.  A request is
- * one instance (host coefficients) solved by one round with the server's
- * parameters and its own seed; the result is bit-identical to ubqp_solve on
- * that instance alone.  `workers` threads, each with its own CUDA stream, take
- * requests in arrival order when a worker is free and the request's device
- * memory fits the budget, so requests that arrive while others run are
- * admitted as memory frees up and their kernels overlap on the GPU.  Request
- * memory comes from the device's stream-ordered pool.  The paper solves one
- * instance per run; serving is this library's addition.
+ * Serving: a request loop that solves instances as they arrive, with
+ * continuous batching.  A request is one instance (host coefficients) solved
+ * by one round with the server's parameters and its own seed; the result is
+ * bit-identical to ubqp_solve on that instance alone.  The server runs
+ * `workers` lanes (threads with their own CUDA streams).  A free lane admits,
+ * in arrival order, every waiting request that fits -- up to max_batch
+ * requests whose device memory fits the budget -- and runs them as one batch:
+ * per-request upload, preparation, start generation and evaluation on the
+ * lane's streams, then one shared launch each for the screen, the climb of
+ * every passing start of every request (one persistent launch, several small
+ * starts per block) and the best-of.  Requests that arrive while batches run
+ * are taken together by the next free lane, so batches grow with the load,
+ * and the lanes' batches overlap on the GPU.  Request memory comes from the
+ * device's stream-ordered pool.  The paper solves one instance per run;
+ * serving is this library's addition.
  *   memory_budget  device bytes the server's requests may hold together
  *                  (0 = workers x the bytes of a max_n request); a request
  *                  larger than the budget still runs, alone.
+ *   max_batch      requests one lane runs together (0 = 16; at most 1024).
  * ubqp_server_submit -- enqueue (returns at once with a ticket).  Q_host: n rows
  *   of ldq int8 coefficients in host memory that must stay valid until the
  *   request completes (pinned memory makes the upload asynchronous).  n above
@@ -431,10 +438,11 @@ int ubqp_batch_get(const ubqp_batch* b, int32_t i, uint64_t* best_x_dev, int64_t
  */
 typedef struct ubqp_server ubqp_server;
 typedef struct ubqp_server_config {
-  int32_t workers;        /* concurrent requests (threads and streams), 1..64 */
-  int32_t max_n;          /* largest n accepted                                */
-  int64_t memory_budget;  /* device bytes, 0 = derived                         */
-  ubqp_params params;     /* round parameters (seed comes from each request)   */
+  int32_t workers;        /* lanes: concurrent batches (threads, streams), 1..64 */
+  int32_t max_n;          /* largest n accepted                                  */
+  int64_t memory_budget;  /* device bytes, 0 = derived                           */
+  ubqp_params params;     /* round parameters (seed comes from each request)     */
+  int32_t max_batch;      /* requests per batch, 0 = 16                          */
 } ubqp_server_config;
 int ubqp_server_create(const ubqp_server_config* cfg, ubqp_server** out);
 int ubqp_server_submit(ubqp_server* s, const int8_t* Q_host, int32_t n, int64_t ldq,
@@ -444,6 +452,9 @@ int ubqp_server_wait(ubqp_server* s, int64_t ticket, int64_t* best_f, uint64_t* 
 int ubqp_server_poll(ubqp_server* s, int64_t ticket, int32_t* done);
 size_t ubqp_server_request_bytes(const ubqp_server* s, int32_t n);
 void ubqp_server_destroy(ubqp_server* s);
+/* Batches run so far, the requests they held and the largest batch (any
+ * pointer may NULL). */
+int ubqp_server_stats(ubqp_server* s, int64_t* batches, int64_t* requests, int64_t* largest);
 /* Fault injection (tests): the next `count` admitted requests fail as if their
  * device allocation had failed -- they complete with UBQP_ERR_NOMEM from
  * ubqp_server_wait, nothing is launched for them, and the server keeps

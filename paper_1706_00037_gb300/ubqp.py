@@ -36,7 +36,7 @@ EXPORTS = ["ubqp_strerror", "ubqp_last_error", "ubqp_abi_version", "ubqp_q_prepa
            "ubqp_relink_workspace_size", "ubqp_relink", "ubqp_server_inject_alloc_failures",
            "ubqp_selftest_timeout", "ubqp_search_resume", "ubqp_q_prepare_into_async",
            "ubqp_ascent_trace", "ubqp_peak_l2_read", "ubqp_peak_int32_ops", "ubqp_peak_int32",
-           "ubqp_batch_schedule", "ubqp_batch_set"]
+           "ubqp_batch_schedule", "ubqp_batch_set", "ubqp_server_stats"]
 
 
 class UbqpError(RuntimeError):
@@ -61,7 +61,8 @@ class SearchParams(ctypes.Structure):
 
 class ServerConfig(ctypes.Structure):
     _fields_ = [("workers", ctypes.c_int32), ("max_n", ctypes.c_int32),
-                ("memory_budget", ctypes.c_int64), ("params", Params)]
+                ("memory_budget", ctypes.c_int64), ("params", Params),
+                ("max_batch", ctypes.c_int32)]
 
 
 class Stats(ctypes.Structure):
@@ -143,6 +144,7 @@ def load() -> ctypes.CDLL:
         "ubqp_server_poll": (ctypes.c_int, [P, i64, ctypes.POINTER(i32)]),
         "ubqp_server_request_bytes": (sz, [P, i32]),
         "ubqp_server_destroy": (None, [P]),
+        "ubqp_server_stats": (ctypes.c_int, [P, P, P, P]),
         "ubqp_peak_l2_read": (ctypes.c_int, [P, sz, i32, P, P]),
         "ubqp_peak_int32_ops": (i64, [i32, i64]),
         "ubqp_peak_int32": (ctypes.c_int, [i32, i64, P, P]),
@@ -533,8 +535,11 @@ class Batch:
 class Server:
     """The request loop (ubqp_server_*): submit host instances, wait for results."""
 
-    def __init__(self, workers: int, max_n: int, params: Params, memory_budget: int = 0):
-        cfg = ServerConfig(workers, max_n, memory_budget, params)
+    def __init__(self, workers: int, max_n: int, params: Params, memory_budget: int = 0,
+                 max_batch: int = 0):
+        """workers: lanes (concurrent batches); max_batch: requests per batch
+        (0 = 16)."""
+        cfg = ServerConfig(workers, max_n, memory_budget, params, max_batch)
         h = ctypes.c_void_p()
         _check(load().ubqp_server_create(ctypes.byref(cfg), ctypes.byref(h)))
         self._h = h
@@ -568,6 +573,12 @@ class Server:
                                          ctypes.byref(t)))
         self._keep[t.value] = (Q, n)
         return t.value
+
+    def stats(self) -> dict:
+        """Batches run so far, the requests they held, the largest batch."""
+        v = [ctypes.c_int64() for _ in range(3)]
+        _check(load().ubqp_server_stats(self._h, *[ctypes.byref(x) for x in v]))
+        return dict(zip(["batches", "requests", "largest"], [x.value for x in v]))
 
     def poll(self, ticket: int) -> bool:
         d = ctypes.c_int32()

@@ -142,3 +142,43 @@ def test_bounded_wait_gives_up_and_context_stays_usable():
     f = ubqp.eval(inst, X)
     inst.sync()
     assert np.array_equal(f.cpu().numpy(), orc.eval(Q, X.cpu().numpy().view(np.uint64)))
+
+
+@pytest.mark.parametrize("max_n,sizes", [
+    (3000, [(2500, 1.0), (100, 0.1), (700, 0.5), (1500, 0.1), (3000, 0.5), (129, 1.0)]),
+    (7000, [(7000, 1.0), (4500, 0.1), (600, 1.0), (2100, 0.5)]),      # packed 256 x 2
+    (9000, [(8500, 0.1), (300, 0.5), (5000, 1.0)]),                    # one start per block
+])
+def test_server_batches_requests_and_results_equal_alone(max_n, sizes):
+    # one lane, requests submitted together: the lane runs them as shared
+    # batches (one screen, one climb and one best-of launch per batch), and
+    # every result equals the instance solved alone
+    Qs = [synth.make_instance(n, d, 80 + k) for k, (n, d) in enumerate(sizes)]
+    params = ubqp.make_params(300, 0.5, seed=0)
+    srv = ubqp.Server(1, max_n, params, max_batch=8, memory_budget=1 << 40)
+    reqs = [(k % len(Qs), 2000 + k) for k in range(2 * len(Qs) + 1)]
+    tickets = [srv.submit(Qs[i], seed) for i, seed in reqs]
+    got = [srv.wait(t) for t in tickets]
+    st = srv.stats()
+    srv.close()
+    assert st["requests"] == len(reqs) and st["batches"] < len(reqs) and st["largest"] > 1
+    for (i, seed), (bf, bx, _) in zip(reqs, got):
+        wf, wx = alone(Qs[i], params, seed)
+        assert bf == wf and np.array_equal(bx, wx), (i, seed)
+
+
+def test_server_principal_submatrix_requests():
+    # a request passed as a principal submatrix of a larger host matrix, in
+    # place (row stride of the larger matrix)
+    M = synth.make_instance(1500, 0.4, 91)
+    params = ubqp.make_params(200, 0.5, seed=0)
+    srv = ubqp.Server(2, 1500, params)
+    Mt = torch.from_numpy(M).pin_memory()
+    cases = [(700, 0), (900, 333), (1, 1499), (1500, 0)]
+    tickets = [srv.submit(Mt, 40 + k, n=n, offset=o) for k, (n, o) in enumerate(cases)]
+    got = [srv.wait(t) for t in tickets]
+    srv.close()
+    for k, ((n, o), (bf, bx, _)) in enumerate(zip(cases, got)):
+        Q = np.ascontiguousarray(M[o:o + n, o:o + n])
+        want = orc.solve(Q, 200, 0.5, seed=40 + k)
+        assert bf == [want["best_f"], want["best_index"]] and np.array_equal(bx, want["best_x"])
