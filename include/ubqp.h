@@ -355,11 +355,15 @@ int ubqp_solve(const ubqp_q* q, const ubqp_params* p, uint64_t* best_x_dev,
 
 /*
  * Batches of instances: one round (as ubqp_solve, with the same parameters) for
- * every instance of a batch of uneven n, run together.  Per-instance start
- * generation and evaluation run concurrently on internal streams; the screen,
- * the ascent of every passing start of every instance (one persistent launch,
- * largest instances first) and the best-of are one launch each.  Each
- * instance's result is bit-identical to ubqp_solve on that instance alone.
+ * every instance of a batch of uneven n, run together.  Start generation and
+ * the tensor-core evaluation are one launch each for all instances (the
+ * evaluation one persistent launch over the work units of every instance) or,
+ * as the tuner decides, per-instance launches on internal streams; the
+ * screen, the ascent of every passing start of every instance (one persistent
+ * launch, largest instances first) and the best-of are one launch each; the
+ * start-up products y = Q x of the passing starts run per instance on the
+ * internal streams.  Each instance's result is bit-identical to ubqp_solve on
+ * that instance alone.
  *
  * ubqp_batch_create -- plan a batch over `count` prepared instances (all on the
  *   current device; the handles must outlive the plan).  Allocates the plan's
@@ -371,21 +375,27 @@ int ubqp_solve(const ubqp_q* q, const ubqp_params* p, uint64_t* best_x_dev,
  *   group shapes (threads x chunks that hold the largest n, one start per
  *   group, or packed: 256-thread blocks climbing up to four starts of one
  *   instance in sub-groups of 64 or 128 threads when its n fits them), the
- *   evaluation paths, the evaluation's schedule (at most 16, 12 or 8 K steps
- *   of 64 per work chunk) and the fork/join stream counts on this batch and
- *   keeps the fastest; drops a captured graph.  Synchronises `stream`.
+ *   evaluation paths, one merged launch for the start generation and the
+ *   tensor-core evaluation of all instances (one persistent launch over the
+ *   work units of every instance, largest first) or one launch per instance,
+ *   the evaluation's schedule (at most 16, 12 or 8 K steps of 64 per work
+ *   chunk) and the fork/join stream counts on this batch and keeps the
+ *   fastest; drops a captured graph.  Synchronises `stream`.
  * ubqp_batch_capture -- records one run into a CUDA graph (after one plain
  *   run); later ubqp_batch_run calls replay it.  Synchronises `stream`.
  * ubqp_batch_result -- device pointers to instance i's best solution (W words)
  *   and {value, start index} (2 int64), valid after the run completes.
  * ubqp_batch_config -- the configuration in use (any pointer may be NULL).
  * ubqp_batch_schedule -- the rest of it: *packed = 1 when the climb is packed,
- *   *eval_kch = the K steps per evaluation work chunk (any pointer may be NULL).
+ *   *eval_kch = the K steps per evaluation work chunk, *eval_merged = 1 when
+ *   start generation and the evaluation of all instances are one launch each
+ *   (any pointer may be NULL).
  * ubqp_batch_set -- pin the configuration instead of tuning it: ascent group
  *   shape (threads x chunks; packed: 256 x 1 or 256 x 2, else 64..512 x 1..2,
- *   holding the largest n), packed 0/1, eval_kch 8, 12 or 16; drops a captured
- *   graph.  UBQP_ERR_UNSUPPORTED for a shape that is not built or cannot hold
- *   the largest n.
+ *   holding the largest n), packed 0/1, eval_kch 8, 12 or 16, eval_merged 0/1
+ *   (1 needs the tensor-core evaluation); drops a captured graph.
+ *   UBQP_ERR_UNSUPPORTED for a shape that is not built or cannot hold the
+ *   largest n, or a merged evaluation without the tensor-core path.
  * The paper runs one instance at a time; batching is this library's addition.
  */
 typedef struct ubqp_batch ubqp_batch;
@@ -399,9 +409,10 @@ int ubqp_batch_result(const ubqp_batch* b, int32_t i, const uint64_t** best_x_de
                       const int64_t** best_f_dev);
 int ubqp_batch_config(const ubqp_batch* b, int32_t* asc_threads, int32_t* asc_chunks,
                       int32_t* eval_path, int32_t* streams, int32_t* graph);
-int ubqp_batch_schedule(const ubqp_batch* b, int32_t* packed, int32_t* eval_kch);
+int ubqp_batch_schedule(const ubqp_batch* b, int32_t* packed, int32_t* eval_kch,
+                        int32_t* eval_merged);
 int ubqp_batch_set(ubqp_batch* b, int32_t asc_threads, int32_t asc_chunks, int32_t packed,
-                   int32_t eval_kch);
+                   int32_t eval_kch, int32_t eval_merged);
 /* Copies instance i's result to caller memory (W words, 2 int64), async. */
 int ubqp_batch_get(const ubqp_batch* b, int32_t i, uint64_t* best_x_dev, int64_t* best_f_dev,
                    void* stream);

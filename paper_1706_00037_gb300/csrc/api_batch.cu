@@ -10,15 +10,19 @@
 //   join   one launch builds the work list (largest instances first), one
 //          persistent launch climbs every passing start of every instance,
 //          one launch takes each instance's best.
+// With the tensor-core evaluation the first two steps can instead be one
+// launch each for all instances: start generation, then one persistent
+// evaluation over the merged work list (instance, chunk, m-tile) of every
+// instance, largest chunks first.
 // The climb is either one start per group of the plan's shape, or packed: a
 // 256-thread block climbs up to four starts of one instance at once in
 // sub-groups of 64 or 128 threads when the instance's n fits them.
 // The whole run can be captured into a CUDA graph and replayed (the seed lives
 // in device memory so a replay can use a new one).  An autotuner times, on the
 // batch itself, the candidate ascent group shapes (plain and packed), the
-// evaluation path, the evaluation's schedule (K steps per work chunk: 16, 12
-// or 8) and the stream count, and keeps the fastest; every choice gives
-// identical results.
+// evaluation path, one merged evaluation launch or one per instance, the
+// evaluation's schedule (K steps per work chunk: 16, 12 or 8) and the stream
+// count, and keeps the fastest; every choice gives identical results.
 #include <algorithm>
 #include <cstring>
 #include <new>
@@ -73,7 +77,16 @@ struct ubqp_batch {
   int asc_T = 256, asc_C = 1, eval_path = UBQP_EVAL_TC, nstreams = 8;
   int asc_grid = 0;
   bool packed = false;                   // packed ascent (sub-groups by n)
-  int eval_kch = 16;                     // K steps per evaluation chunk
+  int eval_kch = 16;                     // K steps per evaluation work chunk
+  // the merged evaluation: start generation and the tensor-core evaluation of
+  // every instance in one launch each (work lists for 16, 12 and 8 K steps)
+  bool eval_merged = false;
+  bool merged_ok = false;
+  ubqp::EvalInst* d_einst = nullptr;
+  void* d_maps = nullptr;
+  ubqp::MUnit* d_munits[3] = {nullptr, nullptr, nullptr};
+  int n_munits[3] = {0, 0, 0};
+  int64_t max_words = 0;
   int max_n = 0;
   std::vector<cudaStream_t> streams;
   std::vector<cudaEvent_t> ev_join;
@@ -95,9 +108,20 @@ void pick_default_shape(ubqp_batch* b) {
 }
 
 // One run of the batch on `stream` (capturable: no host synchronisation).
+int kch_slot(int kch) { return kch == 16 ? 0 : kch == 12 ? 1 : 2; }
+
 int run_body(ubqp_batch* b, cudaStream_t st) {
   const int K = std::min<int>(b->nstreams, (int)b->streams.size());
   const ubqp_params& p = b->p;
+  if (b->eval_merged && b->eval_path == UBQP_EVAL_TC) {
+    // ---- one launch each: every instance's starts (values and flip counts
+    // zeroed), every instance's evaluation
+    UBQP_BCUDA(ubqp::launch_diversify_batch(b->d_desc, b->count, b->max_words, p.mode,
+                                            b->d_seed, p.round, p.div_H, st));
+    const int k = kch_slot(b->eval_kch);
+    UBQP_BCUDA(ubqp::launch_eval_tc_multi(b->d_einst, b->d_maps, b->d_munits[k], b->n_munits[k],
+                                          b->qs[0]->err, b->sm_count, st));
+  } else {
   // ---- fork: start generation and evaluation per instance
   UBQP_BCUDA(cudaEventRecord(b->ev_fork, st));
   for (int k = 0; k < K; ++k) UBQP_BCUDA(cudaStreamWaitEvent(b->streams[k], b->ev_fork, 0));
@@ -123,6 +147,7 @@ int run_body(ubqp_batch* b, cudaStream_t st) {
   for (int k = 0; k < K; ++k) {
     UBQP_BCUDA(cudaEventRecord(b->ev_join[k], b->streams[k]));
     UBQP_BCUDA(cudaStreamWaitEvent(st, b->ev_join[k], 0));
+  }
   }
   // ---- one launch: every instance's screen
   UBQP_BCUDA(ubqp::launch_screen_batch(b->d_desc, b->count, p.lambda, st));
@@ -244,6 +269,17 @@ int ubqp_batch_create(const ubqp_q* const* qs, int32_t count, const ubqp_params*
   const size_t o_units = take(sizeof(int4) * (size_t)S * count);
   const size_t o_nunits = take(16);
   const size_t o_seed = take(16);
+  // the merged evaluation: instances, tensor maps, work lists
+  const size_t o_einst = take(sizeof(ubqp::EvalInst) * count);
+  const size_t o_maps = take(128 * (size_t)count);
+  bool all_tc = true;
+  for (int i = 0; i < count; ++i) all_tc = all_tc && qs[i]->tc_ok;
+  std::vector<ubqp::MUnit> mu[3];
+  size_t o_mu[3] = {0, 0, 0};
+  for (int k = 0; k < 3; ++k) {
+    if (all_tc) mu[k] = ubqp::eval_tc_multi_units(qs, count, S, k == 0 ? 16 : k == 1 ? 12 : 8);
+    o_mu[k] = take(sizeof(ubqp::MUnit) * std::max<size_t>(mu[k].size(), 1));
+  }
   // the alternative evaluation schedules of each instance
   std::vector<std::vector<int4>> alt_tab[2];
   std::vector<size_t> o_alt[2];
@@ -286,6 +322,19 @@ int ubqp_batch_create(const ubqp_q* const* qs, int32_t count, const ubqp_params*
   b->d_items = (int2*)(b->dmem + o_items);
   b->d_nitems = (int64_t*)(b->dmem + o_nitems);
   b->d_units = (int4*)(b->dmem + o_units);
+  b->d_einst = (ubqp::EvalInst*)(b->dmem + o_einst);
+  b->d_maps = b->dmem + o_maps;
+  b->merged_ok = all_tc;
+  for (int k = 0; k < 3; ++k) {
+    b->d_munits[k] = (ubqp::MUnit*)(b->dmem + o_mu[k]);
+    b->n_munits[k] = (int)mu[k].size();
+    if (!mu[k].empty() && cudaMemcpy(b->d_munits[k], mu[k].data(),
+                                     sizeof(ubqp::MUnit) * mu[k].size(),
+                                     cudaMemcpyHostToDevice) != cudaSuccess) {
+      ubqp_batch_destroy(b);
+      return bfail(UBQP_ERR_CUDA, "work list upload failed");
+    }
+  }
   b->d_nunits = (int64_t*)(b->dmem + o_nunits);
   for (int a = 0; a < 2; ++a) {
     for (int i = 0; i < count; ++i) {
@@ -308,6 +357,7 @@ int ubqp_batch_create(const ubqp_q* const* qs, int32_t count, const ubqp_params*
     const ubqp_q* q = qs[i];
     const Off& o = offs[i];
     ubqp::BatchDesc& d = b->h_desc[i];
+    d.x0 = q->x0;
     d.Q8 = q->Q8;
     d.ldq = q->ldq;
     d.n = q->n;
@@ -332,6 +382,22 @@ int ubqp_batch_create(const ubqp_q* const* qs, int32_t count, const ubqp_params*
     // TMA descriptor of the unpacked starts in this instance's scratch
     if (q->tc_ok && !ubqp::eval_tc_map_A(b->mapA[i].bytes, b->scratch[i], S, q->n_tc))
       d.Y = nullptr;
+  }
+  {
+    std::vector<ubqp::EvalInst> ei(count);
+    std::vector<unsigned char> maps(128 * (size_t)count);
+    for (int i = 0; i < count; ++i) {
+      const ubqp::BatchDesc& d = b->h_desc[i];
+      ei[i] = ubqp::EvalInst{d.X, d.f, d.S, d.n, d.W};
+      b->max_words = std::max<int64_t>(b->max_words, d.S * d.W);
+      memcpy(maps.data() + 128 * (size_t)i, qs[i]->tc_mapB, 128);
+    }
+    if (cudaMemcpy(b->d_einst, ei.data(), sizeof(ubqp::EvalInst) * count,
+                   cudaMemcpyHostToDevice) != cudaSuccess ||
+        cudaMemcpy(b->d_maps, maps.data(), maps.size(), cudaMemcpyHostToDevice) != cudaSuccess) {
+      ubqp_batch_destroy(b);
+      return bfail(UBQP_ERR_CUDA, "descriptor upload failed");
+    }
   }
   if (cudaMemcpy(b->d_desc, b->h_desc.data(), sizeof(ubqp::BatchDesc) * count,
                  cudaMemcpyHostToDevice) != cudaSuccess ||
@@ -361,6 +427,7 @@ int ubqp_batch_create(const ubqp_q* const* qs, int32_t count, const ubqp_params*
   b->eval_path = p->eval_path == UBQP_EVAL_PLAIN ? UBQP_EVAL_PLAIN : UBQP_EVAL_TC;  // TC = fused
   for (int i = 0; i < count && b->eval_path == UBQP_EVAL_TC; ++i)
     if (!qs[i]->tc_ok) b->eval_path = UBQP_EVAL_PLAIN;
+  b->eval_merged = b->merged_ok && b->eval_path == UBQP_EVAL_TC;
   int r = set_shape(b, b->asc_T, b->asc_C);
   if (r) {
     ubqp_batch_destroy(b);
@@ -472,6 +539,13 @@ int ubqp_batch_tune(ubqp_batch* b, void* stream) {
       if (t < cur) cur = t; else b->eval_path = keep;
     }
   }
+  if (b->eval_path == UBQP_EVAL_TC && b->merged_ok) {  // one merged launch or per instance
+    const bool keep = b->eval_merged;
+    b->eval_merged = !keep;
+    float t = 0;
+    if ((r = time_run(&t))) goto done;
+    if (t < cur) cur = t; else b->eval_merged = keep;
+  }
   if (b->eval_path == UBQP_EVAL_TC) {  // evaluation schedule: K steps per work chunk
     const int keep = b->eval_kch;
     int bestk = keep;
@@ -514,21 +588,26 @@ int ubqp_batch_config(const ubqp_batch* b, int32_t* asc_threads, int32_t* asc_ch
 }
 
 int ubqp_batch_set(ubqp_batch* b, int32_t asc_threads, int32_t asc_chunks, int32_t packed,
-                   int32_t eval_kch) {
+                   int32_t eval_kch, int32_t eval_merged) {
   if (!b) return bfail(UBQP_ERR_ARG, "batch is NULL");
   if (eval_kch != 16 && eval_kch != ubqp_batch::kAltKch[0] && eval_kch != ubqp_batch::kAltKch[1])
     return bfail(UBQP_ERR_ARG, "eval_kch must be 8, 12 or 16");
+  if (eval_merged && !(b->merged_ok && b->eval_path == UBQP_EVAL_TC))
+    return bfail(UBQP_ERR_UNSUPPORTED, "merged evaluation needs the tensor-core path");
   const int r = set_shape(b, asc_threads, asc_chunks, packed != 0);
   if (r) return r;
   drop_graph(b);
   b->eval_kch = eval_kch;
+  b->eval_merged = eval_merged != 0;
   return UBQP_OK;
 }
 
-int ubqp_batch_schedule(const ubqp_batch* b, int32_t* packed, int32_t* eval_kch) {
+int ubqp_batch_schedule(const ubqp_batch* b, int32_t* packed, int32_t* eval_kch,
+                        int32_t* eval_merged) {
   if (!b) return bfail(UBQP_ERR_ARG, "batch is NULL");
   if (packed) *packed = b->packed ? 1 : 0;
   if (eval_kch) *eval_kch = b->eval_kch;
+  if (eval_merged) *eval_merged = b->eval_merged ? 1 : 0;
   return UBQP_OK;
 }
 

@@ -211,6 +211,7 @@ int run_batch(ubqp_server* s, ServerLane& L, std::vector<Slot*>& live) {
       return st;
     ubqp::BatchDesc& d = L.h_desc[i];
     const ubqp_q* q = sl.h;
+    d.x0 = q->x0;
     d.Q8 = q->Q8;
     d.ldq = q->ldq;
     d.n = q->n;

@@ -504,6 +504,239 @@ eval_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ 
   }
 }
 
+// Row `row` of the A tile of merged unit u (as unit_words, for the instance
+// the unit belongs to).
+__device__ __forceinline__ void munit_words(const EvalInst* __restrict__ insts,
+                                            const MUnit* __restrict__ units, int n_units, int u,
+                                            int row, uint64_t (&wa)[KCH]) {
+  const uint64_t* x0p = nullptr;
+  int k0 = 0, nk = 0, n = 0, W = 0;
+  if (u < n_units) {
+    const MUnit un = units[u];
+    const EvalInst e = insts[un.inst];
+    const int64_t s0 = (int64_t)un.mt * BM + row;
+    if (s0 < e.S) x0p = e.X + s0 * e.W;
+    k0 = un.k0;
+    nk = un.nk;
+    n = e.n;
+    W = e.W;
+  }
+#pragma unroll
+  for (int i = 0; i < KCH; ++i) {
+    const int kw = k0 + i;
+    const bool in = i < nk && kw < W;
+    wa[i] = (x0p && in) ? (__ldg(x0p + kw) & valid_mask(n, kw)) : 0ull;
+  }
+}
+
+// The evaluation of every instance of a batch in one persistent launch: the
+// fused kernel above (A operand written from the solution bits, B = Q' by TMA,
+// int64 row-dot epilogue) over a merged list of work units (instance, chunk,
+// m-tile) of all instances, largest chunks first.  Each unit names its
+// instance, whose starts, values and Q' tensor map (an array in global
+// memory) it uses.  A timeout is recorded in `err`.
+__global__ void __launch_bounds__(THREADS_FUSED, 1)
+eval_tc_multi_kernel(const EvalInst* __restrict__ insts, const CUtensorMap* __restrict__ maps,
+                     const MUnit* __restrict__ units, int n_units, unsigned* __restrict__ err) {
+  extern __shared__ uint8_t smem_raw[];
+  uint8_t* smem = smem_raw + ((1024 - (su32(smem_raw) & 1023)) & 1023);
+  uint64_t* full = reinterpret_cast<uint64_t*>(smem + STAGES * STAGE_BYTES);
+  uint64_t* empty = full + STAGES;
+  uint64_t* tfull = empty + STAGES;
+  uint64_t* tempty = tfull + 2;
+  uint64_t* drain = tempty + 2;
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(drain + 1);
+  volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < STAGES; ++s) {
+      mbar_init(&full[s], 1 + A_WRITERS / 32);  // the TMA arrival + one per A-writer warp
+      mbar_init(&empty[s], 1);
+    }
+    for (int a = 0; a < 2; ++a) {
+      mbar_init(&tfull[a], 1);
+      mbar_init(&tempty[a], 4);  // one arrival per epilogue warp
+    }
+    mbar_init(drain, 1);
+    *abort_flag = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (warp == 1) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                     su32(tmem_slot)),
+                 "r"(TMEM_COLS)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = *tmem_slot;
+
+  if (warp == 0) {
+    if (lane == 0) {
+      // ---------------- TMA producer (B only)
+      int pending[STAGES];
+      for (int s = 0; s < STAGES; ++s) pending[s] = -1;
+      int stage = 0;
+      uint32_t phase = 0;
+      bool ok = true;
+      for (int u = blockIdx.x; u < n_units && ok; u += gridDim.x) {
+        const MUnit un = units[u];
+        const CUtensorMap* map = maps + un.inst;
+        for (int ks = 0; ks < un.nk; ++ks) {
+          if (!mbar_wait(&empty[stage], phase ^ 1u, abort_flag, err)) {
+            ok = false;
+            break;
+          }
+          uint8_t* sa = smem + stage * STAGE_BYTES;
+          mbar_expect_tx(&full[stage], B_BYTES);
+          tma_load_2d(sa + A_BYTES, map, (un.k0 + ks) * BK, un.nb * BN, &full[stage]);
+          pending[stage] = (int)phase;
+          if (++stage == STAGES) {
+            stage = 0;
+            phase ^= 1u;
+          }
+        }
+      }
+      if (!ok) {  // let every issued copy land before the CTA exits
+        for (int s = 0; s < STAGES; ++s)
+          if (pending[s] >= 0) mbar_drain(&full[s], (uint32_t)pending[s]);
+      }
+    }
+  } else if (warp == 1) {
+    if (lane == 0) {
+      // ---------------- MMA issuer
+      int stage = 0;
+      uint32_t phase = 0;
+      bool ok = true;
+      int t = 0;
+      for (int u = blockIdx.x; u < n_units && ok; u += gridDim.x, ++t) {
+        const int nk = units[u].nk;
+        const int a = t & 1;
+        const uint32_t aphase = (uint32_t)((t >> 1) & 1);
+        if (!mbar_wait(&tempty[a], aphase ^ 1u, abort_flag, err)) {
+          ok = false;
+          break;
+        }
+        tc_fence_after();
+        const uint32_t d = tmem + (uint32_t)(a * BN);
+        for (int ks = 0; ks < nk; ++ks) {
+          if (!mbar_wait(&full[stage], phase, abort_flag, err)) {
+            ok = false;
+            break;
+          }
+          tc_fence_after();
+          const uint32_t sa = su32(smem + stage * STAGE_BYTES);
+          const uint64_t adesc = sdesc(sa), bdesc = sdesc(sa + A_BYTES);
+#pragma unroll
+          for (int kk = 0; kk < BK / 16; ++kk)
+            mma_bf16(d, adesc + (uint64_t)(2 * kk), bdesc + (uint64_t)(2 * kk),
+                     (ks | kk) != 0 ? 1u : 0u);
+          mma_commit(&empty[stage]);
+          if (++stage == STAGES) {
+            stage = 0;
+            phase ^= 1u;
+          }
+        }
+        if (ok) mma_commit(&tfull[a]);
+      }
+      if (!ok) {  // wait for the MMAs already issued before TMEM is freed
+        mma_commit(drain);
+        mbar_drain(drain, 0);
+      }
+    }
+  } else if (warp >= THREADS / 32) {
+    // ---------------- A writers (warps 6-9): row t of the A tile
+    const int t = threadIdx.x - THREADS;
+    int stage = 0;
+    uint32_t phase = 0;
+    bool ok = true;
+    uint64_t wa[KCH], wn[KCH];
+    munit_words(insts, units, n_units, blockIdx.x, t, wa);
+    for (int u = blockIdx.x; u < n_units && ok; u += gridDim.x) {
+      const int nk = units[u].nk;
+      munit_words(insts, units, n_units, u + gridDim.x, t, wn);
+#pragma unroll
+      for (int ks = 0; ks < KCH; ++ks) {
+        if (ks >= nk) break;
+        const uint64_t w0 = wa[ks];
+        // the warp arrives as one below: leave together
+        const bool got = mbar_wait(&empty[stage], phase ^ 1u, abort_flag, err);
+        if (!__all_sync(0xffffffffu, got)) {
+          ok = false;
+          break;
+        }
+        uint8_t* r0 = smem + stage * STAGE_BYTES + t * 128;
+#pragma unroll
+        for (int p = 0; p < 4; ++p) {  // 16-byte chunks 2p, 2p + 1
+          uint32_t v[8];
+          expand16((uint32_t)(w0 >> (16 * p)) & 0xFFFFu, v);
+          *reinterpret_cast<uint4*>(r0 + (((2 * p) ^ (t & 7)) << 4)) =
+              make_uint4(v[0], v[1], v[2], v[3]);
+          *reinterpret_cast<uint4*>(r0 + (((2 * p + 1) ^ (t & 7)) << 4)) =
+              make_uint4(v[4], v[5], v[6], v[7]);
+        }
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        __syncwarp();
+        if (lane == 0) mbar_arrive(&full[stage]);
+        if (++stage == STAGES) {
+          stage = 0;
+          phase ^= 1u;
+        }
+      }
+#pragma unroll
+      for (int i = 0; i < KCH; ++i) wa[i] = wn[i];
+    }
+  } else {
+    // ---------------- epilogue: warps 2..5 cover TMEM lanes 64-95, 96-127, 0-31, 32-63
+    const int q = warp & 3;
+    const int row = q * 32 + lane;
+    int t = 0;
+    for (int u = blockIdx.x; u < n_units; u += gridDim.x, ++t) {
+      const MUnit un = units[u];
+      const EvalInst e = insts[un.inst];
+      const int a = t & 1;
+      const uint32_t aphase = (uint32_t)((t >> 1) & 1);
+      const bool got = mbar_wait(&tfull[a], aphase, abort_flag, err);
+      if (!__all_sync(0xffffffffu, got)) break;
+      tc_fence_after();
+      const int64_t s = (int64_t)un.mt * BM + row;
+      const uint32_t base = tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(a * BN);
+      uint64_t xw[4];
+#pragma unroll
+      for (int i = 0; i < 4; ++i) {
+        const int w = un.nb * 4 + i;
+        xw[i] = (s < e.S && w < e.W) ? e.X[s * e.W + w] : 0ull;
+      }
+      int acc = 0;
+#pragma unroll 1
+      for (int cc = 0; cc < BN / 32; ++cc) {
+        uint32_t r[32];
+        tmem_ld32(base + (uint32_t)(cc * 32), r);
+        const uint32_t bits = (uint32_t)(xw[cc >> 1] >> ((cc & 1) * 32));
+#pragma unroll
+        for (int i = 0; i < 32; ++i)
+          if ((bits >> i) & 1u) acc += __float2int_rn(__uint_as_float(r[i]));
+      }
+      tc_fence_before();
+      __syncwarp();
+      if (lane == 0) mbar_arrive(&tempty[a]);
+      if (s < e.S && acc != 0)
+        atomicAdd(reinterpret_cast<unsigned long long*>(&e.f[s]),
+                  (unsigned long long)(long long)acc);
+    }
+  }
+  __syncthreads();
+  if (warp == 1) {
+    tc_fence_after();
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem),
+                 "r"(TMEM_COLS)
+                 : "memory");
+  }
+}
+
 // Evaluate with the A operand in tensor memory (UBQP_EVAL_TC_TMEM).  Same
 // work units and epilogue as eval_tc_kernel with N-blocks of 192 columns;
 // warp 0 loads only B (Q' rows) by TMA, warps 6-13 expand each start's 64
@@ -952,6 +1185,33 @@ static std::vector<int4> make_chunks(int n_tc, int bn, bool full, int kch = KCH)
 // (the handle's own table uses 16): a schedule a batch plan may tune.
 std::vector<int4> eval_tc_chunks(int n_tc, int kch) {
   return make_chunks(n_tc, BN, false, std::max(1, std::min(kch, KCH)));
+}
+
+std::vector<MUnit> eval_tc_multi_units(const ubqp_q* const* qs, int count, int64_t S, int kch) {
+  std::vector<MUnit> us;
+  const int m_tiles = (int)(padded_starts(S) / BM);
+  for (int i = 0; i < count; ++i) {
+    for (const int4& c : make_chunks(qs[i]->n_tc, BN, false, std::max(1, std::min(kch, KCH))))
+      for (int mt = 0; mt < m_tiles; ++mt) us.push_back(MUnit{c.x, c.y, c.z, mt, i, 0, 0, 0});
+  }
+  std::stable_sort(us.begin(), us.end(), [](const MUnit& a, const MUnit& b) { return a.nk > b.nk; });
+  return us;
+}
+
+cudaError_t launch_eval_tc_multi(const EvalInst* insts, const void* maps, const MUnit* units,
+                                 int n_units, unsigned* err, int sm_count, cudaStream_t st) {
+  static std::once_flag once;
+  static cudaError_t attr = cudaSuccess;
+  std::call_once(once, [] {
+    attr = cudaFuncSetAttribute(eval_tc_multi_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                SMEM_BYTES_FUSED);
+  });
+  if (attr != cudaSuccess) return attr;
+  if (n_units < 1) return cudaSuccess;
+  const int grid = n_units < sm_count ? n_units : sm_count;
+  eval_tc_multi_kernel<<<grid, THREADS_FUSED, SMEM_BYTES_FUSED, st>>>(
+      insts, reinterpret_cast<const CUtensorMap*>(maps), units, n_units, err);
+  return cudaGetLastError();
 }
 
 size_t eval_tc_chunk_bytes(int n_tc) {

@@ -69,6 +69,7 @@ struct NvtxRange {
 
 // One instance of a batch (device-resident descriptor of the batched stages).
 struct BatchDesc {
+  const uint64_t* x0;  // first-derivative start (W words)
   const int8_t* Q8;
   int64_t ldq;
   int n, W;
@@ -85,6 +86,18 @@ struct BatchDesc {
   unsigned* err;
   uint64_t* best_x;   // W
   int64_t* best_f;    // 2: value, index
+};
+
+// One instance of a merged evaluation, and a work unit of it: chunk {N-block
+// nb, first K step k0, K steps nk} of instance `inst`, m-tile mt.
+struct EvalInst {
+  const uint64_t* X;
+  int64_t* f;
+  int64_t S;
+  int n, W;
+};
+struct MUnit {
+  int nb, k0, nk, mt, inst, pad0, pad1, pad2;
 };
 
 __host__ __device__ inline int64_t words_of(int64_t n) { return (n + 63) / 64; }
@@ -122,6 +135,11 @@ cudaError_t launch_diversify(const uint64_t* x0, int n, int mode, uint64_t seed,
                              uint64_t round, int64_t S_total, int64_t s_begin,
                              int64_t S_local, int div_H, uint64_t* X, cudaStream_t st,
                              const uint64_t* seed_dev = nullptr);
+// Every instance of a batch in one launch: starts (seed read from seed_dev)
+// into each d[i].X, d[i].f and d[i].flips zeroed; max_words = the largest S W.
+cudaError_t launch_diversify_batch(const BatchDesc* d, int count, int64_t max_words, int mode,
+                                   const uint64_t* seed_dev, uint64_t round, int div_H,
+                                   cudaStream_t st);
 cudaError_t launch_eval_plain(const ubqp_q* h, const uint64_t* X, int64_t S,
                               int64_t* f, cudaStream_t st);
 size_t eval_tc_workspace(const ubqp_q* h, int64_t S);
@@ -129,6 +147,13 @@ cudaError_t eval_tc_upload_tables(ubqp_q* h, cudaStream_t st);
 cudaError_t eval_tc_prepare(ubqp_q* h, cudaStream_t st);
 size_t eval_tc_chunk_bytes(int n_tc);
 std::vector<int4> eval_tc_chunks(int n_tc, int kch);
+// The merged work list of a batch's evaluation (all instances, S starts each,
+// chunks of at most kch K steps), largest chunks first; and its launch.
+// maps: `count` CUtensorMap of the instances' Q' (the handles' own), 64-byte
+// aligned in device memory; f of every instance zeroed before.
+std::vector<MUnit> eval_tc_multi_units(const ubqp_q* const* qs, int count, int64_t S, int kch);
+cudaError_t launch_eval_tc_multi(const EvalInst* insts, const void* maps, const MUnit* units,
+                                 int n_units, unsigned* err, int sm_count, cudaStream_t st);
 size_t eval_tc_static_capacity();
 size_t ascent_tc_workspace(const ubqp_q* h, int64_t S);
 cudaError_t launch_ascent_init_tc(const ubqp_q* h, const uint64_t* X, const int32_t* idx,

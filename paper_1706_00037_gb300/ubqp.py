@@ -132,8 +132,8 @@ def load() -> ctypes.CDLL:
         "ubqp_batch_capture": (ctypes.c_int, [P, P]),
         "ubqp_batch_result": (ctypes.c_int, [P, i32, ctypes.POINTER(P), ctypes.POINTER(P)]),
         "ubqp_batch_config": (ctypes.c_int, [P, P, P, P, P, P]),
-        "ubqp_batch_schedule": (ctypes.c_int, [P, P, P]),
-        "ubqp_batch_set": (ctypes.c_int, [P, i32, i32, i32, i32]),
+        "ubqp_batch_schedule": (ctypes.c_int, [P, P, P, P]),
+        "ubqp_batch_set": (ctypes.c_int, [P, i32, i32, i32, i32, i32]),
         "ubqp_batch_get": (ctypes.c_int, [P, i32, P, P, P]),
         "ubqp_q_arena_size": (sz, [i32]),
         "ubqp_q_prepare_into": (ctypes.c_int, [P, i32, i64, P, sz, P, ctypes.POINTER(P)]),
@@ -506,9 +506,11 @@ class Batch:
     def tune(self, stream=None):
         _check(load().ubqp_batch_tune(self._h, _stream(stream)))
 
-    def set(self, asc_threads: int, asc_chunks: int, packed: bool = False, eval_kch: int = 16):
+    def set(self, asc_threads: int, asc_chunks: int, packed: bool = False, eval_kch: int = 16,
+            eval_merged: bool = False):
         """Pin the configuration (ubqp_batch_set) instead of tuning it."""
-        _check(load().ubqp_batch_set(self._h, asc_threads, asc_chunks, int(packed), eval_kch))
+        _check(load().ubqp_batch_set(self._h, asc_threads, asc_chunks, int(packed), eval_kch,
+                                     int(eval_merged)))
 
     def capture(self, stream=None):
         _check(load().ubqp_batch_capture(self._h, _stream(stream)))
@@ -518,9 +520,10 @@ class Batch:
         _check(load().ubqp_batch_config(self._h, *[ctypes.byref(x) for x in v]))
         out = dict(zip(["asc_threads", "asc_chunks", "eval_path", "streams", "graph"],
                        [x.value for x in v]))
-        pk, kch = ctypes.c_int32(), ctypes.c_int32()
-        _check(load().ubqp_batch_schedule(self._h, ctypes.byref(pk), ctypes.byref(kch)))
-        out.update(packed=pk.value, eval_kch=kch.value)
+        pk, kch, mg = ctypes.c_int32(), ctypes.c_int32(), ctypes.c_int32()
+        _check(load().ubqp_batch_schedule(self._h, ctypes.byref(pk), ctypes.byref(kch),
+                                          ctypes.byref(mg)))
+        out.update(packed=pk.value, eval_kch=kch.value, eval_merged=mg.value)
         return out
 
     def result(self, i: int, stream=None):

@@ -79,9 +79,10 @@ def test_batch_plain_eval_path():
     check_against_single(insts, b, p, 9)
 
 
-@pytest.mark.parametrize("shape,packed,kch", [((256, 1), True, 16), ((256, 2), True, 8),
-                                              ((256, 1), False, 12), ((128, 2), False, 8)])
-def test_batch_pinned_schedules_equal_single_solves(shape, packed, kch):
+@pytest.mark.parametrize("shape,packed,kch,merged", [
+    ((256, 1), True, 16, True), ((256, 2), True, 8, True), ((256, 1), False, 12, False),
+    ((128, 2), False, 8, True), ((256, 1), True, 12, False)])
+def test_batch_pinned_schedules_equal_single_solves(shape, packed, kch, merged):
     # packed climbs (sub-groups of 64 / 128 / 256 threads by n, several starts
     # of one instance per block) and every evaluation schedule give the same
     # results as single solves, with the graph too
@@ -90,10 +91,10 @@ def test_batch_pinned_schedules_equal_single_solves(shape, packed, kch):
     Qs, insts = make_batch(sizes, dens, seed0=700)
     p = ubqp.make_params(257, 0.3, seed=4)
     b = ubqp.Batch(insts, p)
-    b.set(shape[0], shape[1], packed=packed, eval_kch=kch)
+    b.set(shape[0], shape[1], packed=packed, eval_kch=kch, eval_merged=merged)
     cfg = b.config()
-    assert (cfg["asc_threads"], cfg["asc_chunks"], cfg["packed"], cfg["eval_kch"]) == \
-        (shape[0], shape[1], int(packed), kch)
+    assert (cfg["asc_threads"], cfg["asc_chunks"], cfg["packed"], cfg["eval_kch"],
+            cfg["eval_merged"]) == (shape[0], shape[1], int(packed), kch, int(merged))
     b.run(seed=21)
     torch.cuda.synchronize()
     check_against_single(insts, b, p, 21)
@@ -117,3 +118,26 @@ def test_batch_set_rejects_shapes_that_cannot_hold_n():
         b.set(128, 2, packed=True)  # packed blocks are 256 threads
     with pytest.raises(ubqp.UbqpError):
         b.set(256, 1, eval_kch=5)
+    bp = ubqp.Batch(insts, ubqp.make_params(64, 0.5, seed=1, eval_path=ubqp.EVAL_PLAIN))
+    with pytest.raises(ubqp.UbqpError):
+        bp.set(256, 1, eval_merged=True)  # the merged launch is the tensor-core path
+
+
+def test_batch_merged_evaluation_values():
+    # one merged launch each for the start generation and the evaluation of
+    # instances of ragged sizes (single words, word and tile tails, above the
+    # fused path's usual 4096 limit), at every schedule: results equal to
+    # single solves
+    sizes = [60, 700, 2500, 300, 1025, 129, 2100, 513, 1, 64, 65, 4096, 4100]
+    Qs, insts = make_batch(sizes, [0.5] * len(sizes), seed0=950)
+    p = ubqp.make_params(300, 0.5, seed=0)
+    b = ubqp.Batch(insts, p)
+    b.set(256, 2, packed=True, eval_kch=16, eval_merged=True)
+    b.run(seed=31)
+    torch.cuda.synchronize()
+    check_against_single(insts, b, p, 31)
+    for kch in (12, 8):
+        b.set(256, 2, packed=True, eval_kch=kch, eval_merged=True)
+        b.run(seed=32)
+        torch.cuda.synchronize()
+        check_against_single(insts, b, p, 32)
