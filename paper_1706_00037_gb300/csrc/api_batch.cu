@@ -10,10 +10,12 @@
 //   join   one launch builds the work list (largest instances first), one
 //          persistent launch climbs every passing start of every instance,
 //          one launch takes each instance's best.
-// With the tensor-core evaluation the first two steps can instead be one
-// launch each for all instances: start generation, then one persistent
-// evaluation over the merged work list (instance, chunk, m-tile) of every
-// instance, largest chunks first.
+// With the tensor-core evaluation the forks can instead be single launches for
+// all instances: start generation, one persistent evaluation over the merged
+// work list (instance, chunk, m-tile) of every instance, largest chunks
+// first, and for the start-up one unpacking launch and one persistent product
+// over the merged full-square work list, units past an instance's passing
+// count skipped on the device.
 // The climb is either one start per group of the plan's shape, or packed: a
 // 256-thread block climbs up to four starts of one instance at once in
 // sub-groups of 64 or 128 threads when the instance's n fits them.
@@ -87,6 +89,13 @@ struct ubqp_batch {
   ubqp::MUnit* d_munits[3] = {nullptr, nullptr, nullptr};
   int n_munits[3] = {0, 0, 0};
   int64_t max_words = 0;
+  // ... and the start-up products of the passing starts (unpack + one launch)
+  ubqp::YInst* d_yinst = nullptr;
+  void* d_mapsA = nullptr;
+  void* d_mapsF = nullptr;
+  ubqp::MUnit* d_yunits = nullptr;
+  int n_yunits = 0;
+  int64_t max_items = 0;
   int max_n = 0;
   std::vector<cudaStream_t> streams;
   std::vector<cudaEvent_t> ev_join;
@@ -151,6 +160,13 @@ int run_body(ubqp_batch* b, cudaStream_t st) {
   }
   // ---- one launch: every instance's screen
   UBQP_BCUDA(ubqp::launch_screen_batch(b->d_desc, b->count, p.lambda, st));
+  if (b->eval_merged && b->eval_path == UBQP_EVAL_TC) {
+    // ---- one launch each: unpack every instance's passing starts, then the
+    // start-up products y = Q x of all of them
+    UBQP_BCUDA(ubqp::launch_startup_multi(b->d_yinst, b->count, b->max_items, b->d_mapsA,
+                                          b->d_mapsF, b->d_yunits, b->n_yunits, b->qs[0]->err,
+                                          b->sm_count, st));
+  } else {
   // ---- fork: tensor-core start-up of each instance's passing starts
   UBQP_BCUDA(cudaEventRecord(b->ev_fork, st));
   for (int k = 0; k < K; ++k) UBQP_BCUDA(cudaStreamWaitEvent(b->streams[k], b->ev_fork, 0));
@@ -165,6 +181,7 @@ int run_body(ubqp_batch* b, cudaStream_t st) {
   for (int k = 0; k < K; ++k) {
     UBQP_BCUDA(cudaEventRecord(b->ev_join[k], b->streams[k]));
     UBQP_BCUDA(cudaStreamWaitEvent(st, b->ev_join[k], 0));
+  }
   }
   // ---- one launch each: work list, every climb, every best
   if (b->packed) {
@@ -280,6 +297,12 @@ int ubqp_batch_create(const ubqp_q* const* qs, int32_t count, const ubqp_params*
     if (all_tc) mu[k] = ubqp::eval_tc_multi_units(qs, count, S, k == 0 ? 16 : k == 1 ? 12 : 8);
     o_mu[k] = take(sizeof(ubqp::MUnit) * std::max<size_t>(mu[k].size(), 1));
   }
+  const size_t o_yinst = take(sizeof(ubqp::YInst) * count);
+  const size_t o_mapsA = take(128 * (size_t)count);
+  const size_t o_mapsF = take(128 * (size_t)count);
+  std::vector<ubqp::MUnit> yu;
+  if (all_tc) yu = ubqp::eval_tc_multi_y_units(qs, count, S);
+  const size_t o_yu = take(sizeof(ubqp::MUnit) * std::max<size_t>(yu.size(), 1));
   // the alternative evaluation schedules of each instance
   std::vector<std::vector<int4>> alt_tab[2];
   std::vector<size_t> o_alt[2];
@@ -323,6 +346,16 @@ int ubqp_batch_create(const ubqp_q* const* qs, int32_t count, const ubqp_params*
   b->d_nitems = (int64_t*)(b->dmem + o_nitems);
   b->d_units = (int4*)(b->dmem + o_units);
   b->d_einst = (ubqp::EvalInst*)(b->dmem + o_einst);
+  b->d_yinst = (ubqp::YInst*)(b->dmem + o_yinst);
+  b->d_mapsA = b->dmem + o_mapsA;
+  b->d_mapsF = b->dmem + o_mapsF;
+  b->d_yunits = (ubqp::MUnit*)(b->dmem + o_yu);
+  b->n_yunits = (int)yu.size();
+  if (!yu.empty() && cudaMemcpy(b->d_yunits, yu.data(), sizeof(ubqp::MUnit) * yu.size(),
+                                cudaMemcpyHostToDevice) != cudaSuccess) {
+    ubqp_batch_destroy(b);
+    return bfail(UBQP_ERR_CUDA, "work list upload failed");
+  }
   b->d_maps = b->dmem + o_maps;
   b->merged_ok = all_tc;
   for (int k = 0; k < 3; ++k) {
@@ -385,16 +418,30 @@ int ubqp_batch_create(const ubqp_q* const* qs, int32_t count, const ubqp_params*
   }
   {
     std::vector<ubqp::EvalInst> ei(count);
-    std::vector<unsigned char> maps(128 * (size_t)count);
+    std::vector<ubqp::YInst> yi(count);
+    std::vector<unsigned char> maps(128 * (size_t)count), mA(128 * (size_t)count),
+        mF(128 * (size_t)count);
+    const int64_t S_p = (S + 127) / 128 * 128;
     for (int i = 0; i < count; ++i) {
       const ubqp::BatchDesc& d = b->h_desc[i];
       ei[i] = ubqp::EvalInst{d.X, d.f, d.S, d.n, d.W};
       b->max_words = std::max<int64_t>(b->max_words, d.S * d.W);
       memcpy(maps.data() + 128 * (size_t)i, qs[i]->tc_mapB, 128);
+      // the start-up: the unpacked rows at the scratch's start, Y after them
+      yi[i] = ubqp::YInst{d.X, d.idx, d.count, (uint4*)b->scratch[i], const_cast<float*>(d.Y),
+                          S, S_p, d.n, d.W, qs[i]->n_tc, 0};
+      b->max_items = std::max<int64_t>(b->max_items, S_p * (qs[i]->n_tc / 16));
+      memcpy(mA.data() + 128 * (size_t)i, b->mapA[i].bytes, 128);
+      memcpy(mF.data() + 128 * (size_t)i, qs[i]->tc_mapF, 128);
+      if (!d.Y) b->merged_ok = false;
     }
     if (cudaMemcpy(b->d_einst, ei.data(), sizeof(ubqp::EvalInst) * count,
                    cudaMemcpyHostToDevice) != cudaSuccess ||
-        cudaMemcpy(b->d_maps, maps.data(), maps.size(), cudaMemcpyHostToDevice) != cudaSuccess) {
+        cudaMemcpy(b->d_maps, maps.data(), maps.size(), cudaMemcpyHostToDevice) != cudaSuccess ||
+        cudaMemcpy(b->d_yinst, yi.data(), sizeof(ubqp::YInst) * count,
+                   cudaMemcpyHostToDevice) != cudaSuccess ||
+        cudaMemcpy(b->d_mapsA, mA.data(), mA.size(), cudaMemcpyHostToDevice) != cudaSuccess ||
+        cudaMemcpy(b->d_mapsF, mF.data(), mF.size(), cudaMemcpyHostToDevice) != cudaSuccess) {
       ubqp_batch_destroy(b);
       return bfail(UBQP_ERR_CUDA, "descriptor upload failed");
     }

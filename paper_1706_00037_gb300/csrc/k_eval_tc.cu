@@ -737,6 +737,185 @@ eval_tc_multi_kernel(const EvalInst* __restrict__ insts, const CUtensorMap* __re
   }
 }
 
+// The start-up products y = Q x of the passing starts of every instance of a
+// batch in one persistent launch: the staged kernel's Y mode (A = the unpacked
+// passing starts by TMA, B = Q by TMA, fp32 vector atomics into Y) over a
+// merged list of units (instance, full-square chunk, m-tile).  Whether a unit
+// has work depends on the instance's passing count, read on the device: every
+// role skips the units whose m-tile starts at or past it, in the same order,
+// so the stage and accumulator hand-offs stay paired.
+__global__ void __launch_bounds__(THREADS, 1)
+eval_tc_multi_y_kernel(const YInst* __restrict__ yi, const CUtensorMap* __restrict__ mapsA,
+                       const CUtensorMap* __restrict__ mapsF, const MUnit* __restrict__ units,
+                       int n_units, unsigned* __restrict__ err) {
+  extern __shared__ uint8_t smem_raw[];
+  uint8_t* smem = smem_raw + ((1024 - (su32(smem_raw) & 1023)) & 1023);
+  uint64_t* full = reinterpret_cast<uint64_t*>(smem + STAGES * STAGE_BYTES);
+  uint64_t* empty = full + STAGES;
+  uint64_t* tfull = empty + STAGES;
+  uint64_t* tempty = tfull + 2;
+  uint64_t* drain = tempty + 2;
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(drain + 1);
+  volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  // does unit u have work: its m-tile starts below the instance's count
+  auto active = [&](const MUnit& un) {
+    const YInst& e = yi[un.inst];
+    const int64_t c = *e.count;
+    const int64_t rows = c < e.S ? (c > 0 ? c : 0) : e.S;
+    return (int64_t)un.mt * BM < rows;
+  };
+
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < STAGES; ++s) {
+      mbar_init(&full[s], 1);
+      mbar_init(&empty[s], 1);
+    }
+    for (int a = 0; a < 2; ++a) {
+      mbar_init(&tfull[a], 1);
+      mbar_init(&tempty[a], 4);  // one arrival per epilogue warp
+    }
+    mbar_init(drain, 1);
+    *abort_flag = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (warp == 1) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                     su32(tmem_slot)),
+                 "r"(TMEM_COLS)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = *tmem_slot;
+
+  if (warp == 0) {
+    if (lane == 0) {
+      // ---------------- TMA producer
+      int pending[STAGES];
+      for (int s = 0; s < STAGES; ++s) pending[s] = -1;
+      int stage = 0;
+      uint32_t phase = 0;
+      bool ok = true;
+      for (int u = blockIdx.x; u < n_units && ok; u += gridDim.x) {
+        const MUnit un = units[u];
+        if (!active(un)) continue;
+        const CUtensorMap* mA = mapsA + un.inst;
+        const CUtensorMap* mF = mapsF + un.inst;
+        for (int ks = 0; ks < un.nk; ++ks) {
+          if (!mbar_wait(&empty[stage], phase ^ 1u, abort_flag, err)) {
+            ok = false;
+            break;
+          }
+          uint8_t* sa = smem + stage * STAGE_BYTES;
+          mbar_expect_tx(&full[stage], STAGE_BYTES);
+          const int kx = (un.k0 + ks) * BK;
+          tma_load_2d(sa, mA, kx, un.mt * BM, &full[stage]);
+          tma_load_2d(sa + A_BYTES, mF, kx, un.nb * BN, &full[stage]);
+          pending[stage] = (int)phase;
+          if (++stage == STAGES) {
+            stage = 0;
+            phase ^= 1u;
+          }
+        }
+      }
+      if (!ok) {  // let every issued copy land before the CTA exits
+        for (int s = 0; s < STAGES; ++s)
+          if (pending[s] >= 0) mbar_drain(&full[s], (uint32_t)pending[s]);
+      }
+    }
+  } else if (warp == 1) {
+    if (lane == 0) {
+      // ---------------- MMA issuer
+      int stage = 0;
+      uint32_t phase = 0;
+      bool ok = true;
+      int t = 0;
+      for (int u = blockIdx.x; u < n_units && ok; u += gridDim.x) {
+        const MUnit un = units[u];
+        if (!active(un)) continue;
+        const int a = t & 1;
+        const uint32_t aphase = (uint32_t)((t >> 1) & 1);
+        ++t;
+        if (!mbar_wait(&tempty[a], aphase ^ 1u, abort_flag, err)) {
+          ok = false;
+          break;
+        }
+        tc_fence_after();
+        const uint32_t d = tmem + (uint32_t)(a * BN);
+        for (int ks = 0; ks < un.nk; ++ks) {
+          if (!mbar_wait(&full[stage], phase, abort_flag, err)) {
+            ok = false;
+            break;
+          }
+          tc_fence_after();
+          const uint32_t sa = su32(smem + stage * STAGE_BYTES);
+          const uint64_t adesc = sdesc(sa), bdesc = sdesc(sa + A_BYTES);
+#pragma unroll
+          for (int kk = 0; kk < BK / 16; ++kk)
+            mma_bf16(d, adesc + (uint64_t)(2 * kk), bdesc + (uint64_t)(2 * kk),
+                     (ks | kk) != 0 ? 1u : 0u);
+          mma_commit(&empty[stage]);
+          if (++stage == STAGES) {
+            stage = 0;
+            phase ^= 1u;
+          }
+        }
+        if (ok) mma_commit(&tfull[a]);
+      }
+      if (!ok) {  // wait for the MMAs already issued before TMEM is freed
+        mma_commit(drain);
+        mbar_drain(drain, 0);
+      }
+    }
+  } else {
+    // ---------------- epilogue: warps 2..5 cover TMEM lanes 64-95, 96-127, 0-31, 32-63
+    const int q = warp & 3;
+    const int row = q * 32 + lane;
+    int t = 0;
+    for (int u = blockIdx.x; u < n_units; u += gridDim.x) {
+      const MUnit un = units[u];
+      if (!active(un)) continue;
+      const YInst& e = yi[un.inst];
+      const int64_t c = *e.count;
+      const int64_t rows = c < e.S ? (c > 0 ? c : 0) : e.S;
+      const int a = t & 1;
+      const uint32_t aphase = (uint32_t)((t >> 1) & 1);
+      ++t;
+      const bool got = mbar_wait(&tfull[a], aphase, abort_flag, err);
+      if (!__all_sync(0xffffffffu, got)) break;
+      tc_fence_after();
+      const int64_t s = (int64_t)un.mt * BM + row;
+      const uint32_t base = tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(a * BN);
+      float* yrow = e.Y + s * (int64_t)e.n_tc + (int64_t)un.nb * BN;
+#pragma unroll 1
+      for (int cc = 0; cc < BN / 32; ++cc) {
+        uint32_t r[32];
+        tmem_ld32(base + (uint32_t)(cc * 32), r);
+        if (s < rows) {
+#pragma unroll
+          for (int i = 0; i < 8; ++i)
+            atomicAdd(reinterpret_cast<float4*>(yrow + cc * 32 + 4 * i),
+                      make_float4(__uint_as_float(r[4 * i]), __uint_as_float(r[4 * i + 1]),
+                                  __uint_as_float(r[4 * i + 2]), __uint_as_float(r[4 * i + 3])));
+        }
+      }
+      tc_fence_before();
+      __syncwarp();
+      if (lane == 0) mbar_arrive(&tempty[a]);
+    }
+  }
+  __syncthreads();
+  if (warp == 1) {
+    tc_fence_after();
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem),
+                 "r"(TMEM_COLS)
+                 : "memory");
+  }
+}
+
 // Evaluate with the A operand in tensor memory (UBQP_EVAL_TC_TMEM).  Same
 // work units and epilogue as eval_tc_kernel with N-blocks of 192 columns;
 // warp 0 loads only B (Q' rows) by TMA, warps 6-13 expand each start's 64
@@ -990,19 +1169,27 @@ __global__ void selftest_wait_kernel(uint64_t limit_ns, int32_t* status) {
 // Row t is solution idx[t] (t < *count) when idx is given, else solution t
 // (t < S); other rows and columns >= n are zero.  One thread per 16 columns
 // (two 16-byte stores).
-__global__ void unpack_bits_bf16(const uint64_t* __restrict__ X, int n, int W, int64_t S,
-                                 const int32_t* __restrict__ idx,
-                                 const int64_t* __restrict__ count, int64_t S_p, int n_tc,
-                                 uint4* __restrict__ Xe) {
+// Rows of 0.0/1.0 bf16 (the A operand of the staged kernel) from the bit-packed
+// starts, 16 elements per item; with idx, row t is start idx[t] for t < *count
+// and zero up to the next multiple of 128 (the last m-tile the product reads;
+// rows beyond are not written), and with Y the product's rows t < *count are
+// zeroed for its accumulation.
+__device__ __forceinline__ void unpack_rows(const uint64_t* __restrict__ X, int n, int W,
+                                            int64_t S, const int32_t* __restrict__ idx,
+                                            const int64_t* __restrict__ count, int64_t S_p,
+                                            int n_tc, uint4* __restrict__ Xe,
+                                            float* __restrict__ Y, int64_t block,
+                                            int64_t blocks) {
   const int64_t per_row = n_tc / 16;
-  const int64_t total = S_p * per_row;
-  int64_t rows = S;
+  int64_t rows = S, rows_p = S_p;
   if (idx) {
     const int64_t c = *count;
-    rows = c < S ? c : S;
+    rows = c < S ? (c > 0 ? c : 0) : S;
+    rows_p = (rows + BM - 1) / BM * BM;
   }
-  for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < total;
-       t += (int64_t)gridDim.x * blockDim.x) {
+  const int64_t total = rows_p * per_row;
+  for (int64_t t = block * (int64_t)blockDim.x + threadIdx.x; t < total;
+       t += blocks * blockDim.x) {
     const int64_t r = t / per_row;
     const int c = (int)(t - r * per_row);
     const int w = c >> 2;
@@ -1016,7 +1203,30 @@ __global__ void unpack_bits_bf16(const uint64_t* __restrict__ X, int n, int W, i
     expand16(x16, v);
     Xe[2 * t] = make_uint4(v[0], v[1], v[2], v[3]);
     Xe[2 * t + 1] = make_uint4(v[4], v[5], v[6], v[7]);
+    if (Y && r < rows) {
+      float4* yr = reinterpret_cast<float4*>(Y + r * (int64_t)n_tc + 16 * c);
+      const float4 z = make_float4(0.f, 0.f, 0.f, 0.f);
+      yr[0] = z;
+      yr[1] = z;
+      yr[2] = z;
+      yr[3] = z;
+    }
   }
+}
+
+__global__ void unpack_bits_bf16(const uint64_t* __restrict__ X, int n, int W, int64_t S,
+                                 const int32_t* __restrict__ idx,
+                                 const int64_t* __restrict__ count, int64_t S_p, int n_tc,
+                                 uint4* __restrict__ Xe, float* __restrict__ Y) {
+  unpack_rows(X, n, W, S, idx, count, S_p, n_tc, Xe, Y, (int64_t)blockIdx.x, (int64_t)gridDim.x);
+}
+
+// Every instance of a batch (instance blockIdx.y): the passing starts of the
+// start-up product unpacked, and their Y rows zeroed.
+__global__ void unpack_batch_bf16(const YInst* __restrict__ yi) {
+  const YInst& e = yi[blockIdx.y];
+  unpack_rows(e.X, e.n, e.W, e.S, e.idx, e.count, e.S_p, e.n_tc, e.Xe, e.Y, (int64_t)blockIdx.x,
+              (int64_t)gridDim.x);
 }
 
 using EncodeFn = CUresult (*)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*,
@@ -1214,6 +1424,41 @@ cudaError_t launch_eval_tc_multi(const EvalInst* insts, const void* maps, const 
   return cudaGetLastError();
 }
 
+std::vector<MUnit> eval_tc_multi_y_units(const ubqp_q* const* qs, int count, int64_t S) {
+  std::vector<MUnit> us;
+  const int m_tiles = (int)(padded_starts(S) / BM);
+  for (int i = 0; i < count; ++i) {
+    for (const int4& c : make_chunks(qs[i]->n_tc, BN, true))
+      for (int mt = 0; mt < m_tiles; ++mt) us.push_back(MUnit{c.x, c.y, c.z, mt, i, 0, 0, 0});
+  }
+  std::stable_sort(us.begin(), us.end(), [](const MUnit& a, const MUnit& b) { return a.nk > b.nk; });
+  return us;
+}
+
+cudaError_t launch_startup_multi(const YInst* yi, int count, int64_t max_items, const void* mapsA,
+                                 const void* mapsF, const MUnit* units, int n_units,
+                                 unsigned* err, int sm_count, cudaStream_t st) {
+  static std::once_flag once;
+  static cudaError_t attr = cudaSuccess;
+  std::call_once(once, [] {
+    attr = cudaFuncSetAttribute(eval_tc_multi_y_kernel,
+                                cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_BYTES);
+  });
+  if (attr != cudaSuccess) return attr;
+  if (count < 1 || n_units < 1) return cudaSuccess;
+  int64_t blocks = (max_items + 255) / 256;
+  if (blocks > 64) blocks = 64;
+  if (blocks < 1) blocks = 1;
+  unpack_batch_bf16<<<dim3((unsigned)blocks, (unsigned)count), 256, 0, st>>>(yi);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  const int grid = n_units < sm_count ? n_units : sm_count;
+  eval_tc_multi_y_kernel<<<grid, THREADS, SMEM_BYTES, st>>>(
+      yi, reinterpret_cast<const CUtensorMap*>(mapsA), reinterpret_cast<const CUtensorMap*>(mapsF),
+      units, n_units, err);
+  return cudaGetLastError();
+}
+
 size_t eval_tc_chunk_bytes(int n_tc) {
   return sizeof(int4) * (make_chunks(n_tc, BN, false).size() + make_chunks(n_tc, BN, true).size() +
                          make_chunks(n_tc, BN_TS, false).size());
@@ -1288,13 +1533,12 @@ cudaError_t launch_ascent_init_tc(const ubqp_q* h, const uint64_t* X, const int3
     int64_t blocks = (total + 255) / 256;
     if (blocks > (int64_t)h->sm_count * 8) blocks = (int64_t)h->sm_count * 8;
     unpack_bits_bf16<<<(unsigned)blocks, 256, 0, st>>>(X, h->n, h->W, S, idx, count, S_p,
-                                                      h->n_tc, reinterpret_cast<uint4*>(Xe));
+                                                      h->n_tc, reinterpret_cast<uint4*>(Xe), Y);
     if ((e = cudaGetLastError())) return e;
   }
   alignas(64) CUtensorMap mapA;
   if (mapA_in) mapA = *reinterpret_cast<const CUtensorMap*>(mapA_in);
   else if (!make_map(&mapA, Xe, S_p, h->n_tc, BM)) return cudaErrorInvalidValue;
-  if ((e = cudaMemsetAsync(Y, 0, (size_t)S_p * h->n_tc * 4, st))) return e;
   if ((e = set_smem_attr_once<true, false>())) return e;
   const int m_tiles = (int)(S_p / BM);
   const int n_units = h->tc_nchunks_y * m_tiles;
@@ -1345,7 +1589,7 @@ cudaError_t launch_eval_tc(const ubqp_q* h, const uint64_t* X, int64_t S, int64_
     if (blocks > (int64_t)h->sm_count * 8) blocks = (int64_t)h->sm_count * 8;
     unpack_bits_bf16<<<(unsigned)blocks, 256, 0, st>>>(X, h->n, h->W, S, nullptr, nullptr,
                                                       S_p, h->n_tc,
-                                                      reinterpret_cast<uint4*>(ws));
+                                                      reinterpret_cast<uint4*>(ws), nullptr);
     if ((e = cudaGetLastError())) return e;
     if (mapA_in) mapA = *reinterpret_cast<const CUtensorMap*>(mapA_in);
     else if (!make_map(&mapA, ws, S_p, h->n_tc, BM)) return cudaErrorInvalidValue;

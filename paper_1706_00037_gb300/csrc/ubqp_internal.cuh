@@ -99,6 +99,18 @@ struct EvalInst {
 struct MUnit {
   int nb, k0, nk, mt, inst, pad0, pad1, pad2;
 };
+// One instance of a merged start-up product y = Q x of the passing starts:
+// its starts, passing list and count, the unpacked rows Xe (A operand,
+// S_p x n_tc bf16) and the product Y (S_p x n_tc fp32) in its scratch.
+struct YInst {
+  const uint64_t* X;
+  const int32_t* idx;
+  const int64_t* count;
+  uint4* Xe;
+  float* Y;
+  int64_t S, S_p;
+  int n, W, n_tc, pad;
+};
 
 __host__ __device__ inline int64_t words_of(int64_t n) { return (n + 63) / 64; }
 
@@ -154,6 +166,16 @@ std::vector<int4> eval_tc_chunks(int n_tc, int kch);
 std::vector<MUnit> eval_tc_multi_units(const ubqp_q* const* qs, int count, int64_t S, int kch);
 cudaError_t launch_eval_tc_multi(const EvalInst* insts, const void* maps, const MUnit* units,
                                  int n_units, unsigned* err, int sm_count, cudaStream_t st);
+// The start-up products of every instance of a batch in two launches: the
+// unpacking of all passing starts (and the zeroing of their Y rows), then one
+// persistent tensor-core launch over the merged work list of the full-square
+// chunks of every instance (units past an instance's passing count are
+// skipped).  mapsA / mapsF: `count` CUtensorMap each (the unpacked rows of
+// each instance, its bf16 Q), 64-byte aligned in device memory.
+std::vector<MUnit> eval_tc_multi_y_units(const ubqp_q* const* qs, int count, int64_t S);
+cudaError_t launch_startup_multi(const YInst* yi, int count, int64_t max_items, const void* mapsA,
+                                 const void* mapsF, const MUnit* units, int n_units,
+                                 unsigned* err, int sm_count, cudaStream_t st);
 size_t eval_tc_static_capacity();
 size_t ascent_tc_workspace(const ubqp_q* h, int64_t S);
 cudaError_t launch_ascent_init_tc(const ubqp_q* h, const uint64_t* X, const int32_t* idx,
