@@ -614,7 +614,7 @@ class Server:
             pass
 
 
-def measure_peaks(l2_bytes: int = 64 << 20, reps: int = 20, int_iters: int = 200_000) -> dict:
+def measure_peaks(l2_bytes: int = 64 << 20, reps: int = 20, int_iters: int = 50_000) -> dict:
     """The ascent's roofline rates on the current device (ubqp_peak_*), timed
     with CUDA events after one untimed warm-up launch each: L2 read GB/s over
     an L2-resident buffer, the int32 multiply-add rate and the ascent's
