@@ -341,6 +341,11 @@ void lane_main(ubqp_server* s, ServerLane* L) {
     }
     int bst = live.empty() ? UBQP_OK : run_batch(s, *L, live);
     if (!live.empty()) {
+      // a batch that failed part-way may have left work on the fork streams
+      // that the lane's stream never joined: let it finish before the
+      // buffers are freed
+      if (bst)
+        for (int f = 0; f < kForkStreams; ++f) cudaStreamSynchronize(L->fork[f]);
       if (cudaStreamSynchronize(L->st) != cudaSuccess) {
         cudaGetLastError();
         if (!bst) bst = sfail(UBQP_ERR_CUDA, "server batch failed");
