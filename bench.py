@@ -768,6 +768,32 @@ def main():
     inst.sync()
     moves_all = asc_all_flips / (asc_all_ms / 1e3)
 
+    # ---- several independent rounds in flight (ubqp_solve_rounds): one round's
+    # ~50 passers leave most SMs idle during the climb; R rounds of the same
+    # workload (1000 random starts each, each screened on its own) share one
+    # evaluation and one climb launch.  L2 flushed before every call.
+    rounds = {}
+    for R in (1, 2, 3, 4):
+        rp = ubqp.make_params(S, a.lam, mode=ubqp.RANDOM, seed=31_000 + 10 * R, eval_path=path)
+        rws = torch.empty(ubqp.solve_rounds_workspace_size(inst, rp, R), dtype=torch.uint8,
+                          device=dev)
+        rbx = torch.empty((R, W), dtype=torch.int64, device=dev)
+        rbf = torch.empty((R, 2), dtype=torch.int64, device=dev)
+        ts = []
+        for rep in range(7):
+            flush.zero_()
+            rp.seed = 31_000 + 10 * R + 1000 * rep
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            ubqp.solve_rounds(inst, rp, R, ws=rws, best_x=rbx, best_f=rbf)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            if rep >= 2:
+                ts.append(e0.elapsed_time(e1))
+        ms = statistics.median(ts)
+        rounds[str(R)] = {"ms_per_call": ms, "starts_per_s": R * S / (ms / 1e3)}
+    inst.sync()
+
     # ---- roofline of the dominant kernel (ascent).  Per move the ascent reads
     # one int8 row of Q (n bytes, L2-resident) and does 3n integer operations
     # (each element's gain update, key and comparison), so its moves/s are
@@ -955,6 +981,11 @@ def main():
                 "passed_per_step": passers / a.steps, "flips_per_step": flips_timed / a.steps,
                 "kernels": kernels, "roofline": roofline, "roofline_eval": roof_eval,
                 "roofline_ascent_all_starts": roof_asc_all,
+                "rounds_in_flight": {"what": "ubqp_solve_rounds: R independent rounds of the "
+                                             "same workload (1000 random starts each, each "
+                                             "screened on its own), one evaluation and one "
+                                             "climb launch; bit-identical to R ubqp_solve calls",
+                                     "by_R": rounds},
                 "measured_peaks": dict(mp, sm_max_mhz=sm_max,
                                        int32_lane_peak_tops=n_sm * 128 * sm_max * 1e6 / 1e12),
                 "cpu_baseline": cpu, "e2e": e2e,

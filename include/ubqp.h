@@ -354,6 +354,29 @@ int ubqp_solve(const ubqp_q* q, const ubqp_params* p, uint64_t* best_x_dev,
                size_t ws_bytes, void* stream);
 
 /*
+ * ubqp_solve_rounds -- R independent rounds of ubqp_solve on one instance, run
+ * together.  Round k is ubqp_solve with seed p->seed + k and loop-counter
+ * offset p->round + k: its own S starts, its own screen T(lambda) over its own
+ * S values, its own climbs and best, and its result is bit-identical to that
+ * call.  Together means one evaluation launch over the R*S starts and one
+ * climb launch over the passing starts of every round, so the SMs that one
+ * round's few passing starts leave idle climb the other rounds' (at n = 7000
+ * about 54 of 1000 random starts pass, one chain per SM on a 152-SM GPU).
+ *   R           1 .. 1024, with R * num_starts < 2^31.
+ *   best_x_dev  R*W words: round k's best solution at k*W.
+ *   best_f_dev  2R int64: round k's {best value, start index within the
+ *               round} at 2k.
+ *   ws          ubqp_solve_rounds_workspace_size(q, p, R) bytes (16-byte
+ *               aligned; 0 for invalid arguments).
+ * Fully async on `stream`.  The paper runs its rounds one after another, each
+ * from the incumbent of the last (ubqp_search); independent rounds, the
+ * multi-start of the paper restarted with fresh seeds, have no such order.
+ */
+size_t ubqp_solve_rounds_workspace_size(const ubqp_q* q, const ubqp_params* p, int32_t R);
+int ubqp_solve_rounds(const ubqp_q* q, const ubqp_params* p, int32_t R, uint64_t* best_x_dev,
+                      int64_t* best_f_dev, void* ws, size_t ws_bytes, void* stream);
+
+/*
  * Batches of instances: one round (as ubqp_solve, with the same parameters) for
  * every instance of a batch of uneven n, run together.  Start generation and
  * the tensor-core evaluation are one launch each for all instances (the

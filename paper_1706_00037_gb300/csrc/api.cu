@@ -576,6 +576,38 @@ int ubqp_best(const int64_t* f_dev, const uint64_t* X_dev, int64_t S, int32_t wo
   return UBQP_OK;
 }
 
+// Workspace of ubqp_solve_rounds: R rounds' starts, values, passing lists,
+// the combined list, flip counts and small results back to back, then the
+// scratch the evaluation and the climb of all R*S starts share.
+struct RoundsLayout {
+  size_t X, f, idx, idx_all, flips, counts, Tm, sstats, count_all, eval, total;
+};
+RoundsLayout rounds_layout(const ubqp_q* q, const ubqp_params* p, int32_t R) {
+  RoundsLayout L{};
+  const int64_t S = p->num_starts, RS = S * R;
+  size_t off = 0;
+  auto take = [&](size_t bytes) {
+    size_t at = off;
+    off += (size_t)round_up((int64_t)bytes, 256);
+    return at;
+  };
+  L.X = take((size_t)RS * q->W * 8);
+  L.f = take((size_t)RS * 8);
+  L.idx = take((size_t)RS * 4);
+  L.idx_all = take((size_t)RS * 4);
+  L.flips = take((size_t)RS * 4);
+  L.counts = take((size_t)R * 8);
+  L.Tm = take((size_t)R * 16);
+  L.sstats = take((size_t)R * 24);
+  L.count_all = take(8);
+  const int path = resolve_path(q, p->eval_path);
+  const size_t ev = path == UBQP_EVAL_TC_STAGED ? ubqp::eval_tc_workspace(q, RS) : 0;
+  const size_t as = ascent_ws_bytes(q, RS);
+  L.eval = take(ev > as ? ev : as);
+  L.total = off;
+  return L;
+}
+
 size_t ubqp_solve_workspace_size(const ubqp_q* q, const ubqp_params* p) {
   if (!q || !p || p->num_starts < 1) return 0;
   return solve_layout(q, p).total;
@@ -628,6 +660,64 @@ int ubqp_solve(const ubqp_q* q, const ubqp_params* p, uint64_t* best_x_dev, int6
     stats_host->T = hd[0];
     stats_host->mean = hd[1];
   }
+  return UBQP_OK;
+}
+
+size_t ubqp_solve_rounds_workspace_size(const ubqp_q* q, const ubqp_params* p, int32_t R) {
+  if (!q || !p || p->num_starts < 1 || R < 1 || R > 1024 ||
+      p->num_starts * (int64_t)R >= ((int64_t)1 << 31))
+    return 0;
+  return rounds_layout(q, p, R).total;
+}
+
+int ubqp_solve_rounds(const ubqp_q* q, const ubqp_params* p, int32_t R, uint64_t* best_x_dev,
+                      int64_t* best_f_dev, void* ws, size_t ws_bytes, void* stream) {
+  UBQP_RANGE("ubqp:solve_rounds");
+  if (!q || !p || !best_x_dev || !best_f_dev || !ws) return fail(UBQP_ERR_ARG, "NULL argument");
+  if (R < 1 || R > 1024) return fail(UBQP_ERR_ARG, "R outside [1, 1024]");
+  if (p->num_starts < 1 || p->num_starts * (int64_t)R >= ((int64_t)1 << 31))
+    return fail(UBQP_ERR_ARG, "num_starts * R outside [1, 2^31)");
+  if (((uintptr_t)ws & 15) != 0) return fail(UBQP_ERR_ARG, "workspace not 16-byte aligned");
+  const RoundsLayout L = rounds_layout(q, p, R);
+  if (ws_bytes < L.total) return fail(UBQP_ERR_NOMEM, "workspace %zu < %zu bytes", ws_bytes, L.total);
+  const int64_t S = p->num_starts, RS = S * R;
+  const int W = q->W;
+  char* base = (char*)ws;
+  uint64_t* X = (uint64_t*)(base + L.X);
+  int64_t* f = (int64_t*)(base + L.f);
+  int32_t* idx = (int32_t*)(base + L.idx);
+  int32_t* idx_all = (int32_t*)(base + L.idx_all);
+  int32_t* flips = (int32_t*)(base + L.flips);
+  int64_t* counts = (int64_t*)(base + L.counts);
+  double* Tm = (double*)(base + L.Tm);
+  int64_t* sstats = (int64_t*)(base + L.sstats);
+  int64_t* count_all = (int64_t*)(base + L.count_all);
+  cudaStream_t st = (cudaStream_t)stream;
+  int r;
+  // round k: the starts of ubqp_solve with seed + k and loop-counter offset round + k
+  for (int k = 0; k < R; ++k)
+    if ((r = ubqp_diversify(q, nullptr, p->mode, p->seed + (uint64_t)k, p->round + (uint64_t)k,
+                            S, p->div_H, X + (int64_t)k * S * W, stream)))
+      return r;
+  // one evaluation of all R*S starts
+  if ((r = ubqp_eval(q, X, RS, f, p->eval_path, base + L.eval, L.total - L.eval, stream)))
+    return r;
+  // each round's own screen over its own S values
+  for (int k = 0; k < R; ++k)
+    if ((r = ubqp_screen(f + (int64_t)k * S, S, p->lambda, idx + (int64_t)k * S, counts + k,
+                         Tm + 2 * k, sstats + 3 * k, stream)))
+      return r;
+  // one climb of every round's passing starts
+  UBQP_CUDA(ubqp::launch_concat_rounds(idx, counts, R, S, idx_all, count_all, st));
+  UBQP_CUDA(cudaMemsetAsync(flips, 0, sizeof(int32_t) * RS, st));
+  if ((r = ubqp_ascent(q, X, f, idx_all, count_all, RS, p->max_flips, flips, base + L.eval,
+                       L.total - L.eval, stream)))
+    return r;
+  // each round's best, the lowest start index within the round on ties
+  for (int k = 0; k < R; ++k)
+    if ((r = ubqp_best(f + (int64_t)k * S, X + (int64_t)k * S * W, S, W, best_x_dev + (int64_t)k * W,
+                       best_f_dev + 2 * k, stream)))
+      return r;
   return UBQP_OK;
 }
 

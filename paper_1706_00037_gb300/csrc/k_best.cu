@@ -98,6 +98,31 @@ batch_units_kernel(const BatchDesc* __restrict__ d, const int32_t* __restrict__ 
   if (threadIdx.x == 0) *n_units = ubase;
 }
 
+// The passing starts of R rounds held back to back (round r's S values at
+// r*S, its passing list at idx[r*S], its count at counts[r]) as one list of
+// global start indices r*S + idx, and its length.  R <= 1024.
+__global__ void __launch_bounds__(THREADS)
+concat_rounds_kernel(const int32_t* __restrict__ idx, const int64_t* __restrict__ counts, int R,
+                     int64_t S, int32_t* __restrict__ idx_all, int64_t* __restrict__ count_all) {
+  __shared__ int64_t off[1025];
+  if (threadIdx.x == 0) {
+    int64_t o = 0;
+    for (int r = 0; r < R; ++r) {
+      off[r] = o;
+      const int64_t c = counts[r];
+      o += c < 0 ? 0 : (c > S ? S : c);
+    }
+    off[R] = o;
+    *count_all = o;
+  }
+  __syncthreads();
+  for (int r = 0; r < R; ++r) {
+    const int64_t c = off[r + 1] - off[r];
+    for (int64_t t = threadIdx.x; t < c; t += THREADS)
+      idx_all[off[r] + t] = (int32_t)(r * S + idx[r * S + t]);
+  }
+}
+
 // out = {passed, total flips, max flips of one start, batch max, best index, sum}
 __global__ void __launch_bounds__(THREADS)
 solve_stats_kernel(const int64_t* __restrict__ count, const int32_t* __restrict__ idx,
@@ -200,6 +225,12 @@ cudaError_t launch_batch_items(const BatchDesc* d, const int32_t* order, int cou
 cudaError_t launch_batch_units(const BatchDesc* d, const int32_t* order, int count, int T, int C,
                                int2* items, int4* units, int64_t* n_units, cudaStream_t st) {
   batch_units_kernel<<<1, THREADS, 0, st>>>(d, order, count, T, C, items, units, n_units);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_concat_rounds(const int32_t* idx, const int64_t* counts, int R, int64_t S,
+                                 int32_t* idx_all, int64_t* count_all, cudaStream_t st) {
+  concat_rounds_kernel<<<1, THREADS, 0, st>>>(idx, counts, R, S, idx_all, count_all);
   return cudaGetLastError();
 }
 

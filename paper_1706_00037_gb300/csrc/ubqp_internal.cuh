@@ -220,6 +220,10 @@ cudaError_t launch_ascent_traced(const ubqp_q* h, uint64_t* X, int64_t* f, const
                                  const int64_t* count, int64_t S, int32_t max_flips,
                                  int32_t* flips, const float* Y, unsigned long long* next,
                                  uint16_t* trace, int64_t ldt, cudaStream_t st);
+// R rounds' passing lists (back to back, round r at idx + r S, count counts[r])
+// concatenated as global start indices r S + idx into idx_all, total count_all.
+cudaError_t launch_concat_rounds(const int32_t* idx, const int64_t* counts, int R, int64_t S,
+                                 int32_t* idx_all, int64_t* count_all, cudaStream_t st);
 cudaError_t launch_best(const int64_t* f, const uint64_t* X, int64_t S, int W,
                         uint64_t* best_x, int64_t* best_f, cudaStream_t st);
 cudaError_t launch_search_update(const int64_t* cand, const uint64_t* X, int W,

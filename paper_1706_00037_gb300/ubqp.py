@@ -36,7 +36,8 @@ EXPORTS = ["ubqp_strerror", "ubqp_last_error", "ubqp_abi_version", "ubqp_q_prepa
            "ubqp_relink_workspace_size", "ubqp_relink", "ubqp_server_inject_alloc_failures",
            "ubqp_selftest_timeout", "ubqp_search_resume", "ubqp_q_prepare_into_async",
            "ubqp_ascent_trace", "ubqp_peak_l2_read", "ubqp_peak_int32_ops", "ubqp_peak_int32",
-           "ubqp_batch_schedule", "ubqp_batch_set", "ubqp_server_stats"]
+           "ubqp_batch_schedule", "ubqp_batch_set", "ubqp_server_stats",
+           "ubqp_solve_rounds_workspace_size", "ubqp_solve_rounds"]
 
 
 class UbqpError(RuntimeError):
@@ -121,6 +122,8 @@ def load() -> ctypes.CDLL:
         "ubqp_solve_workspace_size": (sz, [P, ctypes.POINTER(Params)]),
         "ubqp_solve": (ctypes.c_int, [P, ctypes.POINTER(Params), P, P, ctypes.POINTER(Stats),
                                       P, sz, P]),
+        "ubqp_solve_rounds_workspace_size": (sz, [P, ctypes.POINTER(Params), i32]),
+        "ubqp_solve_rounds": (ctypes.c_int, [P, ctypes.POINTER(Params), i32, P, P, P, sz, P]),
         "ubqp_search_workspace_size": (sz, [P, ctypes.POINTER(SearchParams)]),
         "ubqp_search": (ctypes.c_int, [P, ctypes.POINTER(SearchParams), P, P, P, P, P, sz, P]),
         "ubqp_search_resume": (ctypes.c_int, [P, ctypes.POINTER(SearchParams), i32, P, P, P, P,
@@ -438,6 +441,28 @@ def solve(inst: Instance, params: Params, ws: torch.Tensor | None = None,
                              ctypes.byref(st) if st is not None else None, _ptr(ws),
                              ws.numel(), _stream(stream)))
     return bx, bf, (st.as_dict() if st is not None else None)
+
+
+def solve_rounds_workspace_size(inst: Instance, params: Params, R: int) -> int:
+    return int(load().ubqp_solve_rounds_workspace_size(inst.handle, ctypes.byref(params), R))
+
+
+def solve_rounds(inst: Instance, params: Params, R: int, ws: torch.Tensor | None = None,
+                 best_x: torch.Tensor | None = None, best_f: torch.Tensor | None = None,
+                 stream=None):
+    """R independent rounds run together (ubqp_solve_rounds): round k equals
+    solve() with seed + k and round + k.  Returns (best_x (R, W), best_f (R, 2))."""
+    dev = inst.device
+    if ws is None:
+        ws = torch.empty(max(solve_rounds_workspace_size(inst, params, R), 16),
+                         dtype=torch.uint8, device=dev)
+    if best_x is None:
+        best_x = torch.empty((R, inst.words), dtype=torch.int64, device=dev)
+    if best_f is None:
+        best_f = torch.empty((R, 2), dtype=torch.int64, device=dev)
+    _check(load().ubqp_solve_rounds(inst.handle, ctypes.byref(params), R, _ptr(best_x),
+                                    _ptr(best_f), _ptr(ws), ws.numel(), _stream(stream)))
+    return best_x, best_f
 
 
 def search(inst: Instance, num_samples: int, starts_per_round: int, rounds: int, lam: float,

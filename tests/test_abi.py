@@ -60,6 +60,8 @@ def test_host_side_argument_errors():
     assert lib.ubqp_ascent_trace(None, None, None, None, None, 1, 0, None, None, 4, None, 0,
                                  None) == -1
     assert b"trace" in lib.ubqp_last_error()
+    assert lib.ubqp_solve_rounds(None, ctypes.byref(p), 2, None, None, None, 0, None) == -1
+    assert lib.ubqp_solve_rounds_workspace_size(None, ctypes.byref(p), 2) == 0
     lib.ubqp_q_destroy(None)  # no-op
     # relinking, search, batch plans and the server validate on the host too
     assert lib.ubqp_relink(None, None, None, None, 4, None, None, None, None, 0, None) == -1
