@@ -17,6 +17,7 @@ import numpy as np
 import pytest
 import torch
 
+import oracle as orc
 from paper_1706_00037_gb300 import synth, ubqp
 
 pytestmark = pytest.mark.gpu
@@ -48,6 +49,9 @@ def test_noalloc_eval_equals_workspace_eval_on_consecutive_calls(n, density, S):
         assert _noalloc(lib, inst, X, got) == 0, lib.ubqp_last_error()
         inst.sync()
         assert torch.equal(got, want)
+        if n <= 1000:  # and every value against the CPU oracle
+            Xh = X.cpu().numpy().view(np.uint64)
+            assert np.array_equal(got.cpu().numpy(), orc.eval(Q, Xh))
 
 
 def test_noalloc_eval_exactly_fills_the_builtin_scratch():
