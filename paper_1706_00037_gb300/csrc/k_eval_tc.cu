@@ -25,6 +25,14 @@
 // one unit overlap the MMAs of the next.  Every wait is bounded: on timeout the
 // kernel records UBQP_DEVERR_TIMEOUT, drains its in-flight copies and MMAs,
 // frees its tensor memory and returns.
+//
+// Variants in this file: the fused A operand (four more warps write the 0/1
+// rows into the shared-memory stage from the bits), the A operand in tensor
+// memory, the Y mode (y = Q x of the passing starts over the full square, the
+// ascent's start-up), and for batches of instances the merged kernels: one
+// fused evaluation and one Y-mode product over work lists that mix the units
+// of every instance, each unit naming its instance and that instance's tensor
+// maps (arrays in global memory).
 #include <cuda.h>
 
 #include <algorithm>
