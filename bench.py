@@ -858,6 +858,20 @@ def main():
                      "peak_source": "derived: dp4a, 4 MACs per int32 lane-op x "
                                     f"{n_sm} SMs x 128 lanes x {sm_max:.0f} MHz"}
     roof_eval["frac"] = roof_eval["achieved"] / roof_eval["peak"]
+    if tc == ubqp.EVAL_TC:
+        # the operand tiles the tensor-core evaluation moves from L2 into shared
+        # memory: per K step of 64, a 128 x 64 bf16 A tile and a 256 x 64 B tile,
+        # for every m-tile of 128 starts and every 256-column block J over its
+        # K range [0, 256 (J + 1)) (chunks of at most 16 steps)
+        n_tc = (n + 255) // 256 * 256
+        k_steps = ((S + 127) // 128) * sum(min(4 * (J + 1), n_tc // 64)
+                                           for J in range(n_tc // 256))
+        tile_bytes = k_steps * (128 + 256) * 64 * 2
+        roof_eval["l2_leg"] = {"tile_bytes_per_launch": tile_bytes,
+                               "achieved_gbs": tile_bytes * a.steps / eval_s / 1e9,
+                               "peak_gbs": mp["l2_read_gbs"],
+                               "frac": tile_bytes * a.steps / eval_s / 1e9 / mp["l2_read_gbs"],
+                               "peak_source": "measured in this run: L2 read rate"}
     roof_eval["traffic"] = (profiled_traffic("eval_tc_n7000_dense.md",
                                              "traffic_bytes_per_launch_eval")
                             if n == 7000 and tc == ubqp.EVAL_TC else None)
