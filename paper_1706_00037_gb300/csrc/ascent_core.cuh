@@ -782,31 +782,53 @@ cudaError_t launch_block_occ(const ubqp_q* h, uint64_t* X, int64_t* f, const int
   return cudaGetLastError();
 }
 
-// Block groups.  With at most one listed start per SM every start climbs
-// alone on its SM, and the registers sized for one block per SM give the
-// shortest chain (measured at n = 7000: 1.91 ms for the ~52 passers of 1000
-// random starts, against 2.14 ms with registers sized for two).  With more
-// starts than SMs, two resident 256-thread blocks per SM overlap one chain's
-// waits with the other's work (1000 starts all climbed: 10.2 ms against
-// 12.2 ms).  The count is known only on the device, so for lists that may be
-// longer than the SM count both launches are made and each climbs only for
-// its own range of counts; the other returns at once.
+// Block groups, registers sized for one block per SM: with at most one listed
+// start per SM every start climbs alone on its SM, and this gives the shortest
+// chain (measured at n = 7000: 1.91 ms for the ~52 passers of 1000 random
+// starts, against 2.14 ms with registers sized for two).  The smaller groups
+// (64 and 128 threads) still fit several blocks per SM.  Climbs only for
+// counts up to cnt_hi; returns its resident capacity (blocks per SM x SMs).
 template <int T, int C, bool TR>
 cudaError_t launch_block(const ubqp_q* h, uint64_t* X, int64_t* f, const int32_t* idx,
                          const int64_t* count, int64_t S, int32_t max_flips, int32_t* flips,
                          const float* Y, unsigned long long* next, uint16_t* trace, int64_t ldt,
-                         cudaStream_t st) {
-  if constexpr (T == 256) {
-    if (S > h->sm_count) {
-      cudaError_t e = launch_block_occ<T, C, TR, 1>(h, X, f, idx, count, S, max_flips, flips, Y,
-                                                    next, trace, ldt, 0, h->sm_count, st);
-      if (e != cudaSuccess) return e;
-      return launch_block_occ<T, C, TR, 2>(h, X, f, idx, count, S, max_flips, flips, Y, next,
-                                           trace, ldt, (int64_t)h->sm_count + 1, INT64_MAX, st);
-    }
-  }
+                         int64_t cnt_hi, cudaStream_t st) {
   return launch_block_occ<T, C, TR, 1>(h, X, f, idx, count, S, max_flips, flips, Y, next, trace,
-                                       ldt, 0, INT64_MAX, st);
+                                       ldt, 0, cnt_hi, st);
+}
+template <int T, int C, bool TR>
+int64_t block_capacity(const ubqp_q* h) {
+  return resident_grid(ascent_block_kernel<T, C, kSpecRows, TR, 1>, T, h->sm_count);
+}
+
+// With more listed starts than the one-block-per-SM launch holds at once,
+// several blocks per SM overlap one chain's waits with the others' work:
+// groups of two 16-index chunks per thread, the fewest threads that hold n,
+// and as many blocks per SM as their registers allow (measured, 1000 starts
+// all climbed: n = 2000 0.94 vs 1.25 ms, 3000 2.02 vs 2.97, 4000 3.17 vs 4.02,
+// 6000 7.29 vs 8.63; n = 5000 with 8192 diversified starts, ~4500 passing:
+// 9.6 vs 13.5 ms).  Up to n = 1024 the one-block-per-SM groups, six per SM,
+// are faster at every count, and so are 256-thread groups above n = 6144.
+// The count is known only on the device, so for a list that may exceed the
+// capacity both launches are made; each climbs only for its own range of
+// counts and the other returns at once.
+template <bool TR>
+cudaError_t launch_block_many(const ubqp_q* h, uint64_t* X, int64_t* f, const int32_t* idx,
+                              const int64_t* count, int64_t S, int32_t max_flips,
+                              int32_t* flips, const float* Y, unsigned long long* next,
+                              uint16_t* trace, int64_t ldt, int64_t cnt_lo, cudaStream_t st) {
+  const int n = h->n;
+#define UBQP_MANY(TT, OCC)                                                                   \
+  return launch_block_occ<TT, 2, TR, OCC>(h, X, f, idx, count, S, max_flips, flips, Y, next, \
+                                          trace, ldt, cnt_lo, INT64_MAX, st)
+  if (n <= 2048) UBQP_MANY(64, 8);
+  if (n <= 3072) UBQP_MANY(96, 5);
+  if (n <= 4096) UBQP_MANY(128, 4);
+  if (n <= 5120) UBQP_MANY(160, 3);
+  if (n <= 6144) UBQP_MANY(192, 2);
+  if (n <= 8192) UBQP_MANY(256, 2);
+#undef UBQP_MANY
+  return cudaErrorInvalidValue;
 }
 
 template <int C, bool TR>
@@ -823,7 +845,10 @@ cudaError_t launch_warp(const ubqp_q* h, uint64_t* X, int64_t* f, const int32_t*
   return cudaGetLastError();
 }
 
-// One ascent launch over the listed starts, with the group shape that holds n.
+// One ascent launch over the listed starts, with the group shape that holds
+// n; for 1024 < n <= 8192 and a list that may be longer than that launch's
+// resident capacity, also the several-blocks-per-SM launch, the two splitting
+// the counts at the capacity.
 template <bool TR>
 cudaError_t launch_ascent_shaped(const ubqp_q* h, uint64_t* X, int64_t* f, const int32_t* idx,
                                  const int64_t* count, int64_t S, int32_t max_flips,
@@ -834,16 +859,22 @@ cudaError_t launch_ascent_shaped(const ubqp_q* h, uint64_t* X, int64_t* f, const
     cudaError_t e = cudaMemsetAsync(next, 0, sizeof(unsigned long long), st);
     if (e != cudaSuccess) return e;
   }
-#define UBQP_ASC_ARGS h, X, f, idx, count, S, max_flips, flips, Y, next, trace, ldt, st
-  if (n <= 256) return launch_warp<1, TR>(UBQP_ASC_ARGS);
-  if (n <= 512) return launch_warp<2, TR>(UBQP_ASC_ARGS);
-  if (n <= 1024) return launch_block<64, 1, TR>(UBQP_ASC_ARGS);
-  if (n <= 2048) return launch_block<128, 1, TR>(UBQP_ASC_ARGS);
-  if (n <= 4096) return launch_block<256, 1, TR>(UBQP_ASC_ARGS);
-  if (n <= 8192) return launch_block<256, 2, TR>(UBQP_ASC_ARGS);
-  if (n <= 16384) return launch_block<512, 2, TR>(UBQP_ASC_ARGS);
+#define UBQP_ASC_ARGS h, X, f, idx, count, S, max_flips, flips, Y, next, trace, ldt
+  if (n <= 256) return launch_warp<1, TR>(UBQP_ASC_ARGS, st);
+  if (n <= 512) return launch_warp<2, TR>(UBQP_ASC_ARGS, st);
+  if (n <= 1024) return launch_block<64, 1, TR>(UBQP_ASC_ARGS, INT64_MAX, st);
+  if (n > 8192) return launch_block<512, 2, TR>(UBQP_ASC_ARGS, INT64_MAX, st);
+  const int64_t cap = n <= 2048 ? block_capacity<128, 1, TR>(h)
+                      : n <= 4096 ? block_capacity<256, 1, TR>(h)
+                                  : block_capacity<256, 2, TR>(h);
+  const bool many = S > cap;
+  const int64_t hi = many ? cap : INT64_MAX;
+  cudaError_t e = n <= 2048   ? launch_block<128, 1, TR>(UBQP_ASC_ARGS, hi, st)
+                  : n <= 4096 ? launch_block<256, 1, TR>(UBQP_ASC_ARGS, hi, st)
+                              : launch_block<256, 2, TR>(UBQP_ASC_ARGS, hi, st);
+  if (e != cudaSuccess || !many) return e;
+  return launch_block_many<TR>(UBQP_ASC_ARGS, cap + 1, st);
 #undef UBQP_ASC_ARGS
-  return cudaErrorInvalidValue;
 }
 
 template <int T, int C>
