@@ -981,7 +981,7 @@ def main():
         # diversify 1, eval 1 (fused or plain) or 2 (unpack + tensor-core, staged),
         # screen 1, ascent 3 (unpack + tensor-core start-up + climb), best 1
         n_tc = (n + 255) // 256 * 256
-        staged = path == ubqp.EVAL_TC_STAGED or (path == ubqp.EVAL_AUTO and n_tc > 4096)
+        staged = path == ubqp.EVAL_TC_STAGED or (path == ubqp.EVAL_AUTO and not (n_tc <= 1024 and S >= 4096))
         launches_per_step = 1 + (2 if staged else 1) + 1 + 3 + 1
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
                 "steps": a.steps, "warmup": a.warmup, "ms_per_step": max_total / a.steps,

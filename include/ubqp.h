@@ -186,8 +186,9 @@ int ubqp_diversify_range(const ubqp_q* q, const uint64_t* x0_dev, int32_t mode,
  *        carries only Q'; needs no workspace.
  *   path UBQP_EVAL_PLAIN: one block per solution on the CUDA cores (dp4a);
  *        needs no workspace.
- *   path UBQP_EVAL_AUTO: UBQP_EVAL_TC up to n_pad = 4096 (n rounded up to
- *        256), UBQP_EVAL_TC_STAGED above (the faster of the two, measured).
+ *   path UBQP_EVAL_AUTO: UBQP_EVAL_TC_STAGED, except UBQP_EVAL_TC for
+ *        n_pad <= 1024 (n rounded up to 256) with S >= 4096 (the faster of
+ *        the two, measured).
  * Returns UBQP_ERR_RANGE if the exactness bound fails (see top of file).
  */
 size_t ubqp_eval_workspace_size(const ubqp_q* q, int64_t S, int32_t path);

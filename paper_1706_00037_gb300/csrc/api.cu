@@ -62,13 +62,11 @@ const int8_t* kernel_readable(const int8_t* p) {
   return nullptr;
 }
 
-// AUTO: the fused tensor-core evaluation up to n_pad 4096, the staged one above
-// (measured faster at n = 7000: 61 vs 67 us for 1000 starts; fused wins at
-// n = 2500: 23 vs 27 us).  Results are identical either way.
-constexpr int kFusedMaxNtc = 4096;
-int resolve_path(const ubqp_q* q, int path) {
+// AUTO: the staged or the fused tensor-core evaluation, whichever is faster
+// for this size (ubqp::eval_auto_fused).
+int resolve_path(const ubqp_q* q, int64_t S, int path) {
   if (path != UBQP_EVAL_AUTO) return path;
-  return (q && q->n_tc > kFusedMaxNtc) ? UBQP_EVAL_TC_STAGED : UBQP_EVAL_TC;
+  return (q && ubqp::eval_auto_fused(q->n_tc, S)) ? UBQP_EVAL_TC : UBQP_EVAL_TC_STAGED;
 }
 
 // Workspace of ubqp_solve, carved in this order (each piece 256-byte aligned).
@@ -93,7 +91,7 @@ SolveLayout solve_layout(const ubqp_q* q, const ubqp_params* p) {
   L.idx = take((size_t)S * 4);
   L.flips = take((size_t)S * 4);
   L.small = take(kSmallBytes);
-  const int path = resolve_path(q, p->eval_path);
+  const int path = resolve_path(q, S, p->eval_path);
   const size_t ev = path == UBQP_EVAL_TC_STAGED ? ubqp::eval_tc_workspace(q, S) : 0;
   const size_t as = ascent_ws_bytes(q, S);
   L.eval = take(ev > as ? ev : as);
@@ -344,7 +342,7 @@ int ubqp_diversify(const ubqp_q* q, const uint64_t* x0_dev, int32_t mode, uint64
 
 size_t ubqp_eval_workspace_size(const ubqp_q* q, int64_t S, int32_t path) {
   if (!q || S < 0) return 0;
-  return resolve_path(q, path) == UBQP_EVAL_TC_STAGED ? ubqp::eval_tc_workspace(q, S) : 0;
+  return resolve_path(q, S, path) == UBQP_EVAL_TC_STAGED ? ubqp::eval_tc_workspace(q, S) : 0;
 }
 
 int ubqp_eval(const ubqp_q* q, const uint64_t* X_dev, int64_t S, int64_t* f_dev, int32_t path,
@@ -352,7 +350,7 @@ int ubqp_eval(const ubqp_q* q, const uint64_t* X_dev, int64_t S, int64_t* f_dev,
   UBQP_RANGE("ubqp:eval");
   if (!q || !X_dev || !f_dev) return fail(UBQP_ERR_ARG, "NULL argument");
   if (S < 0) return fail(UBQP_ERR_ARG, "S < 0");
-  path = resolve_path(q, path);
+  path = resolve_path(q, S, path);
   if (path != UBQP_EVAL_TC && path != UBQP_EVAL_PLAIN && path != UBQP_EVAL_TC_STAGED &&
       path != UBQP_EVAL_TC_TMEM)
     return fail(UBQP_ERR_ARG, "unknown eval path %d", path);
@@ -600,7 +598,7 @@ RoundsLayout rounds_layout(const ubqp_q* q, const ubqp_params* p, int32_t R) {
   L.Tm = take((size_t)R * 16);
   L.sstats = take((size_t)R * 24);
   L.count_all = take(8);
-  const int path = resolve_path(q, p->eval_path);
+  const int path = resolve_path(q, RS, p->eval_path);
   const size_t ev = path == UBQP_EVAL_TC_STAGED ? ubqp::eval_tc_workspace(q, RS) : 0;
   const size_t as = ascent_ws_bytes(q, RS);
   L.eval = take(ev > as ? ev : as);
@@ -744,9 +742,12 @@ SearchLayout search_layout(const ubqp_q* q, const ubqp_search_params* p) {
   L.small = take(256);
   L.inc_x = take((size_t)q->W * 8);
   L.cand_x = take((size_t)q->W * 8);
-  const int path = resolve_path(q, p->eval_path);
+  // the samples and the rounds' starts are evaluated apart (each count may
+  // resolve AUTO its own way)
+  const bool staged = resolve_path(q, S, p->eval_path) == UBQP_EVAL_TC_STAGED ||
+                      resolve_path(q, NS, p->eval_path) == UBQP_EVAL_TC_STAGED;
   const int64_t big = S > NS ? S : NS;
-  const size_t ev = path == UBQP_EVAL_TC_STAGED ? ubqp::eval_tc_workspace(q, big) : 0;
+  const size_t ev = staged ? ubqp::eval_tc_workspace(q, big) : 0;
   const size_t as = ascent_ws_bytes(q, S);
   L.scratch = take(ev > as ? ev : as);
   L.total = off;

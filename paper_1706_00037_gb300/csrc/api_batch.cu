@@ -141,12 +141,13 @@ int run_body(ubqp_batch* b, cudaStream_t st) {
     UBQP_BCUDA(ubqp::launch_diversify(q->x0, q->n, p.mode, p.seed, p.round, p.num_starts, 0,
                                       p.num_starts, p.div_H, d.X, s, b->d_seed));
     if (b->eval_path == UBQP_EVAL_TC) {
-      // fused operand build up to n_pad 4096, staged above (as UBQP_EVAL_AUTO)
+      // fused or staged operand build, as UBQP_EVAL_AUTO picks for this size
       const int alt = b->eval_kch == ubqp_batch::kAltKch[0] ? 0
                       : b->eval_kch == ubqp_batch::kAltKch[1] ? 1 : -1;
       UBQP_BCUDA(ubqp::launch_eval_tc(q, d.X, p.num_starts, d.f, b->scratch[i],
                                       b->scratch_bytes[i], s, b->mapA[i].bytes,
-                                      q->n_tc <= 4096, alt >= 0 ? b->alt_chunks[alt][i] : nullptr,
+                                      ubqp::eval_auto_fused(q->n_tc, p.num_starts),
+                                      alt >= 0 ? b->alt_chunks[alt][i] : nullptr,
                                       alt >= 0 ? b->alt_nchunks[alt][i] : 0));
     } else {
       UBQP_BCUDA(ubqp::launch_eval_plain(q, d.X, p.num_starts, d.f, s));

@@ -113,7 +113,7 @@ namespace {
 int resolve_path(const ubqp_server_config& c, int n_tc) {
   const int p = c.params.eval_path;
   if (p != UBQP_EVAL_AUTO) return p;
-  return n_tc > 4096 ? UBQP_EVAL_TC_STAGED : UBQP_EVAL_TC;
+  return ubqp::eval_auto_fused(n_tc, c.params.num_starts) ? UBQP_EVAL_TC : UBQP_EVAL_TC_STAGED;
 }
 
 // Device bytes of one request of size n, carved in this order (each piece

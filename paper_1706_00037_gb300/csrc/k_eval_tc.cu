@@ -286,13 +286,6 @@ eval_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ 
   volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  int64_t rows = S;
-  if (YMODE) {
-    const int64_t c = *count;
-    rows = c < S ? (c > 0 ? c : 0) : S;
-    m_tiles = (int)((rows + BM - 1) / BM);
-  }
-  const int n_units = n_chunks * m_tiles;
 
   if (threadIdx.x == 0) {
     for (int s = 0; s < STAGES; ++s) {
@@ -319,6 +312,17 @@ eval_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ 
   __syncthreads();
   tc_fence_after();
   const uint32_t tmem = *tmem_slot;
+  // Launched as a programmatic dependent of the unpacking (or of whatever
+  // kernel precedes it on the stream): everything above overlaps that grid's
+  // tail; nothing below reads memory before it has finished.
+  asm volatile("griddepcontrol.wait;" ::: "memory");
+  int64_t rows = S;
+  if (YMODE) {
+    const int64_t c = *count;
+    rows = c < S ? (c > 0 ? c : 0) : S;
+    m_tiles = (int)((rows + BM - 1) / BM);
+  }
+  const int n_units = n_chunks * m_tiles;
 
   if (warp == 0) {
     if (lane == 0) {
@@ -1173,59 +1177,68 @@ __global__ void selftest_wait_kernel(uint64_t limit_ns, int32_t* status) {
   }
 }
 
-// Unpack bit-packed solutions into the bf16 A operand: S_p x n_tc of 0.0 / 1.0.
-// Row t is solution idx[t] (t < *count) when idx is given, else solution t
-// (t < S); other rows and columns >= n are zero.  One thread per 16 columns
-// (two 16-byte stores).
 // Rows of 0.0/1.0 bf16 (the A operand of the staged kernel) from the bit-packed
-// starts, 16 elements per item; with idx, row t is start idx[t] for t < *count
-// and zero up to the next multiple of 128 (the last m-tile the product reads;
-// rows beyond are not written), and with Y the product's rows t < *count are
-// zeroed for its accumulation.
+// starts, 16 elements (two 16-byte stores) per item: S_p x n_tc, row t is
+// start t (t < S), or with idx start idx[t] for t < *count and zero up to the
+// next multiple of 128 (the last m-tile the product reads; rows beyond are not
+// written); columns >= n are zero.  With Y the product's rows t < *count are
+// zeroed for its accumulation.  Blocks take rows, threads the 16-column items
+// of a row (no 64-bit division).
 __device__ __forceinline__ void unpack_rows(const uint64_t* __restrict__ X, int n, int W,
                                             int64_t S, const int32_t* __restrict__ idx,
                                             const int64_t* __restrict__ count, int64_t S_p,
                                             int n_tc, uint4* __restrict__ Xe,
                                             float* __restrict__ Y, int64_t block,
                                             int64_t blocks) {
-  const int64_t per_row = n_tc / 16;
+  const int per_row = n_tc / 16;
   int64_t rows = S, rows_p = S_p;
   if (idx) {
     const int64_t c = *count;
     rows = c < S ? (c > 0 ? c : 0) : S;
     rows_p = (rows + BM - 1) / BM * BM;
   }
-  const int64_t total = rows_p * per_row;
-  for (int64_t t = block * (int64_t)blockDim.x + threadIdx.x; t < total;
-       t += blocks * blockDim.x) {
-    const int64_t r = t / per_row;
-    const int c = (int)(t - r * per_row);
-    const int w = c >> 2;
-    uint32_t x16 = 0;
-    if (r < rows && w < W) {
+  for (int64_t r = block; r < rows_p; r += blocks) {
+    const uint64_t* xr = nullptr;
+    if (r < rows) {
       const int64_t src = idx ? (int64_t)idx[r] : r;
-      if (src >= 0 && src < S)
-        x16 = (uint32_t)(((X[src * W + w] & valid_mask(n, w)) >> ((c & 3) * 16)) & 0xFFFFu);
+      if (src >= 0 && src < S) xr = X + src * W;
     }
-    uint32_t v[8];
-    expand16(x16, v);
-    Xe[2 * t] = make_uint4(v[0], v[1], v[2], v[3]);
-    Xe[2 * t + 1] = make_uint4(v[4], v[5], v[6], v[7]);
-    if (Y && r < rows) {
-      float4* yr = reinterpret_cast<float4*>(Y + r * (int64_t)n_tc + 16 * c);
-      const float4 z = make_float4(0.f, 0.f, 0.f, 0.f);
-      yr[0] = z;
-      yr[1] = z;
-      yr[2] = z;
-      yr[3] = z;
+    uint4* er = Xe + 2 * r * per_row;
+    for (int c = threadIdx.x; c < per_row; c += blockDim.x) {
+      const int w = c >> 2;
+      uint32_t x16 = 0;
+      if (xr && w < W)
+        x16 = (uint32_t)(((xr[w] & valid_mask(n, w)) >> ((c & 3) * 16)) & 0xFFFFu);
+      uint32_t v[8];
+      expand16(x16, v);
+      er[2 * c] = make_uint4(v[0], v[1], v[2], v[3]);
+      er[2 * c + 1] = make_uint4(v[4], v[5], v[6], v[7]);
+      if (Y && r < rows) {
+        float4* yr = reinterpret_cast<float4*>(Y + r * (int64_t)n_tc + 16 * c);
+        const float4 z = make_float4(0.f, 0.f, 0.f, 0.f);
+        yr[0] = z;
+        yr[1] = z;
+        yr[2] = z;
+        yr[3] = z;
+      }
     }
   }
 }
 
+// The evaluation's and the start-up's unpacking.  It lets the product that
+// follows on the stream (launched as a programmatic dependent) start its
+// set-up at once; that kernel waits for this grid to finish before it reads
+// what this one writes.  With fz, f[0 .. nfz) is zeroed for the evaluation's
+// accumulation (in place of a separate memset).
 __global__ void unpack_bits_bf16(const uint64_t* __restrict__ X, int n, int W, int64_t S,
                                  const int32_t* __restrict__ idx,
                                  const int64_t* __restrict__ count, int64_t S_p, int n_tc,
-                                 uint4* __restrict__ Xe, float* __restrict__ Y) {
+                                 uint4* __restrict__ Xe, float* __restrict__ Y,
+                                 int64_t* __restrict__ fz, int64_t nfz) {
+  asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+  for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; fz && t < nfz;
+       t += (int64_t)gridDim.x * blockDim.x)
+    fz[t] = 0;
   unpack_rows(X, n, W, S, idx, count, S_p, n_tc, Xe, Y, (int64_t)blockIdx.x, (int64_t)gridDim.x);
 }
 
@@ -1517,6 +1530,30 @@ cudaError_t eval_tc_prepare(ubqp_q* h, cudaStream_t) {
   return cudaSuccess;
 }
 
+// Launch a product kernel as a programmatic dependent of the unpacking kernel
+// launched just before it on the same stream (the kernel waits for that grid
+// with griddepcontrol.wait before its first dependent read).
+template <bool YMODE, bool FUSED>
+cudaError_t launch_product(int grid, int threads, int smem, cudaStream_t st, const CUtensorMap& mapA,
+                           const CUtensorMap& mapB, const uint64_t* X, int n, int W, int64_t S,
+                           int m_tiles, const int4* chunks, int n_chunks, int64_t* f,
+                           const int64_t* count, float* Y, int64_t ldy, unsigned* err) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3((unsigned)grid);
+  cfg.blockDim = dim3((unsigned)threads);
+  cfg.dynamicSmemBytes = (size_t)smem;
+  cfg.stream = st;
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  at[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = at;
+  cfg.numAttrs = 1;
+  void* args[] = {const_cast<CUtensorMap*>(&mapA), const_cast<CUtensorMap*>(&mapB), &X, &n, &W,
+                  &S, &m_tiles, &chunks, &n_chunks, &f, &count, &Y, &ldy, &err};
+  return cudaLaunchKernelExC(&cfg, reinterpret_cast<const void*>(&eval_tc_kernel<YMODE, FUSED>),
+                             args);
+}
+
 size_t ascent_tc_workspace(const ubqp_q* h, int64_t S) {
   return (size_t)padded_starts(S) * (size_t)h->n_tc * (2 + 4);
 }
@@ -1537,11 +1574,10 @@ cudaError_t launch_ascent_init_tc(const ubqp_q* h, const uint64_t* X, const int3
   float* Y = reinterpret_cast<float*>(Xe + (size_t)S_p * h->n_tc * 2);
   cudaError_t e;
   {
-    const int64_t total = S_p * (h->n_tc / 16);
-    int64_t blocks = (total + 255) / 256;
-    if (blocks > (int64_t)h->sm_count * 8) blocks = (int64_t)h->sm_count * 8;
+    const int64_t blocks = std::min<int64_t>(S_p, (int64_t)h->sm_count * 8);
     unpack_bits_bf16<<<(unsigned)blocks, 256, 0, st>>>(X, h->n, h->W, S, idx, count, S_p,
-                                                      h->n_tc, reinterpret_cast<uint4*>(Xe), Y);
+                                                      h->n_tc, reinterpret_cast<uint4*>(Xe), Y,
+                                                      nullptr, 0);
     if ((e = cudaGetLastError())) return e;
   }
   alignas(64) CUtensorMap mapA;
@@ -1551,11 +1587,11 @@ cudaError_t launch_ascent_init_tc(const ubqp_q* h, const uint64_t* X, const int3
   const int m_tiles = (int)(S_p / BM);
   const int n_units = h->tc_nchunks_y * m_tiles;
   const int grid = n_units < h->sm_count ? n_units : h->sm_count;
-  eval_tc_kernel<true, false><<<grid, THREADS, SMEM_BYTES, st>>>(
-      mapA, *reinterpret_cast<const CUtensorMap*>(h->tc_mapF), X, h->n, h->W, S, m_tiles,
-      reinterpret_cast<const int4*>(h->tc_chunks) + h->tc_nchunks, h->tc_nchunks_y, nullptr,
-      count, Y, h->n_tc, h->err);
-  if ((e = cudaGetLastError())) return e;
+  if ((e = launch_product<true, false>(
+           grid, THREADS, SMEM_BYTES, st, mapA, *reinterpret_cast<const CUtensorMap*>(h->tc_mapF),
+           X, h->n, h->W, S, m_tiles, reinterpret_cast<const int4*>(h->tc_chunks) + h->tc_nchunks,
+           h->tc_nchunks_y, nullptr, count, Y, (int64_t)h->n_tc, h->err)))
+    return e;
   *Y_out = Y;
   return cudaSuccess;
 }
@@ -1590,19 +1626,18 @@ cudaError_t launch_eval_tc(const ubqp_q* h, const uint64_t* X, int64_t S, int64_
   alignas(64) CUtensorMap mapA;
   if (fused) {
     mapA = *reinterpret_cast<const CUtensorMap*>(h->tc_mapB);  // unused by the fused kernel
+    if ((e = cudaMemsetAsync(f, 0, sizeof(int64_t) * S, st))) return e;
   } else {
     if (ws_bytes < eval_tc_workspace(h, S)) return cudaErrorInvalidValue;
-    const int64_t total = S_p * (h->n_tc / 16);
-    int64_t blocks = (total + 255) / 256;
-    if (blocks > (int64_t)h->sm_count * 8) blocks = (int64_t)h->sm_count * 8;
-    unpack_bits_bf16<<<(unsigned)blocks, 256, 0, st>>>(X, h->n, h->W, S, nullptr, nullptr,
-                                                      S_p, h->n_tc,
-                                                      reinterpret_cast<uint4*>(ws), nullptr);
-    if ((e = cudaGetLastError())) return e;
     if (mapA_in) mapA = *reinterpret_cast<const CUtensorMap*>(mapA_in);
     else if (!make_map(&mapA, ws, S_p, h->n_tc, BM)) return cudaErrorInvalidValue;
+    // the unpacking also zeroes f
+    const int64_t blocks = std::min<int64_t>(S_p, (int64_t)h->sm_count * 8);
+    unpack_bits_bf16<<<(unsigned)blocks, 256, 0, st>>>(X, h->n, h->W, S, nullptr, nullptr,
+                                                      S_p, h->n_tc,
+                                                      reinterpret_cast<uint4*>(ws), nullptr, f, S);
+    if ((e = cudaGetLastError())) return e;
   }
-  if ((e = cudaMemsetAsync(f, 0, sizeof(int64_t) * S, st))) return e;
   const int m_tiles = (int)(S_p / BM);
   const int4* ch = chunks_in ? chunks_in : reinterpret_cast<const int4*>(h->tc_chunks);
   const int nch = chunks_in ? nchunks_in : h->tc_nchunks;
@@ -1616,9 +1651,8 @@ cudaError_t launch_eval_tc(const ubqp_q* h, const uint64_t* X, int64_t S, int64_
         h->err);
   } else {
     if ((e = set_smem_attr_once<false, false>())) return e;
-    eval_tc_kernel<false, false><<<grid, THREADS, SMEM_BYTES, st>>>(
-        mapA, mapB, X, h->n, h->W, S, m_tiles, ch, nch, f, nullptr, nullptr, 0,
-        h->err);
+    return launch_product<false, false>(grid, THREADS, SMEM_BYTES, st, mapA, mapB, X, h->n, h->W,
+                                        S, m_tiles, ch, nch, f, nullptr, nullptr, 0, h->err);
   }
   return cudaGetLastError();
 }

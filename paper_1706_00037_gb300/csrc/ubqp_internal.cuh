@@ -56,6 +56,14 @@ struct ubqp_q {
 
 namespace ubqp {
 
+// The tensor-core evaluation UBQP_EVAL_AUTO takes for S starts of an instance
+// padded to n_tc: the fused operand build only for small instances with many
+// starts, the staged one otherwise (measured on GB300, L2 flushed: 1000
+// starts at n = 2500 staged 19.6 us vs fused 22.2, at n = 7000 51.9 vs 64.2;
+// 8192 starts at n = 200 staged 19.1 vs fused 16.0, at n = 1500 36.5 vs 38.0).
+// Results are identical either way.
+inline bool eval_auto_fused(int n_tc, int64_t S) { return n_tc <= 1024 && S >= 4096; }
+
 // An NVTX range named after the API call, for timeline tools (a no-op
 // without one attached).
 struct NvtxRange {

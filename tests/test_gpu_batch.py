@@ -125,9 +125,9 @@ def test_batch_set_rejects_shapes_that_cannot_hold_n():
 
 def test_batch_merged_evaluation_values():
     # one merged launch each for the start generation and the evaluation of
-    # instances of ragged sizes (single words, word and tile tails, above the
-    # fused path's usual 4096 limit), at every schedule: results equal to
-    # single solves
+    # instances of ragged sizes (single words, word and tile tails, and sizes
+    # where single solves take the staged evaluation), at every schedule:
+    # results equal to single solves
     sizes = [60, 700, 2500, 300, 1025, 129, 2100, 513, 1, 64, 65, 4096, 4100]
     Qs, insts = make_batch(sizes, [0.5] * len(sizes), seed0=950)
     p = ubqp.make_params(300, 0.5, seed=0)
