@@ -210,16 +210,56 @@ __device__ __forceinline__ void tmem_st16(uint32_t taddr, const uint32_t (&v)[16
 
 #define UBQP_R8(i) "=r"(r[i]), "=r"(r[i + 1]), "=r"(r[i + 2]), "=r"(r[i + 3]), \
                    "=r"(r[i + 4]), "=r"(r[i + 5]), "=r"(r[i + 6]), "=r"(r[i + 7])
+// 32 consecutive 32-bit columns of this thread's lane, loaded and waited for
+// in one statement (so no use of r can be scheduled before the wait).
 __device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&r)[32]) {
   asm volatile(
       "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10,"
       " %11, %12, %13, %14, %15, %16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27,"
-      " %28, %29, %30, %31}, [%32];"
+      " %28, %29, %30, %31}, [%32];\n"
+      "tcgen05.wait::ld.sync.aligned;"
       : UBQP_R8(0), UBQP_R8(8), UBQP_R8(16), UBQP_R8(24)
-      : "r"(taddr));
-  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+      : "r"(taddr)
+      : "memory");
 }
 #undef UBQP_R8
+
+#define UBQP_R8(i) "=r"(r[i]), "=r"(r[i + 1]), "=r"(r[i + 2]), "=r"(r[i + 3]), \
+                   "=r"(r[i + 4]), "=r"(r[i + 5]), "=r"(r[i + 6]), "=r"(r[i + 7])
+// 64 consecutive 32-bit columns of this thread's lane, loaded and waited for
+// in one statement (so no use of r can be scheduled before the wait).
+__device__ __forceinline__ void tmem_ld64(uint32_t taddr, uint32_t (&r)[64]) {
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x64.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10,"
+      " %11, %12, %13, %14, %15, %16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27,"
+      " %28, %29, %30, %31, %32, %33, %34, %35, %36, %37, %38, %39, %40, %41, %42, %43, %44,"
+      " %45, %46, %47, %48, %49, %50, %51, %52, %53, %54, %55, %56, %57, %58, %59, %60, %61,"
+      " %62, %63}, [%64];\n"
+      "tcgen05.wait::ld.sync.aligned;"
+      : UBQP_R8(0), UBQP_R8(8), UBQP_R8(16), UBQP_R8(24), UBQP_R8(32), UBQP_R8(40),
+        UBQP_R8(48), UBQP_R8(56)
+      : "r"(taddr)
+      : "memory");
+}
+#undef UBQP_R8
+
+// The evaluation epilogue's share of 64 accumulator columns: the sum of the
+// columns whose solution bit is set.  Every column value is an integer of
+// magnitude at most 2^18 (a unit sums at most 1024 products of magnitude
+// <= 256), so each fp32 partial over 16 columns (<= 2^22) is exact.
+__device__ __forceinline__ int row_dot64(uint32_t taddr, uint64_t bits) {
+  uint32_t r[64];
+  tmem_ld64(taddr, r);
+  float p[4] = {0.f, 0.f, 0.f, 0.f};
+#pragma unroll
+  for (int i = 0; i < 16; ++i) {
+#pragma unroll
+    for (int g = 0; g < 4; ++g)
+      if ((bits >> (16 * g + i)) & 1ull) p[g] += __uint_as_float(r[16 * g + i]);
+  }
+  return __float2int_rn(p[0]) + __float2int_rn(p[1]) + __float2int_rn(p[2]) +
+         __float2int_rn(p[3]);
+}
 
 struct Unit {
   int nb, k0, nk, mt;
@@ -453,10 +493,28 @@ eval_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ 
     const int q = warp & 3;
     const int row = q * 32 + lane;
     int t = 0;
+    // the solution words of a unit's 256 columns in this row, loaded one unit
+    // ahead (their latency off the accumulator hand-off)
+    auto unit_xw = [&](int u, uint64_t (&w4)[4]) {
+      const uint64_t* xp = nullptr;
+      int w0 = 0;
+      if (!YMODE && u < n_units) {
+        const Unit v = unit_of(chunks, m_tiles, u);
+        const int64_t sv = (int64_t)v.mt * BM + row;
+        if (sv < S) xp = X + sv * W;
+        w0 = v.nb * 4;
+      }
+#pragma unroll
+      for (int i = 0; i < 4; ++i) w4[i] = (xp && w0 + i < W) ? xp[w0 + i] : 0ull;
+    };
+    uint64_t xw[4];
+    unit_xw(blockIdx.x, xw);
     for (int u = blockIdx.x; u < n_units; u += gridDim.x, ++t) {
       const Unit un = unit_of(chunks, m_tiles, u);
       const int a = t & 1;
       const uint32_t aphase = (uint32_t)((t >> 1) & 1);
+      uint64_t xn[4];
+      unit_xw(u + gridDim.x, xn);
       // the warp arrives as one on tempty below: leave together
       const bool got = mbar_wait(&tfull[a], aphase, abort_flag, err);
       if (!__all_sync(0xffffffffu, got)) break;
@@ -482,22 +540,9 @@ eval_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ 
         __syncwarp();
         if (lane == 0) mbar_arrive(&tempty[a]);
       } else {
-        uint64_t xw[4];
-#pragma unroll
-        for (int i = 0; i < 4; ++i) {
-          const int w = un.nb * 4 + i;
-          xw[i] = (s < S && w < W) ? X[s * W + w] : 0ull;
-        }
         int acc = 0;
 #pragma unroll 1
-        for (int cc = 0; cc < BN / 32; ++cc) {
-          uint32_t r[32];
-          tmem_ld32(base + (uint32_t)(cc * 32), r);
-          const uint32_t bits = (uint32_t)(xw[cc >> 1] >> ((cc & 1) * 32));
-#pragma unroll
-          for (int i = 0; i < 32; ++i)
-            if ((bits >> i) & 1u) acc += __float2int_rn(__uint_as_float(r[i]));
-        }
+        for (int cc = 0; cc < BN / 64; ++cc) acc += row_dot64(base + (uint32_t)(cc * 64), xw[cc]);
         tc_fence_before();
         __syncwarp();
         if (lane == 0) mbar_arrive(&tempty[a]);
@@ -505,6 +550,8 @@ eval_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ 
           atomicAdd(reinterpret_cast<unsigned long long*>(&f[s]),
                     (unsigned long long)(long long)acc);
       }
+#pragma unroll
+      for (int i = 0; i < 4; ++i) xw[i] = xn[i];
     }
   }
   __syncthreads();
@@ -706,38 +753,46 @@ eval_tc_multi_kernel(const EvalInst* __restrict__ insts, const CUtensorMap* __re
     const int q = warp & 3;
     const int row = q * 32 + lane;
     int t = 0;
+    // the unit's solution words in this row, loaded one unit ahead
+    auto unit_xw = [&](int u, uint64_t (&w4)[4]) {
+      const uint64_t* xp = nullptr;
+      int w0 = 0, Wv = 0;
+      if (u < n_units) {
+        const MUnit v = units[u];
+        const EvalInst& ev = insts[v.inst];
+        const int64_t sv = (int64_t)v.mt * BM + row;
+        if (sv < ev.S) xp = ev.X + sv * ev.W;
+        w0 = v.nb * 4;
+        Wv = ev.W;
+      }
+#pragma unroll
+      for (int i = 0; i < 4; ++i) w4[i] = (xp && w0 + i < Wv) ? xp[w0 + i] : 0ull;
+    };
+    uint64_t xw[4];
+    unit_xw(blockIdx.x, xw);
     for (int u = blockIdx.x; u < n_units; u += gridDim.x, ++t) {
       const MUnit un = units[u];
       const EvalInst e = insts[un.inst];
       const int a = t & 1;
       const uint32_t aphase = (uint32_t)((t >> 1) & 1);
+      uint64_t xn[4];
+      unit_xw(u + gridDim.x, xn);
       const bool got = mbar_wait(&tfull[a], aphase, abort_flag, err);
       if (!__all_sync(0xffffffffu, got)) break;
       tc_fence_after();
       const int64_t s = (int64_t)un.mt * BM + row;
       const uint32_t base = tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(a * BN);
-      uint64_t xw[4];
-#pragma unroll
-      for (int i = 0; i < 4; ++i) {
-        const int w = un.nb * 4 + i;
-        xw[i] = (s < e.S && w < e.W) ? e.X[s * e.W + w] : 0ull;
-      }
       int acc = 0;
 #pragma unroll 1
-      for (int cc = 0; cc < BN / 32; ++cc) {
-        uint32_t r[32];
-        tmem_ld32(base + (uint32_t)(cc * 32), r);
-        const uint32_t bits = (uint32_t)(xw[cc >> 1] >> ((cc & 1) * 32));
-#pragma unroll
-        for (int i = 0; i < 32; ++i)
-          if ((bits >> i) & 1u) acc += __float2int_rn(__uint_as_float(r[i]));
-      }
+      for (int cc = 0; cc < BN / 64; ++cc) acc += row_dot64(base + (uint32_t)(cc * 64), xw[cc]);
       tc_fence_before();
       __syncwarp();
       if (lane == 0) mbar_arrive(&tempty[a]);
       if (s < e.S && acc != 0)
         atomicAdd(reinterpret_cast<unsigned long long*>(&e.f[s]),
                   (unsigned long long)(long long)acc);
+#pragma unroll
+      for (int i = 0; i < 4; ++i) xw[i] = xn[i];
     }
   }
   __syncthreads();
@@ -1133,14 +1188,8 @@ eval_ts_kernel(const __grid_constant__ CUtensorMap tmB, const uint64_t* __restri
       }
       int acc = 0;
 #pragma unroll 1
-      for (int cc = 0; cc < BN_TS / 32; ++cc) {
-        uint32_t r[32];
-        tmem_ld32(base + (uint32_t)(cc * 32), r);
-        const uint32_t bits = (uint32_t)(xw[cc >> 1] >> ((cc & 1) * 32));
-#pragma unroll
-        for (int i = 0; i < 32; ++i)
-          if ((bits >> i) & 1u) acc += __float2int_rn(__uint_as_float(r[i]));
-      }
+      for (int cc = 0; cc < BN_TS / 64; ++cc)
+        acc += row_dot64(base + (uint32_t)(cc * 64), xw[cc]);
       tc_fence_before();
       __syncwarp();
       if (lane == 0) mbar_arrive(&tempty[a]);
@@ -1178,18 +1227,21 @@ __global__ void selftest_wait_kernel(uint64_t limit_ns, int32_t* status) {
 }
 
 // Rows of 0.0/1.0 bf16 (the A operand of the staged kernel) from the bit-packed
-// starts, 16 elements (two 16-byte stores) per item: S_p x n_tc, row t is
-// start t (t < S), or with idx start idx[t] for t < *count and zero up to the
-// next multiple of 128 (the last m-tile the product reads; rows beyond are not
-// written); columns >= n are zero.  With Y the product's rows t < *count are
-// zeroed for its accumulation.  Blocks take rows, threads the 16-column items
-// of a row (no 64-bit division).
+// starts: S_p x n_tc, row t is start t (t < S), or with idx start idx[t] for
+// t < *count and zero up to the next multiple of 128 (the last m-tile the
+// product reads; rows beyond are not written); columns >= n are zero.  With Y the product's rows t < *count are
+// zeroed for its accumulation.  Blocks (of kUnpackThreads) take rows: the
+// row's words are read once into shared memory, then each thread expands
+// 8-column pieces of it (no 64-bit division).
+constexpr int kUnpackThreads = 256;
+static_assert(kUnpackThreads * 64 >= UBQP_MAX_N, "one word per thread covers a row");
 __device__ __forceinline__ void unpack_rows(const uint64_t* __restrict__ X, int n, int W,
                                             int64_t S, const int32_t* __restrict__ idx,
                                             const int64_t* __restrict__ count, int64_t S_p,
                                             int n_tc, uint4* __restrict__ Xe,
                                             float* __restrict__ Y, int64_t block,
                                             int64_t blocks) {
+  __shared__ uint64_t words[kUnpackThreads];
   const int per_row = n_tc / 16;
   int64_t rows = S, rows_p = S_p;
   if (idx) {
@@ -1203,25 +1255,24 @@ __device__ __forceinline__ void unpack_rows(const uint64_t* __restrict__ X, int 
       const int64_t src = idx ? (int64_t)idx[r] : r;
       if (src >= 0 && src < S) xr = X + src * W;
     }
+    const int w = threadIdx.x;
+    words[w] = (xr && w < W) ? (xr[w] & valid_mask(n, w)) : 0ull;
+    __syncthreads();
+    // consecutive threads write consecutive 16-byte pieces (8 columns each)
     uint4* er = Xe + 2 * r * per_row;
-    for (int c = threadIdx.x; c < per_row; c += blockDim.x) {
-      const int w = c >> 2;
-      uint32_t x16 = 0;
-      if (xr && w < W)
-        x16 = (uint32_t)(((xr[w] & valid_mask(n, w)) >> ((c & 3) * 16)) & 0xFFFFu);
+    for (int h = threadIdx.x; h < 2 * per_row; h += blockDim.x) {
+      const uint32_t x8 = (uint32_t)(words[h >> 3] >> ((h & 7) * 8)) & 0xFFu;
       uint32_t v[8];
-      expand16(x16, v);
-      er[2 * c] = make_uint4(v[0], v[1], v[2], v[3]);
-      er[2 * c + 1] = make_uint4(v[4], v[5], v[6], v[7]);
+      expand16(x8, v);
+      er[h] = make_uint4(v[0], v[1], v[2], v[3]);
       if (Y && r < rows) {
-        float4* yr = reinterpret_cast<float4*>(Y + r * (int64_t)n_tc + 16 * c);
+        float4* yr = reinterpret_cast<float4*>(Y + r * (int64_t)n_tc + 8 * h);
         const float4 z = make_float4(0.f, 0.f, 0.f, 0.f);
         yr[0] = z;
         yr[1] = z;
-        yr[2] = z;
-        yr[3] = z;
       }
     }
+    __syncthreads();  // words[] is rewritten for the next row
   }
 }
 
@@ -1470,7 +1521,7 @@ cudaError_t launch_startup_multi(const YInst* yi, int count, int64_t max_items, 
   int64_t blocks = (max_items + 255) / 256;
   if (blocks > 64) blocks = 64;
   if (blocks < 1) blocks = 1;
-  unpack_batch_bf16<<<dim3((unsigned)blocks, (unsigned)count), 256, 0, st>>>(yi);
+  unpack_batch_bf16<<<dim3((unsigned)blocks, (unsigned)count), kUnpackThreads, 0, st>>>(yi);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   const int grid = n_units < sm_count ? n_units : sm_count;
@@ -1534,10 +1585,11 @@ cudaError_t eval_tc_prepare(ubqp_q* h, cudaStream_t) {
 // launched just before it on the same stream (the kernel waits for that grid
 // with griddepcontrol.wait before its first dependent read).
 template <bool YMODE, bool FUSED>
-cudaError_t launch_product(int grid, int threads, int smem, cudaStream_t st, const CUtensorMap& mapA,
-                           const CUtensorMap& mapB, const uint64_t* X, int n, int W, int64_t S,
-                           int m_tiles, const int4* chunks, int n_chunks, int64_t* f,
-                           const int64_t* count, float* Y, int64_t ldy, unsigned* err) {
+cudaError_t launch_product(int grid, int threads, int smem, cudaStream_t st,
+                           const CUtensorMap& mapA, const CUtensorMap& mapB, const uint64_t* X,
+                           int n, int W, int64_t S, int m_tiles, const int4* chunks, int n_chunks,
+                           int64_t* f, const int64_t* count, float* Y, int64_t ldy,
+                           unsigned* err) {
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3((unsigned)grid);
   cfg.blockDim = dim3((unsigned)threads);
@@ -1575,9 +1627,8 @@ cudaError_t launch_ascent_init_tc(const ubqp_q* h, const uint64_t* X, const int3
   cudaError_t e;
   {
     const int64_t blocks = std::min<int64_t>(S_p, (int64_t)h->sm_count * 8);
-    unpack_bits_bf16<<<(unsigned)blocks, 256, 0, st>>>(X, h->n, h->W, S, idx, count, S_p,
-                                                      h->n_tc, reinterpret_cast<uint4*>(Xe), Y,
-                                                      nullptr, 0);
+    unpack_bits_bf16<<<(unsigned)blocks, kUnpackThreads, 0, st>>>(
+        X, h->n, h->W, S, idx, count, S_p, h->n_tc, reinterpret_cast<uint4*>(Xe), Y, nullptr, 0);
     if ((e = cudaGetLastError())) return e;
   }
   alignas(64) CUtensorMap mapA;
@@ -1633,9 +1684,9 @@ cudaError_t launch_eval_tc(const ubqp_q* h, const uint64_t* X, int64_t S, int64_
     else if (!make_map(&mapA, ws, S_p, h->n_tc, BM)) return cudaErrorInvalidValue;
     // the unpacking also zeroes f
     const int64_t blocks = std::min<int64_t>(S_p, (int64_t)h->sm_count * 8);
-    unpack_bits_bf16<<<(unsigned)blocks, 256, 0, st>>>(X, h->n, h->W, S, nullptr, nullptr,
-                                                      S_p, h->n_tc,
-                                                      reinterpret_cast<uint4*>(ws), nullptr, f, S);
+    unpack_bits_bf16<<<(unsigned)blocks, kUnpackThreads, 0, st>>>(
+        X, h->n, h->W, S, nullptr, nullptr, S_p, h->n_tc, reinterpret_cast<uint4*>(ws), nullptr, f,
+        S);
     if ((e = cudaGetLastError())) return e;
   }
   const int m_tiles = (int)(S_p / BM);
