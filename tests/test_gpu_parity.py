@@ -155,6 +155,25 @@ def test_eval_tc_workspace_errors():
     assert ubqp.eval_workspace_size(inst, S, ubqp.EVAL_TC_TMEM) == 0
 
 
+@pytest.mark.parametrize("n,S,fused", [(300, 50, False), (300, 4095, False), (300, 4096, True),
+                                       (1024, 8192, True), (1025, 8192, False),
+                                       (7000, 1000, False)])
+def test_eval_auto_path_choice(n, S, fused):
+    # AUTO takes the fused operand build (no workspace) only for n padded to
+    # at most 1024 with at least 4096 starts, the staged one otherwise; the
+    # values agree either way
+    Q, inst = instance(n, 0.5, 3)
+    need = ubqp.eval_workspace_size(inst, S, ubqp.EVAL_AUTO)
+    assert need == (0 if fused else ubqp.eval_workspace_size(inst, S, ubqp.EVAL_TC_STAGED))
+    X = words_dev(synth.random_solutions(n, S, 4))
+    f_auto = ubqp.eval(inst, X, path=ubqp.EVAL_AUTO)
+    f_other = ubqp.eval(inst, X, path=ubqp.EVAL_TC_STAGED if fused else ubqp.EVAL_TC)
+    assert torch.equal(f_auto, f_other)
+    pick = np.arange(0, S, max(1, S // 7))
+    Xh = synth.random_solutions(n, S, 4)
+    assert np.array_equal(f_auto.cpu().numpy()[pick], orc.eval(Q, Xh[pick]))
+
+
 @pytest.mark.parametrize("n", [1, 65, 257, 1000, 2100])
 @pytest.mark.parametrize("S", [1, 129, 300])
 def test_eval_tc_staged_matches_oracle(n, S):
