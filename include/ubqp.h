@@ -129,7 +129,9 @@ int ubqp_q_prepare_into_async(const int8_t* Q_dev, int32_t n, int64_t ldq, void*
 int ubqp_q_info(const ubqp_q* q, int32_t* n, int32_t* words, int32_t* n_pad,
                 int32_t* max_abs, int64_t* device_bytes);
 /* Synchronise `stream` and report (then clear) any error a kernel recorded in
- * the handle's error word since the last ubqp_sync.  For a handle from
+ * the handle's error word since the last ubqp_sync; the reads and the reset
+ * run on `stream`, so work queued on other streams (the next solve, say) is
+ * not waited for.  For a handle from
  * ubqp_q_prepare_into_async the first call also reads the symmetry check and
  * max|Q|; an asymmetric Q gives UBQP_ERR_NOT_SYMMETRIC from then on. */
 int ubqp_sync(const ubqp_q* q, void* stream);

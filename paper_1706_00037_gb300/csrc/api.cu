@@ -289,20 +289,25 @@ int ubqp_q_info(const ubqp_q* q, int32_t* n, int32_t* words, int32_t* n_pad, int
 
 int ubqp_sync(const ubqp_q* q, void* stream) {
   if (!q) return fail(UBQP_ERR_ARG, "q is NULL");
+  // every read and the reset stay on `stream` (a plain cudaMemcpy would also
+  // wait for work queued on other streams, e.g. the next solve)
   cudaStream_t st = (cudaStream_t)stream;
   UBQP_CUDA(cudaStreamSynchronize(st));
   if (q->deferred) {  // the validation of ubqp_q_prepare_into_async
     unsigned flags[2] = {0, 0};
-    UBQP_CUDA(cudaMemcpy(flags, q->scratch_flags, sizeof(flags), cudaMemcpyDeviceToHost));
+    UBQP_CUDA(cudaMemcpyAsync(flags, q->scratch_flags, sizeof(flags), cudaMemcpyDeviceToHost, st));
+    UBQP_CUDA(cudaStreamSynchronize(st));
     q->deferred = false;
     q->asymmetric = flags[0] != 0;
     const_cast<ubqp_q*>(q)->max_abs = (int32_t)flags[1];
   }
   if (q->asymmetric) return fail(UBQP_ERR_NOT_SYMMETRIC, "Q is not symmetric");
   unsigned e = 0;
-  UBQP_CUDA(cudaMemcpy(&e, q->err, sizeof(unsigned), cudaMemcpyDeviceToHost));
+  UBQP_CUDA(cudaMemcpyAsync(&e, q->err, sizeof(unsigned), cudaMemcpyDeviceToHost, st));
+  UBQP_CUDA(cudaStreamSynchronize(st));
   if (e) {
-    UBQP_CUDA(cudaMemset(q->err, 0, sizeof(unsigned)));
+    UBQP_CUDA(cudaMemsetAsync(q->err, 0, sizeof(unsigned), st));
+    UBQP_CUDA(cudaStreamSynchronize(st));
     if (e & UBQP_DEVERR_TIMEOUT) return fail(UBQP_ERR_TIMEOUT, "a kernel wait timed out");
     return fail(UBQP_ERR_ARG, "a kernel saw an index outside [0, S)");
   }
