@@ -126,7 +126,7 @@ void ubqp_q_destroy(ubqp_q* q) {
   if (q->owns_memory) {
     cudaFree(q->Q8);
     cudaFree(q->Qt);
-    cudaFree(q->Qf);
+    cudaFree(q->Qu);
     cudaFree(q->rowsum);
     cudaFree(q->x0);
     cudaFree(q->err);
@@ -194,7 +194,7 @@ int prepare_impl(const int8_t* Q_dev, int32_t n, int64_t ldq, void* stream, void
     h->owns_memory = false;
     h->Q8 = (int8_t*)(a + L.q8);
     h->Qt = (uint16_t*)(a + L.qt);
-    h->Qf = (uint16_t*)(a + L.qt + qt);
+    h->Qu = (uint16_t*)(a + L.qt + qt);
     h->rowsum = (int32_t*)(a + L.rowsum);
     h->x0 = (uint64_t*)(a + L.x0);
     h->err = (unsigned*)(a + L.err);
@@ -202,7 +202,7 @@ int prepare_impl(const int8_t* Q_dev, int32_t n, int64_t ldq, void* stream, void
   } else {
     h->owns_memory = true;
     if (cudaMalloc(&h->Q8, q8) != cudaSuccess || cudaMalloc(&h->Qt, qt) != cudaSuccess ||
-        cudaMalloc(&h->Qf, qt) != cudaSuccess ||
+        cudaMalloc(&h->Qu, qt) != cudaSuccess ||
         cudaMalloc(&h->rowsum, sizeof(int32_t) * n) != cudaSuccess ||
         cudaMalloc(&h->x0, sizeof(uint64_t) * h->W) != cudaSuccess ||
         cudaMalloc(&h->err, 4 * sizeof(unsigned)) != cudaSuccess) {

@@ -92,7 +92,7 @@ struct ubqp_batch {
   // ... and the start-up products of the passing starts (unpack + one launch)
   ubqp::YInst* d_yinst = nullptr;
   void* d_mapsA = nullptr;
-  void* d_mapsF = nullptr;
+  void* d_mapsU = nullptr;
   ubqp::MUnit* d_yunits = nullptr;
   int n_yunits = 0;
   int64_t max_items = 0;
@@ -165,8 +165,8 @@ int run_body(ubqp_batch* b, cudaStream_t st) {
     // ---- one launch each: unpack every instance's passing starts, then the
     // start-up products y = Q x of all of them
     UBQP_BCUDA(ubqp::launch_startup_multi(b->d_yinst, b->count, b->max_items, b->d_mapsA,
-                                          b->d_mapsF, b->d_yunits, b->n_yunits, b->qs[0]->err,
-                                          b->sm_count, st));
+                                          b->d_maps, b->d_mapsU, b->d_yunits, b->n_yunits,
+                                          b->qs[0]->err, b->sm_count, st));
   } else {
   // ---- fork: tensor-core start-up of each instance's passing starts
   UBQP_BCUDA(cudaEventRecord(b->ev_fork, st));
@@ -300,7 +300,7 @@ int ubqp_batch_create(const ubqp_q* const* qs, int32_t count, const ubqp_params*
   }
   const size_t o_yinst = take(sizeof(ubqp::YInst) * count);
   const size_t o_mapsA = take(128 * (size_t)count);
-  const size_t o_mapsF = take(128 * (size_t)count);
+  const size_t o_mapsU = take(128 * (size_t)count);
   std::vector<ubqp::MUnit> yu;
   if (all_tc) yu = ubqp::eval_tc_multi_y_units(qs, count, S);
   const size_t o_yu = take(sizeof(ubqp::MUnit) * std::max<size_t>(yu.size(), 1));
@@ -349,7 +349,7 @@ int ubqp_batch_create(const ubqp_q* const* qs, int32_t count, const ubqp_params*
   b->d_einst = (ubqp::EvalInst*)(b->dmem + o_einst);
   b->d_yinst = (ubqp::YInst*)(b->dmem + o_yinst);
   b->d_mapsA = b->dmem + o_mapsA;
-  b->d_mapsF = b->dmem + o_mapsF;
+  b->d_mapsU = b->dmem + o_mapsU;
   b->d_yunits = (ubqp::MUnit*)(b->dmem + o_yu);
   b->n_yunits = (int)yu.size();
   if (!yu.empty() && cudaMemcpy(b->d_yunits, yu.data(), sizeof(ubqp::MUnit) * yu.size(),
@@ -421,7 +421,7 @@ int ubqp_batch_create(const ubqp_q* const* qs, int32_t count, const ubqp_params*
     std::vector<ubqp::EvalInst> ei(count);
     std::vector<ubqp::YInst> yi(count);
     std::vector<unsigned char> maps(128 * (size_t)count), mA(128 * (size_t)count),
-        mF(128 * (size_t)count);
+        mU(128 * (size_t)count);
     const int64_t S_p = (S + 127) / 128 * 128;
     for (int i = 0; i < count; ++i) {
       const ubqp::BatchDesc& d = b->h_desc[i];
@@ -433,7 +433,7 @@ int ubqp_batch_create(const ubqp_q* const* qs, int32_t count, const ubqp_params*
                           S, S_p, d.n, d.W, qs[i]->n_tc, 0};
       b->max_items = std::max<int64_t>(b->max_items, S_p * (qs[i]->n_tc / 16));
       memcpy(mA.data() + 128 * (size_t)i, b->mapA[i].bytes, 128);
-      memcpy(mF.data() + 128 * (size_t)i, qs[i]->tc_mapF, 128);
+      memcpy(mU.data() + 128 * (size_t)i, qs[i]->tc_mapU, 128);
       if (!d.Y) b->merged_ok = false;
     }
     if (cudaMemcpy(b->d_einst, ei.data(), sizeof(ubqp::EvalInst) * count,
@@ -442,7 +442,7 @@ int ubqp_batch_create(const ubqp_q* const* qs, int32_t count, const ubqp_params*
         cudaMemcpy(b->d_yinst, yi.data(), sizeof(ubqp::YInst) * count,
                    cudaMemcpyHostToDevice) != cudaSuccess ||
         cudaMemcpy(b->d_mapsA, mA.data(), mA.size(), cudaMemcpyHostToDevice) != cudaSuccess ||
-        cudaMemcpy(b->d_mapsF, mF.data(), mF.size(), cudaMemcpyHostToDevice) != cudaSuccess) {
+        cudaMemcpy(b->d_mapsU, mU.data(), mU.size(), cudaMemcpyHostToDevice) != cudaSuccess) {
       ubqp_batch_destroy(b);
       return bfail(UBQP_ERR_CUDA, "descriptor upload failed");
     }

@@ -28,8 +28,10 @@
 //
 // Variants in this file: the fused A operand (four more warps write the 0/1
 // rows into the shared-memory stage from the bits), the A operand in tensor
-// memory, the Y mode (y = Q x of the passing starts over the full square, the
-// ascent's start-up), and for batches of instances the merged kernels: one
+// memory, the Y mode (y = Q x of the passing starts, the ascent's start-up:
+// since Q' + Q'^t = 2Q, each N-block sums its lower-triangle K steps from Q'
+// and its upper-triangle steps from Q'^t, and the epilogue halves the
+// result), and for batches of instances the merged kernels: one
 // fused evaluation and one Y-mode product over work lists that mix the units
 // of every instance, each unit naming its instance and that instance's tensor
 // maps (arrays in global memory).
@@ -303,15 +305,19 @@ __device__ __forceinline__ void expand16(uint32_t x16, uint32_t (&v)[8]) {
 }
 
 // YMODE = false: f_s += sum_j x_sj D_sj over the lower block triangle (Evaluate).
-// YMODE = true:  Y = Xe Qf^t over the full square, accumulated in fp32 (exact
-// integers) with vector atomics -- y = Q x for the starts an ascent climbs.
+// YMODE = true:  Y = (Xe Q'^t + Xe Q') / 2 = Xe Q (Q symmetric), N-block J
+// taking K steps [0, 4(J+1)) of Q' (tmB) and then [4J, n_tc/64) of Q'^t
+// (tmU), accumulated in fp32 with vector atomics -- y = Q x for the starts an
+// ascent climbs.  Exact: a unit's partial is an integer of magnitude <= 2^18,
+// its half a multiple of 1/2, and every sum of halves stays below 2^22.
 // FUSED (evaluation only): the A operand is written to shared memory directly
 // from the bit-packed solutions by warps 6-9 (no unpacked copy in global
 // memory); otherwise both operands arrive by TMA.
 template <bool YMODE, bool FUSED>
 __global__ void __launch_bounds__(FUSED ? THREADS_FUSED : THREADS, 1)
 eval_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
-               const uint64_t* __restrict__ X, int n, int W, int64_t S, int m_tiles,
+               const __grid_constant__ CUtensorMap tmU, const uint64_t* __restrict__ X, int n,
+               int W, int64_t S, int m_tiles,
                const int4* __restrict__ chunks, int n_chunks, int64_t* __restrict__ f,
                const int64_t* __restrict__ count, float* __restrict__ Y, int64_t ldy,
                unsigned* __restrict__ err) {
@@ -371,6 +377,9 @@ eval_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ 
         asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&tmA))
                      : "memory");
       asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&tmB)) : "memory");
+      if (YMODE)
+        asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&tmU))
+                     : "memory");
       int pending[STAGES];
       for (int s = 0; s < STAGES; ++s) pending[s] = -1;
       int stage = 0;
@@ -385,9 +394,17 @@ eval_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ 
           }
           uint8_t* sa = smem + stage * STAGE_BYTES;
           mbar_expect_tx(&full[stage], FUSED ? B_BYTES : STAGE_BYTES);
-          const int kx = (un.k0 + ks) * BK;
+          int kx = (un.k0 + ks) * BK;
+          const CUtensorMap* mb = &tmB;
+          if (YMODE) {  // past the block's lower-triangle steps: Q'^t from the block's diagonal
+            const int c = un.k0 + ks, ql = (un.nb + 1) * (BN / BK);
+            if (c >= ql) {
+              mb = &tmU;
+              kx = (un.nb * (BN / BK) + c - ql) * BK;
+            }
+          }
           if (!FUSED) tma_load_2d(sa, &tmA, kx, un.mt * BM, &full[stage]);
-          tma_load_2d(sa + A_BYTES, &tmB, kx, un.nb * BN, &full[stage]);
+          tma_load_2d(sa + A_BYTES, mb, kx, un.nb * BN, &full[stage]);
           pending[stage] = (int)phase;
           if (++stage == STAGES) {
             stage = 0;
@@ -531,9 +548,10 @@ eval_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ 
 #pragma unroll
             for (int i = 0; i < 8; ++i)
               atomicAdd(reinterpret_cast<float4*>(yrow + cc * 32 + 4 * i),
-                        make_float4(__uint_as_float(r[4 * i]), __uint_as_float(r[4 * i + 1]),
-                                    __uint_as_float(r[4 * i + 2]),
-                                    __uint_as_float(r[4 * i + 3])));
+                        make_float4(0.5f * __uint_as_float(r[4 * i]),
+                                    0.5f * __uint_as_float(r[4 * i + 1]),
+                                    0.5f * __uint_as_float(r[4 * i + 2]),
+                                    0.5f * __uint_as_float(r[4 * i + 3])));
           }
         }
         tc_fence_before();
@@ -813,8 +831,8 @@ eval_tc_multi_kernel(const EvalInst* __restrict__ insts, const CUtensorMap* __re
 // so the stage and accumulator hand-offs stay paired.
 __global__ void __launch_bounds__(THREADS, 1)
 eval_tc_multi_y_kernel(const YInst* __restrict__ yi, const CUtensorMap* __restrict__ mapsA,
-                       const CUtensorMap* __restrict__ mapsF, const MUnit* __restrict__ units,
-                       int n_units, unsigned* __restrict__ err) {
+                       const CUtensorMap* __restrict__ mapsB, const CUtensorMap* __restrict__ mapsU,
+                       const MUnit* __restrict__ units, int n_units, unsigned* __restrict__ err) {
   extern __shared__ uint8_t smem_raw[];
   uint8_t* smem = smem_raw + ((1024 - (su32(smem_raw) & 1023)) & 1023);
   uint64_t* full = reinterpret_cast<uint64_t*>(smem + STAGES * STAGE_BYTES);
@@ -870,7 +888,6 @@ eval_tc_multi_y_kernel(const YInst* __restrict__ yi, const CUtensorMap* __restri
         const MUnit un = units[u];
         if (!active(un)) continue;
         const CUtensorMap* mA = mapsA + un.inst;
-        const CUtensorMap* mF = mapsF + un.inst;
         for (int ks = 0; ks < un.nk; ++ks) {
           if (!mbar_wait(&empty[stage], phase ^ 1u, abort_flag, err)) {
             ok = false;
@@ -878,9 +895,12 @@ eval_tc_multi_y_kernel(const YInst* __restrict__ yi, const CUtensorMap* __restri
           }
           uint8_t* sa = smem + stage * STAGE_BYTES;
           mbar_expect_tx(&full[stage], STAGE_BYTES);
-          const int kx = (un.k0 + ks) * BK;
+          // as the single-instance Y mode: Q' below the block's diagonal, Q'^t from it
+          const int c = un.k0 + ks, ql = (un.nb + 1) * (BN / BK);
+          const CUtensorMap* mb = c < ql ? mapsB + un.inst : mapsU + un.inst;
+          const int kx = (c < ql ? c : un.nb * (BN / BK) + c - ql) * BK;
           tma_load_2d(sa, mA, kx, un.mt * BM, &full[stage]);
-          tma_load_2d(sa + A_BYTES, mF, kx, un.nb * BN, &full[stage]);
+          tma_load_2d(sa + A_BYTES, mb, kx, un.nb * BN, &full[stage]);
           pending[stage] = (int)phase;
           if (++stage == STAGES) {
             stage = 0;
@@ -965,8 +985,10 @@ eval_tc_multi_y_kernel(const YInst* __restrict__ yi, const CUtensorMap* __restri
 #pragma unroll
           for (int i = 0; i < 8; ++i)
             atomicAdd(reinterpret_cast<float4*>(yrow + cc * 32 + 4 * i),
-                      make_float4(__uint_as_float(r[4 * i]), __uint_as_float(r[4 * i + 1]),
-                                  __uint_as_float(r[4 * i + 2]), __uint_as_float(r[4 * i + 3])));
+                      make_float4(0.5f * __uint_as_float(r[4 * i]),
+                                  0.5f * __uint_as_float(r[4 * i + 1]),
+                                  0.5f * __uint_as_float(r[4 * i + 2]),
+                                  0.5f * __uint_as_float(r[4 * i + 3])));
         }
       }
       tc_fence_before();
@@ -1463,6 +1485,26 @@ static std::vector<int4> make_chunks(int n_tc, int bn, bool full, int kch = KCH)
   return ch;
 }
 
+// The start-up's chunks: y = (Q' x + Q'^t x) / 2, so N-block J runs its K steps
+// [0, 4(J+1)) of Q' and then [4J, n_tc/64) of Q'^t: one combined sequence of
+// n_tc/64 + 4 steps per block (the diagonal block's halves from both), split
+// into near-equal chunks of at most kch steps, largest first.  Combined step c
+// of block J is Q' step c below 4(J+1), else Q'^t step 4J + c - 4(J+1).
+static std::vector<int4> make_chunks_y(int n_tc, int kch = KCH) {
+  std::vector<int4> ch;
+  const int NB = n_tc / BN, nk = n_tc / BK + BN / BK;
+  for (int J = 0; J < NB; ++J) {
+    const int parts = (nk + kch - 1) / kch;
+    for (int p = 0, k0 = 0; p < parts; ++p) {
+      const int len = nk / parts + (p < nk % parts ? 1 : 0);
+      ch.push_back(make_int4(J, k0, len, 0));
+      k0 += len;
+    }
+  }
+  std::stable_sort(ch.begin(), ch.end(), [](const int4& a, const int4& b) { return a.z > b.z; });
+  return ch;
+}
+
 // The evaluation's work chunks with at most kch (1..16) K steps of 64 each
 // (the handle's own table uses 16): a schedule a batch plan may tune.
 std::vector<int4> eval_tc_chunks(int n_tc, int kch) {
@@ -1500,7 +1542,7 @@ std::vector<MUnit> eval_tc_multi_y_units(const ubqp_q* const* qs, int count, int
   std::vector<MUnit> us;
   const int m_tiles = (int)(padded_starts(S) / BM);
   for (int i = 0; i < count; ++i) {
-    for (const int4& c : make_chunks(qs[i]->n_tc, BN, true))
+    for (const int4& c : make_chunks_y(qs[i]->n_tc))
       for (int mt = 0; mt < m_tiles; ++mt) us.push_back(MUnit{c.x, c.y, c.z, mt, i, 0, 0, 0});
   }
   std::stable_sort(us.begin(), us.end(), [](const MUnit& a, const MUnit& b) { return a.nk > b.nk; });
@@ -1508,8 +1550,8 @@ std::vector<MUnit> eval_tc_multi_y_units(const ubqp_q* const* qs, int count, int
 }
 
 cudaError_t launch_startup_multi(const YInst* yi, int count, int64_t max_items, const void* mapsA,
-                                 const void* mapsF, const MUnit* units, int n_units,
-                                 unsigned* err, int sm_count, cudaStream_t st) {
+                                 const void* mapsB, const void* mapsU, const MUnit* units,
+                                 int n_units, unsigned* err, int sm_count, cudaStream_t st) {
   static std::once_flag once;
   static cudaError_t attr = cudaSuccess;
   std::call_once(once, [] {
@@ -1518,21 +1560,22 @@ cudaError_t launch_startup_multi(const YInst* yi, int count, int64_t max_items, 
   });
   if (attr != cudaSuccess) return attr;
   if (count < 1 || n_units < 1) return cudaSuccess;
+  // blocks take rows of every instance (blockIdx.y)
   int64_t blocks = (max_items + 255) / 256;
-  if (blocks > 64) blocks = 64;
+  if (blocks > 256) blocks = 256;
   if (blocks < 1) blocks = 1;
   unpack_batch_bf16<<<dim3((unsigned)blocks, (unsigned)count), kUnpackThreads, 0, st>>>(yi);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   const int grid = n_units < sm_count ? n_units : sm_count;
   eval_tc_multi_y_kernel<<<grid, THREADS, SMEM_BYTES, st>>>(
-      yi, reinterpret_cast<const CUtensorMap*>(mapsA), reinterpret_cast<const CUtensorMap*>(mapsF),
-      units, n_units, err);
+      yi, reinterpret_cast<const CUtensorMap*>(mapsA), reinterpret_cast<const CUtensorMap*>(mapsB),
+      reinterpret_cast<const CUtensorMap*>(mapsU), units, n_units, err);
   return cudaGetLastError();
 }
 
 size_t eval_tc_chunk_bytes(int n_tc) {
-  return sizeof(int4) * (make_chunks(n_tc, BN, false).size() + make_chunks(n_tc, BN, true).size() +
+  return sizeof(int4) * (make_chunks(n_tc, BN, false).size() + make_chunks_y(n_tc).size() +
                          make_chunks(n_tc, BN_TS, false).size());
 }
 
@@ -1548,7 +1591,7 @@ static const ChunkTables& chunk_tables(int n_tc) {
   auto it = cache.find(n_tc);
   if (it != cache.end()) return it->second;
   ChunkTables t;
-  std::vector<int4> full = make_chunks(n_tc, BN, true), ts = make_chunks(n_tc, BN_TS, false);
+  std::vector<int4> full = make_chunks_y(n_tc), ts = make_chunks(n_tc, BN_TS, false);
   t.all = make_chunks(n_tc, BN, false);
   t.n_eval = (int)t.all.size();
   t.n_full = (int)full.size();
@@ -1575,7 +1618,7 @@ cudaError_t eval_tc_upload_tables(ubqp_q* h, cudaStream_t st) {
 // The TMA descriptors of the prepared operands (host only).
 cudaError_t eval_tc_prepare(ubqp_q* h, cudaStream_t) {
   h->tc_ok = make_map(reinterpret_cast<CUtensorMap*>(h->tc_mapB), h->Qt, h->n_tc, h->n_tc, BN) &&
-             make_map(reinterpret_cast<CUtensorMap*>(h->tc_mapF), h->Qf, h->n_tc, h->n_tc, BN) &&
+             make_map(reinterpret_cast<CUtensorMap*>(h->tc_mapU), h->Qu, h->n_tc, h->n_tc, BN) &&
              make_map(reinterpret_cast<CUtensorMap*>(h->tc_mapB_ts), h->Qt, h->n_tc, h->n_tc,
                       BN_TS);
   return cudaSuccess;
@@ -1586,10 +1629,10 @@ cudaError_t eval_tc_prepare(ubqp_q* h, cudaStream_t) {
 // with griddepcontrol.wait before its first dependent read).
 template <bool YMODE, bool FUSED>
 cudaError_t launch_product(int grid, int threads, int smem, cudaStream_t st,
-                           const CUtensorMap& mapA, const CUtensorMap& mapB, const uint64_t* X,
-                           int n, int W, int64_t S, int m_tiles, const int4* chunks, int n_chunks,
-                           int64_t* f, const int64_t* count, float* Y, int64_t ldy,
-                           unsigned* err) {
+                           const CUtensorMap& mapA, const CUtensorMap& mapB,
+                           const CUtensorMap& mapU, const uint64_t* X, int n, int W, int64_t S,
+                           int m_tiles, const int4* chunks, int n_chunks, int64_t* f,
+                           const int64_t* count, float* Y, int64_t ldy, unsigned* err) {
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3((unsigned)grid);
   cfg.blockDim = dim3((unsigned)threads);
@@ -1600,8 +1643,9 @@ cudaError_t launch_product(int grid, int threads, int smem, cudaStream_t st,
   at[0].val.programmaticStreamSerializationAllowed = 1;
   cfg.attrs = at;
   cfg.numAttrs = 1;
-  void* args[] = {const_cast<CUtensorMap*>(&mapA), const_cast<CUtensorMap*>(&mapB), &X, &n, &W,
-                  &S, &m_tiles, &chunks, &n_chunks, &f, &count, &Y, &ldy, &err};
+  void* args[] = {const_cast<CUtensorMap*>(&mapA), const_cast<CUtensorMap*>(&mapB),
+                  const_cast<CUtensorMap*>(&mapU), &X, &n, &W, &S, &m_tiles, &chunks, &n_chunks,
+                  &f, &count, &Y, &ldy, &err};
   return cudaLaunchKernelExC(&cfg, reinterpret_cast<const void*>(&eval_tc_kernel<YMODE, FUSED>),
                              args);
 }
@@ -1639,9 +1683,10 @@ cudaError_t launch_ascent_init_tc(const ubqp_q* h, const uint64_t* X, const int3
   const int n_units = h->tc_nchunks_y * m_tiles;
   const int grid = n_units < h->sm_count ? n_units : h->sm_count;
   if ((e = launch_product<true, false>(
-           grid, THREADS, SMEM_BYTES, st, mapA, *reinterpret_cast<const CUtensorMap*>(h->tc_mapF),
-           X, h->n, h->W, S, m_tiles, reinterpret_cast<const int4*>(h->tc_chunks) + h->tc_nchunks,
-           h->tc_nchunks_y, nullptr, count, Y, (int64_t)h->n_tc, h->err)))
+           grid, THREADS, SMEM_BYTES, st, mapA, *reinterpret_cast<const CUtensorMap*>(h->tc_mapB),
+           *reinterpret_cast<const CUtensorMap*>(h->tc_mapU), X, h->n, h->W, S, m_tiles,
+           reinterpret_cast<const int4*>(h->tc_chunks) + h->tc_nchunks, h->tc_nchunks_y, nullptr,
+           count, Y, (int64_t)h->n_tc, h->err)))
     return e;
   *Y_out = Y;
   return cudaSuccess;
@@ -1698,12 +1743,12 @@ cudaError_t launch_eval_tc(const ubqp_q* h, const uint64_t* X, int64_t S, int64_
   if (fused) {
     if ((e = set_smem_attr_once<false, true>())) return e;
     eval_tc_kernel<false, true><<<grid, THREADS_FUSED, SMEM_BYTES_FUSED, st>>>(
-        mapA, mapB, X, h->n, h->W, S, m_tiles, ch, nch, f, nullptr, nullptr, 0,
-        h->err);
+        mapA, mapB, mapB, X, h->n, h->W, S, m_tiles, ch, nch, f, nullptr, nullptr, 0, h->err);
   } else {
     if ((e = set_smem_attr_once<false, false>())) return e;
-    return launch_product<false, false>(grid, THREADS, SMEM_BYTES, st, mapA, mapB, X, h->n, h->W,
-                                        S, m_tiles, ch, nch, f, nullptr, nullptr, 0, h->err);
+    return launch_product<false, false>(grid, THREADS, SMEM_BYTES, st, mapA, mapB, mapB, X, h->n,
+                                        h->W, S, m_tiles, ch, nch, f, nullptr, nullptr, 0,
+                                        h->err);
   }
   return cudaGetLastError();
 }

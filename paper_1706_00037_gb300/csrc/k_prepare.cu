@@ -1,8 +1,9 @@
 // k_prepare.cu -- one pass over Q: symmetry check (problem (P) requires a
 // symmetric Q), max|Q|, the padded int8 copy read by the ascent, the bf16
-// tensor-core operands Q' = 2*tril(Q,-1) + diag(Q) (evaluation) and Q (the
-// ascent's y = Q x), and the row sums behind the
-// first-derivative start of Fig. 2 (CalculateFirstDerivativeSolution).
+// tensor-core operands Q' = 2*tril(Q,-1) + diag(Q) (evaluation) and its
+// transpose 2*triu(Q,1) + diag(Q) (with Q', the ascent's y = Q x), and the row
+// sums behind the first-derivative start of Fig. 2
+// (CalculateFirstDerivativeSolution).
 #include <cuda_bf16.h>
 
 #include "ubqp_internal.cuh"
@@ -44,13 +45,14 @@ __device__ __forceinline__ int qt_kmax(int j0) {
 // compared with U transposed (the symmetry check of problem (P)); then for
 // each of the two tiles every thread takes 16 consecutive columns of one row
 // and writes them as 16-byte vectors: the int8 copy (rows < n), Q' = 2
-// tril(Q,-1) + diag(Q) (tiles the evaluation reads) and Q in bf16 (zero
-// outside n, so the padded squares need no separate clearing), and adds its
-// row's partial sum.  It also tracks max|Q|.
+// tril(Q,-1) + diag(Q) (tiles the evaluation reads) and Q'^t = 2 triu(Q,1) +
+// diag(Q) (the upper block triangle, which the start-up reads), both in bf16
+// and zero outside n (so the padded squares need no separate clearing), and
+// adds its row's partial sum.  It also tracks max|Q|.
 template <bool W4>
 __global__ void __launch_bounds__(PTHREADS)
 prepare_pairs(const int8_t* __restrict__ Q, int n, int64_t ldq_in, int8_t* __restrict__ Q8,
-              int64_t ldq, uint16_t* __restrict__ Qt, uint16_t* __restrict__ Qf, int n_tc,
+              int64_t ldq, uint16_t* __restrict__ Qt, uint16_t* __restrict__ Qu, int n_tc,
               int32_t* __restrict__ rowsum, unsigned* __restrict__ flags) {
   const int bi = blockIdx.x, bj = blockIdx.y;
   if (bi > bj) return;  // the pair (bj, bi) covers this tile
@@ -73,7 +75,7 @@ prepare_pairs(const int8_t* __restrict__ Q, int n, int64_t ldq_in, int8_t* __res
     const int8_t(*other)[PT + 4] = tile[nt - 1 - u];  // the transposed partner
     int sum = 0;
     uint32_t b8[4] = {0, 0, 0, 0};
-    uint32_t ht[8], hf[8];
+    uint32_t ht[8], hu[8];
 #pragma unroll
     for (int i = 0; i < 16; ++i) {
       const int k = kb + c0 + i;
@@ -83,14 +85,15 @@ prepare_pairs(const int8_t* __restrict__ Q, int n, int64_t ldq_in, int8_t* __res
       sum += v;
       b8[i >> 2] |= (uint32_t)(uint8_t)v << (8 * (i & 3));
       const int w = k < j ? 2 * v : (k == j ? v : 0);
+      const int wu = k > j ? 2 * v : (k == j ? v : 0);
       const uint32_t bt = __bfloat16_as_ushort(__float2bfloat16_rn((float)w));
-      const uint32_t bf = __bfloat16_as_ushort(__float2bfloat16_rn((float)v));
+      const uint32_t bu = __bfloat16_as_ushort(__float2bfloat16_rn((float)wu));
       if (i & 1) {
         ht[i >> 1] |= bt << 16;
-        hf[i >> 1] |= bf << 16;
+        hu[i >> 1] |= bu << 16;
       } else {
         ht[i >> 1] = bt;
-        hf[i >> 1] = bf;
+        hu[i >> 1] = bu;
       }
     }
     const int k = kb + c0;
@@ -103,9 +106,11 @@ prepare_pairs(const int8_t* __restrict__ Q, int n, int64_t ldq_in, int8_t* __res
         dt[0] = make_uint4(ht[0], ht[1], ht[2], ht[3]);
         dt[1] = make_uint4(ht[4], ht[5], ht[6], ht[7]);
       }
-      uint4* df = reinterpret_cast<uint4*>(Qf + (int64_t)j * n_tc + k);
-      df[0] = make_uint4(hf[0], hf[1], hf[2], hf[3]);
-      df[1] = make_uint4(hf[4], hf[5], hf[6], hf[7]);
+      if (kb >= r0[u] / 256 * 256) {  // the upper block triangle of 256-row blocks
+        uint4* du = reinterpret_cast<uint4*>(Qu + (int64_t)j * n_tc + k);
+        du[0] = make_uint4(hu[0], hu[1], hu[2], hu[3]);
+        du[1] = make_uint4(hu[4], hu[5], hu[6], hu[7]);
+      }
     }
     // the row's partial sum over this tile: the 4 threads of row r are lanes
     // 4m .. 4m+3 of one warp
@@ -147,10 +152,10 @@ cudaError_t launch_prepare(const int8_t* Q, int n, int64_t ldq_in, ubqp_q* h,
   const int tiles = h->n_tc / PT;
   dim3 grid(tiles, tiles);
   if (((uintptr_t)Q & 3) == 0 && (ldq_in & 3) == 0)
-    prepare_pairs<true><<<grid, PTHREADS, 0, st>>>(Q, n, ldq_in, h->Q8, h->ldq, h->Qt, h->Qf,
+    prepare_pairs<true><<<grid, PTHREADS, 0, st>>>(Q, n, ldq_in, h->Q8, h->ldq, h->Qt, h->Qu,
                                                    h->n_tc, h->rowsum, h->scratch_flags);
   else
-    prepare_pairs<false><<<grid, PTHREADS, 0, st>>>(Q, n, ldq_in, h->Q8, h->ldq, h->Qt, h->Qf,
+    prepare_pairs<false><<<grid, PTHREADS, 0, st>>>(Q, n, ldq_in, h->Q8, h->ldq, h->Qt, h->Qu,
                                                     h->n_tc, h->rowsum, h->scratch_flags);
   if ((e = cudaGetLastError())) return e;
   first_derivative_bits<<<(h->W + 127) / 128, 128, 0, st>>>(h->rowsum, n, h->W, h->x0);

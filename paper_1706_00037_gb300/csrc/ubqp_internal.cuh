@@ -27,7 +27,10 @@ struct ubqp_q {
   uint16_t* Qt;     // n_tc x n_tc bf16 bits of Q' = 2 tril(Q,-1) + diag(Q); only the
                     // tiles the evaluation reads (row j: columns below the end of
                     // its 256- and 192-row blocks) are written
-  uint16_t* Qf;     // n_tc x n_tc bf16 bits of Q (full, for y = Q x)
+  uint16_t* Qu;     // n_tc x n_tc bf16 bits of Q'^t = 2 triu(Q,1) + diag(Q); only the
+                    // upper block triangle (row j: columns from the start of its
+                    // 256-row block) is written.  With Qt it gives the ascent's
+                    // start-up y = Q x = (Q' x + Q'^t x) / 2
   int32_t* rowsum;  // n
   uint64_t* x0;     // W words: first-derivative start
   unsigned* err;    // device error word
@@ -48,7 +51,7 @@ struct ubqp_q {
   mutable bool deferred;
   mutable bool asymmetric;
   alignas(64) unsigned char tc_mapB[128];  // TMA descriptor of Qt
-  alignas(64) unsigned char tc_mapF[128];  // TMA descriptor of Qf
+  alignas(64) unsigned char tc_mapU[128];  // TMA descriptor of Qu
   alignas(64) unsigned char tc_mapB_ts[128];  // TMA descriptor of Qt, 192-row boxes
 };
 
@@ -178,12 +181,12 @@ cudaError_t launch_eval_tc_multi(const EvalInst* insts, const void* maps, const 
 // unpacking of all passing starts (and the zeroing of their Y rows), then one
 // persistent tensor-core launch over the merged work list of the full-square
 // chunks of every instance (units past an instance's passing count are
-// skipped).  mapsA / mapsF: `count` CUtensorMap each (the unpacked rows of
-// each instance, its bf16 Q), 64-byte aligned in device memory.
+// skipped).  mapsA / mapsB / mapsU: `count` CUtensorMap each (the unpacked
+// rows of each instance, its Q' and its Q'^t), 64-byte aligned in device memory.
 std::vector<MUnit> eval_tc_multi_y_units(const ubqp_q* const* qs, int count, int64_t S);
 cudaError_t launch_startup_multi(const YInst* yi, int count, int64_t max_items, const void* mapsA,
-                                 const void* mapsF, const MUnit* units, int n_units,
-                                 unsigned* err, int sm_count, cudaStream_t st);
+                                 const void* mapsB, const void* mapsU, const MUnit* units,
+                                 int n_units, unsigned* err, int sm_count, cudaStream_t st);
 size_t eval_tc_static_capacity();
 size_t ascent_tc_workspace(const ubqp_q* h, int64_t S);
 cudaError_t launch_ascent_init_tc(const ubqp_q* h, const uint64_t* X, const int32_t* idx,
