@@ -582,11 +582,11 @@ ascent_batch_kernel(const BatchDesc* __restrict__ d, const int2* __restrict__ it
 }
 
 // All passing starts of a batch of instances in one persistent launch, packed
-// by size: a work unit is up to 2^cls starts of one instance (cls 0, 1, 2),
+// by size: a work unit is up to 2^cls starts of one instance (cls 0 .. 3),
 // climbed together by the block's 2^cls sub-groups of T >> cls threads (the
-// smallest sub-group whose 16 (T >> cls) C elements hold the instance's n), so
-// that a block climbs four small starts at once instead of one with mostly
-// idle elements.  Units run largest instances first: the first wave one per
+// smallest sub-group whose 16 (T >> cls) C elements hold the instance's n;
+// T >> 3 = 32 is one warp), so that a block climbs up to eight small starts
+// at once instead of one with mostly idle elements.  Units run largest instances first: the first wave one per
 // block, the rest from the counter *next.
 template <int T, int C, int R, int TS>
 __device__ __forceinline__ void climb_packed(const BatchDesc* __restrict__ d,
@@ -609,6 +609,12 @@ __device__ __forceinline__ void climb_packed(const BatchDesc* __restrict__ d,
     ascend_one<T, C, R>(b.Q8, b.ldq, b.ldy, b.n, b.W, b.X + (int64_t)s * b.W, b.f + s, max_flips,
                         b.flips ? b.flips + s : nullptr, b.err, xs, spec_slots,
                         b.Y ? b.Y + (int64_t)it.y * b.ldy : nullptr, grp);
+  } else if constexpr (TS == 32) {  // one warp per start: warp-level reductions only
+    Group<32> grp;
+    ascend_one<32, C, R>(b.Q8, b.ldq, b.ldy, b.n, b.W, b.X + (int64_t)s * b.W, b.f + s,
+                         max_flips, b.flips ? b.flips + s : nullptr, b.err, xs + sg * (32 * C / 4),
+                         spec_slots + sg * spec_slot_count<32, C, R>(),
+                         b.Y ? b.Y + (int64_t)it.y * b.ldy : nullptr, grp);
   } else {
     SubGroup<TS> grp{reinterpret_cast<int2 (*)[TS / 32]>(rec_flat + sg * 2 * (TS / 32)), 0,
                      sg * TS, 1 + sg};
@@ -624,7 +630,7 @@ __global__ void __launch_bounds__(T, 2)
 ascent_batch_packed_kernel(const BatchDesc* __restrict__ d, const int2* __restrict__ items,
                            const int4* __restrict__ units, const int64_t* __restrict__ n_units,
                            int32_t max_flips, unsigned long long* __restrict__ next) {
-  static_assert(T / 4 >= 64, "sub-groups of at least two warps");
+  static_assert(T / 8 == 32, "sub-groups down to one warp");
   __shared__ int2 rec_flat[2 * (T / 32)];
   __shared__ uint64_t xs[T * C / 4];
   __shared__ uint4 spec_slots[spec_slot_count<T, C, R>()];
@@ -644,7 +650,9 @@ ascent_batch_packed_kernel(const BatchDesc* __restrict__ d, const int2* __restri
     if (un.x == 0) climb_packed<T, C, R, T>(d, items, un, max_flips, rec_flat, xs, spec_slots);
     else if (un.x == 1)
       climb_packed<T, C, R, T / 2>(d, items, un, max_flips, rec_flat, xs, spec_slots);
-    else climb_packed<T, C, R, T / 4>(d, items, un, max_flips, rec_flat, xs, spec_slots);
+    else if (un.x == 2)
+      climb_packed<T, C, R, T / 4>(d, items, un, max_flips, rec_flat, xs, spec_slots);
+    else climb_packed<T, C, R, T / 8>(d, items, un, max_flips, rec_flat, xs, spec_slots);
     __syncthreads();  // every sub-group done before the block takes the next unit
   }
 }

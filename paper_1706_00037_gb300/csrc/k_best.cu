@@ -57,45 +57,87 @@ __global__ void __launch_bounds__(THREADS) best_batch_kernel(const BatchDesc* __
 
 // The batch's ascent work list: (instance, position in its passing list) for
 // every passing start, instances in the given order (largest first).
+// The instances order[k0 .. k0 + m) (m <= THREADS) of a batch's lists: each
+// thread reads one instance's passing count (and, for the packed list, its
+// unit class), then one thread turns them into exclusive offsets in shared
+// memory, so that no global load waits inside the loop over instances.
+struct ListChunk {
+  int inst[THREADS];
+  int cls[THREADS];
+  long long cnt[THREADS], base[THREADS], ubase[THREADS];
+  long long base_end, ubase_end;
+};
+__device__ void list_chunk(const BatchDesc* __restrict__ d, const int32_t* __restrict__ order,
+                           int k0, int m, int T, int C, bool packed, ListChunk& L) {
+  if ((int)threadIdx.x < m) {
+    const int i = order[k0 + (int)threadIdx.x];
+    const int n = d[i].n;
+    L.inst[threadIdx.x] = i;
+    L.cnt[threadIdx.x] = *d[i].count;
+    L.cls[threadIdx.x] = !packed                 ? 0
+                         : n <= 16 * (T >> 3) * C ? 3
+                         : n <= 16 * (T >> 2) * C ? 2
+                         : n <= 16 * (T >> 1) * C ? 1
+                                                  : 0;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    long long b = L.base_end, ub = L.ubase_end;
+    for (int j = 0; j < m; ++j) {
+      L.base[j] = b;
+      L.ubase[j] = ub;
+      const long long per = 1ll << L.cls[j];
+      b += L.cnt[j];
+      ub += (L.cnt[j] + per - 1) / per;
+    }
+    L.base_end = b;
+    L.ubase_end = ub;
+  }
+  __syncthreads();
+}
+
 __global__ void __launch_bounds__(THREADS)
 batch_items_kernel(const BatchDesc* __restrict__ d, const int32_t* __restrict__ order, int count,
                    int2* __restrict__ items, int64_t* __restrict__ n_items) {
-  int64_t base = 0;
-  for (int k = 0; k < count; ++k) {
-    const int i = order[k];
-    const int64_t c = *d[i].count;
-    for (int64_t t = threadIdx.x; t < c; t += THREADS) items[base + t] = make_int2(i, (int)t);
-    base += c;
+  __shared__ ListChunk L;
+  if (threadIdx.x == 0) L.base_end = L.ubase_end = 0;
+  for (int k0 = 0; k0 < count; k0 += THREADS) {
+    const int m = count - k0 < THREADS ? count - k0 : THREADS;
+    list_chunk(d, order, k0, m, 0, 0, false, L);
+    for (int j = 0; j < m; ++j)
+      for (long long t = threadIdx.x; t < L.cnt[j]; t += THREADS)
+        items[L.base[j] + t] = make_int2(L.inst[j], (int)t);
+    __syncthreads();  // L is rewritten by the next chunk
   }
-  if (threadIdx.x == 0) *n_items = base;
+  if (threadIdx.x == 0) *n_items = L.base_end;
 }
 
 // The work list of the packed batch ascent: the items as batch_items_kernel
 // writes them, and units {cls, first item, items in the unit, 0} of up to
-// 2^cls items of one instance, cls the largest of 0, 1, 2 whose sub-group of
+// 2^cls items of one instance, cls the largest of 0 .. 3 whose sub-group of
 // T >> cls threads (16 (T >> cls) C elements) holds the instance's n.
 __global__ void __launch_bounds__(THREADS)
 batch_units_kernel(const BatchDesc* __restrict__ d, const int32_t* __restrict__ order, int count,
                    int T, int C, int2* __restrict__ items, int4* __restrict__ units,
                    int64_t* __restrict__ n_units) {
-  int64_t base = 0, ubase = 0;
-  for (int k = 0; k < count; ++k) {
-    const int i = order[k];
-    const int64_t c = *d[i].count;
-    const int n = d[i].n;
-    const int cls = n <= 16 * (T >> 2) * C ? 2 : n <= 16 * (T >> 1) * C ? 1 : 0;
-    const int64_t per = (int64_t)1 << cls;
-    const int64_t nu = (c + per - 1) / per;
-    for (int64_t t = threadIdx.x; t < c; t += THREADS) items[base + t] = make_int2(i, (int)t);
-    for (int64_t u = threadIdx.x; u < nu; u += THREADS) {
-      const int64_t first = u * per;
-      const int64_t m = c - first < per ? c - first : per;
-      units[ubase + u] = make_int4(cls, (int)(base + first), (int)m, 0);
+  __shared__ ListChunk L;
+  if (threadIdx.x == 0) L.base_end = L.ubase_end = 0;
+  for (int k0 = 0; k0 < count; k0 += THREADS) {
+    const int m = count - k0 < THREADS ? count - k0 : THREADS;
+    list_chunk(d, order, k0, m, T, C, true, L);
+    for (int j = 0; j < m; ++j) {
+      const long long c = L.cnt[j], per = 1ll << L.cls[j], nu = (c + per - 1) / per;
+      for (long long t = threadIdx.x; t < c; t += THREADS)
+        items[L.base[j] + t] = make_int2(L.inst[j], (int)t);
+      for (long long u = threadIdx.x; u < nu; u += THREADS) {
+        const long long first = u * per;
+        const long long mm = c - first < per ? c - first : per;
+        units[L.ubase[j] + u] = make_int4(L.cls[j], (int)(L.base[j] + first), (int)mm, 0);
+      }
     }
-    base += c;
-    ubase += nu;
+    __syncthreads();  // L is rewritten by the next chunk
   }
-  if (threadIdx.x == 0) *n_units = ubase;
+  if (threadIdx.x == 0) *n_units = L.ubase_end;
 }
 
 // The passing starts of R rounds held back to back (round r's S values at

@@ -83,7 +83,7 @@ def test_batch_plain_eval_path():
     ((256, 1), True, 16, True), ((256, 2), True, 8, True), ((256, 1), False, 12, False),
     ((128, 2), False, 8, True), ((256, 1), True, 12, False)])
 def test_batch_pinned_schedules_equal_single_solves(shape, packed, kch, merged):
-    # packed climbs (sub-groups of 64 / 128 / 256 threads by n, several starts
+    # packed climbs (sub-groups of 32 / 64 / 128 / 256 threads by n, several starts
     # of one instance per block) and every evaluation schedule give the same
     # results as single solves, with the graph too
     sizes = [60, 700, 2500, 300, 1025, 129, 2100, 513, 1024, 1023, 2048, 2049]
