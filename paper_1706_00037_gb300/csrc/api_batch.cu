@@ -68,8 +68,8 @@ struct ubqp_batch {
   std::vector<void*> scratch;            // per instance: unpacked starts, then y
   std::vector<size_t> scratch_bytes;
   std::vector<TmaDesc> mapA;             // TMA descriptor of each scratch
-  int4* d_units = nullptr;               // packed ascent: units of up to 4 items
-  int64_t* d_nunits = nullptr;           // 16 bytes: unit count, then the unit counter
+  int4* d_units = nullptr;               // packed ascent: the item range of each class
+  int64_t* d_nunits = nullptr;           // the item count, then the four class counters
   // evaluation schedules: per instance, chunk tables of at most 8 and 12 K steps
   // (the handle's own table has 16)
   static constexpr int kAltKch[2] = {8, 12};
@@ -190,8 +190,8 @@ int run_body(ubqp_batch* b, cudaStream_t st) {
                                         b->d_items, b->d_units, b->d_nunits, st));
     // the unit counter: the second word of the 16-byte unit-count slot
     UBQP_BCUDA(ubqp::launch_ascent_batch_packed(
-        b->d_desc, b->d_items, b->d_units, b->d_nunits, b->asc_T, b->asc_C, p.max_flips,
-        b->asc_grid, reinterpret_cast<unsigned long long*>(b->d_nunits + 1), st));
+        b->d_desc, b->d_items, b->d_units, b->asc_T, b->asc_C, p.max_flips, b->asc_grid,
+        reinterpret_cast<unsigned long long*>(b->d_nunits + 1), st));
   } else {
     UBQP_BCUDA(ubqp::launch_batch_items(b->d_desc, b->d_order, b->count, b->d_items,
                                         b->d_nitems, st));
@@ -284,8 +284,8 @@ int ubqp_batch_create(const ubqp_q* const* qs, int32_t count, const ubqp_params*
   const size_t o_order = take(sizeof(int32_t) * count);
   const size_t o_items = take(sizeof(int2) * (size_t)S * count);
   const size_t o_nitems = take(16);
-  const size_t o_units = take(sizeof(int4) * (size_t)S * count);
-  const size_t o_nunits = take(16);
+  const size_t o_units = take(std::max<size_t>(sizeof(int4) * (size_t)S * count, 4 * sizeof(int4)));
+  const size_t o_nunits = take(5 * sizeof(int64_t));  // item count, one start counter per class
   const size_t o_seed = take(16);
   // the merged evaluation: instances, tensor maps, work lists
   const size_t o_einst = take(sizeof(ubqp::EvalInst) * count);

@@ -83,7 +83,7 @@ struct ServerLane {
   int32_t* d_order = nullptr;
   int2* d_items = nullptr;
   int4* d_units = nullptr;
-  int64_t* d_nitems = nullptr;  // 16 bytes: item (or unit) count, then the counter
+  int64_t* d_nitems = nullptr;  // the item count, then the start counter(s): one per class packed
   std::thread th;
 };
 
@@ -273,8 +273,8 @@ int run_batch(ubqp_server* s, ServerLane& L, std::vector<Slot*>& live) {
   if (s->packed) {
     LCUDA(ubqp::launch_batch_units(L.d_desc, L.d_order, m, s->asc_T, s->asc_C, L.d_items,
                                    L.d_units, L.d_nitems, L.st));
-    LCUDA(ubqp::launch_ascent_batch_packed(L.d_desc, L.d_items, L.d_units, L.d_nitems, s->asc_T,
-                                           s->asc_C, p.max_flips, s->asc_grid, next, L.st));
+    LCUDA(ubqp::launch_ascent_batch_packed(L.d_desc, L.d_items, L.d_units, s->asc_T, s->asc_C,
+                                           p.max_flips, s->asc_grid, next, L.st));
   } else {
     LCUDA(ubqp::launch_batch_items(L.d_desc, L.d_order, m, L.d_items, L.d_nitems, L.st));
     LCUDA(ubqp::launch_ascent_batch(L.d_desc, L.d_items, L.d_nitems, s->asc_T, s->asc_C,
@@ -426,7 +426,8 @@ int make_lane(ubqp_server* s, ServerLane* L) {
   const size_t o_order = rup(sizeof(ubqp::BatchDesc) * B, 256);
   const size_t o_items = o_order + rup(sizeof(int32_t) * B, 256);
   const size_t o_units = o_items + rup(sizeof(int2) * (size_t)S * B, 256);
-  const size_t o_cnt = o_units + rup(sizeof(int4) * (size_t)S * B, 256);
+  const size_t o_cnt =
+      o_units + rup(std::max<int64_t>(sizeof(int4) * (size_t)S * B, 4 * sizeof(int4)), 256);
   if (cudaMalloc(&L->dmem, o_cnt + 256) != cudaSuccess) return UBQP_ERR_NOMEM;
   L->d_desc = (ubqp::BatchDesc*)(L->dmem + o_desc);
   L->d_order = (int32_t*)(L->dmem + o_order);

@@ -582,21 +582,19 @@ ascent_batch_kernel(const BatchDesc* __restrict__ d, const int2* __restrict__ it
 }
 
 // All passing starts of a batch of instances in one persistent launch, packed
-// by size: a work unit is up to 2^cls starts of one instance (cls 0 .. 3),
-// climbed together by the block's 2^cls sub-groups of T >> cls threads (the
-// smallest sub-group whose 16 (T >> cls) C elements hold the instance's n;
-// T >> 3 = 32 is one warp), so that a block climbs up to eight small starts
-// at once instead of one with mostly idle elements.  Units run largest instances first: the first wave one per
-// block, the rest from the counter *next.
+// by size.  Class c (0 .. 3) holds the instances whose n fits a sub-group of
+// T >> c threads (16 (T >> c) C elements; T >> 3 = 32 is one warp), and its
+// items form the range ranges[c] = {first item, items, 0, 0} (instances come
+// largest first, so each class is contiguous).  Each block runs the classes
+// in turn, split into 2^c sub-groups for class c, and every sub-group takes
+// the class's next start from its counter next[c] as soon as it has finished
+// the previous one: a block climbs up to eight small starts at once, and no
+// sub-group waits for another's longer climb except at the three class
+// boundaries.
 template <int T, int C, int R, int TS>
-__device__ __forceinline__ void climb_packed(const BatchDesc* __restrict__ d,
-                                             const int2* __restrict__ items, int4 un,
-                                             int32_t max_flips, int2* rec_flat, uint64_t* xs,
-                                             uint4* spec_slots) {
-  constexpr int K = T / TS;  // sub-groups per block
-  const int sg = (int)threadIdx.x / TS;
-  if (sg >= un.z) return;
-  const int2 it = items[un.y + sg];
+__device__ __forceinline__ void climb_item(const BatchDesc* __restrict__ d, int2 it,
+                                           int32_t max_flips, int2* rec_flat, uint64_t* xs,
+                                           uint4* spec_slots, int sg) {
   const BatchDesc& b = d[it.x];
   if (b.err[1] != 0) return;  // Q failed its symmetry check: no climb
   const int s = b.idx[it.y];
@@ -604,7 +602,7 @@ __device__ __forceinline__ void climb_packed(const BatchDesc* __restrict__ d,
     if ((int)threadIdx.x == sg * TS) atomicOr(b.err, UBQP_DEVERR_BADIDX);
     return;
   }
-  if constexpr (K == 1) {
+  if constexpr (TS == T) {
     Group<T> grp{reinterpret_cast<int2 (*)[T / 32]>(rec_flat), 0};
     ascend_one<T, C, R>(b.Q8, b.ldq, b.ldy, b.n, b.W, b.X + (int64_t)s * b.W, b.f + s, max_flips,
                         b.flips ? b.flips + s : nullptr, b.err, xs, spec_slots,
@@ -625,36 +623,54 @@ __device__ __forceinline__ void climb_packed(const BatchDesc* __restrict__ d,
   }
 }
 
+// The sub-groups of one class take its starts from the class's counter (or,
+// without counters, round robin over all sub-groups of the grid).
+template <int T, int C, int R, int TS>
+__device__ __forceinline__ void climb_class(const BatchDesc* __restrict__ d,
+                                            const int2* __restrict__ items, int4 range,
+                                            int32_t max_flips, unsigned long long* next,
+                                            int2* rec_flat, uint64_t* xs, uint4* spec_slots,
+                                            long long* slot) {
+  constexpr int K = T / TS;
+  const int sg = (int)threadIdx.x / TS, r = (int)threadIdx.x % TS;
+  auto sg_sync = [&]() {
+    if constexpr (TS == T) __syncthreads();
+    else if constexpr (TS == 32) __syncwarp();
+    else named_sync(1 + sg, TS);
+  };
+  for (long long k = 0;; ++k) {
+    if (r == 0)
+      slot[sg] = next ? (long long)atomicAdd(next, 1ull)
+                      : ((long long)blockIdx.x * K + sg) + k * (long long)gridDim.x * K;
+    sg_sync();
+    const long long t = slot[sg];
+    sg_sync();  // every thread has read slot[sg] before its leader writes it again
+    if (t >= range.y) break;
+    climb_item<T, C, R, TS>(d, items[range.x + t], max_flips, rec_flat, xs, spec_slots, sg);
+  }
+}
+
 template <int T, int C, int R>
 __global__ void __launch_bounds__(T, 2)
 ascent_batch_packed_kernel(const BatchDesc* __restrict__ d, const int2* __restrict__ items,
-                           const int4* __restrict__ units, const int64_t* __restrict__ n_units,
-                           int32_t max_flips, unsigned long long* __restrict__ next) {
+                           const int4* __restrict__ ranges, int32_t max_flips,
+                           unsigned long long* __restrict__ next) {
   static_assert(T / 8 == 32, "sub-groups down to one warp");
   __shared__ int2 rec_flat[2 * (T / 32)];
   __shared__ uint64_t xs[T * C / 4];
   __shared__ uint4 spec_slots[spec_slot_count<T, C, R>()];
-  __shared__ unsigned long long ticket;
-  const int64_t cnt = *n_units;
-  auto take = [&](int64_t t) -> int64_t {
-    if (t < 0) return blockIdx.x;
-    if (!next) return t + gridDim.x;
-    if (threadIdx.x == 0) ticket = atomicAdd(next, 1ull);
-    __syncthreads();
-    const int64_t v = (int64_t)gridDim.x + (int64_t)ticket;
-    __syncthreads();
-    return v;
-  };
-  for (int64_t t = take(-1); t < cnt; t = take(t)) {
-    const int4 un = units[t];
-    if (un.x == 0) climb_packed<T, C, R, T>(d, items, un, max_flips, rec_flat, xs, spec_slots);
-    else if (un.x == 1)
-      climb_packed<T, C, R, T / 2>(d, items, un, max_flips, rec_flat, xs, spec_slots);
-    else if (un.x == 2)
-      climb_packed<T, C, R, T / 4>(d, items, un, max_flips, rec_flat, xs, spec_slots);
-    else climb_packed<T, C, R, T / 8>(d, items, un, max_flips, rec_flat, xs, spec_slots);
-    __syncthreads();  // every sub-group done before the block takes the next unit
-  }
+  __shared__ long long slot[8];
+  climb_class<T, C, R, T>(d, items, ranges[0], max_flips, next ? next : nullptr, rec_flat, xs,
+                          spec_slots, slot);
+  __syncthreads();
+  climb_class<T, C, R, T / 2>(d, items, ranges[1], max_flips, next ? next + 1 : nullptr,
+                              rec_flat, xs, spec_slots, slot);
+  __syncthreads();
+  climb_class<T, C, R, T / 4>(d, items, ranges[2], max_flips, next ? next + 2 : nullptr,
+                              rec_flat, xs, spec_slots, slot);
+  __syncthreads();
+  climb_class<T, C, R, T / 8>(d, items, ranges[3], max_flips, next ? next + 3 : nullptr,
+                              rec_flat, xs, spec_slots, slot);
 }
 
 // Four independent warps per block, one start each (n <= 512).

@@ -107,18 +107,18 @@ int ascent_packed_grid(int T, int C, int sm_count) {
   return per_sm * sm_count;
 }
 
-cudaError_t launch_ascent_batch_packed(const BatchDesc* d, const int2* items, const int4* units,
-                                       const int64_t* n_units, int T, int C, int32_t max_flips,
-                                       int grid, unsigned long long* next, cudaStream_t st) {
-  if (next) {
-    cudaError_t e = cudaMemsetAsync(next, 0, sizeof(unsigned long long), st);
+cudaError_t launch_ascent_batch_packed(const BatchDesc* d, const int2* items, const int4* ranges,
+                                       int T, int C, int32_t max_flips, int grid,
+                                       unsigned long long* next, cudaStream_t st) {
+  if (next) {  // one start counter per class
+    cudaError_t e = cudaMemsetAsync(next, 0, 4 * sizeof(unsigned long long), st);
     if (e != cudaSuccess) return e;
   }
   if (T == 256 && C == 1)
-    ascent_batch_packed_kernel<256, 1, kSpecRows><<<grid, 256, 0, st>>>(d, items, units, n_units,
+    ascent_batch_packed_kernel<256, 1, kSpecRows><<<grid, 256, 0, st>>>(d, items, ranges,
                                                                          max_flips, next);
   else if (T == 256 && C == 2)
-    ascent_batch_packed_kernel<256, 2, kSpecRows><<<grid, 256, 0, st>>>(d, items, units, n_units,
+    ascent_batch_packed_kernel<256, 2, kSpecRows><<<grid, 256, 0, st>>>(d, items, ranges,
                                                                          max_flips, next);
   else
     return cudaErrorInvalidValue;

@@ -113,31 +113,39 @@ batch_items_kernel(const BatchDesc* __restrict__ d, const int32_t* __restrict__ 
 }
 
 // The work list of the packed batch ascent: the items as batch_items_kernel
-// writes them, and units {cls, first item, items in the unit, 0} of up to
-// 2^cls items of one instance, cls the largest of 0 .. 3 whose sub-group of
-// T >> cls threads (16 (T >> cls) C elements) holds the instance's n.
+// writes them, and the range {first item, items, 0, 0} of each class c = 0 ..
+// 3, an instance being of the largest class whose sub-group of T >> c threads
+// (16 (T >> c) C elements) holds its n.  Instances come largest first, so
+// each class's items are contiguous.
 __global__ void __launch_bounds__(THREADS)
 batch_units_kernel(const BatchDesc* __restrict__ d, const int32_t* __restrict__ order, int count,
-                   int T, int C, int2* __restrict__ items, int4* __restrict__ units,
-                   int64_t* __restrict__ n_units) {
+                   int T, int C, int2* __restrict__ items, int4* __restrict__ ranges,
+                   int64_t* __restrict__ n_items) {
   __shared__ ListChunk L;
-  if (threadIdx.x == 0) L.base_end = L.ubase_end = 0;
+  __shared__ long long cbeg[4], ccnt[4];
+  if (threadIdx.x == 0) {
+    L.base_end = L.ubase_end = 0;
+    for (int c = 0; c < 4; ++c) cbeg[c] = -1, ccnt[c] = 0;
+  }
   for (int k0 = 0; k0 < count; k0 += THREADS) {
     const int m = count - k0 < THREADS ? count - k0 : THREADS;
     list_chunk(d, order, k0, m, T, C, true, L);
-    for (int j = 0; j < m; ++j) {
-      const long long c = L.cnt[j], per = 1ll << L.cls[j], nu = (c + per - 1) / per;
-      for (long long t = threadIdx.x; t < c; t += THREADS)
-        items[L.base[j] + t] = make_int2(L.inst[j], (int)t);
-      for (long long u = threadIdx.x; u < nu; u += THREADS) {
-        const long long first = u * per;
-        const long long mm = c - first < per ? c - first : per;
-        units[L.ubase[j] + u] = make_int4(L.cls[j], (int)(L.base[j] + first), (int)mm, 0);
+    if (threadIdx.x == 0)
+      for (int j = 0; j < m; ++j) {
+        const int c = L.cls[j];
+        if (cbeg[c] < 0) cbeg[c] = L.base[j];
+        ccnt[c] += L.cnt[j];
       }
-    }
+    for (int j = 0; j < m; ++j)
+      for (long long t = threadIdx.x; t < L.cnt[j]; t += THREADS)
+        items[L.base[j] + t] = make_int2(L.inst[j], (int)t);
     __syncthreads();  // L is rewritten by the next chunk
   }
-  if (threadIdx.x == 0) *n_units = L.ubase_end;
+  if (threadIdx.x == 0) {
+    for (int c = 0; c < 4; ++c)
+      ranges[c] = make_int4(cbeg[c] < 0 ? 0 : (int)cbeg[c], (int)ccnt[c], 0, 0);
+    *n_items = L.base_end;
+  }
 }
 
 // The passing starts of R rounds held back to back (round r's S values at
@@ -265,8 +273,8 @@ cudaError_t launch_batch_items(const BatchDesc* d, const int32_t* order, int cou
 }
 
 cudaError_t launch_batch_units(const BatchDesc* d, const int32_t* order, int count, int T, int C,
-                               int2* items, int4* units, int64_t* n_units, cudaStream_t st) {
-  batch_units_kernel<<<1, THREADS, 0, st>>>(d, order, count, T, C, items, units, n_units);
+                               int2* items, int4* ranges, int64_t* n_items, cudaStream_t st) {
+  batch_units_kernel<<<1, THREADS, 0, st>>>(d, order, count, T, C, items, ranges, n_items);
   return cudaGetLastError();
 }
 

@@ -251,13 +251,16 @@ cudaError_t launch_batch_items(const BatchDesc* d, const int32_t* order, int cou
 cudaError_t launch_ascent_batch(const BatchDesc* d, const int2* items, const int64_t* n_items,
                                 int T, int C, int32_t max_flips, int grid,
                                 unsigned long long* next, cudaStream_t st);
-// packed batch ascent: units of up to 4 starts of one instance per block of T
-// threads (sub-groups of T, T/2 or T/4 threads by n)
+// packed batch ascent: blocks of T threads split into sub-groups of T, T/2,
+// T/4 or T/8 threads by n; the items of each of the four classes form one
+// range (ranges: 4 int4 {first item, items, 0, 0}; n_items: the item count),
+// and next holds one start counter per class (4 x 8 bytes, zeroed by the
+// launch; NULL: round robin)
 cudaError_t launch_batch_units(const BatchDesc* d, const int32_t* order, int count, int T, int C,
-                               int2* items, int4* units, int64_t* n_units, cudaStream_t st);
-cudaError_t launch_ascent_batch_packed(const BatchDesc* d, const int2* items, const int4* units,
-                                       const int64_t* n_units, int T, int C, int32_t max_flips,
-                                       int grid, unsigned long long* next, cudaStream_t st);
+                               int2* items, int4* ranges, int64_t* n_items, cudaStream_t st);
+cudaError_t launch_ascent_batch_packed(const BatchDesc* d, const int2* items, const int4* ranges,
+                                       int T, int C, int32_t max_flips, int grid,
+                                       unsigned long long* next, cudaStream_t st);
 bool ascent_packed_supported(int T, int C);
 int ascent_packed_grid(int T, int C, int sm_count);
 int ascent_batch_grid(int T, int C, int sm_count);
