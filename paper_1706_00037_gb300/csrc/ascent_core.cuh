@@ -623,8 +623,10 @@ __device__ __forceinline__ void climb_item(const BatchDesc* __restrict__ d, int2
   }
 }
 
-// The sub-groups of one class take its starts from the class's counter (or,
-// without counters, round robin over all sub-groups of the grid).
+// The sub-groups of one class take its starts: the first wave spread over the
+// blocks (start sg * blocks + block, so that a short list lands one start per
+// block, not several on the blocks of one SM), then from the class's counter
+// (or, without counters, round robin over all sub-groups of the grid).
 template <int T, int C, int R, int TS>
 __device__ __forceinline__ void climb_class(const BatchDesc* __restrict__ d,
                                             const int2* __restrict__ items, int4 range,
@@ -638,13 +640,15 @@ __device__ __forceinline__ void climb_class(const BatchDesc* __restrict__ d,
     else if constexpr (TS == 32) __syncwarp();
     else named_sync(1 + sg, TS);
   };
+  const long long wave = (long long)gridDim.x * K;
   for (long long k = 0;; ++k) {
-    if (r == 0)
-      slot[sg] = next ? (long long)atomicAdd(next, 1ull)
-                      : ((long long)blockIdx.x * K + sg) + k * (long long)gridDim.x * K;
-    sg_sync();
-    const long long t = slot[sg];
-    sg_sync();  // every thread has read slot[sg] before its leader writes it again
+    long long t = (long long)sg * gridDim.x + blockIdx.x;
+    if (k > 0) {
+      if (r == 0) slot[sg] = next ? wave + (long long)atomicAdd(next, 1ull) : t + k * wave;
+      sg_sync();
+      t = slot[sg];
+      sg_sync();  // every thread has read slot[sg] before its leader writes it again
+    }
     if (t >= range.y) break;
     climb_item<T, C, R, TS>(d, items[range.x + t], max_flips, rec_flat, xs, spec_slots, sg);
   }
