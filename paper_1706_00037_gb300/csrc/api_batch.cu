@@ -70,6 +70,7 @@ struct ubqp_batch {
   std::vector<TmaDesc> mapA;             // TMA descriptor of each scratch
   int4* d_units = nullptr;               // packed ascent: the item range of each class
   int64_t* d_nunits = nullptr;           // the item count, then the four class counters
+  unsigned long long* d_next = nullptr;  // per instance: the start counter of its own climb
   // evaluation schedules: per instance, chunk tables of at most 8 and 12 K steps
   // (the handle's own table has 16)
   static constexpr int kAltKch[2] = {8, 12};
@@ -186,12 +187,32 @@ int run_body(ubqp_batch* b, cudaStream_t st) {
   }
   // ---- one launch each: work list, every climb, every best
   if (b->packed) {
+    // instances too large for half a block climb in launches of their own on
+    // the fork streams, beside the packed launch of the others
+    const bool own = ubqp::packed_own_climb(b->max_n, b->asc_T, b->asc_C);
     UBQP_BCUDA(ubqp::launch_batch_units(b->d_desc, b->d_order, b->count, b->asc_T, b->asc_C,
-                                        b->d_items, b->d_units, b->d_nunits, st));
-    // the unit counter: the second word of the 16-byte unit-count slot
+                                        own, b->d_items, b->d_units, b->d_nunits, st));
+    if (own) {
+      UBQP_BCUDA(cudaEventRecord(b->ev_fork, st));
+      for (int k = 0; k < K; ++k) UBQP_BCUDA(cudaStreamWaitEvent(b->streams[k], b->ev_fork, 0));
+      for (int k = 0, j = 0; k < b->count; ++k) {
+        const int i = b->order[k];
+        const ubqp_q* q = b->qs[i];
+        if (!ubqp::packed_own_climb(q->n, b->asc_T, b->asc_C)) continue;
+        const ubqp::BatchDesc& d = b->h_desc[i];
+        UBQP_BCUDA(ubqp::launch_ascent(q, d.X, d.f, d.idx, d.count, p.num_starts, p.max_flips,
+                                       d.flips, d.Y, b->d_next + i, b->streams[j++ % K]));
+      }
+    }
+    // the class counters: the words after the item count
     UBQP_BCUDA(ubqp::launch_ascent_batch_packed(
         b->d_desc, b->d_items, b->d_units, b->asc_T, b->asc_C, p.max_flips, b->asc_grid,
         reinterpret_cast<unsigned long long*>(b->d_nunits + 1), st));
+    if (own)
+      for (int k = 0; k < K; ++k) {
+        UBQP_BCUDA(cudaEventRecord(b->ev_join[k], b->streams[k]));
+        UBQP_BCUDA(cudaStreamWaitEvent(st, b->ev_join[k], 0));
+      }
   } else {
     UBQP_BCUDA(ubqp::launch_batch_items(b->d_desc, b->d_order, b->count, b->d_items,
                                         b->d_nitems, st));
@@ -286,6 +307,7 @@ int ubqp_batch_create(const ubqp_q* const* qs, int32_t count, const ubqp_params*
   const size_t o_nitems = take(16);
   const size_t o_units = take(std::max<size_t>(sizeof(int4) * (size_t)S * count, 4 * sizeof(int4)));
   const size_t o_nunits = take(5 * sizeof(int64_t));  // item count, one start counter per class
+  const size_t o_next = take(sizeof(unsigned long long) * (size_t)count);
   const size_t o_seed = take(16);
   // the merged evaluation: instances, tensor maps, work lists
   const size_t o_einst = take(sizeof(ubqp::EvalInst) * count);
@@ -370,6 +392,7 @@ int ubqp_batch_create(const ubqp_q* const* qs, int32_t count, const ubqp_params*
     }
   }
   b->d_nunits = (int64_t*)(b->dmem + o_nunits);
+  b->d_next = (unsigned long long*)(b->dmem + o_next);
   for (int a = 0; a < 2; ++a) {
     for (int i = 0; i < count; ++i) {
       b->alt_chunks[a].push_back((int4*)(b->dmem + o_alt[a][i]));

@@ -118,8 +118,10 @@ int resolve_path(const ubqp_server_config& c, int n_tc) {
 
 // Device bytes of one request of size n, carved in this order (each piece
 // 256-byte aligned): coefficients, prepared instance, starts, values, passing
-// indices, flip counts, small results (count, T and Mean, screen stats), best
-// solution and value, and the scratch the evaluation and the start-up share.
+// indices, flip counts, small results (count, T and Mean, screen stats, and at
+// kClimbCounter the start counter of a climb of its own), best solution and
+// value, and the scratch the evaluation and the start-up share.
+constexpr size_t kClimbCounter = 64;
 struct ReqLayout {
   size_t Q, arena, X, f, idx, flips, small, bx, bf, scratch, scratch_bytes, total;
 };
@@ -271,10 +273,28 @@ int run_batch(ubqp_server* s, ServerLane& L, std::vector<Slot*>& live) {
   // ---- one persistent launch climbs every passing start of the batch
   unsigned long long* next = reinterpret_cast<unsigned long long*>(L.d_nitems + 1);
   if (s->packed) {
-    LCUDA(ubqp::launch_batch_units(L.d_desc, L.d_order, m, s->asc_T, s->asc_C, L.d_items,
+    // requests too large for half a block climb in launches of their own on
+    // the fork streams, beside the packed launch of the others
+    const bool own = ubqp::packed_own_climb(live[L.h_order[0]]->r->n, s->asc_T, s->asc_C);
+    LCUDA(ubqp::launch_batch_units(L.d_desc, L.d_order, m, s->asc_T, s->asc_C, own, L.d_items,
                                    L.d_units, L.d_nitems, L.st));
+    if (own) {
+      if ((st = fork())) return st;
+      for (int k = 0, j = 0; k < m; ++k) {
+        const int i = L.h_order[k];
+        Slot& sl = *live[i];
+        if (!ubqp::packed_own_climb(sl.h->n, s->asc_T, s->asc_C)) continue;
+        const ubqp::BatchDesc& d = L.h_desc[i];
+        const ReqLayout RL = req_layout(c, sl.h->n);
+        // the climb's start counter: past the small results
+        auto* cnt = reinterpret_cast<unsigned long long*>(sl.buf + RL.small + kClimbCounter);
+        LCUDA(ubqp::launch_ascent(sl.h, d.X, d.f, d.idx, d.count, S, p.max_flips, d.flips, d.Y,
+                                  cnt, L.fork[j++ % kForkStreams]));
+      }
+    }
     LCUDA(ubqp::launch_ascent_batch_packed(L.d_desc, L.d_items, L.d_units, s->asc_T, s->asc_C,
                                            p.max_flips, s->asc_grid, next, L.st));
+    if (own && (st = join())) return st;
   } else {
     LCUDA(ubqp::launch_batch_items(L.d_desc, L.d_order, m, L.d_items, L.d_nitems, L.st));
     LCUDA(ubqp::launch_ascent_batch(L.d_desc, L.d_items, L.d_nitems, s->asc_T, s->asc_C,

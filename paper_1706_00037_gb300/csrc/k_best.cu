@@ -60,7 +60,9 @@ __global__ void __launch_bounds__(THREADS) best_batch_kernel(const BatchDesc* __
 // The instances order[k0 .. k0 + m) (m <= THREADS) of a batch's lists: each
 // thread reads one instance's passing count (and, for the packed list, its
 // unit class), then one thread turns them into exclusive offsets in shared
-// memory, so that no global load waits inside the loop over instances.
+// memory, so that no global load waits inside the loop over instances.  With
+// skip0 the instances of class 0 (climbed by launches of their own) add no
+// items.
 struct ListChunk {
   int inst[THREADS];
   int cls[THREADS];
@@ -68,7 +70,7 @@ struct ListChunk {
   long long base_end, ubase_end;
 };
 __device__ void list_chunk(const BatchDesc* __restrict__ d, const int32_t* __restrict__ order,
-                           int k0, int m, int T, int C, bool packed, ListChunk& L) {
+                           int k0, int m, int T, int C, bool packed, bool skip0, ListChunk& L) {
   if ((int)threadIdx.x < m) {
     const int i = order[k0 + (int)threadIdx.x];
     const int n = d[i].n;
@@ -79,6 +81,7 @@ __device__ void list_chunk(const BatchDesc* __restrict__ d, const int32_t* __res
                          : n <= 16 * (T >> 2) * C ? 2
                          : n <= 16 * (T >> 1) * C ? 1
                                                   : 0;
+    if (skip0 && L.cls[threadIdx.x] == 0) L.cnt[threadIdx.x] = 0;
   }
   __syncthreads();
   if (threadIdx.x == 0) {
@@ -103,7 +106,7 @@ batch_items_kernel(const BatchDesc* __restrict__ d, const int32_t* __restrict__ 
   if (threadIdx.x == 0) L.base_end = L.ubase_end = 0;
   for (int k0 = 0; k0 < count; k0 += THREADS) {
     const int m = count - k0 < THREADS ? count - k0 : THREADS;
-    list_chunk(d, order, k0, m, 0, 0, false, L);
+    list_chunk(d, order, k0, m, 0, 0, false, false, L);
     for (int j = 0; j < m; ++j)
       for (long long t = threadIdx.x; t < L.cnt[j]; t += THREADS)
         items[L.base[j] + t] = make_int2(L.inst[j], (int)t);
@@ -116,10 +119,11 @@ batch_items_kernel(const BatchDesc* __restrict__ d, const int32_t* __restrict__ 
 // writes them, and the range {first item, items, 0, 0} of each class c = 0 ..
 // 3, an instance being of the largest class whose sub-group of T >> c threads
 // (16 (T >> c) C elements) holds its n.  Instances come largest first, so
-// each class's items are contiguous.
+// each class's items are contiguous.  With skip0 class 0 is left out (its
+// instances climb in launches of their own).
 __global__ void __launch_bounds__(THREADS)
 batch_units_kernel(const BatchDesc* __restrict__ d, const int32_t* __restrict__ order, int count,
-                   int T, int C, int2* __restrict__ items, int4* __restrict__ ranges,
+                   int T, int C, int skip0, int2* __restrict__ items, int4* __restrict__ ranges,
                    int64_t* __restrict__ n_items) {
   __shared__ ListChunk L;
   __shared__ long long cbeg[4], ccnt[4];
@@ -129,7 +133,7 @@ batch_units_kernel(const BatchDesc* __restrict__ d, const int32_t* __restrict__ 
   }
   for (int k0 = 0; k0 < count; k0 += THREADS) {
     const int m = count - k0 < THREADS ? count - k0 : THREADS;
-    list_chunk(d, order, k0, m, T, C, true, L);
+    list_chunk(d, order, k0, m, T, C, true, skip0 != 0, L);
     if (threadIdx.x == 0)
       for (int j = 0; j < m; ++j) {
         const int c = L.cls[j];
@@ -273,8 +277,10 @@ cudaError_t launch_batch_items(const BatchDesc* d, const int32_t* order, int cou
 }
 
 cudaError_t launch_batch_units(const BatchDesc* d, const int32_t* order, int count, int T, int C,
-                               int2* items, int4* ranges, int64_t* n_items, cudaStream_t st) {
-  batch_units_kernel<<<1, THREADS, 0, st>>>(d, order, count, T, C, items, ranges, n_items);
+                               bool skip0, int2* items, int4* ranges, int64_t* n_items,
+                               cudaStream_t st) {
+  batch_units_kernel<<<1, THREADS, 0, st>>>(d, order, count, T, C, skip0 ? 1 : 0, items, ranges,
+                                            n_items);
   return cudaGetLastError();
 }
 

@@ -255,9 +255,16 @@ cudaError_t launch_ascent_batch(const BatchDesc* d, const int2* items, const int
 // T/4 or T/8 threads by n; the items of each of the four classes form one
 // range (ranges: 4 int4 {first item, items, 0, 0}; n_items: the item count),
 // and next holds one start counter per class (4 x 8 bytes, zeroed by the
-// launch; NULL: round robin)
+// launch; NULL: round robin).  skip0: class 0 left out of the list (its
+// instances climbed by launch_ascent of their own; see packed_own_climb)
 cudaError_t launch_batch_units(const BatchDesc* d, const int32_t* order, int count, int T, int C,
-                               int2* items, int4* ranges, int64_t* n_items, cudaStream_t st);
+                               bool skip0, int2* items, int4* ranges, int64_t* n_items,
+                               cudaStream_t st);
+// Packed batch climbs leave the instances too large for half a block (class
+// 0) to the single-instance launcher, whose group shapes for large n climb
+// faster (n = 5000, ~450 passers: 1.40 ms with 160-thread groups three per SM
+// against 2.01 ms packed).
+inline bool packed_own_climb(int n, int T, int C) { return n > 16 * (T / 2) * C; }
 cudaError_t launch_ascent_batch_packed(const BatchDesc* d, const int2* items, const int4* ranges,
                                        int T, int C, int32_t max_flips, int grid,
                                        unsigned long long* next, cudaStream_t st);
