@@ -399,8 +399,11 @@ int ubqp_solve_rounds(const ubqp_q* q, const ubqp_params* p, int32_t R, uint64_t
  *   when there is one.
  * ubqp_batch_tune -- the autotuner: times the run for the candidate ascent
  *   group shapes (threads x chunks that hold the largest n, one start per
- *   group, or packed: 256-thread blocks climbing up to four starts of one
- *   instance in sub-groups of 64 or 128 threads when its n fits them), the
+ *   group, or packed: 256-thread blocks climbing up to eight starts at once
+ *   in sub-groups of 32, 64, 128 or 256 threads, the smallest that holds the
+ *   instance's n, each taking its next start as soon as its climb ends; the
+ *   instances too large for half a block climb in launches of their own
+ *   beside it), the
  *   evaluation paths, one merged launch for the start generation and the
  *   tensor-core evaluation of all instances (one persistent launch over the
  *   work units of every instance, largest first) or one launch per instance,
@@ -454,7 +457,8 @@ int ubqp_batch_get(const ubqp_batch* b, int32_t i, uint64_t* best_x_dev, int64_t
  * per-request upload, preparation, start generation and evaluation on the
  * lane's streams, then one shared launch each for the screen, the climb of
  * every passing start of every request (one persistent launch, several small
- * starts per block) and the best-of.  Requests that arrive while batches run
+ * starts per block; requests too large for half a block climb in launches of
+ * their own beside it) and the best-of.  Requests that arrive while batches run
  * are taken together by the next free lane, so batches grow with the load,
  * and the lanes' batches overlap on the GPU.  Request memory comes from the
  * device's stream-ordered pool.  The paper solves one instance per run;
