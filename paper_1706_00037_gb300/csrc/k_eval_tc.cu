@@ -1251,10 +1251,10 @@ __global__ void selftest_wait_kernel(uint64_t limit_ns, int32_t* status) {
 // Rows of 0.0/1.0 bf16 (the A operand of the staged kernel) from the bit-packed
 // starts: S_p x n_tc, row t is start t (t < S), or with idx start idx[t] for
 // t < *count and zero up to the next multiple of 128 (the last m-tile the
-// product reads; rows beyond are not written); columns >= n are zero.  With Y the product's rows t < *count are
-// zeroed for its accumulation.  Blocks (of kUnpackThreads) take rows: the
-// row's words are read once into shared memory, then each thread expands
-// 8-column pieces of it (no 64-bit division).
+// product reads; rows beyond are not written); columns >= n are zero.  With Y
+// the product's rows t < *count are zeroed for its accumulation.  Blocks (of
+// kUnpackThreads) take rows: the row's words are read once into shared
+// memory, then each thread expands 8-column pieces of it (no 64-bit division).
 constexpr int kUnpackThreads = 256;
 static_assert(kUnpackThreads * 64 >= UBQP_MAX_N, "one word per thread covers a row");
 __device__ __forceinline__ void unpack_rows(const uint64_t* __restrict__ X, int n, int W,
@@ -1518,7 +1518,8 @@ std::vector<MUnit> eval_tc_multi_units(const ubqp_q* const* qs, int count, int64
     for (const int4& c : make_chunks(qs[i]->n_tc, BN, false, std::max(1, std::min(kch, KCH))))
       for (int mt = 0; mt < m_tiles; ++mt) us.push_back(MUnit{c.x, c.y, c.z, mt, i, 0, 0, 0});
   }
-  std::stable_sort(us.begin(), us.end(), [](const MUnit& a, const MUnit& b) { return a.nk > b.nk; });
+  std::stable_sort(us.begin(), us.end(),
+                   [](const MUnit& a, const MUnit& b) { return a.nk > b.nk; });
   return us;
 }
 
@@ -1545,7 +1546,8 @@ std::vector<MUnit> eval_tc_multi_y_units(const ubqp_q* const* qs, int count, int
     for (const int4& c : make_chunks_y(qs[i]->n_tc))
       for (int mt = 0; mt < m_tiles; ++mt) us.push_back(MUnit{c.x, c.y, c.z, mt, i, 0, 0, 0});
   }
-  std::stable_sort(us.begin(), us.end(), [](const MUnit& a, const MUnit& b) { return a.nk > b.nk; });
+  std::stable_sort(us.begin(), us.end(),
+                   [](const MUnit& a, const MUnit& b) { return a.nk > b.nk; });
   return us;
 }
 
