@@ -993,10 +993,14 @@ def main():
 
     if rank == 0:
         # diversify 1, eval 1 (fused or plain) or 2 (unpack + tensor-core, staged),
-        # screen 1, ascent 3 (unpack + tensor-core start-up + climb), best 1
+        # screen 1, ascent 3 or 4 (unpack + tensor-core start-up + the climb, and
+        # for more listed starts than its blocks hold at once the count-gated
+        # throughput twin), best 1
         n_tc = (n + 255) // 256 * 256
         staged = path == ubqp.EVAL_TC_STAGED or (path == ubqp.EVAL_AUTO and not (n_tc <= 1024 and S >= 4096))
-        launches_per_step = 1 + (2 if staged else 1) + 1 + 3 + 1
+        cap = 152 if n > 4096 else (304 if n > 2048 else 456)
+        twin = 1024 < n <= 8192 and S > cap
+        launches_per_step = 1 + (2 if staged else 1) + 1 + (4 if twin else 3) + 1
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
                 "steps": a.steps, "warmup": a.warmup, "ms_per_step": max_total / a.steps,
                 "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
