@@ -564,8 +564,17 @@ def run_configs(a):
                                     want_stats=False), 20)
     ref = orc.solve(Qh, 1000, 0.5, 0, 0, orc.DIVERSIFY)
     assert int(bf[0].item()) == ref["best_f"]
+    # the same round as a one-instance batch plan replayed from its CUDA graph
+    # (one launch from the host instead of one per kernel)
+    b1 = ubqp.Batch([inst], params)
+    b1.tune()
+    b1.capture()
+    ms_graph = timed(lambda r: b1.run(0), 20)
+    _, bfg = b1.result(0)
+    assert int(bfg[0].item()) == ref["best_f"]
+    b1.close()
     c1 = {"solve_us": ms * 1e3, "evals_per_s": 1000 / (ms / 1e3), "best_f": ref["best_f"],
-          "equals_oracle": True}
+          "graph_batch_us": ms_graph * 1e3, "equals_oracle": True}
     inst.sync()
     del inst
 
