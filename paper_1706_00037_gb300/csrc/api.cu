@@ -321,10 +321,13 @@ int ubqp_first_derivative(const ubqp_q* q, uint64_t* x0_dev, void* stream) {
   return UBQP_OK;
 }
 
-int ubqp_diversify_range(const ubqp_q* q, const uint64_t* x0_dev, int32_t mode, uint64_t seed,
-                         uint64_t round, int64_t S_total, int64_t s_begin, int64_t S_local,
-                         int32_t div_H, uint64_t* X_dev, void* stream) {
-  UBQP_RANGE("ubqp:diversify");
+}  // extern "C"
+
+// ubqp_diversify_range, and with flips0 the round's flip counts zeroed in the
+// same launch (ubqp_solve).
+static int diversify_impl(const ubqp_q* q, const uint64_t* x0_dev, int32_t mode, uint64_t seed,
+                          uint64_t round, int64_t S_total, int64_t s_begin, int64_t S_local,
+                          int32_t div_H, uint64_t* X_dev, void* stream, int32_t* flips0) {
   if (!q || !X_dev) return fail(UBQP_ERR_ARG, "NULL argument");
   if (S_total < 0 || s_begin < 0 || S_local < 0 || s_begin + S_local > S_total)
     return fail(UBQP_ERR_ARG, "range [%lld, %lld) outside a batch of %lld", (long long)s_begin,
@@ -335,8 +338,18 @@ int ubqp_diversify_range(const ubqp_q* q, const uint64_t* x0_dev, int32_t mode, 
   if (S_local == 0) return UBQP_OK;
   const uint64_t* x0 = x0_dev ? x0_dev : q->x0;
   UBQP_CUDA(ubqp::launch_diversify(x0, q->n, mode, seed, round, S_total, s_begin, S_local, div_H,
-                                   X_dev, (cudaStream_t)stream));
+                                   X_dev, (cudaStream_t)stream, nullptr, flips0));
   return UBQP_OK;
+}
+
+extern "C" {
+
+int ubqp_diversify_range(const ubqp_q* q, const uint64_t* x0_dev, int32_t mode, uint64_t seed,
+                         uint64_t round, int64_t S_total, int64_t s_begin, int64_t S_local,
+                         int32_t div_H, uint64_t* X_dev, void* stream) {
+  UBQP_RANGE("ubqp:diversify");
+  return diversify_impl(q, x0_dev, mode, seed, round, S_total, s_begin, S_local, div_H, X_dev,
+                        stream, nullptr);
 }
 
 int ubqp_diversify(const ubqp_q* q, const uint64_t* x0_dev, int32_t mode, uint64_t seed,
@@ -637,17 +650,19 @@ int ubqp_solve(const ubqp_q* q, const ubqp_params* p, uint64_t* best_x_dev, int6
   int64_t* sout = (int64_t*)(base + L.small + 48);
   cudaStream_t st = (cudaStream_t)stream;
   int r;
-  if ((r = ubqp_diversify(q, nullptr, p->mode, p->seed, p->round, S, p->div_H, X, stream)))
+  // the starts, with the round's flip counts zeroed in the same launch
+  if ((r = diversify_impl(q, nullptr, p->mode, p->seed, p->round, S, 0, S, p->div_H, X, stream,
+                          flips)))
     return r;
   if ((r = ubqp_eval(q, X, S, f, p->eval_path, base + L.eval, L.total - L.eval, stream)))
     return r;
   if ((r = ubqp_screen(f, S, p->lambda, idx, count, Tm, sstats, stream))) return r;
-  UBQP_CUDA(cudaMemsetAsync(flips, 0, sizeof(int32_t) * S, st));
   if ((r = ubqp_ascent(q, X, f, idx, count, S, p->max_flips, flips, base + L.eval,
                        L.total - L.eval, stream)))
     return r;
-  if ((r = ubqp_best(f, X, S, q->W, best_x_dev, best_f_dev, stream))) return r;
-  UBQP_CUDA(ubqp::launch_solve_stats(count, idx, flips, Tm, sstats, best_f_dev, sout, st));
+  // the best-of and the round's statistics in one launch
+  UBQP_CUDA(ubqp::launch_best_stats(f, X, S, q->W, best_x_dev, best_f_dev, count, idx, flips,
+                                    sstats, sout, st));
   if (stats_host) {
     int64_t hs[6];
     double hd[2];

@@ -177,11 +177,14 @@ concat_rounds_kernel(const int32_t* __restrict__ idx, const int64_t* __restrict_
   }
 }
 
-// out = {passed, total flips, max flips of one start, batch max, best index, sum}
-__global__ void __launch_bounds__(THREADS)
-solve_stats_kernel(const int64_t* __restrict__ count, const int32_t* __restrict__ idx,
-                   const int32_t* __restrict__ flips, const int64_t* __restrict__ sstats,
-                   const int64_t* __restrict__ best, int64_t* __restrict__ out) {
+// The round's statistics {passed, total flips, max flips of one start, batch
+// max, best index, sum} from the passing list, the flip counts, the screen's
+// statistics and the best-of; one block.
+__device__ void block_solve_stats(const int64_t* __restrict__ count,
+                                  const int32_t* __restrict__ idx,
+                                  const int32_t* __restrict__ flips,
+                                  const int64_t* __restrict__ sstats,
+                                  const int64_t* __restrict__ best, int64_t* __restrict__ out) {
   __shared__ long long s_tot[WARPS], s_mx[WARPS];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int64_t c = *count;
@@ -212,6 +215,26 @@ solve_stats_kernel(const int64_t* __restrict__ count, const int32_t* __restrict_
     out[4] = best[1];
     out[5] = sstats[0];
   }
+}
+
+__global__ void __launch_bounds__(THREADS)
+solve_stats_kernel(const int64_t* __restrict__ count, const int32_t* __restrict__ idx,
+                   const int32_t* __restrict__ flips, const int64_t* __restrict__ sstats,
+                   const int64_t* __restrict__ best, int64_t* __restrict__ out) {
+  block_solve_stats(count, idx, flips, sstats, best, out);
+}
+
+// The best-of, then the statistics (the best-of's value and index written by
+// this block before its barrier are what they read).
+__global__ void __launch_bounds__(THREADS)
+best_stats_kernel(const int64_t* __restrict__ f, const uint64_t* __restrict__ X, int64_t S, int W,
+                  uint64_t* __restrict__ best_x, int64_t* __restrict__ best_f,
+                  const int64_t* __restrict__ count, const int32_t* __restrict__ idx,
+                  const int32_t* __restrict__ flips, const int64_t* __restrict__ sstats,
+                  int64_t* __restrict__ out) {
+  block_best(f, X, S, W, best_x, best_f);
+  __syncthreads();
+  block_solve_stats(count, idx, flips, sstats, best_f, out);
 }
 
 // UpdateBestAndT of Fig. 2 after a round: the round's best {value, index}
@@ -293,6 +316,15 @@ cudaError_t launch_concat_rounds(const int32_t* idx, const int64_t* counts, int 
 cudaError_t launch_best(const int64_t* f, const uint64_t* X, int64_t S, int W,
                         uint64_t* best_x, int64_t* best_f, cudaStream_t st) {
   best_kernel<<<1, THREADS, 0, st>>>(f, X, S, W, best_x, best_f);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_best_stats(const int64_t* f, const uint64_t* X, int64_t S, int W,
+                              uint64_t* best_x, int64_t* best_f, const int64_t* count,
+                              const int32_t* idx, const int32_t* flips, const int64_t* sstats,
+                              int64_t* out, cudaStream_t st) {
+  best_stats_kernel<<<1, THREADS, 0, st>>>(f, X, S, W, best_x, best_f, count, idx, flips, sstats,
+                                           out);
   return cudaGetLastError();
 }
 

@@ -47,7 +47,8 @@ __device__ __forceinline__ uint64_t start_word(const uint64_t* __restrict__ x0, 
 __global__ void diversify_words(const uint64_t* __restrict__ x0, int n, int W, int mode,
                                 uint64_t seed, uint64_t round, int64_t S_total, int64_t s_begin,
                                 int64_t S_local, int div_H, uint64_t* __restrict__ X,
-                                const uint64_t* __restrict__ seed_dev) {
+                                const uint64_t* __restrict__ seed_dev,
+                                int32_t* __restrict__ flips0) {
   if (seed_dev) seed = *seed_dev;
   const int64_t total = S_local * W;
   for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < total;
@@ -55,6 +56,7 @@ __global__ void diversify_words(const uint64_t* __restrict__ x0, int n, int W, i
     const int64_t sl = t / W;
     const int w = (int)(t - sl * W);
     X[t] = start_word(x0, n, mode, seed, round, S_total, s_begin + sl, w, div_H);
+    if (flips0 && w == 0) flips0[sl] = 0;
   }
 }
 
@@ -84,13 +86,13 @@ __global__ void diversify_batch_words(const BatchDesc* __restrict__ d, int mode,
 cudaError_t launch_diversify(const uint64_t* x0, int n, int mode, uint64_t seed,
                              uint64_t round, int64_t S_total, int64_t s_begin,
                              int64_t S_local, int div_H, uint64_t* X, cudaStream_t st,
-                             const uint64_t* seed_dev) {
+                             const uint64_t* seed_dev, int32_t* flips0) {
   const int W = (int)words_of(n);
   int64_t total = S_local * W;
   int64_t blocks = (total + 255) / 256;
   if (blocks > 152 * 16) blocks = 152 * 16;
   diversify_words<<<(unsigned)blocks, 256, 0, st>>>(x0, n, W, mode, seed, round, S_total,
-                                                   s_begin, S_local, div_H, X, seed_dev);
+                                                   s_begin, S_local, div_H, X, seed_dev, flips0);
   return cudaGetLastError();
 }
 

@@ -153,11 +153,12 @@ int record_error(int status, const char* fmt, ...) __attribute__((format(printf,
 cudaError_t launch_prepare(const int8_t* Q, int n, int64_t ldq_in, ubqp_q* h,
                            cudaStream_t st);
 // seed_dev: when not null the seed is read from device memory at run time
-// (lets a captured graph be replayed with a new seed).
+// (lets a captured graph be replayed with a new seed).  flips0: when not null,
+// flips0[0 .. S_local) is zeroed as well (a round's flip counts).
 cudaError_t launch_diversify(const uint64_t* x0, int n, int mode, uint64_t seed,
                              uint64_t round, int64_t S_total, int64_t s_begin,
                              int64_t S_local, int div_H, uint64_t* X, cudaStream_t st,
-                             const uint64_t* seed_dev = nullptr);
+                             const uint64_t* seed_dev = nullptr, int32_t* flips0 = nullptr);
 // Every instance of a batch in one launch: starts (seed read from seed_dev)
 // into each d[i].X, d[i].f and d[i].flips zeroed; max_words = the largest S W.
 cudaError_t launch_diversify_batch(const BatchDesc* d, int count, int64_t max_words, int mode,
@@ -278,5 +279,10 @@ cudaError_t launch_solve_stats(const int64_t* count, const int32_t* idx,
                                const int32_t* flips, const double* Tm,
                                const int64_t* sstats, const int64_t* best,
                                int64_t* out, cudaStream_t st);
+// launch_best followed by launch_solve_stats (its best = best_f), in one launch
+cudaError_t launch_best_stats(const int64_t* f, const uint64_t* X, int64_t S, int W,
+                              uint64_t* best_x, int64_t* best_f, const int64_t* count,
+                              const int32_t* idx, const int32_t* flips, const int64_t* sstats,
+                              int64_t* out, cudaStream_t st);
 
 }  // namespace ubqp
