@@ -482,26 +482,28 @@ static int ascent_impl(const ubqp_q* q, uint64_t* X_dev, int64_t* f_dev, const i
   if (ws && ((uintptr_t)ws & 15) != 0) return fail(UBQP_ERR_ARG, "workspace not 16-byte aligned");
   if (S == 0) return UBQP_OK;
   cudaStream_t st = (cudaStream_t)stream;
-  float* Y = nullptr;
-  if (ws && ws_bytes >= ubqp::ascent_tc_workspace(q, S) &&
-      (int64_t)coeff_bound(q) * q->n_tc < (1 << 24)) {
-    cudaError_t e = ubqp::launch_ascent_init_tc(q, X_dev, idx_dev, count_dev, S, ws, ws_bytes,
-                                                &Y, st);
-    if (e == cudaErrorNotSupported) Y = nullptr;
-    else if (e != cudaSuccess) return cuda_fail(e, "ascent start-up (tensor cores)");
-  }
   // the start counter in the workspace's last 256 bytes (round robin without)
   const size_t as = ascent_ws_bytes(q, S);
   unsigned long long* next =
       ws && ws_bytes >= as
           ? reinterpret_cast<unsigned long long*>(static_cast<char*>(ws) + as - 256)
           : nullptr;
+  float* Y = nullptr;
+  if (ws && ws_bytes >= ubqp::ascent_tc_workspace(q, S) &&
+      (int64_t)coeff_bound(q) * q->n_tc < (1 << 24)) {
+    // the start-up's unpacking also zeroes the counter
+    cudaError_t e = ubqp::launch_ascent_init_tc(q, X_dev, idx_dev, count_dev, S, ws, ws_bytes,
+                                                &Y, st, nullptr, next);
+    if (e == cudaErrorNotSupported) Y = nullptr;
+    else if (e != cudaSuccess) return cuda_fail(e, "ascent start-up (tensor cores)");
+  }
+  const bool zeroed = Y != nullptr;
   if (trace_dev)
     UBQP_CUDA(ubqp::launch_ascent_traced(q, X_dev, f_dev, idx_dev, count_dev, S, max_flips,
-                                         flips_dev, Y, next, trace_dev, ldt, st));
+                                         flips_dev, Y, next, trace_dev, ldt, st, zeroed));
   else
     UBQP_CUDA(ubqp::launch_ascent(q, X_dev, f_dev, idx_dev, count_dev, S, max_flips, flips_dev,
-                                  Y, next, st));
+                                  Y, next, st, zeroed));
   return UBQP_OK;
 }
 

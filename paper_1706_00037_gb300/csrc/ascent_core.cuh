@@ -502,7 +502,8 @@ __device__ __forceinline__ void ascend_one(const int8_t* __restrict__ Q8, int64_
 // the registers are sized for.  The kernel climbs only when the number of
 // listed starts lies in [cnt_lo, cnt_hi] and returns at once otherwise, so
 // that two launches of different OCC can share one list, each taking the
-// counts it is faster for, with no host round trip for the count.
+// counts it is faster for, with no host round trip for the count.  A
+// programmatic dependent of the kernel before it on the stream (pdl_wait).
 template <int T, int C, int R, bool TR, int OCC>
 __global__ void __launch_bounds__(T, OCC)
 ascent_block_kernel(const int8_t* __restrict__ Q8, int64_t ldq, int n, int W,
@@ -517,6 +518,7 @@ ascent_block_kernel(const int8_t* __restrict__ Q8, int64_t ldq, int n, int W,
   __shared__ uint4 spec_slots[spec_slot_count<T, C, R>()];
   __shared__ unsigned long long ticket;
   Group<T> grp{rec, 0};
+  pdl_wait();  // no early release: see pdl_release
   if (err[1] != 0) return;  // Q failed its symmetry check: no climb
   const int64_t cnt = *count;
   if (cnt < cnt_lo || cnt > cnt_hi) return;  // the other launch's counts
@@ -677,7 +679,8 @@ ascent_batch_packed_kernel(const BatchDesc* __restrict__ d, const int2* __restri
                               rec_flat, xs, spec_slots, slot);
 }
 
-// Four independent warps per block, one start each (n <= 512).
+// Four independent warps per block, one start each (n <= 512); a
+// programmatic dependent like the block kernel.
 template <int C, int R, bool TR>
 __global__ void __launch_bounds__(128)
 ascent_warp_kernel(const int8_t* __restrict__ Q8, int64_t ldq, int n, int W,
@@ -691,6 +694,7 @@ ascent_warp_kernel(const int8_t* __restrict__ Q8, int64_t ldq, int n, int W,
   __shared__ uint4 spec_slots[4 * spec_slot_count<32, C, R>()];
   Group<32> grp;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  pdl_wait();  // no early release: see pdl_release
   if (err[1] != 0) return;  // Q failed its symmetry check: no climb
   const int64_t cnt = *count;
   auto take = [&](int64_t t) -> int64_t {  // the warp's next start (see the block kernel)
@@ -804,10 +808,9 @@ cudaError_t launch_block_occ(const ubqp_q* h, uint64_t* X, int64_t* f, const int
                              int64_t ldt, int64_t cnt_lo, int64_t cnt_hi, cudaStream_t st) {
   int grid = resident_grid(ascent_block_kernel<T, C, kSpecRows, TR, OCC>, T, h->sm_count);
   if ((int64_t)grid > S) grid = (int)S;
-  ascent_block_kernel<T, C, kSpecRows, TR, OCC><<<grid, T, 0, st>>>(
-      h->Q8, h->ldq, h->n, h->W, X, f, idx, count, S, max_flips, flips, Y, h->n_tc, h->err,
-      next, trace, ldt, cnt_lo, cnt_hi);
-  return cudaGetLastError();
+  return launch_pdl(ascent_block_kernel<T, C, kSpecRows, TR, OCC>, dim3(grid), dim3(T), 0, st,
+                    h->Q8, h->ldq, h->n, h->W, X, f, idx, count, S, max_flips, flips, Y,
+                    (int64_t)h->n_tc, h->err, next, trace, ldt, cnt_lo, cnt_hi);
 }
 
 // Block groups, registers sized for one block per SM: with at most one listed
@@ -867,10 +870,9 @@ cudaError_t launch_warp(const ubqp_q* h, uint64_t* X, int64_t* f, const int32_t*
   int grid = resident_grid(ascent_warp_kernel<C, kSpecRows, TR>, 128, h->sm_count);
   const int64_t need = (S + 3) / 4;
   if ((int64_t)grid > need) grid = (int)need;
-  ascent_warp_kernel<C, kSpecRows, TR><<<grid, 128, 0, st>>>(
-      h->Q8, h->ldq, h->n, h->W, X, f, idx, count, S, max_flips, flips, Y, h->n_tc, h->err,
-      next, trace, ldt);
-  return cudaGetLastError();
+  return launch_pdl(ascent_warp_kernel<C, kSpecRows, TR>, dim3(grid), dim3(128), 0, st, h->Q8,
+                    h->ldq, h->n, h->W, X, f, idx, count, S, max_flips, flips, Y,
+                    (int64_t)h->n_tc, h->err, next, trace, ldt);
 }
 
 // One ascent launch over the listed starts, with the group shape that holds
@@ -881,9 +883,10 @@ template <bool TR>
 cudaError_t launch_ascent_shaped(const ubqp_q* h, uint64_t* X, int64_t* f, const int32_t* idx,
                                  const int64_t* count, int64_t S, int32_t max_flips,
                                  int32_t* flips, const float* Y, unsigned long long* next,
-                                 uint16_t* trace, int64_t ldt, cudaStream_t st) {
+                                 uint16_t* trace, int64_t ldt, cudaStream_t st,
+                                 bool next_zeroed) {
   const int n = h->n;
-  if (next) {
+  if (next && !next_zeroed) {
     cudaError_t e = cudaMemsetAsync(next, 0, sizeof(unsigned long long), st);
     if (e != cudaSuccess) return e;
   }

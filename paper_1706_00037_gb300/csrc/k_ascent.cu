@@ -127,9 +127,10 @@ cudaError_t launch_ascent_batch_packed(const BatchDesc* d, const int2* items, co
 
 cudaError_t launch_ascent(const ubqp_q* h, uint64_t* X, int64_t* f, const int32_t* idx,
                           const int64_t* count, int64_t S, int32_t max_flips, int32_t* flips,
-                          const float* Y, unsigned long long* next, cudaStream_t st) {
+                          const float* Y, unsigned long long* next, cudaStream_t st,
+                          bool next_zeroed) {
   return launch_ascent_shaped<false>(h, X, f, idx, count, S, max_flips, flips, Y, next, nullptr,
-                                     0, st);
+                                     0, st, next_zeroed);
 }
 
 }  // namespace ubqp

@@ -12,9 +12,10 @@ namespace ubqp {
 cudaError_t launch_ascent_traced(const ubqp_q* h, uint64_t* X, int64_t* f, const int32_t* idx,
                                  const int64_t* count, int64_t S, int32_t max_flips,
                                  int32_t* flips, const float* Y, unsigned long long* next,
-                                 uint16_t* trace, int64_t ldt, cudaStream_t st) {
+                                 uint16_t* trace, int64_t ldt, cudaStream_t st,
+                                 bool next_zeroed) {
   return launch_ascent_shaped<true>(h, X, f, idx, count, S, max_flips, flips, Y, next, trace,
-                                    ldt, st);
+                                    ldt, st, next_zeroed);
 }
 
 }  // namespace ubqp

@@ -225,13 +225,15 @@ solve_stats_kernel(const int64_t* __restrict__ count, const int32_t* __restrict_
 }
 
 // The best-of, then the statistics (the best-of's value and index written by
-// this block before its barrier are what they read).
+// this block before its barrier are what they read); a programmatic
+// dependent of the ascent.
 __global__ void __launch_bounds__(THREADS)
 best_stats_kernel(const int64_t* __restrict__ f, const uint64_t* __restrict__ X, int64_t S, int W,
                   uint64_t* __restrict__ best_x, int64_t* __restrict__ best_f,
                   const int64_t* __restrict__ count, const int32_t* __restrict__ idx,
                   const int32_t* __restrict__ flips, const int64_t* __restrict__ sstats,
                   int64_t* __restrict__ out) {
+  pdl_enter();
   block_best(f, X, S, W, best_x, best_f);
   __syncthreads();
   block_solve_stats(count, idx, flips, sstats, best_f, out);
@@ -323,9 +325,8 @@ cudaError_t launch_best_stats(const int64_t* f, const uint64_t* X, int64_t S, in
                               uint64_t* best_x, int64_t* best_f, const int64_t* count,
                               const int32_t* idx, const int32_t* flips, const int64_t* sstats,
                               int64_t* out, cudaStream_t st) {
-  best_stats_kernel<<<1, THREADS, 0, st>>>(f, X, S, W, best_x, best_f, count, idx, flips, sstats,
-                                           out);
-  return cudaGetLastError();
+  return launch_pdl(best_stats_kernel, dim3(1), dim3(THREADS), 0, st, f, X, S, W, best_x, best_f,
+                    count, idx, flips, sstats, out);
 }
 
 cudaError_t launch_solve_stats(const int64_t* count, const int32_t* idx, const int32_t* flips,

@@ -43,12 +43,14 @@ __device__ __forceinline__ uint64_t start_word(const uint64_t* __restrict__ x0, 
 }
 
 // Starts s_begin .. s_begin + S_local - 1 of a batch of S_total (loop counter
-// i = round * S_total + s), written to X[(s - s_begin) * W + w].
+// i = round * S_total + s), written to X[(s - s_begin) * W + w]; a
+// programmatic dependent of whatever precedes it on the stream.
 __global__ void diversify_words(const uint64_t* __restrict__ x0, int n, int W, int mode,
                                 uint64_t seed, uint64_t round, int64_t S_total, int64_t s_begin,
                                 int64_t S_local, int div_H, uint64_t* __restrict__ X,
                                 const uint64_t* __restrict__ seed_dev,
                                 int32_t* __restrict__ flips0) {
+  pdl_enter();
   if (seed_dev) seed = *seed_dev;
   const int64_t total = S_local * W;
   for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < total;
@@ -91,9 +93,8 @@ cudaError_t launch_diversify(const uint64_t* x0, int n, int mode, uint64_t seed,
   int64_t total = S_local * W;
   int64_t blocks = (total + 255) / 256;
   if (blocks > 152 * 16) blocks = 152 * 16;
-  diversify_words<<<(unsigned)blocks, 256, 0, st>>>(x0, n, W, mode, seed, round, S_total,
-                                                   s_begin, S_local, div_H, X, seed_dev, flips0);
-  return cudaGetLastError();
+  return launch_pdl(diversify_words, dim3((unsigned)blocks), dim3(256), 0, st, x0, n, W, mode,
+                    seed, round, S_total, s_begin, S_local, div_H, X, seed_dev, flips0);
 }
 
 cudaError_t launch_diversify_batch(const BatchDesc* d, int count, int64_t max_words, int mode,

@@ -360,8 +360,11 @@ eval_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ 
   const uint32_t tmem = *tmem_slot;
   // Launched as a programmatic dependent of the unpacking (or of whatever
   // kernel precedes it on the stream): everything above overlaps that grid's
-  // tail; nothing below reads memory before it has finished.
-  asm volatile("griddepcontrol.wait;" ::: "memory");
+  // tail; nothing below reads memory before it has finished.  The kernel
+  // after the evaluation (the screen) may then be scheduled; the ascent after
+  // the start-up product waits for its completion.
+  pdl_wait();
+  if (!YMODE) pdl_release();
   int64_t rows = S;
   if (YMODE) {
     const int64_t c = *count;
@@ -1298,17 +1301,18 @@ __device__ __forceinline__ void unpack_rows(const uint64_t* __restrict__ X, int 
   }
 }
 
-// The evaluation's and the start-up's unpacking.  It lets the product that
-// follows on the stream (launched as a programmatic dependent) start its
-// set-up at once; that kernel waits for this grid to finish before it reads
-// what this one writes.  With fz, f[0 .. nfz) is zeroed for the evaluation's
-// accumulation (in place of a separate memset).
+// The evaluation's and the start-up's unpacking, a programmatic dependent of
+// the kernel before it (pdl_enter).  It lets the product that follows on the
+// stream start its set-up at once; that kernel waits for this grid to finish
+// before it reads what this one writes.  With fz, fz[0 .. nfz) is zeroed: the
+// evaluation's values f for its accumulation, or the ascent's start counter,
+// in place of a separate memset.
 __global__ void unpack_bits_bf16(const uint64_t* __restrict__ X, int n, int W, int64_t S,
                                  const int32_t* __restrict__ idx,
                                  const int64_t* __restrict__ count, int64_t S_p, int n_tc,
                                  uint4* __restrict__ Xe, float* __restrict__ Y,
                                  int64_t* __restrict__ fz, int64_t nfz) {
-  asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+  pdl_enter();
   for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; fz && t < nfz;
        t += (int64_t)gridDim.x * blockDim.x)
     fz[t] = 0;
@@ -1664,7 +1668,8 @@ bool eval_tc_map_A(void* out128, const void* Xe, int64_t S, int n_tc) {
 
 cudaError_t launch_ascent_init_tc(const ubqp_q* h, const uint64_t* X, const int32_t* idx,
                                   const int64_t* count, int64_t S, void* ws, size_t ws_bytes,
-                                  float** Y_out, cudaStream_t st, const void* mapA_in) {
+                                  float** Y_out, cudaStream_t st, const void* mapA_in,
+                                  unsigned long long* zero_next) {
   if (!h->tc_ok) return cudaErrorNotSupported;
   const int64_t S_p = padded_starts(S);
   if (ws_bytes < ascent_tc_workspace(h, S)) return cudaErrorInvalidValue;
@@ -1673,9 +1678,10 @@ cudaError_t launch_ascent_init_tc(const ubqp_q* h, const uint64_t* X, const int3
   cudaError_t e;
   {
     const int64_t blocks = std::min<int64_t>(S_p, (int64_t)h->sm_count * 8);
-    unpack_bits_bf16<<<(unsigned)blocks, kUnpackThreads, 0, st>>>(
-        X, h->n, h->W, S, idx, count, S_p, h->n_tc, reinterpret_cast<uint4*>(Xe), Y, nullptr, 0);
-    if ((e = cudaGetLastError())) return e;
+    if ((e = launch_pdl(unpack_bits_bf16, dim3((unsigned)blocks), dim3(kUnpackThreads), 0, st, X,
+                        h->n, h->W, S, idx, count, S_p, h->n_tc, reinterpret_cast<uint4*>(Xe), Y,
+                        reinterpret_cast<int64_t*>(zero_next), (int64_t)(zero_next ? 1 : 0))))
+      return e;
   }
   alignas(64) CUtensorMap mapA;
   if (mapA_in) mapA = *reinterpret_cast<const CUtensorMap*>(mapA_in);
@@ -1731,10 +1737,10 @@ cudaError_t launch_eval_tc(const ubqp_q* h, const uint64_t* X, int64_t S, int64_
     else if (!make_map(&mapA, ws, S_p, h->n_tc, BM)) return cudaErrorInvalidValue;
     // the unpacking also zeroes f
     const int64_t blocks = std::min<int64_t>(S_p, (int64_t)h->sm_count * 8);
-    unpack_bits_bf16<<<(unsigned)blocks, kUnpackThreads, 0, st>>>(
-        X, h->n, h->W, S, nullptr, nullptr, S_p, h->n_tc, reinterpret_cast<uint4*>(ws), nullptr, f,
-        S);
-    if ((e = cudaGetLastError())) return e;
+    if ((e = launch_pdl(unpack_bits_bf16, dim3((unsigned)blocks), dim3(kUnpackThreads), 0, st, X,
+                        h->n, h->W, S, nullptr, nullptr, S_p, h->n_tc,
+                        reinterpret_cast<uint4*>(ws), nullptr, f, S)))
+      return e;
   }
   const int m_tiles = (int)(S_p / BM);
   const int4* ch = chunks_in ? chunks_in : reinterpret_cast<const int4*>(h->tc_chunks);

@@ -105,10 +105,12 @@ screen_apply_kernel(const int64_t* __restrict__ f, int64_t S, const int64_t* __r
 }
 
 // The whole screen of one batch in one block (statistics, then threshold and
-// compaction): the unsharded ubqp_screen.
+// compaction): the unsharded ubqp_screen, a programmatic dependent of the
+// evaluation.
 __global__ void __launch_bounds__(THREADS)
 screen_kernel(const int64_t* __restrict__ f, int64_t S, double lambda, int32_t* __restrict__ idx,
               int64_t* __restrict__ count, double* __restrict__ Tm, int64_t* __restrict__ stats) {
+  pdl_enter();
   block_screen_stats(f, S, 0, stats);
   block_screen_apply(f, S, stats, S, lambda, idx, count, Tm);
 }
@@ -131,8 +133,8 @@ cudaError_t launch_screen_stats(const int64_t* f, int64_t S, int64_t offset, int
 
 cudaError_t launch_screen(const int64_t* f, int64_t S, double lambda, int32_t* idx,
                           int64_t* count, double* Tm, int64_t* stats, cudaStream_t st) {
-  screen_kernel<<<1, THREADS, 0, st>>>(f, S, lambda, idx, count, Tm, stats);
-  return cudaGetLastError();
+  return launch_pdl(screen_kernel, dim3(1), dim3(THREADS), 0, st, f, S, lambda, idx, count, Tm,
+                    stats);
 }
 
 cudaError_t launch_screen_batch(const BatchDesc* d, int count, double lambda, cudaStream_t st) {

@@ -77,6 +77,45 @@ struct NvtxRange {
 };
 #define UBQP_RANGE(name) ::ubqp::NvtxRange ubqp_nvtx_range_(name)
 
+// Programmatic dependent launch.  The kernels of one round (start generation,
+// unpacking, evaluation, screen, start-up, ascent, best-of) are launched with
+// programmatic stream serialisation, so that a kernel's blocks can be
+// scheduled while the kernel before it on the stream is still running.  Each
+// such kernel calls pdl_wait() before its first access to global memory:
+// griddepcontrol.wait returns once the preceding grid has completed and its
+// writes are visible (at once for a kernel launched without the attribute).
+// pdl_release() (griddepcontrol.launch_dependents) then lets the next kernel
+// be scheduled; a kernel that does not call it releases the next one when it
+// completes.  Since every kernel of the chain waits before it can finish, each
+// one also finishes after everything queued before it, and at most one kernel
+// waits while another runs.  The start-up product and the ascent do not
+// release early: the ascent hands its first starts to its blocks in launch
+// order and relies on the block scheduler spreading them over idle SMs, which
+// blocks placed beside a running kernel would not be.
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+__device__ __forceinline__ void pdl_release() {
+  asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+}
+__device__ __forceinline__ void pdl_enter() {
+  pdl_wait();
+  pdl_release();
+}
+
+template <typename... P, typename... A>
+cudaError_t launch_pdl(void (*kernel)(P...), dim3 grid, dim3 block, size_t smem,
+                       cudaStream_t st, A&&... args) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = grid;
+  cfg.blockDim = block;
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = st;
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  at[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = at;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, kernel, static_cast<A&&>(args)...);
+}
 
 // One instance of a batch (device-resident descriptor of the batched stages).
 struct BatchDesc {
@@ -190,10 +229,14 @@ cudaError_t launch_startup_multi(const YInst* yi, int count, int64_t max_items, 
                                  int n_units, unsigned* err, int sm_count, cudaStream_t st);
 size_t eval_tc_static_capacity();
 size_t ascent_tc_workspace(const ubqp_q* h, int64_t S);
+// The ascent's start-up y = Q x of the listed starts on the tensor cores, into
+// ws (Y_out: the product).  zero_next: a counter that the unpacking zeroes
+// for the ascent launched after it (or NULL).
 cudaError_t launch_ascent_init_tc(const ubqp_q* h, const uint64_t* X, const int32_t* idx,
                                   const int64_t* count, int64_t S, void* ws, size_t ws_bytes,
                                   float** Y_out, cudaStream_t st,
-                                  const void* mapA_in = nullptr);
+                                  const void* mapA_in = nullptr,
+                                  unsigned long long* zero_next = nullptr);
 cudaError_t eval_tc_static_scratch(void** out);
 // mapA_in: a TMA descriptor (128 bytes) of the unpacked starts in ws made by
 // eval_tc_map_A, or nullptr to build one per call.
@@ -220,18 +263,20 @@ cudaError_t launch_relink(const ubqp_q* h, const uint64_t* X, const int64_t* f, 
                           int64_t P, uint64_t* Xb, int64_t* fb, int32_t* dist, uint16_t* trace,
                           int64_t ldt, const float* Y, unsigned long long* next,
                           cudaStream_t st);
-// next: a device counter the launch zeroes and the groups take starts from
-// (NULL: round robin).
+// next: a device counter the launch zeroes (unless next_zeroed: an earlier
+// kernel on the stream did) and the groups take starts from (NULL: round
+// robin).
 cudaError_t launch_ascent(const ubqp_q* h, uint64_t* X, int64_t* f, const int32_t* idx,
                           const int64_t* count, int64_t S, int32_t max_flips,
                           int32_t* flips, const float* Y, unsigned long long* next,
-                          cudaStream_t st);
+                          cudaStream_t st, bool next_zeroed = false);
 // launch_ascent that also writes start s's flipped indices, in order, to
 // trace[s * ldt ...] (the first ldt of them).
 cudaError_t launch_ascent_traced(const ubqp_q* h, uint64_t* X, int64_t* f, const int32_t* idx,
                                  const int64_t* count, int64_t S, int32_t max_flips,
                                  int32_t* flips, const float* Y, unsigned long long* next,
-                                 uint16_t* trace, int64_t ldt, cudaStream_t st);
+                                 uint16_t* trace, int64_t ldt, cudaStream_t st,
+                                 bool next_zeroed = false);
 // R rounds' passing lists (back to back, round r at idx + r S, count counts[r])
 // concatenated as global start indices r S + idx into idx_all, total count_all.
 cudaError_t launch_concat_rounds(const int32_t* idx, const int64_t* counts, int R, int64_t S,
