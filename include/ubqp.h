@@ -562,7 +562,9 @@ typedef struct ubqp_search_params {
  * value; 1 int64), history_dev[r] = incumbent value after round r (rounds
  * int64), stats_dev = {starts that passed, flips, sum over the sample}
  * (3 int64).  No host round trip: fully async on `stream`.  ws must hold
- * ubqp_search_workspace_size(q, p) bytes (16-byte aligned).
+ * ubqp_search_workspace_size(q, p) bytes (16-byte aligned).  Errors:
+ * UBQP_ERR_ARG for a NULL pointer, counts out of range or a lambda that is not
+ * finite; UBQP_ERR_NOMEM for a short workspace.
  */
 size_t ubqp_search_workspace_size(const ubqp_q* q, const ubqp_search_params* p);
 int ubqp_search(const ubqp_q* q, const ubqp_search_params* p, uint64_t* best_x_dev,

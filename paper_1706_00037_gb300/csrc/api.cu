@@ -802,6 +802,8 @@ int search_check(const ubqp_q* q, const ubqp_search_params* p, uint64_t* best_x_
       p->num_samples < 1 || p->num_samples >= ((int64_t)1 << 31) || p->rounds < 0 ||
       p->max_flips < 0)
     return fail(UBQP_ERR_ARG, "starts, samples, rounds or max_flips out of range");
+  if (!(p->lambda == p->lambda) || p->lambda > 1e300 || p->lambda < -1e300)
+    return fail(UBQP_ERR_ARG, "lambda is not finite");
   if (p->rounds > 0 && !history_dev) return fail(UBQP_ERR_ARG, "history_dev is NULL");
   if (((uintptr_t)ws & 15) != 0) return fail(UBQP_ERR_ARG, "workspace not 16-byte aligned");
   const SearchLayout L = search_layout(q, p);
@@ -835,21 +837,23 @@ int search_rounds(const ubqp_q* q, const ubqp_search_params* p, int32_t first_ro
   int r;
   for (int32_t i = 0; i < p->rounds; ++i) {
     const uint64_t rd = (uint64_t)first_round + (uint64_t)i;
-    if ((r = ubqp_diversify(q, b.inc_x, UBQP_MODE_DIVERSIFY, p->seed, rd, S, p->div_H, b.X,
-                            stream)))
+    // the round's starts around the incumbent, its flip counts zeroed in the
+    // same launch
+    if ((r = diversify_impl(q, b.inc_x, UBQP_MODE_DIVERSIFY, p->seed, rd, S, 0, S, p->div_H,
+                            b.X, stream, b.flips)))
       return r;
     if ((r = ubqp_eval(q, b.X, S, b.f, p->eval_path, b.scratch, b.scratch_bytes, stream)))
       return r;
-    UBQP_CUDA(cudaMemcpyAsync(b.gstats + 1, best_f_dev, 8, cudaMemcpyDeviceToDevice, st));
-    if ((r = ubqp_screen_apply(b.f, S, b.gstats, NS, p->lambda, b.idx, b.count, b.Tm, stream)))
-      return r;
-    UBQP_CUDA(cudaMemsetAsync(b.flips, 0, sizeof(int32_t) * S, st));
+    // T from the sample's Mean and the incumbent's value, read in place
+    UBQP_CUDA(ubqp::launch_screen_apply(b.f, S, b.gstats, NS, p->lambda, b.idx, b.count, b.Tm,
+                                        st, best_f_dev));
     if ((r = ubqp_ascent(q, b.X, b.f, b.idx, b.count, S, p->max_flips, b.flips, b.scratch,
                          b.scratch_bytes, stream)))
       return r;
-    if ((r = ubqp_best(b.f, b.X, S, q->W, b.cand_x, b.cand, stream))) return r;
-    UBQP_CUDA(ubqp::launch_search_update(b.cand, b.X, q->W, b.count, b.idx, b.flips, best_f_dev,
-                                         b.inc_x, history_dev + i, stats_dev, st));
+    // the round's best and UpdateBestAndT in one launch
+    UBQP_CUDA(ubqp::launch_search_update(b.f, b.X, S, q->W, b.cand_x, b.cand, b.count, b.idx,
+                                         b.flips, best_f_dev, b.inc_x, history_dev + i,
+                                         stats_dev, st));
   }
   return UBQP_OK;
 }

@@ -43,9 +43,11 @@ __device__ void block_best(const int64_t* __restrict__ f, const uint64_t* __rest
   for (int w = threadIdx.x; w < W; w += THREADS) best_x[w] = X[a * W + w];
 }
 
+// A programmatic dependent of the kernel before it (pdl_enter).
 __global__ void __launch_bounds__(THREADS)
 best_kernel(const int64_t* __restrict__ f, const uint64_t* __restrict__ X, int64_t S, int W,
             uint64_t* __restrict__ best_x, int64_t* __restrict__ best_f) {
+  pdl_enter();
   block_best(f, X, S, W, best_x, best_f);
 }
 
@@ -240,16 +242,21 @@ best_stats_kernel(const int64_t* __restrict__ f, const uint64_t* __restrict__ X,
 }
 
 // UpdateBestAndT of Fig. 2 after a round: the round's best {value, index}
-// replaces the incumbent when strictly better; history[round] = incumbent
-// value; stats {passed, flips} accumulate the round's counts.
+// (block_best into cand_x / cand) replaces the incumbent when strictly better;
+// history[round] = incumbent value; stats {passed, flips} accumulate the
+// round's counts.  One launch, a programmatic dependent of the ascent.
 __global__ void __launch_bounds__(THREADS)
-search_update_kernel(const int64_t* __restrict__ cand, const uint64_t* __restrict__ X, int W,
+search_update_kernel(const int64_t* __restrict__ f, const uint64_t* __restrict__ X, int64_t S,
+                     int W, uint64_t* __restrict__ cand_x, int64_t* __restrict__ cand,
                      const int64_t* __restrict__ count, const int32_t* __restrict__ idx,
                      const int32_t* __restrict__ flips, int64_t* __restrict__ inc_f,
                      uint64_t* __restrict__ inc_x, int64_t* __restrict__ history,
                      int64_t* __restrict__ stats) {
   __shared__ long long s_tot[WARPS];
   __shared__ int s_take;
+  pdl_enter();
+  block_best(f, X, S, W, cand_x, cand);
+  __syncthreads();  // cand, written by thread 0, is read below
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int64_t c = *count;
   long long tot = 0;
@@ -276,13 +283,13 @@ __global__ void set_u64_kernel(uint64_t* dst, uint64_t v) { *dst = v; }
 
 }  // namespace
 
-cudaError_t launch_search_update(const int64_t* cand, const uint64_t* X, int W,
-                                 const int64_t* count, const int32_t* idx, const int32_t* flips,
-                                 int64_t* inc_f, uint64_t* inc_x, int64_t* history,
-                                 int64_t* stats, cudaStream_t st) {
-  search_update_kernel<<<1, THREADS, 0, st>>>(cand, X, W, count, idx, flips, inc_f, inc_x,
-                                              history, stats);
-  return cudaGetLastError();
+cudaError_t launch_search_update(const int64_t* f, const uint64_t* X, int64_t S, int W,
+                                 uint64_t* cand_x, int64_t* cand, const int64_t* count,
+                                 const int32_t* idx, const int32_t* flips, int64_t* inc_f,
+                                 uint64_t* inc_x, int64_t* history, int64_t* stats,
+                                 cudaStream_t st) {
+  return launch_pdl(search_update_kernel, dim3(1), dim3(THREADS), 0, st, f, X, S, W, cand_x, cand,
+                    count, idx, flips, inc_f, inc_x, history, stats);
 }
 
 cudaError_t launch_set_u64(uint64_t* dst, uint64_t v, cudaStream_t st) {
@@ -317,8 +324,7 @@ cudaError_t launch_concat_rounds(const int32_t* idx, const int64_t* counts, int 
 
 cudaError_t launch_best(const int64_t* f, const uint64_t* X, int64_t S, int W,
                         uint64_t* best_x, int64_t* best_f, cudaStream_t st) {
-  best_kernel<<<1, THREADS, 0, st>>>(f, X, S, W, best_x, best_f);
-  return cudaGetLastError();
+  return launch_pdl(best_kernel, dim3(1), dim3(THREADS), 0, st, f, X, S, W, best_x, best_f);
 }
 
 cudaError_t launch_best_stats(const int64_t* f, const uint64_t* X, int64_t S, int W,

@@ -62,13 +62,13 @@ screen_stats_kernel(const int64_t* __restrict__ f, int64_t S, int64_t offset,
 __device__ void block_screen_apply(const int64_t* __restrict__ f, int64_t S,
                                    const int64_t* gstats, int64_t S_total, double lambda,
                                    int32_t* __restrict__ idx, int64_t* __restrict__ count,
-                                   double* __restrict__ Tm) {
+                                   double* __restrict__ Tm, const int64_t* gmax = nullptr) {
   __shared__ int s_cnt[WARPS];
   __shared__ double s_T;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   if (threadIdx.x == 0) {
     const double mean = __ddiv_rn(__ll2double_rn(gstats[0]), __ll2double_rn(S_total));
-    const double diff = __dsub_rn(__ll2double_rn(gstats[1]), mean);
+    const double diff = __dsub_rn(__ll2double_rn(gmax ? gmax[0] : gstats[1]), mean);
     const double scaled = __dmul_rn(lambda, diff);
     const double T = __dadd_rn(mean, scaled);
     s_T = T;
@@ -97,11 +97,14 @@ __device__ void block_screen_apply(const int64_t* __restrict__ f, int64_t S,
   if (threadIdx.x == 0) *count = base;
 }
 
+// A programmatic dependent of the kernel before it (pdl_enter).
 __global__ void __launch_bounds__(THREADS)
 screen_apply_kernel(const int64_t* __restrict__ f, int64_t S, const int64_t* __restrict__ gstats,
                     int64_t S_total, double lambda, int32_t* __restrict__ idx,
-                    int64_t* __restrict__ count, double* __restrict__ Tm) {
-  block_screen_apply(f, S, gstats, S_total, lambda, idx, count, Tm);
+                    int64_t* __restrict__ count, double* __restrict__ Tm,
+                    const int64_t* __restrict__ gmax) {
+  pdl_enter();
+  block_screen_apply(f, S, gstats, S_total, lambda, idx, count, Tm, gmax);
 }
 
 // The whole screen of one batch in one block (statistics, then threshold and
@@ -144,9 +147,9 @@ cudaError_t launch_screen_batch(const BatchDesc* d, int count, double lambda, cu
 
 cudaError_t launch_screen_apply(const int64_t* f, int64_t S, const int64_t* gstats,
                                 int64_t S_total, double lambda, int32_t* idx, int64_t* count,
-                                double* Tm, cudaStream_t st) {
-  screen_apply_kernel<<<1, THREADS, 0, st>>>(f, S, gstats, S_total, lambda, idx, count, Tm);
-  return cudaGetLastError();
+                                double* Tm, cudaStream_t st, const int64_t* gmax) {
+  return launch_pdl(screen_apply_kernel, dim3(1), dim3(THREADS), 0, st, f, S, gstats, S_total,
+                    lambda, idx, count, Tm, gmax);
 }
 
 }  // namespace ubqp

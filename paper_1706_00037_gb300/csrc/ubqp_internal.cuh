@@ -251,9 +251,10 @@ cudaError_t launch_eval_tc(const ubqp_q* h, const uint64_t* X, int64_t S, int64_
 bool eval_tc_map_A(void* out128, const void* Xe, int64_t S, int n_tc);
 cudaError_t launch_screen_stats(const int64_t* f, int64_t S, int64_t offset, int64_t* stats,
                                 cudaStream_t st);
+// gmax: where the maximum is read (NULL: gstats[1]).
 cudaError_t launch_screen_apply(const int64_t* f, int64_t S, const int64_t* gstats,
                                 int64_t S_total, double lambda, int32_t* idx, int64_t* count,
-                                double* Tm, cudaStream_t st);
+                                double* Tm, cudaStream_t st, const int64_t* gmax = nullptr);
 cudaError_t launch_selftest_wait(uint64_t limit_ns, int32_t* status, cudaStream_t st);
 // Evaluation with the A operand in tensor memory (no workspace).
 cudaError_t launch_eval_ts(const ubqp_q* h, const uint64_t* X, int64_t S, int64_t* f,
@@ -283,10 +284,13 @@ cudaError_t launch_concat_rounds(const int32_t* idx, const int64_t* counts, int 
                                  int32_t* idx_all, int64_t* count_all, cudaStream_t st);
 cudaError_t launch_best(const int64_t* f, const uint64_t* X, int64_t S, int W,
                         uint64_t* best_x, int64_t* best_f, cudaStream_t st);
-cudaError_t launch_search_update(const int64_t* cand, const uint64_t* X, int W,
-                                 const int64_t* count, const int32_t* idx, const int32_t* flips,
-                                 int64_t* inc_f, uint64_t* inc_x, int64_t* history,
-                                 int64_t* stats, cudaStream_t st);
+// The round's best of f / X into cand_x / cand, then UpdateBestAndT: the
+// incumbent inc_f / inc_x, history and stats (one launch).
+cudaError_t launch_search_update(const int64_t* f, const uint64_t* X, int64_t S, int W,
+                                 uint64_t* cand_x, int64_t* cand, const int64_t* count,
+                                 const int32_t* idx, const int32_t* flips, int64_t* inc_f,
+                                 uint64_t* inc_x, int64_t* history, int64_t* stats,
+                                 cudaStream_t st);
 // batched stages: one launch over all instances of a batch
 cudaError_t launch_screen(const int64_t* f, int64_t S, double lambda, int32_t* idx,
                           int64_t* count, double* Tm, int64_t* stats, cudaStream_t st);

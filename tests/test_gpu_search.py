@@ -52,3 +52,13 @@ def test_search_resume_equals_one_search(split):
     assert torch.equal(rest["stats"], whole["stats"])
     hist = torch.cat([first["history"], rest["history"]])
     assert torch.equal(hist, whole["history"])
+
+
+@pytest.mark.parametrize("lam", [float("nan"), float("inf")])
+def test_search_rejects_non_finite_lambda(lam):
+    """T(lambda) needs a finite lambda: the call fails before any round."""
+    Q = synth.make_instance(64, 0.5, 2)
+    inst = ubqp.Instance(torch.from_numpy(Q).cuda())
+    with pytest.raises(ubqp.UbqpError) as e:
+        ubqp.search(inst, num_samples=10, starts_per_round=8, rounds=2, lam=lam)
+    assert e.value.status == -1  # UBQP_ERR_ARG
