@@ -20,7 +20,12 @@
  *    memory, allocates device memory only inside a ubqp_q handle, and never
  *    synchronises a stream unless the call's comment says so.
  *  - `stream` is a cudaStream_t passed as void* (NULL = the legacy default
- *    stream).  All device work of a call is enqueued on it, in order.
+ *    stream).  All device work of a call is enqueued on it, in order.  Most
+ *    kernels are launched with programmatic stream serialisation and let the
+ *    next kernel be scheduled before they finish; an ordinary launch after a
+ *    call is ordered as usual, but a kernel of the caller's that is itself
+ *    launched with programmatic serialisation must wait for its grid
+ *    dependency (griddepcontrol.wait) before it reads what the call wrote.
  *  - A solution x is bit-packed: W = ceil(n/64) uint64 words, bit j of x is
  *    (x[j/64] >> (j%64)) & 1.  A batch of S solutions is S*W words, solution s
  *    at X[s*W].  Bits >= n ("pad bits") must be 0; every routine that reads
